@@ -1,0 +1,101 @@
+"""Seeded synthetic inputs shared by the oracle tests, the CUDA tests and the benchmark.
+
+This module holds no arithmetic of the least-squares method: it only draws the data
+pair (A, b) of the problem x* = argmin 1/2 <x, A^T A x> - <b, x>.  The recipe follows
+the workloads of the randomized-preconditioning literature the paper builds on (the
+paper itself does not state its data):
+
+    A = G diag(sigma),  G iid N(0,1),  sigma_j = sigma_max^(j/(d-1))  (log-spaced 1..sigma_max)
+    optionally a fraction of rows scaled x100 (high-leverage outliers)
+    x_true ~ N(0, I),  y = A x_true + noise * N(0, I),  b = A^T y
+
+Draws use numpy's Philox bit generator, keyed by (seed, stream, chunk) so that the
+result does not depend on the number of threads that fill it.
+"""
+from __future__ import annotations
+
+import concurrent.futures as _cf
+import math
+import os
+
+import numpy as np
+
+_ROW_CHUNK = 1 << 16
+
+
+def sigma(d: int, sigma_max: float) -> np.ndarray:
+    if d == 1:
+        return np.ones(1)
+    return sigma_max ** (np.arange(d) / (d - 1))
+
+
+def _gen(seed: int, stream: int, chunk: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=[(seed << 20) ^ (stream << 12) ^ 0x5EED, chunk]))
+
+
+def _fill_normal(out: np.ndarray, seed: int, stream: int, threads: int) -> None:
+    n = out.shape[0]
+    chunks = [(c, min(c + _ROW_CHUNK, n)) for c in range(0, n, _ROW_CHUNK)]
+
+    def work(k):
+        lo, hi = chunks[k]
+        g = _gen(seed, stream, k)
+        if out.dtype == np.float64:
+            g.standard_normal(out=out[lo:hi])
+        else:
+            out[lo:hi] = g.standard_normal(size=out[lo:hi].shape)
+
+    if threads <= 1 or len(chunks) == 1:
+        for k in range(len(chunks)):
+            work(k)
+    else:
+        with _cf.ThreadPoolExecutor(threads) as ex:
+            list(ex.map(work, range(len(chunks))))
+
+
+def make_problem(n: int, d: int, sigma_max: float, seed: int = 1, noise: float = 0.1,
+                 dtype=np.float64, outlier_frac: float = 0.0, outlier_scale: float = 100.0,
+                 threads: int | None = None):
+    """Returns dict(A (n x d, row-major, `dtype`), b (d, FP64), x_true, y).
+
+    For FP32 A, b is formed from the FP32 values (upcast), so that (A, b) is an exact
+    FP64 problem whose matrix is representable in FP32."""
+    threads = threads or min(16, os.cpu_count() or 1)
+    A = np.empty((n, d), dtype=dtype)
+    _fill_normal(A, seed, 0, threads)
+    A *= sigma(d, sigma_max).astype(dtype)
+    if outlier_frac > 0:
+        u = _gen(seed, 3).random(n)
+        A[u < outlier_frac] *= dtype(outlier_scale) if dtype != np.float64 else outlier_scale
+    x_true = _gen(seed, 1).standard_normal(d)
+    eps = np.empty(n)
+    _fill_normal(eps, seed, 2, threads)
+    A64 = A if A.dtype == np.float64 else A.astype(np.float64)
+    y = A64 @ x_true + noise * eps
+    b = A64.T @ y
+    return {"A": A, "b": np.ascontiguousarray(b), "x_true": x_true, "y": y}
+
+
+def small_problem(n: int, d: int, kappa: float = 1e2, seed: int = 7):
+    """Small dense test problem with column scales log-spaced 1..kappa."""
+    return make_problem(n, d, kappa, seed=seed)
+
+
+# Workloads, named by what they are.  Each entry: shape, conditioning, sketch, target.
+WORKLOADS = {
+    # Gaussian embedding, FP64, the small case the oracle finishes in seconds.
+    "gauss_4096x64_m256": dict(n=4096, d=64, sigma_max=1e4, dtype="f64", sketch="gauss", m=256,
+                               seed_data=1, seed_sketch=0, tol=1e-12),
+    # FP64 at scale: SRHT / SJLT(s=8) sketches, m in {1024, 2048, 4096}.
+    "fp64_1048576x512": dict(n=1 << 20, d=512, sigma_max=1e6, dtype="f64", sketch="srht", m=4096,
+                             ms=(1024, 2048, 4096), s=8, seed_data=1, seed_sketch=0, tol=1e-10),
+    # FP32-stored A with outliers, Gaussian m=4096.
+    "fp32_4194304x1024": dict(n=1 << 22, d=1024, sigma_max=1e5, dtype="f32", sketch="gauss", m=4096,
+                              outlier_frac=0.05, seed_data=1, seed_sketch=0, tol=1e-10),
+}
+
+
+def log_spaced_count(lo: float, hi: float, k: int, seed: int) -> np.ndarray:
+    """k integers log-uniform in [lo, hi] (for uneven problem batches)."""
+    u = _gen(seed, 9).random(k)
+    return np.floor(np.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))).astype(np.int64)
