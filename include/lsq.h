@@ -1,0 +1,220 @@
+/*
+ * lsq.h -- C ABI of the GB300 (sm_103a) library for randomized-preconditioned
+ * least squares, after Lacotte & Pilanci, "Faster Least Squares Optimization"
+ * (arXiv 1911.02675).
+ *
+ * Problem (Section 1, eq. eqnconvexquadratic):
+ *     x* = argmin_x  1/2 <x, H x> - <b, x>,   H = A^T A,  A in R^{n x d}, n >= d, b in R^d.
+ * Method: a random embedding S (m x n) gives H_S = (SA)^T (SA) = R^T R; PCG with the
+ * fixed preconditioner H_S (Section 1, eq. (PCG)), or IHS / Polyak-IHS (Section 1,
+ * eqs. eqnihs and eqnpolyakihs) with a fixed or refreshed embedding (Sections 3, 4).
+ *
+ * Conventions for every entry point:
+ *   - All pointers marked "device" are CUDA device pointers on the context's device;
+ *     the library never frees or retains them past the call.
+ *   - Matrices are row-major.  A has n rows of d entries, consecutive rows ld >= d
+ *     elements apart.  SA is m x d with stride d.  R and W are d x d with stride d.
+ *   - Work is issued on the context's stream.  lsq_sketch and lsq_factor return once
+ *     the work is enqueued (their status covers argument checks and launch errors);
+ *     lsq_solve waits for its own work to finish so that it can fill `info`.
+ *   - Errors are reported as status codes; no entry point aborts the process.
+ *     Scratch memory is owned by the context (grown on demand, freed by lsq_destroy).
+ *   - Randomness: Philox4x32-10 (Salmon et al., SC'11) with key = (seed lo, seed hi),
+ *     counter = (index lo, index hi or draw, sketch instance t, stream tag); see the
+ *     individual sketches below.  The same seed and t give bit-identical embeddings.
+ */
+#ifndef LSQ_H
+#define LSQ_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LSQ_API __attribute__((visibility("default")))
+#else
+#define LSQ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LSQ_OK = 0,
+  LSQ_ERR_ARG = 1,        /* invalid argument (sizes, types, alignment, m < d, s > m, ...) */
+  LSQ_ERR_RANK = 2,       /* H_S not positive definite: a Cholesky pivot <= 0 (SA rank deficient) */
+  LSQ_ERR_BREAKDOWN = 3,  /* p^T H p <= 0 or a non-finite value inside the iteration */
+  LSQ_ERR_MAXIT = 4,      /* tolerance not met within maxit iterations; x holds the last iterate */
+  LSQ_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up (the context stays usable) */
+  LSQ_ERR_CUDA = 6,       /* a CUDA runtime call failed */
+  LSQ_ERR_ALLOC = 7       /* device scratch allocation failed */
+} lsq_status;
+
+typedef enum { LSQ_F64 = 0, LSQ_F32 = 1 } lsq_dtype;
+
+typedef enum {
+  LSQ_SKETCH_GAUSS = 0, /* Section 2: iid N(0, 1/m) entries */
+  LSQ_SKETCH_SRHT = 1,  /* Section 2: S = R H E (sampling, Hadamard, signs), zero padding */
+  LSQ_SKETCH_SJLT = 2   /* Section 2: s entries +-1/sqrt(s) per column of S */
+} lsq_sketch_type;
+
+typedef enum {
+  LSQ_PCG = 0,        /* Section 1, eq. (PCG); fixed embedding */
+  LSQ_IHS = 1,        /* Section 1, eq. eqnihs */
+  LSQ_POLYAK_IHS = 2  /* Section 1, eq. eqnpolyakihs */
+} lsq_method;
+
+/* Arithmetic used for the passes over A inside lsq_solve.
+ *   LSQ_PREC_F64:   native FP64 for every operation (the plain FP64 method).
+ *   LSQ_PREC_MIXED: passes over A in FP32 arithmetic, with the residual b - H x
+ *                   re-evaluated in emulated double-FP32 (about 48 significant bits)
+ *                   every `refresh_every` iterations and at the end; x, r and the
+ *                   preconditioner stay FP64.  Reaches the same tolerance as F64. */
+typedef enum { LSQ_PREC_F64 = 0, LSQ_PREC_MIXED = 1 } lsq_precision;
+
+/* A dense matrix in device memory (row-major, stride ld elements). */
+typedef struct {
+  const void* data; /* device; 16-byte aligned for the fast paths (any alignment of the element works) */
+  int64_t n;        /* rows, 1 <= n < 2^31 */
+  int64_t d;        /* columns, 1 <= d <= 1024 */
+  int64_t ld;       /* row stride in elements, ld >= d */
+  int32_t dtype;    /* lsq_dtype */
+} lsq_matrix;
+
+typedef struct lsq_ctx lsq_ctx;
+
+/* Creates a context on the current CUDA device that issues its work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Returns LSQ_ERR_CUDA if no
+ * device is usable.  No device memory is allocated until the first call that needs it. */
+LSQ_API lsq_status lsq_create(lsq_ctx** ctx, void* cuda_stream);
+
+/* Waits for the context's stream and frees its scratch.  NULL is accepted. */
+LSQ_API lsq_status lsq_destroy(lsq_ctx* ctx);
+
+/* Replaces the stream of the context (the previous stream is not synchronised). */
+LSQ_API lsq_status lsq_set_stream(lsq_ctx* ctx, void* cuda_stream);
+
+/* Arithmetic of lsq_sketch.
+ *   LSQ_SKETCH_F64: FP64 (the +-1 weights of SRHT/SJLT are exact; agrees with an FP64
+ *                   evaluation of S A to rounding).
+ *   LSQ_SKETCH_F32: A rounded to FP32 on load, FP32 arithmetic, FP64 output.  A sketch
+ *                   only has to be a subspace embedding; the preconditioner it yields is
+ *                   as good, and the solve still reaches its tolerance against FP64 x*. */
+typedef enum { LSQ_SKETCH_F64 = 0, LSQ_SKETCH_F32 = 1 } lsq_sketch_precision;
+
+typedef struct {
+  uint32_t t;        /* sketch instance (Philox counter word 2): 0 for a fixed embedding,
+                        the iteration index for refreshed embeddings */
+  int32_t s;         /* SJLT nonzeros per column of S, 1..32 (default 8); ignored otherwise */
+  int32_t precision; /* lsq_sketch_precision (default LSQ_SKETCH_F64) */
+} lsq_sketch_opts;
+
+/* ---------------------------------------------------------------------------------
+ * lsq_sketch: SA = S A for one draw of the embedding S (Section 2).
+ *   A     : the data matrix (device).
+ *   type  : lsq_sketch_type.
+ *   m     : sketch size, 1 <= m <= 65536; SRHT also m <= N = 2^ceil(log2 n) and
+ *           (FP64) m <= 16384; SJLT s <= m.
+ *   seed  : Philox key.
+ *   opts  : may be NULL (t = 0, s = 8, FP64).
+ *   SA    : device, m x d FP64 output (row-major), caller-owned.
+ * Scaling makes E[S^T S] = I_n for every type:
+ *   Gaussian  S[j,i] = z(j,i)/sqrt(m), z from Box-Muller on Philox(i, j/2, t, 1)
+ *             (even j: cosine branch, odd j: sine branch; 53-bit uniforms (k+1/2) 2^-53
+ *             from the word pairs (w0,w1) and (w2,w3));
+ *   SRHT      S = (1/sqrt(m)) P H E on the zero-padded N rows; E_ii = -1 iff bit 0 of
+ *             Philox(i, 0, t, 2).w0 is set; P keeps the m rows with the smallest 64-bit
+ *             key (Philox(i, 0, t, 3).w0 << 32 | .w1, ties by index) in ascending order;
+ *             H is the +-1 Sylvester Hadamard matrix in natural order;
+ *   SJLT      column i of S holds s distinct rows drawn by Lemire's bounded-integer
+ *             method from the successive words of Philox(i, r, t, 4), r = 0, 1, ...,
+ *             duplicates skipped; the k-th drawn row has sign -1 iff bit k of
+ *             Philox(i, 0, t, 5).w0 is set; entries +-1/sqrt(s).
+ * --------------------------------------------------------------------------------- */
+LSQ_API lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, int64_t m, uint64_t seed,
+                      const lsq_sketch_opts* opts, double* SA);
+
+/* ---------------------------------------------------------------------------------
+ * lsq_factor: the preconditioner factor of H_S = (SA)^T (SA) (Section 1, PCG
+ * paragraph; Section 6, which allows either a QR of SA or a Cholesky factor of H_S).
+ *   SA : device, m x d FP64 (row-major), m >= d.
+ *   R  : device, d x d FP64 output: upper triangular, positive diagonal, R^T R = H_S
+ *        (Gram in FP64, then Cholesky); the strict lower triangle is written as 0.
+ *   W  : device, d x d FP64 output: W = R^{-1} (upper triangular), which lsq_solve
+ *        uses to apply H_S^{-1} r = W (W^T r) as two parallel triangular products.
+ * Status LSQ_ERR_RANK (after a synchronisation) if a pivot is not positive. This call
+ * waits for its own work so that it can report the rank check.
+ * --------------------------------------------------------------------------------- */
+LSQ_API lsq_status lsq_factor(lsq_ctx* ctx, const double* SA, int64_t m, int64_t d, double* R, double* W);
+
+/* Options of lsq_solve; lsq_solve_opts_default fills the defaults noted below. */
+typedef struct {
+  double rho;          /* deviation parameter rho in (0,1) of the event E_rho (Section 3);
+                          default (<= 0): d/m for the fixed embedding, where m comes from
+                          `m` below (required for IHS/Polyak defaults and the stopping rule) */
+  double mu;           /* step size; default (NaN): IHS fixed (1-rho)^2/(1+rho), Polyak fixed
+                          (1-rho)^2 (theorem theoremihsfixed); refreshed theta1/theta2
+                          (theorem theoremexacterrorrefreshed, Gaussian moments of Section 2;
+                          SRHT: Haar trace approximations rescaled to E[S^T S] = I) */
+  double beta;         /* momentum; default (NaN): rho for fixed Polyak-IHS, 0.1 refreshed */
+  int32_t refresh;     /* IHS / Polyak only: 1 = a fresh embedding every iteration */
+  int32_t sketch_type; /* refreshed embeddings: lsq_sketch_type */
+  int64_t m;           /* sketch size of the embedding behind W (fixed) or refreshed */
+  uint64_t seed;       /* refreshed embeddings: Philox key (instance t = iteration index) */
+  int32_t s;           /* refreshed SJLT: nonzeros per column (default 8) */
+  int32_t precision;   /* lsq_precision (default LSQ_PREC_F64) */
+  int32_t refresh_every; /* MIXED only: iterations between exact residual replacements (default 8) */
+  int32_t grid_blocks; /* 0 = automatic; else the number of resident CTAs of the solve kernel */
+  int32_t x0_zero;     /* 1: x0 is zero, so the initial residual b - H x0 = b needs no pass over A */
+} lsq_solve_opts;
+
+/* Results of lsq_solve. */
+typedef struct {
+  int32_t iters;        /* iterations taken (passes of the loop; PCG: updates of x) */
+  int32_t status;       /* same as the return value */
+  int32_t passes;       /* passes over A, including the initial residual and replacements */
+  int32_t exact_passes; /* of which passes in full precision (MIXED: the residual replacements) */
+  double est_err;       /* final stopping quantity sqrt((1+sqrt(rho))^2 r^T H_S^-1 r / <b,x>) */
+  double ms_total;      /* device time of the whole call (ms), CUDA events */
+  double ms_sketch;     /* refreshed only: time in sketch + factor (ms) */
+} lsq_solve_info;
+
+LSQ_API void lsq_solve_opts_default(lsq_solve_opts* opts);
+
+/* ---------------------------------------------------------------------------------
+ * lsq_solve: iterates from x0 to an approximation of x*.
+ *   A      : the data matrix (device).
+ *   b      : device, d FP64.
+ *   method : lsq_method.
+ *   W      : device, d x d FP64, W = R^{-1} from lsq_factor (fixed embedding); NULL
+ *            with opts->refresh = 1 draws a new embedding every iteration (IHS/Polyak).
+ *   x      : device, d FP64; in: x0, out: the last iterate.
+ *   tol    : stop when (1+sqrt(rho))^2 r^T H_S^{-1} r <= tol^2 <b, x>, which bounds the
+ *            relative H-norm error ||x - x*||_H / ||x*||_H by tol on the event E_rho
+ *            (Section 3) since r^T H_S^{-1} r = Delta^T C_S^{-1} Delta; tol = 0 runs maxit.
+ *   maxit  : iteration limit (>= 0).
+ *   opts   : may be NULL (defaults); info: may be NULL.
+ * Returns LSQ_OK, LSQ_ERR_MAXIT (x = last iterate), LSQ_ERR_BREAKDOWN, LSQ_ERR_RANK
+ * (refreshed factor), LSQ_ERR_TIMEOUT, LSQ_ERR_ARG or LSQ_ERR_CUDA.
+ * --------------------------------------------------------------------------------- */
+LSQ_API lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double* b, int32_t method,
+                     const double* W, double* x, double tol, int32_t maxit,
+                     const lsq_solve_opts* opts, lsq_solve_info* info);
+
+/* One fused pass over A: v = A^T (A p) and q = ||A p||^2 = p^T H p (the iteration cost
+ * of Section 6), FP64 arithmetic.  p, v: device, d FP64; q: device, 1 FP64. */
+LSQ_API lsq_status lsq_hmatvec(lsq_ctx* ctx, const lsq_matrix* A, const double* p, double* v, double* q);
+
+/* Human-readable name of a status code (static storage). */
+LSQ_API const char* lsq_status_str(int32_t status);
+
+/* Number of CUDA kernels this library has launched in the calling process so far
+ * (host-side counter; lets a caller count the kernels inside a timed region). */
+LSQ_API uint64_t lsq_launch_count(void);
+
+/* Library version string (static storage). */
+LSQ_API const char* lsq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSQ_H */

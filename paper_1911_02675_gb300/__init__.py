@@ -1,0 +1,247 @@
+"""GB300 (sm_103a) randomized-preconditioned least squares, after Lacotte & Pilanci,
+"Faster Least Squares Optimization" (arXiv 1911.02675).
+
+This module is a thin ctypes binding over the C ABI of ``include/lsq.h`` (library
+``_build/liblsq.so``, built by ``build.py``).  It only marshals arguments: torch
+tensors give device pointers and the current CUDA stream; every step of the method
+runs in the library's kernels.  If the library is missing the import fails; there
+is no CPU path.
+
+Entry points (same names as the C ABI):
+    lsq_sketch(ctx, A, kind, m, seed, t=0, s=8, precision="f64") -> SA      (Section 2)
+    lsq_factor(ctx, SA) -> (R, W)                                           (Section 1, PCG; Section 6)
+    lsq_solve(ctx, A, b, method, W, x0=None, tol=1e-10, maxit=..., **opts)  (Section 1; Sections 3-4)
+    lsq_hmatvec(ctx, A, p) -> (v, q)                                        (one fused pass over A)
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblsq.so")
+
+STATUS = {0: "LSQ_OK", 1: "LSQ_ERR_ARG", 2: "LSQ_ERR_RANK", 3: "LSQ_ERR_BREAKDOWN", 4: "LSQ_ERR_MAXIT",
+          5: "LSQ_ERR_TIMEOUT", 6: "LSQ_ERR_CUDA", 7: "LSQ_ERR_ALLOC"}
+LSQ_OK, LSQ_ERR_ARG, LSQ_ERR_RANK, LSQ_ERR_BREAKDOWN, LSQ_ERR_MAXIT, LSQ_ERR_TIMEOUT, LSQ_ERR_CUDA, LSQ_ERR_ALLOC = range(8)
+SKETCH = {"gauss": 0, "srht": 1, "sjlt": 2}
+METHOD = {"pcg": 0, "ihs": 1, "polyak": 2}
+PRECISION = {"f64": 0, "mixed": 1}
+SKETCH_PRECISION = {"f64": 0, "f32": 1}
+DTYPE = {torch.float64: 0, torch.float32: 1}
+
+# every symbol the header declares
+EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_sketch", "lsq_factor", "lsq_solve",
+           "lsq_solve_opts_default", "lsq_hmatvec", "lsq_status_str", "lsq_version", "lsq_launch_count")
+
+
+class LsqError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({_status_str(status)})")
+
+
+class LsqMatrix(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("dtype", ctypes.c_int32)]
+
+
+class LsqSketchOpts(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_uint32), ("s", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class LsqSolveOpts(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("mu", ctypes.c_double), ("beta", ctypes.c_double),
+                ("refresh", ctypes.c_int32), ("sketch_type", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("s", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("refresh_every", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("x0_zero", ctypes.c_int32)]
+
+
+class LsqSolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("exact_passes", ctypes.c_int32), ("est_err", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_sketch", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1911_02675_gb300.build` (no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i64, i32, u64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+    L.lsq_create.argtypes = [ctypes.POINTER(P), P]
+    L.lsq_destroy.argtypes = [P]
+    L.lsq_set_stream.argtypes = [P, P]
+    L.lsq_sketch.argtypes = [P, ctypes.POINTER(LsqMatrix), i32, i64, u64, ctypes.POINTER(LsqSketchOpts), P]
+    L.lsq_factor.argtypes = [P, P, i64, i64, P, P]
+    L.lsq_solve.argtypes = [P, ctypes.POINTER(LsqMatrix), P, i32, P, P, dbl, i32, ctypes.POINTER(LsqSolveOpts),
+                            ctypes.POINTER(LsqSolveInfo)]
+    L.lsq_solve_opts_default.argtypes = [ctypes.POINTER(LsqSolveOpts)]
+    L.lsq_solve_opts_default.restype = None
+    L.lsq_hmatvec.argtypes = [P, ctypes.POINTER(LsqMatrix), P, P, P]
+    L.lsq_status_str.argtypes = [i32]
+    L.lsq_status_str.restype = ctypes.c_char_p
+    L.lsq_version.restype = ctypes.c_char_p
+    L.lsq_launch_count.restype = ctypes.c_uint64
+    for name in ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_sketch", "lsq_factor", "lsq_solve", "lsq_hmatvec"):
+        getattr(L, name).restype = ctypes.c_int
+    return L
+
+
+_L = _load()
+
+
+def lib():
+    return _L
+
+
+def _status_str(s: int) -> str:
+    return _L.lsq_status_str(int(s)).decode()
+
+
+def lsq_launch_count() -> int:
+    return int(_L.lsq_launch_count())
+
+
+def lsq_version() -> str:
+    return _L.lsq_version().decode()
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_handle(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _check_vec(v: torch.Tensor, d: int, name: str):
+    if not v.is_cuda or v.dtype != torch.float64 or v.numel() != d or not v.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of {d} entries")
+
+
+def as_matrix(A: torch.Tensor) -> LsqMatrix:
+    if A.dim() != 2 or not A.is_cuda or A.dtype not in DTYPE or A.stride(1) != 1 or A.stride(0) < A.shape[1]:
+        raise ValueError("A must be a 2-D CUDA float64/float32 tensor with unit column stride")
+    return LsqMatrix(A.data_ptr(), A.shape[0], A.shape[1], A.stride(0), DTYPE[A.dtype])
+
+
+class Context:
+    """Owns an lsq_ctx (stream = the current torch stream of `device` at creation)."""
+
+    def __init__(self, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
+        with torch.cuda.device(self.device):
+            h = ctypes.c_void_p()
+            st = _L.lsq_create(ctypes.byref(h), _stream_handle(self.device))
+            if st:
+                raise LsqError(st, "lsq_create")
+        self.handle = h
+
+    def sync_stream(self):
+        _L.lsq_set_stream(self.handle, _stream_handle(self.device))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _L.lsq_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lsq_create(device=None) -> Context:
+    return Context(device)
+
+
+def lsq_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def lsq_sketch(ctx: Context, A: torch.Tensor, kind: str, m: int, seed: int, t: int = 0, s: int = 8,
+               precision: str = "f64", out: torch.Tensor | None = None) -> torch.Tensor:
+    ctx.sync_stream()
+    M = as_matrix(A)
+    SA = out if out is not None else torch.empty((m, A.shape[1]), dtype=torch.float64, device=A.device)
+    opts = LsqSketchOpts(t, s, SKETCH_PRECISION[precision])
+    st = _L.lsq_sketch(ctx.handle, ctypes.byref(M), SKETCH[kind], m, seed, ctypes.byref(opts), _ptr(SA))
+    if st:
+        raise LsqError(st, "lsq_sketch")
+    return SA
+
+
+def lsq_factor(ctx: Context, SA: torch.Tensor, R: torch.Tensor | None = None, W: torch.Tensor | None = None):
+    ctx.sync_stream()
+    if SA.dtype != torch.float64 or not SA.is_contiguous() or not SA.is_cuda:
+        raise ValueError("SA must be a contiguous CUDA float64 matrix")
+    m, d = SA.shape
+    R = R if R is not None else torch.empty((d, d), dtype=torch.float64, device=SA.device)
+    W = W if W is not None else torch.empty((d, d), dtype=torch.float64, device=SA.device)
+    st = _L.lsq_factor(ctx.handle, _ptr(SA), m, d, _ptr(R), _ptr(W))
+    if st:
+        raise LsqError(st, "lsq_factor")
+    return R, W
+
+
+def solve_opts(**kw) -> LsqSolveOpts:
+    o = LsqSolveOpts()
+    _L.lsq_solve_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "sketch_type" and isinstance(v, str):
+            v = SKETCH[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        setattr(o, k, v)
+    return o
+
+
+def lsq_solve(ctx: Context, A: torch.Tensor, b: torch.Tensor, method: str, W: torch.Tensor | None,
+              x0: torch.Tensor | None = None, tol: float = 1e-10, maxit: int = 1000, raise_on_maxit: bool = False,
+              **opts):
+    """Returns (x, info dict).  Raises LsqError for errors other than LSQ_ERR_MAXIT."""
+    ctx.sync_stream()
+    M = as_matrix(A)
+    d = A.shape[1]
+    _check_vec(b, d, "b")
+    x = torch.zeros(d, dtype=torch.float64, device=A.device) if x0 is None else x0.clone()
+    _check_vec(x, d, "x0")
+    if W is not None and (W.shape != (d, d) or W.dtype != torch.float64 or not W.is_contiguous()):
+        raise ValueError("W must be a contiguous d x d float64 tensor")
+    if x0 is None:
+        opts.setdefault("x0_zero", 1)
+    o = solve_opts(**opts)
+    info = LsqSolveInfo()
+    st = _L.lsq_solve(ctx.handle, ctypes.byref(M), _ptr(b), METHOD[method], _ptr(W), _ptr(x), float(tol), int(maxit),
+                      ctypes.byref(o), ctypes.byref(info))
+    if st and not (st == LSQ_ERR_MAXIT and not raise_on_maxit):
+        raise LsqError(st, "lsq_solve")
+    return x, info.as_dict()
+
+
+def lsq_hmatvec(ctx: Context, A: torch.Tensor, p: torch.Tensor):
+    ctx.sync_stream()
+    M = as_matrix(A)
+    d = A.shape[1]
+    _check_vec(p, d, "p")
+    v = torch.empty(d, dtype=torch.float64, device=A.device)
+    q = torch.empty(1, dtype=torch.float64, device=A.device)
+    st = _L.lsq_hmatvec(ctx.handle, ctypes.byref(M), _ptr(p), _ptr(v), _ptr(q))
+    if st:
+        raise LsqError(st, "lsq_hmatvec")
+    return v, q
+
+
+def default_rho(d: int, m: int) -> float:
+    return d / m
+
+
+def lam1_bound(rho: float) -> float:
+    return (1 + math.sqrt(rho)) ** 2

@@ -1,0 +1,155 @@
+// common.cuh -- internal helpers of the GB300 least-squares library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lsq.h"
+
+#define LSQ_WARPS 8
+#define LSQ_THREADS (LSQ_WARPS * 32)
+#define LSQ_MAX_D 1024
+
+// Philox stream tags (counter word 3); must stay equal to the documented ABI values.
+#define TAG_GAUSS 1u
+#define TAG_SIGN 2u
+#define TAG_SAMPLE 3u
+#define TAG_SJLT 4u
+#define TAG_SJLT_SIGN 5u
+
+struct lsq_ctx {
+  int device;
+  int sm_count;
+  cudaStream_t stream;
+  void* scratch;           // device arena of sketch / factor / single passes, grown on demand
+  size_t scratch_bytes;
+  void* state;             // device arena of the solver's iteration state (separate, so that a
+  size_t state_bytes;      // refreshed solve can call the sketch and the factor between steps)
+  int* host_status;        // pinned host word for status read-back
+  cudaEvent_t ev0, ev1;
+};
+
+#define LSQ_CUDA_TRY(expr)                         \
+  do {                                             \
+    cudaError_t e__ = (expr);                      \
+    if (e__ != cudaSuccess) {                      \
+      (void)cudaGetLastError();                    \
+      return LSQ_ERR_CUDA;                         \
+    }                                              \
+  } while (0)
+
+// Number of kernels this library has launched in the process (lsq_launch_count).
+void lsq_count_launch();
+
+#define LSQ_LAUNCH_CHECK()                         \
+  do {                                             \
+    lsq_count_launch();                            \
+    cudaError_t e__ = cudaGetLastError();          \
+    if (e__ != cudaSuccess) return LSQ_ERR_CUDA;   \
+  } while (0)
+
+// Ensures the context arena holds at least `bytes` (256-byte aligned carving is the caller's).
+lsq_status lsq_ensure_scratch(lsq_ctx* ctx, size_t bytes);
+lsq_status lsq_ensure_state(lsq_ctx* ctx, size_t bytes);
+
+static inline size_t lsq_align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carves consecutive 256-byte aligned regions out of a base pointer.
+struct Carver {
+  char* base;
+  size_t off;
+  template <typename T>
+  T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base + off);
+    off += lsq_align256(count * sizeof(T));
+    return p;
+  }
+};
+
+// ----------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, multipliers
+// 0xD2511F53 / 0xCD9E8D57, key increments 0x9E3779B9 / 0xBB67AE85.
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 philox_at(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t t, uint32_t tag) {
+  return philox4x32_10(make_uint4(c0, c1, t, tag), (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// ----------------------------------------------------------------------------------
+// Warp reductions (fixed butterfly order: every lane ends with the same value).
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ----------------------------------------------------------------------------------
+// Grid-wide barrier for cooperatively launched kernels, with a bounded wait.
+// `bar[0]` counts arrivals, `bar[1]` is the generation.  A CTA that waits more than
+// `LSQ_SPIN_LIMIT` polls sets *err = LSQ_ERR_TIMEOUT and leaves the barrier; callers
+// test the flag after every barrier and return, so the kernel always terminates.
+// ----------------------------------------------------------------------------------
+#define LSQ_SPIN_LIMIT (1u << 24)
+#define LSQ_WAIT_NS 4000000000ull
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned gen = ld_acquire_u32(bar + 1);
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == nblocks) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      unsigned spins = 0;
+      while (ld_acquire_u32(bar + 1) == gen) {
+        if (*(volatile int*)err != 0) break;  // another CTA already gave up
+        if (++spins > LSQ_SPIN_LIMIT || global_ns() - t0 > LSQ_WAIT_NS) {
+          atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)err;
+}
+
+static inline int lsq_ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

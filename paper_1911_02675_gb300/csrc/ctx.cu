@@ -1,0 +1,95 @@
+// ctx.cu -- context, scratch arena and status strings of the C ABI.
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+
+#include "common.cuh"
+
+extern "C" lsq_status lsq_create(lsq_ctx** out, void* stream) {
+  if (!out) return LSQ_ERR_ARG;
+  *out = nullptr;
+  int dev = 0;
+  LSQ_CUDA_TRY(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  LSQ_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+  if (!prop.cooperativeLaunch) return LSQ_ERR_CUDA;
+  lsq_ctx* c = (lsq_ctx*)calloc(1, sizeof(lsq_ctx));
+  if (!c) return LSQ_ERR_ALLOC;
+  c->device = dev;
+  c->sm_count = prop.multiProcessorCount;
+  c->stream = (cudaStream_t)stream;
+  if (cudaMallocHost((void**)&c->host_status, 64) != cudaSuccess ||
+      cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (c->host_status) cudaFreeHost(c->host_status);
+    free(c);
+    return LSQ_ERR_CUDA;
+  }
+  *out = c;
+  return LSQ_OK;
+}
+
+extern "C" lsq_status lsq_destroy(lsq_ctx* c) {
+  if (!c) return LSQ_OK;
+  cudaStreamSynchronize(c->stream);
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->state) cudaFree(c->state);
+  cudaFreeHost(c->host_status);
+  cudaEventDestroy(c->ev0);
+  cudaEventDestroy(c->ev1);
+  (void)cudaGetLastError();
+  free(c);
+  return LSQ_OK;
+}
+
+extern "C" lsq_status lsq_set_stream(lsq_ctx* c, void* stream) {
+  if (!c) return LSQ_ERR_ARG;
+  c->stream = (cudaStream_t)stream;
+  return LSQ_OK;
+}
+
+static lsq_status grow(lsq_ctx* c, void** buf, size_t* have, size_t bytes) {
+  if (bytes <= *have) return LSQ_OK;
+  // the old buffer may still be in use by work queued on the stream
+  LSQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (*buf) {
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+  }
+  size_t want = lsq_align256(bytes + (bytes >> 3));
+  if (cudaMalloc(buf, want) != cudaSuccess) {
+    (void)cudaGetLastError();
+    *buf = nullptr;
+    return LSQ_ERR_ALLOC;
+  }
+  *have = want;
+  return LSQ_OK;
+}
+
+lsq_status lsq_ensure_scratch(lsq_ctx* c, size_t bytes) { return grow(c, &c->scratch, &c->scratch_bytes, bytes); }
+
+lsq_status lsq_ensure_state(lsq_ctx* c, size_t bytes) { return grow(c, &c->state, &c->state_bytes, bytes); }
+
+extern "C" const char* lsq_status_str(int32_t s) {
+  switch (s) {
+    case LSQ_OK: return "ok";
+    case LSQ_ERR_ARG: return "invalid argument";
+    case LSQ_ERR_RANK: return "sketched Hessian not positive definite (rank deficient)";
+    case LSQ_ERR_BREAKDOWN: return "iteration breakdown (non-positive curvature or non-finite value)";
+    case LSQ_ERR_MAXIT: return "tolerance not reached within maxit iterations";
+    case LSQ_ERR_TIMEOUT: return "bounded device-side wait timed out";
+    case LSQ_ERR_CUDA: return "CUDA runtime error";
+    case LSQ_ERR_ALLOC: return "device allocation failed";
+    default: return "unknown status";
+  }
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void lsq_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" uint64_t lsq_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" const char* lsq_version(void) { return "lsq-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,339 @@
+// factor.cu -- H_S = (SA)^T (SA) = R^T R and W = R^{-1} (Section 1, PCG paragraph;
+// Section 6: a factorisation of H_S costs O(m d^2) and makes each solve with H_S O(d^2)).
+//
+// (1) Gram G = (SA)^T (SA) in FP64: split-K tiles over the upper triangle, fixed-order
+//     reduction, padded to dp = 32 ceil(d/32) with an identity block.
+// (2) One cooperative kernel: right-looking blocked Cholesky with 32 x 32 blocks
+//     (diagonal block on one CTA, panel and trailing update as 32 x 8 tile tasks over
+//     the whole grid), then W = R^{-1} by recursive doubling over a binary tree of the
+//     diagonal blocks: for R = [[A, B], [0, C]], R^{-1} = [[A^-1, -A^-1 B C^-1], [0, C^-1]].
+//     Phases are separated by bounded grid barriers.
+#include <algorithm>
+#include <math.h>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int TB = 64, TK = 16;
+
+// part[split][dp][dp] (upper tiles only) = sum over the split's rows of SA^T SA
+__global__ void __launch_bounds__(256) gram_kernel(const double* __restrict__ SA, int m, int d, int dp,
+                                                   int rows_per_split, const int2* __restrict__ tiles,
+                                                   double* __restrict__ part) {
+  __shared__ double Xa[TK][TB];
+  __shared__ double Xb[TK][TB];
+  const int2 tl = tiles[blockIdx.x];
+  const int a0 = tl.x * TB, b0 = tl.y * TB;
+  const int r_begin = blockIdx.y * rows_per_split;
+  const int r_end = min(m, r_begin + rows_per_split);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int r0 = r_begin; r0 < r_end; r0 += TK) {
+    for (int e = threadIdx.x; e < TK * TB; e += 256) {
+      const int k = e / TB, c = e % TB;
+      const int r = r0 + k;
+      Xa[k][c] = (r < r_end && a0 + c < d) ? SA[(int64_t)r * d + a0 + c] : 0.0;
+      Xb[k][c] = (r < r_end && b0 + c < d) ? SA[(int64_t)r * d + b0 + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < TK; ++k) {
+      double x[4], y[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = Xa[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) y[j] = Xb[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(x[i], y[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* out = part + (int64_t)blockIdx.y * dp * dp;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
+      if (a < dp && b < dp) out[(int64_t)a * dp + b] = acc[i][j];
+    }
+}
+
+// G = sum of the splits on the upper tiles, mirrored; identity on the padded diagonal
+__global__ void gram_reduce_kernel(const double* __restrict__ part, int splits, int d, int dp, double* __restrict__ G) {
+  const int64_t total = (int64_t)dp * dp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e / dp), b = (int)(e % dp);
+    double v;
+    if (a >= d || b >= d) {
+      v = (a == b) ? 1.0 : 0.0;
+    } else {
+      const int lo = min(a, b), hi = max(a, b);
+      // the tile holding (lo, hi) is an upper tile (tile row <= tile column)
+      const int64_t idx = (int64_t)lo * dp + hi;
+      const bool upper_tile = (lo / TB) <= (hi / TB);
+      const int64_t src = upper_tile ? idx : (int64_t)hi * dp + lo;
+      v = 0.0;
+      for (int g = 0; g < splits; ++g) v += part[(int64_t)g * dp * dp + src];
+    }
+    G[e] = v;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// 32 x 8 tile task: out(r, c) = (acc ? out(r, c) : 0) + alpha * sum_k X(r, k) Y(k, c),
+// X(r, k) = Xm[r*ld + k] (or Xm[k*ld + r] when transX), Y(k, c) = Ym[k*ld + c], k < K.
+// ------------------------------------------------------------------------------------
+struct TileSmem {
+  double X[32][33];
+  double Y[32][8];
+};
+
+__device__ void tile_task(TileSmem& sm, double* out, const double* Xm, bool transX, const double* Ym, int K, int ld,
+                          double alpha, bool acc) {
+  const int r = threadIdx.x >> 3, c = threadIdx.x & 7;
+  double sum = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      if (transX) {
+        const int kk = e >> 5, rr = e & 31;
+        sm.X[rr][kk] = Xm[(int64_t)(k0 + kk) * ld + rr];
+      } else {
+        const int rr = e >> 5, kk = e & 31;
+        sm.X[rr][kk] = Xm[(int64_t)rr * ld + k0 + kk];
+      }
+    }
+    {
+      const int kk = threadIdx.x >> 3, cc = threadIdx.x & 7;
+      sm.Y[kk][cc] = Ym[(int64_t)(k0 + kk) * ld + cc];
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) sum = fma(sm.X[r][kk], sm.Y[kk][c], sum);
+    __syncthreads();
+  }
+  double* o = out + (int64_t)r * ld + c;
+  *o = (acc ? *o : 0.0) + alpha * sum;
+}
+
+// Cholesky of one 32 x 32 diagonal block (one warp) and the inverse of its factor.
+// Returns false (and sets *err) on a non-positive or non-finite pivot.
+__device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, int* err) {
+  __shared__ double Rs[32][33];
+  __shared__ double Ws[32][33];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+    for (int i = 0; i < 32; ++i) Rs[i][l] = 0.0;
+    __syncwarp();
+    for (int j = 0; j < 32; ++j) {
+      double t = Gkk[(int64_t)j * ld + l];
+      for (int i = 0; i < j; ++i) t -= Rs[i][j] * Rs[i][l];
+      const double piv = __shfl_sync(0xffffffffu, t, j);
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        if (l == 0) bad = 1;
+        break;
+      }
+      const double rjj = sqrt(piv);
+      if (l == j) Rs[j][j] = rjj;
+      else if (l > j) Rs[j][l] = t / rjj;
+      __syncwarp();
+    }
+    __syncwarp();
+    // column l of the inverse by back substitution
+    for (int i = 0; i < 32; ++i) Ws[i][l] = 0.0;
+    if (!bad) {
+      for (int i = l; i >= 0; --i) {
+        double s = (i == l) ? 1.0 : 0.0;
+        for (int k = i + 1; k <= l; ++k) s -= Rs[i][k] * Ws[k][l];
+        Ws[i][l] = s / Rs[i][i];
+      }
+    }
+    __syncwarp();
+    for (int i = 0; i < 32; ++i) {
+      Rkk[(int64_t)i * ld + l] = Rs[i][l];
+      Wkk[(int64_t)i * ld + l] = Ws[i][l];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && bad) atomicCAS(err, 0, (int)LSQ_ERR_RANK);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) chol_inv_kernel(double* __restrict__ G, double* __restrict__ Rf,
+                                                       double* __restrict__ Wf, double* __restrict__ Tb, int nblk,
+                                                       const int4* __restrict__ nodes, const int* __restrict__ level_start,
+                                                       int nlevels, unsigned* bar, int* err) {
+  __shared__ TileSmem sm;
+  const int dp = nblk * 32;
+  const unsigned nb = gridDim.x;
+  for (int k = 0; k < nblk; ++k) {
+    const int64_t kk = (int64_t)k * 32;
+    if (blockIdx.x == 0) diag_block(G + kk * dp + kk, Rf + kk * dp + kk, Wf + kk * dp + kk, dp, err);
+    if (grid_barrier(bar, nb, err)) return;
+    const int rest = nblk - 1 - k;
+    // panel: R[k][j] = W[k][k]^T G[k][j]
+    for (int task = blockIdx.x; task < rest * 4; task += nb) {
+      const int j = k + 1 + task / 4, q = task % 4;
+      const int64_t col = (int64_t)j * 32 + q * 8;
+      tile_task(sm, Rf + kk * dp + col, Wf + kk * dp + kk, true, G + kk * dp + col, 32, dp, 1.0, false);
+    }
+    if (grid_barrier(bar, nb, err)) return;
+    // trailing update: G[i][j] -= R[k][i]^T R[k][j], k < i <= j
+    const int pairs = rest * (rest + 1) / 2;
+    for (int task = blockIdx.x; task < pairs * 4; task += nb) {
+      int p = task / 4;
+      const int q = task % 4;
+      int i = 0;
+      while (p >= rest - i) { p -= rest - i; ++i; }
+      const int bi = k + 1 + i, bj = bi + p;
+      const int64_t col = (int64_t)bj * 32 + q * 8;
+      tile_task(sm, G + (int64_t)bi * 32 * dp + col, Rf + kk * dp + (int64_t)bi * 32, true, Rf + kk * dp + col, 32, dp,
+                -1.0, true);
+    }
+    if (grid_barrier(bar, nb, err)) return;
+  }
+  // W = R^{-1}: merge sibling blocks bottom-up
+  for (int lev = 0; lev < nlevels; ++lev) {
+    const int n0 = level_start[lev], n1 = level_start[lev + 1];
+    // phase 1: T[a:mid, mid:b] = R[a:mid, mid:b] W[mid:b, mid:b]
+    int base = 0;
+    for (int nd = n0; nd < n1; ++nd) {
+      const int4 t = nodes[nd];
+      const int rows = t.y - t.x, cols4 = (t.z - t.y) * 4;
+      for (int task = (int)((blockIdx.x + nb - (unsigned)(base % nb)) % nb); task < rows * cols4; task += nb) {
+        const int rb = task / cols4, cs = task % cols4;
+        const int64_t r0 = (int64_t)(t.x + rb) * 32, c0 = (int64_t)t.y * 32 + cs * 8;
+        tile_task(sm, Tb + r0 * dp + c0, Rf + r0 * dp + (int64_t)t.y * 32, false, Wf + (int64_t)t.y * 32 * dp + c0,
+                  (t.z - t.y) * 32, dp, 1.0, false);
+      }
+      base += rows * cols4;
+    }
+    if (grid_barrier(bar, nb, err)) return;
+    // phase 2: W[a:mid, mid:b] = -W[a:mid, a:mid] T[a:mid, mid:b]
+    base = 0;
+    for (int nd = n0; nd < n1; ++nd) {
+      const int4 t = nodes[nd];
+      const int rows = t.y - t.x, cols4 = (t.z - t.y) * 4;
+      for (int task = (int)((blockIdx.x + nb - (unsigned)(base % nb)) % nb); task < rows * cols4; task += nb) {
+        const int rb = task / cols4, cs = task % cols4;
+        const int64_t r0 = (int64_t)(t.x + rb) * 32, c0 = (int64_t)t.y * 32 + cs * 8;
+        tile_task(sm, Wf + r0 * dp + c0, Wf + r0 * dp + (int64_t)t.x * 32, false, Tb + (int64_t)t.x * 32 * dp + c0,
+                  (t.y - t.x) * 32, dp, -1.0, false);
+      }
+      base += rows * cols4;
+    }
+    if (grid_barrier(bar, nb, err)) return;
+  }
+}
+
+__global__ void copy_out_kernel(const double* __restrict__ Rf, const double* __restrict__ Wf, int d, int dp,
+                                double* __restrict__ R, double* __restrict__ W) {
+  const int64_t total = (int64_t)d * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e / d), b = (int)(e % d);
+    const bool up = b >= a;
+    R[e] = up ? Rf[(int64_t)a * dp + b] : 0.0;
+    W[e] = up ? Wf[(int64_t)a * dp + b] : 0.0;
+  }
+}
+
+static void build_tree(int a, int b, int depth, std::vector<std::vector<int4>>& by_depth) {
+  if (b - a <= 1) return;
+  const int mid = a + (b - a) / 2;
+  build_tree(a, mid, depth + 1, by_depth);
+  build_tree(mid, b, depth + 1, by_depth);
+  if ((int)by_depth.size() <= depth) by_depth.resize(depth + 1);
+  by_depth[depth].push_back(make_int4(a, mid, b, 0));
+}
+
+}  // namespace
+
+extern "C" lsq_status lsq_factor(lsq_ctx* ctx, const double* SA, int64_t m, int64_t d, double* R, double* W) {
+  if (!ctx || !SA || !R || !W) return LSQ_ERR_ARG;
+  if (d < 1 || d > LSQ_MAX_D || m < d || m > (1ll << 31) - 1) return LSQ_ERR_ARG;
+  const int di = (int)d, mi = (int)m;
+  const int nblk = (di + 31) / 32, dp = nblk * 32;
+
+  // Gram tiles (upper triangle of 64 x 64 tiles) and split-K
+  const int nt = (dp + TB - 1) / TB;
+  std::vector<int2> tiles;
+  for (int a = 0; a < nt; ++a)
+    for (int b = a; b < nt; ++b) tiles.push_back(make_int2(a, b));
+  int splits = std::max(1, (2 * ctx->sm_count + (int)tiles.size() - 1) / (int)tiles.size());
+  splits = std::min(splits, std::max(1, mi / 64));
+  splits = std::min(splits, std::max(1, (int)(((int64_t)128 << 20) / ((int64_t)dp * dp * 8))));
+  const int rows_per_split = ((mi + splits - 1) / splits + TK - 1) / TK * TK;
+  splits = (mi + rows_per_split - 1) / rows_per_split;
+
+  // inverse tree levels, deepest first
+  std::vector<std::vector<int4>> by_depth;
+  build_tree(0, nblk, 0, by_depth);
+  std::vector<int4> nodes;
+  std::vector<int> level_start;
+  for (int dep = (int)by_depth.size() - 1; dep >= 0; --dep) {
+    level_start.push_back((int)nodes.size());
+    for (auto& t : by_depth[dep]) nodes.push_back(t);
+  }
+  level_start.push_back((int)nodes.size());
+  const int nlevels = (int)level_start.size() - 1;
+
+  const size_t mat = (size_t)dp * dp;
+  size_t need = lsq_align256((size_t)splits * mat * 8) + 4 * lsq_align256(mat * 8) + lsq_align256(tiles.size() * 8) +
+                lsq_align256(std::max<size_t>(1, nodes.size()) * 16) + lsq_align256(level_start.size() * 4) +
+                lsq_align256(64);
+  lsq_status st = lsq_ensure_scratch(ctx, need);
+  if (st != LSQ_OK) return st;
+  Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};
+  double* part = cv.take<double>((size_t)splits * mat);
+  double* G = cv.take<double>(mat);
+  double* Rf = cv.take<double>(mat);
+  double* Wf = cv.take<double>(mat);
+  double* Tb = cv.take<double>(mat);
+  int2* d_tiles = cv.take<int2>(tiles.size());
+  int4* d_nodes = cv.take<int4>(std::max<size_t>(1, nodes.size()));
+  int* d_levels = cv.take<int>(level_start.size());
+  unsigned* bar = cv.take<unsigned>(16);
+  int* err = reinterpret_cast<int*>(bar + 8);
+  cudaStream_t s = ctx->stream;
+
+  LSQ_CUDA_TRY(cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  if (!nodes.empty())
+    LSQ_CUDA_TRY(cudaMemcpyAsync(d_nodes, nodes.data(), nodes.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  LSQ_CUDA_TRY(cudaMemcpyAsync(d_levels, level_start.data(), level_start.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  LSQ_CUDA_TRY(cudaMemsetAsync(bar, 0, 64, s));
+  LSQ_CUDA_TRY(cudaMemsetAsync(Rf, 0, mat * 8, s));
+  LSQ_CUDA_TRY(cudaMemsetAsync(Wf, 0, mat * 8, s));
+
+  gram_kernel<<<dim3((unsigned)tiles.size(), (unsigned)splits), 256, 0, s>>>(SA, mi, di, dp, rows_per_split, d_tiles,
+                                                                             part);
+  LSQ_LAUNCH_CHECK();
+  gram_reduce_kernel<<<std::min(4 * ctx->sm_count, (int)((mat + 255) / 256)), 256, 0, s>>>(part, splits, di, dp, G);
+  LSQ_LAUNCH_CHECK();
+
+  int per_sm = 0;
+  LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_inv_kernel, 256, 0));
+  if (per_sm < 1) return LSQ_ERR_CUDA;
+  int grid = std::min(per_sm, 2) * ctx->sm_count;
+  const int max_tasks = std::max(4 * nblk * nblk, 8);
+  grid = std::max(1, std::min(grid, max_tasks));
+  void* args[] = {&G, &Rf, &Wf, &Tb, (void*)&nblk, &d_nodes, &d_levels, (void*)&nlevels, &bar, &err};
+  int nblk_v = nblk, nlev_v = nlevels;
+  args[4] = &nblk_v;
+  args[7] = &nlev_v;
+  LSQ_CUDA_TRY(cudaLaunchCooperativeKernel((void*)chol_inv_kernel, dim3(grid), dim3(256), args, 0, s));
+  lsq_count_launch();
+  copy_out_kernel<<<std::min(4 * ctx->sm_count, (int)((d * d + 255) / 256)), 256, 0, s>>>(Rf, Wf, di, dp, R, W);
+  LSQ_LAUNCH_CHECK();
+  LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+  const int code = *ctx->host_status;
+  if (code == LSQ_ERR_RANK) return LSQ_ERR_RANK;
+  if (code != 0) return (lsq_status)code;
+  return LSQ_OK;
+}

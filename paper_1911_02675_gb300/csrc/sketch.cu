@@ -1,0 +1,615 @@
+// sketch.cu -- SA = S A for the three embeddings of Section 2 (Gaussian, SRHT, SJLT).
+//
+// Every kernel streams A once (Gaussian: once per 64-row slab of S) and generates its
+// randomness on the fly from Philox4x32-10; S is never stored.  Partial sums go to a
+// per-split scratch slab and a fixed-order reduction writes SA, so results repeat run
+// to run (SJLT: up to the order of its shared-memory additions).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T load_as(const void* base, int64_t idx, int dtype) {
+  if (dtype == LSQ_F64) return (T)__ldg(reinterpret_cast<const double*>(base) + idx);
+  return (T)__ldg(reinterpret_cast<const float*>(base) + idx);
+}
+
+// 53 random bits -> (k + 1/2) 2^-53 in the open unit interval
+__device__ __forceinline__ double unit_open53(uint32_t hi, uint32_t lo) {
+  const unsigned long long k = ((((unsigned long long)hi) << 32) | lo) >> 11;
+  return ((double)k + 0.5) * 0x1p-53;
+}
+
+// Box-Muller pair (cosine branch, sine branch) in the arithmetic type T
+template <typename T>
+__device__ __forceinline__ void box_muller(uint4 w, T& z_cos, T& z_sin);
+
+template <>
+__device__ __forceinline__ void box_muller<double>(uint4 w, double& zc, double& zs) {
+  const double u1 = unit_open53(w.x, w.y);
+  const double u2 = unit_open53(w.z, w.w);
+  const double rad = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  zc = rad * c;
+  zs = rad * s;
+}
+
+template <>
+__device__ __forceinline__ void box_muller<float>(uint4 w, float& zc, float& zs) {
+  // the same 53-bit uniforms, evaluated in FP32 (u1 > 0 is kept by the +1/2 offset)
+  const float u1 = (float)unit_open53(w.x, w.y);
+  const float u2 = (float)unit_open53(w.z, w.w);
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  zc = rad * c;
+  zs = rad * s;
+}
+
+// out[j*d + c] = scale * sum_g part[g][j][c]   (fixed order in g)
+template <typename TP>
+__global__ void reduce_splits_kernel(const TP* __restrict__ part, int splits, int64_t md, double scale,
+                                     double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < md; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < splits; ++g) s += (double)part[(int64_t)g * md + e];
+    out[e] = scale * s;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Gaussian: SA = S A, S[j,i] = z(j,i)/sqrt(m).  Split-K GEMM over the rows of A; each
+// CTA owns a 64 x 64 tile of SA and a contiguous range of rows, regenerates its 64 x 16
+// tile of S per step (one Philox call per pair of sketch rows) and accumulates 4 x 4
+// outputs per thread.  Scaling by 1/sqrt(m) happens in the reduction.
+// ------------------------------------------------------------------------------------
+constexpr int GM = 64, GD = 64, GK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) gauss_sketch_kernel(const void* __restrict__ A, int dtype, int64_t n, int d,
+                                                          int64_t ld, int m, uint64_t seed, uint32_t t,
+                                                          int64_t rows_per_split, T* __restrict__ part) {
+  __shared__ T Ss[GK][GM];
+  __shared__ T As[GK][GD];
+  const int j0 = blockIdx.x * GM, c0 = blockIdx.y * GD;
+  const int64_t i_begin = (int64_t)blockIdx.z * rows_per_split;
+  const int64_t i_end = min(n, i_begin + rows_per_split);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+
+  for (int64_t i0 = i_begin; i0 < i_end; i0 += GK) {
+    for (int e = threadIdx.x; e < (GM / 2) * GK; e += 256) {
+      const int jp = e / GK, k = e % GK;
+      const int64_t i = i0 + k;
+      T zc = (T)0, zs = (T)0;
+      if (i < i_end) box_muller<T>(philox_at(seed, (uint32_t)i, (uint32_t)((j0 >> 1) + jp), t, TAG_GAUSS), zc, zs);
+      Ss[k][2 * jp] = zc;
+      Ss[k][2 * jp + 1] = zs;
+    }
+    for (int e = threadIdx.x; e < GK * GD; e += 256) {
+      const int k = e / GD, c = e % GD;
+      const int64_t i = i0 + k;
+      As[k][c] = (i < i_end && c0 + c < d) ? load_as<T>(A, i * ld + c0 + c, dtype) : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+      T s[4], a[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) s[r] = Ss[k][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[c] = As[k][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(s[r], a[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+  T* out = part + (int64_t)blockIdx.z * m * d;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int j = j0 + ty + 16 * r;
+    if (j >= m) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int col = c0 + tx + 16 * c;
+      if (col < d) out[(int64_t)j * d + col] = acc[r][c];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// SRHT: S = (1/sqrt m) P H E on N = 2^ceil(log2 n) zero-padded rows.
+//   (1) keys/signs: sample key and sign bit of every row i < N;
+//   (2) radix select: the m-th smallest (key, index) by four 16-bit digit rounds;
+//   (3) compaction: the selected rows in ascending index order;
+//   (4) two-level transform: N = N1 * N2, i = i1 * N2 + i2, and
+//       (H x)[k1 N2 + k2] = sum_{i1} (-1)^{popc(k1 & i1)} (H_{N2} x_{i1})[k2],
+//       so each CTA runs length-N2 transforms of row blocks in shared memory and adds
+//       the signed block outputs for the m sampled rows only.
+// ------------------------------------------------------------------------------------
+__global__ void srht_keys_kernel(int64_t N, uint64_t seed, uint32_t t, unsigned long long* __restrict__ keys,
+                                 uint32_t* __restrict__ signbits, unsigned* __restrict__ hist) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    bool neg = false;
+    if (i < N) {
+      const uint4 k = philox_at(seed, (uint32_t)i, (uint32_t)(i >> 32), t, TAG_SAMPLE);
+      const unsigned long long key = (((unsigned long long)k.x) << 32) | k.y;
+      keys[i] = key;
+      atomicAdd(&hist[key >> 48], 1u);
+      neg = (philox_at(seed, (uint32_t)i, (uint32_t)(i >> 32), t, TAG_SIGN).x & 1u) != 0u;
+    }
+    const unsigned word = __ballot_sync(0xffffffffu, neg);
+    if ((threadIdx.x & 31) == 0 && i < N) signbits[i >> 5] = word;
+  }
+}
+
+// state: [0] prefix (digits found so far), [1] need (rank still to reach, 1-based),
+//        [2] count of keys strictly below the current prefix bucket
+__global__ void radix_hist_kernel(const unsigned long long* __restrict__ keys, int64_t N, int shift,
+                                  const unsigned long long* __restrict__ state, unsigned* __restrict__ hist) {
+  const unsigned long long prefix = state[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long key = keys[i];
+    if ((key >> (shift + 16)) == prefix) atomicAdd(&hist[(key >> shift) & 0xFFFFu], 1u);
+  }
+}
+
+// one CTA of 1024 threads: finds the bucket holding rank `need`, clears the histogram
+__global__ void radix_pick_kernel(unsigned* __restrict__ hist, unsigned long long* __restrict__ state) {
+  __shared__ unsigned long long part[1024];
+  __shared__ int found;
+  const int tid = threadIdx.x;
+  unsigned long long local = 0;
+  for (int b = tid * 64; b < tid * 64 + 64; ++b) local += hist[b];
+  part[tid] = local;
+  if (tid == 0) found = 0;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long need = state[1], below = state[2], cum = 0;
+    for (int g = 0; g < 1024 && !found; ++g) {
+      if (cum + part[g] >= need) {
+        for (int b = g * 64; b < g * 64 + 64; ++b) {
+          if (cum + hist[b] >= need) {
+            state[0] = (state[0] << 16) | (unsigned long long)b;
+            state[1] = need - cum;
+            state[2] = below + cum;
+            found = 1;
+            break;
+          }
+          cum += hist[b];
+        }
+      } else {
+        cum += part[g];
+      }
+    }
+  }
+  __syncthreads();
+  for (int b = tid; b < 65536; b += 1024) hist[b] = 0u;
+}
+
+constexpr int SCAN_BLOCK = 1024;
+
+// per block of 1024 rows: counts of keys < K and == K (K = state[0] after 4 rounds)
+__global__ void select_count_kernel(const unsigned long long* __restrict__ keys, int64_t N,
+                                    const unsigned long long* __restrict__ state, unsigned* __restrict__ cnt_lt,
+                                    unsigned* __restrict__ cnt_eq) {
+  __shared__ unsigned s_lt, s_eq;
+  if (threadIdx.x == 0) { s_lt = 0; s_eq = 0; }
+  __syncthreads();
+  const unsigned long long K = state[0];
+  const int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+  if (i < N) {
+    const unsigned long long key = keys[i];
+    if (key < K) atomicAdd(&s_lt, 1u);
+    else if (key == K) atomicAdd(&s_eq, 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) { cnt_lt[blockIdx.x] = s_lt; cnt_eq[blockIdx.x] = s_eq; }
+}
+
+// exclusive prefix sums over the blocks (single CTA, sequential chunks)
+__global__ void select_scan_kernel(unsigned* __restrict__ cnt_lt, unsigned* __restrict__ cnt_eq, int nb) {
+  __shared__ unsigned long long carry_lt, carry_eq;
+  __shared__ unsigned buf_lt[1024], buf_eq[1024];
+  if (threadIdx.x == 0) { carry_lt = 0; carry_eq = 0; }
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    const int b = base + threadIdx.x;
+    buf_lt[threadIdx.x] = b < nb ? cnt_lt[b] : 0u;
+    buf_eq[threadIdx.x] = b < nb ? cnt_eq[b] : 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long a = carry_lt, e = carry_eq;
+      for (int k = 0; k < 1024; ++k) {
+        const unsigned vl = buf_lt[k], ve = buf_eq[k];
+        buf_lt[k] = (unsigned)a;
+        buf_eq[k] = (unsigned)e;
+        a += vl;
+        e += ve;
+      }
+      carry_lt = a;
+      carry_eq = e;
+    }
+    __syncthreads();
+    if (b < nb) { cnt_lt[b] = buf_lt[threadIdx.x]; cnt_eq[b] = buf_eq[threadIdx.x]; }
+    __syncthreads();
+  }
+}
+
+__global__ void select_write_kernel(const unsigned long long* __restrict__ keys, int64_t N,
+                                    const unsigned long long* __restrict__ state, const unsigned* __restrict__ pre_lt,
+                                    const unsigned* __restrict__ pre_eq, int64_t* __restrict__ rows, int m) {
+  __shared__ unsigned warp_sel[32], warp_eq[32];
+  const unsigned long long K = state[0];
+  const unsigned need_eq = (unsigned)state[1];
+  const int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long key = 0;
+  if (i < N) key = keys[i];
+  const bool lt = (i < N) && key < K;
+  const bool eq = (i < N) && key == K;
+  // rank of this row among the block's equal keys
+  const unsigned eq_mask = __ballot_sync(0xffffffffu, eq);
+  if (lane == 0) warp_eq[w] = __popc(eq_mask);
+  __syncthreads();
+  unsigned eq_before = pre_eq[blockIdx.x];
+  for (int k = 0; k < w; ++k) eq_before += warp_eq[k];
+  eq_before += __popc(eq_mask & ((1u << lane) - 1u));
+  const bool sel = lt || (eq && eq_before < need_eq);
+  const unsigned sel_mask = __ballot_sync(0xffffffffu, sel);
+  if (lane == 0) warp_sel[w] = __popc(sel_mask);
+  __syncthreads();
+  // rows selected before this block: keys < K plus the equal keys admitted so far
+  unsigned long long pos = (unsigned long long)pre_lt[blockIdx.x] + min(pre_eq[blockIdx.x], need_eq);
+  for (int k = 0; k < w; ++k) pos += warp_sel[k];
+  pos += __popc(sel_mask & ((1u << lane) - 1u));
+  if (sel && pos < (unsigned long long)m) rows[pos] = i;
+}
+
+// two-level transform; TC = arithmetic type, DC columns per CTA, N2 = 2^logN2 rows per block
+template <typename TC, int DC>
+__global__ void __launch_bounds__(256) srht_transform_kernel(const void* __restrict__ A, int dtype, int64_t n, int d,
+                                                             int64_t ld, int logN2, int64_t N1, int64_t blocks_per_group,
+                                                             const uint32_t* __restrict__ signbits,
+                                                             const int64_t* __restrict__ rows, int m,
+                                                             TC* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N2 = 1 << logN2;
+  TC* Z = reinterpret_cast<TC*>(smem_raw);  // [N2][DC]
+  TC* Y = Z + (size_t)N2 * DC;              // [m][DC]
+  const int c0 = blockIdx.x * DC;
+  const int64_t b_begin = (int64_t)blockIdx.y * blocks_per_group;
+  const int64_t b_end = min(N1, b_begin + blocks_per_group);
+  for (int e = threadIdx.x; e < m * DC; e += blockDim.x) Y[e] = (TC)0;
+
+  for (int64_t i1 = b_begin; i1 < b_end; ++i1) {
+    __syncthreads();
+    const int64_t row0 = i1 << logN2;
+    for (int e = threadIdx.x; e < N2 * DC; e += blockDim.x) {
+      const int k = e / DC, c = e % DC;
+      const int64_t i = row0 + k;
+      TC v = (TC)0;
+      if (i < n && c0 + c < d) {
+        v = load_as<TC>(A, i * ld + c0 + c, dtype);
+        if ((signbits[i >> 5] >> (i & 31)) & 1u) v = -v;
+      }
+      Z[e] = v;
+    }
+    __syncthreads();
+    // unnormalised Sylvester butterflies, natural order
+    for (int h = 1; h < N2; h <<= 1) {
+      for (int e = threadIdx.x; e < (N2 >> 1) * DC; e += blockDim.x) {
+        const int p = e / DC, c = e % DC;
+        const int k = ((p / h) * 2 * h) + (p % h);
+        const TC u = Z[k * DC + c], v = Z[(k + h) * DC + c];
+        Z[k * DC + c] = u + v;
+        Z[(k + h) * DC + c] = u - v;
+      }
+      __syncthreads();
+    }
+    // second level, sampled rows only
+    for (int s = threadIdx.x; s < m; s += blockDim.x) {
+      const int64_t k = rows[s];
+      const int64_t k1 = k >> logN2;
+      const int k2 = (int)(k & (N2 - 1));
+      const bool neg = (__popcll((unsigned long long)(k1 & i1)) & 1) != 0;
+#pragma unroll
+      for (int c = 0; c < DC; ++c) {
+        const TC z = Z[k2 * DC + c];
+        Y[s * DC + c] += neg ? -z : z;
+      }
+    }
+  }
+  __syncthreads();
+  TC* out = part + (int64_t)blockIdx.y * m * d;
+  for (int e = threadIdx.x; e < m * DC; e += blockDim.x) {
+    const int s = e / DC, c = e % DC;
+    if (c0 + c < d) out[(int64_t)s * d + c0 + c] = Y[e];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// SJLT: s distinct rows per column of S by Lemire's method on successive Philox words,
+// then a shared-memory scatter of each data row into its s target rows.
+// ------------------------------------------------------------------------------------
+__global__ void sjlt_hash_kernel(int64_t n, int m, int s, uint64_t seed, uint32_t t, int32_t* __restrict__ h,
+                                 uint32_t* __restrict__ signs) {
+  const uint32_t range = (uint32_t)m;
+  const uint32_t threshold = (uint32_t)(0u - range) % range;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t picked[32];
+    int got = 0;
+    for (uint32_t draw = 0; got < s && draw < 4096u; ++draw) {
+      const uint4 w = philox_at(seed, (uint32_t)i, draw, t, TAG_SJLT);
+      const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (got >= s) break;
+        const unsigned long long prod = (unsigned long long)words[k] * range;
+        const uint32_t low = (uint32_t)prod;
+        if (low < range && low < threshold) continue;
+        const int32_t v = (int32_t)(prod >> 32);
+        bool dup = false;
+        for (int q = 0; q < got; ++q) dup |= (picked[q] == v);
+        if (!dup) picked[got++] = v;
+      }
+    }
+    for (int k = got; k < s; ++k) picked[k] = 0;  // unreachable for s <= m; keeps every index in range
+    for (int k = 0; k < s; ++k) h[i * s + k] = picked[k];
+    signs[i] = philox_at(seed, (uint32_t)i, 0u, t, TAG_SJLT_SIGN).x;
+  }
+}
+
+template <typename TC, int DC>
+__global__ void __launch_bounds__(256) sjlt_scatter_kernel(const void* __restrict__ A, int dtype, int64_t n, int d,
+                                                           int64_t ld, int m, int s, const int32_t* __restrict__ h,
+                                                           const uint32_t* __restrict__ signs, int64_t rows_per_group,
+                                                           TC* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* Y = reinterpret_cast<TC*>(smem_raw);  // [m][DC]
+  const int c0 = blockIdx.x * DC;
+  const int64_t i_begin = (int64_t)blockIdx.y * rows_per_group;
+  const int64_t i_end = min(n, i_begin + rows_per_group);
+  for (int e = threadIdx.x; e < m * DC; e += blockDim.x) Y[e] = (TC)0;
+  __syncthreads();
+  constexpr int RPI = 256 / DC;  // rows per step
+  const int rl = threadIdx.x / DC, c = threadIdx.x % DC;
+  const bool col_ok = (c0 + c) < d;
+  for (int64_t i = i_begin + rl; i < i_end; i += RPI) {
+    const TC a = col_ok ? load_as<TC>(A, i * ld + c0 + c, dtype) : (TC)0;
+    const uint32_t sw = signs[i];
+    for (int k = 0; k < s; ++k) {
+      const int target = h[i * s + k];
+      atomicAdd(&Y[target * DC + c], ((sw >> k) & 1u) ? -a : a);
+    }
+  }
+  __syncthreads();
+  TC* out = part + (int64_t)blockIdx.y * m * d;
+  for (int e = threadIdx.x; e < m * DC; e += blockDim.x) {
+    const int row = e / DC, cc = e % DC;
+    if (c0 + cc < d) out[(int64_t)row * d + c0 + cc] = Y[e];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------
+static int grid_for(int64_t work, int threads, int cap) {
+  int64_t g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+static lsq_status validate_matrix(const lsq_matrix* A) {
+  if (!A || !A->data) return LSQ_ERR_ARG;
+  if (A->n < 1 || A->n >= (1ll << 31) || A->d < 1 || A->d > LSQ_MAX_D || A->ld < A->d) return LSQ_ERR_ARG;
+  if (A->dtype != LSQ_F64 && A->dtype != LSQ_F32) return LSQ_ERR_ARG;
+  const size_t es = A->dtype == LSQ_F64 ? 8 : 4;
+  if (((uintptr_t)A->data) % es) return LSQ_ERR_ARG;
+  return LSQ_OK;
+}
+
+template <typename TC>
+static lsq_status gauss_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA) {
+  const int d = (int)A->d;
+  const int gx = lsq_ceil_div(m, GM), gy = lsq_ceil_div(d, GD);
+  const int64_t ksteps = (A->n + GK - 1) / GK;
+  int64_t splits = ((int64_t)2 * ctx->sm_count + gx * gy - 1) / (gx * gy);
+  const int64_t cap = std::max<int64_t>(1, ((int64_t)256 << 20) / ((int64_t)m * d * (int64_t)sizeof(TC)));
+  splits = std::max<int64_t>(1, std::min(std::min(splits, ksteps), cap));
+  const int64_t rows_per_split = ((ksteps + splits - 1) / splits) * GK;
+  splits = (A->n + rows_per_split - 1) / rows_per_split;
+  lsq_status st = lsq_ensure_scratch(ctx, lsq_align256((size_t)splits * m * d * sizeof(TC)));
+  if (st != LSQ_OK) return st;
+  TC* part = reinterpret_cast<TC*>(ctx->scratch);
+  dim3 grid(gx, gy, (unsigned)splits);
+  gauss_sketch_kernel<TC><<<grid, 256, 0, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, seed, t,
+                                                          rows_per_split, part);
+  LSQ_LAUNCH_CHECK();
+  const int64_t md = (int64_t)m * d;
+  reduce_splits_kernel<TC><<<grid_for(md, 256, 4 * ctx->sm_count), 256, 0, ctx->stream>>>(
+      part, (int)splits, md, 1.0 / sqrt((double)m), SA);
+  LSQ_LAUNCH_CHECK();
+  return LSQ_OK;
+}
+
+template <typename TC, int DC>
+static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN2, int64_t N1,
+                              const uint32_t* signbits, const int64_t* rows, TC* part, int groups,
+                              int64_t blocks_per_group) {
+  const int d = (int)A->d;
+  const size_t smem = (size_t)((1 << logN2) + m) * DC * sizeof(TC);
+  auto kern = srht_transform_kernel<TC, DC>;
+  LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(lsq_ceil_div(d, DC), groups);
+  kern<<<grid, 256, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, logN2, N1, blocks_per_group, signbits,
+                                          rows, m, part);
+  LSQ_LAUNCH_CHECK();
+  return LSQ_OK;
+}
+
+template <typename TC>
+static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA) {
+  const int d = (int)A->d;
+  int64_t N = 1;
+  int logN = 0;
+  while (N < A->n) { N <<= 1; ++logN; }
+  if (m > N) return LSQ_ERR_ARG;
+  // shared memory budget: (N2 + m) * DC * sizeof(TC) <= 200 KB, DC as large as possible
+  const size_t budget = 200 * 1024;
+  int DC = (int)(sizeof(TC) == 8 ? 4 : 8);
+  int logN2 = std::min(logN, 11);
+  auto fits = [&](int dc, int l2) { return (size_t)((1ll << l2) + m) * dc * sizeof(TC) <= budget; };
+  while (DC > 1 && !fits(DC, logN2)) DC >>= 1;
+  while (logN2 > 0 && !fits(DC, logN2)) --logN2;
+  if (!fits(DC, logN2)) return LSQ_ERR_ARG;
+  const int64_t N1 = N >> logN2;
+  const int tiles = lsq_ceil_div(d, DC);
+  int64_t groups = std::max<int64_t>(1, (ctx->sm_count + tiles - 1) / tiles);
+  groups = std::min(groups, N1);
+  const int64_t cap = std::max<int64_t>(1, ((int64_t)256 << 20) / ((int64_t)m * d * (int64_t)sizeof(TC)));
+  groups = std::min(groups, cap);
+  const int64_t blocks_per_group = (N1 + groups - 1) / groups;
+  groups = (N1 + blocks_per_group - 1) / blocks_per_group;
+
+  const int64_t nscan = (N + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  size_t need = lsq_align256((size_t)N * 8) + lsq_align256((size_t)((N + 31) / 32) * 4) + lsq_align256(65536 * 4) +
+                lsq_align256(4 * 8) + 2 * lsq_align256((size_t)nscan * 4) + lsq_align256((size_t)m * 8) +
+                lsq_align256((size_t)groups * m * d * sizeof(TC));
+  lsq_status st = lsq_ensure_scratch(ctx, need);
+  if (st != LSQ_OK) return st;
+  Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};
+  unsigned long long* keys = cv.take<unsigned long long>(N);
+  uint32_t* signbits = cv.take<uint32_t>((N + 31) / 32);
+  unsigned* hist = cv.take<unsigned>(65536);
+  unsigned long long* state = cv.take<unsigned long long>(4);
+  unsigned* cnt_lt = cv.take<unsigned>(nscan);
+  unsigned* cnt_eq = cv.take<unsigned>(nscan);
+  int64_t* rows = cv.take<int64_t>(m);
+  TC* part = cv.take<TC>((size_t)groups * m * d);
+
+  unsigned long long init_state[4] = {0ull, (unsigned long long)m, 0ull, 0ull};
+  LSQ_CUDA_TRY(cudaMemsetAsync(hist, 0, 65536 * 4, ctx->stream));
+  LSQ_CUDA_TRY(cudaMemcpyAsync(state, init_state, sizeof(init_state), cudaMemcpyHostToDevice, ctx->stream));
+  srht_keys_kernel<<<grid_for(N, 256, 8 * ctx->sm_count), 256, 0, ctx->stream>>>(N, seed, t, keys, signbits, hist);
+  LSQ_LAUNCH_CHECK();
+  radix_pick_kernel<<<1, 1024, 0, ctx->stream>>>(hist, state);
+  LSQ_LAUNCH_CHECK();
+  for (int shift = 32; shift >= 0; shift -= 16) {
+    radix_hist_kernel<<<grid_for(N, 256, 8 * ctx->sm_count), 256, 0, ctx->stream>>>(keys, N, shift, state, hist);
+    LSQ_LAUNCH_CHECK();
+    radix_pick_kernel<<<1, 1024, 0, ctx->stream>>>(hist, state);
+    LSQ_LAUNCH_CHECK();
+  }
+  select_count_kernel<<<(unsigned)nscan, SCAN_BLOCK, 0, ctx->stream>>>(keys, N, state, cnt_lt, cnt_eq);
+  LSQ_LAUNCH_CHECK();
+  select_scan_kernel<<<1, 1024, 0, ctx->stream>>>(cnt_lt, cnt_eq, (int)nscan);
+  LSQ_LAUNCH_CHECK();
+  select_write_kernel<<<(unsigned)nscan, SCAN_BLOCK, 0, ctx->stream>>>(keys, N, state, cnt_lt, cnt_eq, rows, m);
+  LSQ_LAUNCH_CHECK();
+
+  switch (DC) {
+    case 8: st = srht_launch<TC, 8>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group); break;
+    case 4: st = srht_launch<TC, 4>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group); break;
+    case 2: st = srht_launch<TC, 2>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group); break;
+    default: st = srht_launch<TC, 1>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group); break;
+  }
+  if (st != LSQ_OK) return st;
+  const int64_t md = (int64_t)m * d;
+  reduce_splits_kernel<TC><<<grid_for(md, 256, 4 * ctx->sm_count), 256, 0, ctx->stream>>>(
+      part, (int)groups, md, 1.0 / sqrt((double)m), SA);
+  LSQ_LAUNCH_CHECK();
+  return LSQ_OK;
+}
+
+template <typename TC, int DC>
+static lsq_status sjlt_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, const int32_t* h,
+                              const uint32_t* signs, TC* part, int groups, int64_t rows_per_group) {
+  const int d = (int)A->d;
+  const size_t smem = (size_t)m * DC * sizeof(TC);
+  auto kern = sjlt_scatter_kernel<TC, DC>;
+  LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(lsq_ceil_div(d, DC), groups);
+  kern<<<grid, 256, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, s, h, signs, rows_per_group, part);
+  LSQ_LAUNCH_CHECK();
+  return LSQ_OK;
+}
+
+template <typename TC>
+static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint64_t seed, uint32_t t, double* SA) {
+  const int d = (int)A->d;
+  const int64_t n = A->n;
+  const size_t budget = 200 * 1024;
+  int DC = (int)(sizeof(TC) == 8 ? 4 : 8);
+  while (DC > 1 && (size_t)m * DC * sizeof(TC) > budget) DC >>= 1;
+  if ((size_t)m * DC * sizeof(TC) > budget) return LSQ_ERR_ARG;
+  const int tiles = lsq_ceil_div(d, DC);
+  int64_t groups = std::max<int64_t>(1, (2 * ctx->sm_count + tiles - 1) / tiles);
+  groups = std::min<int64_t>(groups, (n + 255) / 256);
+  const int64_t cap = std::max<int64_t>(1, ((int64_t)256 << 20) / ((int64_t)m * d * (int64_t)sizeof(TC)));
+  groups = std::max<int64_t>(1, std::min(groups, cap));
+  const int64_t rows_per_group = (n + groups - 1) / groups;
+  groups = (n + rows_per_group - 1) / rows_per_group;
+  size_t need = lsq_align256((size_t)n * s * 4) + lsq_align256((size_t)n * 4) +
+                lsq_align256((size_t)groups * m * d * sizeof(TC));
+  lsq_status st = lsq_ensure_scratch(ctx, need);
+  if (st != LSQ_OK) return st;
+  Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};
+  int32_t* h = cv.take<int32_t>((size_t)n * s);
+  uint32_t* signs = cv.take<uint32_t>(n);
+  TC* part = cv.take<TC>((size_t)groups * m * d);
+  sjlt_hash_kernel<<<grid_for(n, 256, 16 * ctx->sm_count), 256, 0, ctx->stream>>>(n, m, s, seed, t, h, signs);
+  LSQ_LAUNCH_CHECK();
+  switch (DC) {
+    case 8: st = sjlt_launch<TC, 8>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group); break;
+    case 4: st = sjlt_launch<TC, 4>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group); break;
+    case 2: st = sjlt_launch<TC, 2>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group); break;
+    default: st = sjlt_launch<TC, 1>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group); break;
+  }
+  if (st != LSQ_OK) return st;
+  const int64_t md = (int64_t)m * d;
+  reduce_splits_kernel<TC><<<grid_for(md, 256, 4 * ctx->sm_count), 256, 0, ctx->stream>>>(
+      part, (int)groups, md, 1.0 / sqrt((double)s), SA);
+  LSQ_LAUNCH_CHECK();
+  return LSQ_OK;
+}
+
+}  // namespace
+
+extern "C" lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, int64_t m, uint64_t seed,
+                                 const lsq_sketch_opts* opts, double* SA) {
+  if (!ctx || !SA) return LSQ_ERR_ARG;
+  lsq_status st = validate_matrix(A);
+  if (st != LSQ_OK) return st;
+  if (m < 1 || m > 65536) return LSQ_ERR_ARG;
+  const uint32_t t = opts ? opts->t : 0u;
+  const int s = (opts && opts->s > 0) ? opts->s : 8;
+  const int prec = opts ? opts->precision : LSQ_SKETCH_F64;
+  if (prec != LSQ_SKETCH_F64 && prec != LSQ_SKETCH_F32) return LSQ_ERR_ARG;
+  const bool f64 = prec == LSQ_SKETCH_F64;
+  switch (type) {
+    case LSQ_SKETCH_GAUSS:
+      return f64 ? gauss_run<double>(ctx, A, (int)m, seed, t, SA) : gauss_run<float>(ctx, A, (int)m, seed, t, SA);
+    case LSQ_SKETCH_SRHT:
+      return f64 ? srht_run<double>(ctx, A, (int)m, seed, t, SA) : srht_run<float>(ctx, A, (int)m, seed, t, SA);
+    case LSQ_SKETCH_SJLT:
+      if (s < 1 || s > 32 || s > m) return LSQ_ERR_ARG;
+      return f64 ? sjlt_run<double>(ctx, A, (int)m, s, seed, t, SA) : sjlt_run<float>(ctx, A, (int)m, s, seed, t, SA);
+    default:
+      return LSQ_ERR_ARG;
+  }
+}

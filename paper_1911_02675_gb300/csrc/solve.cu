@@ -1,0 +1,681 @@
+// solve.cu -- the iteration loop: PCG (Section 1, eq. (PCG)), IHS and Polyak-IHS
+// (Section 1, eqs. eqnihs / eqnpolyakihs) with a fixed or refreshed embedding.
+//
+// One persistent cooperative kernel runs the whole loop.  Each iteration is
+//   A pass   : v = A^T (A p) and q = ||A p||^2 in one read of every row of A
+//              (CTA-private partials, no atomics)                         -- barrier
+//   columns  : fixed-order reduction of the partials, x and r updates       -- barrier
+//   W^T r    : z = W^T r, one warp per output                                -- barrier
+//   W z      : r^ = W z and r^T r^ partials                                  -- barrier
+//   tail     : every CTA forms rho, beta, p (kept whole in shared memory) and
+//              the stopping decision from the same numbers in the same order.
+// H_S^{-1} r = R^{-1} R^{-T} r is applied as W (W^T r) with W = R^{-1}, two parallel
+// triangular products instead of two sequential triangular solves.
+#include <algorithm>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace {
+
+struct SolveArgs {
+  const void* A;
+  int dtype;
+  int64_t n;
+  int d;
+  int dp;  // d rounded up to 32 * EPL
+  int64_t ld;
+  int64_t rows_per_cta;
+  const double* b;
+  const double* W;   // d x d upper, stride d
+  const double* WT;  // W^T (lower), stride d
+  double* x;         // user x (in: x0, out)
+  double* xprev;     // IHS/Polyak: x_{t-1} carried between single-step launches
+  int method;
+  double mu, beta;
+  double tol2;       // tol^2 / (1 + sqrt(rho))^2
+  double lam1;       // (1 + sqrt(rho))^2
+  int maxit;
+  int x0_zero;       // PCG: skip the initial pass when x0 = 0
+  int first_step;    // IHS single-step launches: 1 when x_{-1} = x_0
+  double* part;      // [(dp + 1)][P] pass partials
+  double* red;       // [4][P] scalar partials
+  double* r;         // dp each
+  double* z;
+  double* rh;
+  double* g;
+  unsigned* bar;
+  int* err;
+  double* out;       // [0] iters, [1] status, [2] passes, [3] est_err
+};
+
+template <typename TA>
+__device__ __forceinline__ double ld_elem(const TA* p) {
+  return (double)__ldg(p);
+}
+
+// ------------------------------------------------------------------------------------
+// Fused pass over the rows [r0, r1): per-warp accumulators of v = A^T (A p) in
+// registers (lane owns columns lane + 32 k), q = sum (a_i . p)^2; then a fixed-order
+// CTA reduction into part[c * P + cta].  The next row is loaded before the current
+// one is used so that each warp keeps two rows in flight.
+// ------------------------------------------------------------------------------------
+template <typename TA, int EPL>
+__device__ void fused_pass(const TA* __restrict__ A, int64_t ld, int d, int dp, int64_t r0, int64_t r1,
+                           const double* vec_s, double* wred, double* qred, double* part, int P, int cta) {
+  constexpr bool PV_REG = EPL <= 8;   // keep p in registers while they are plentiful
+  constexpr bool PREFETCH = EPL <= 16;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double pv[PV_REG ? EPL : 1], acc[EPL], cur[EPL], nxt[PREFETCH ? EPL : 1];
+  bool ok[EPL];
+#pragma unroll
+  for (int k = 0; k < EPL; ++k) {
+    const int c = lane + 32 * k;
+    ok[k] = c < d;
+    if (PV_REG) pv[k] = ok[k] ? vec_s[c] : 0.0;
+    acc[k] = 0.0;
+  }
+  double q = 0.0;
+  int64_t i = r0 + warp;
+  if (PREFETCH && i < r1) {
+    const TA* a = A + i * ld;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? ld_elem(a + lane + 32 * k) : 0.0;
+  }
+  for (; i < r1; i += LSQ_WARPS) {
+    if (PREFETCH) {
+      const int64_t inext = i + LSQ_WARPS;
+      if (inext < r1) {
+        const TA* a = A + inext * ld;
+#pragma unroll
+        for (int k = 0; k < (PREFETCH ? EPL : 1); ++k) nxt[k] = ok[k] ? ld_elem(a + lane + 32 * k) : 0.0;
+      }
+    } else {
+      const TA* a = A + i * ld;
+#pragma unroll
+      for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? ld_elem(a + lane + 32 * k) : 0.0;
+    }
+    double w = 0.0;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) w = fma(cur[k], PV_REG ? pv[PV_REG ? k : 0] : vec_s[lane + 32 * k], w);
+    w = warp_sum(w);
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) acc[k] = fma(w, cur[k], acc[k]);
+    q = fma(w, w, q);
+    if (PREFETCH) {
+#pragma unroll
+      for (int k = 0; k < EPL; ++k) cur[k] = nxt[PREFETCH ? k : 0];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < EPL; ++k) {
+    const int c = lane + 32 * k;
+    if (c < dp) wred[warp * dp + c] = acc[k];
+  }
+  if (lane == 0) qred[warp] = q;
+  __syncthreads();
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < LSQ_WARPS; ++w) s += wred[w * dp + c];
+    part[(int64_t)c * P + cta] = s;
+  }
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < LSQ_WARPS; ++w) s += qred[w];
+    part[(int64_t)dp * P + cta] = s;
+  }
+  __syncthreads();
+}
+
+// sum_{j < P} src[j] by one warp, fixed order
+__device__ __forceinline__ double warp_sum_strip(const double* src, int P) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int j = lane; j < P; j += 32) s += src[j];
+  return warp_sum(s);
+}
+
+// out[i] = sum_k M[i*d + k] vec_s[k] for k in [k_lo(i), k_hi(i)), one warp per output
+__device__ __forceinline__ double warp_row_dot(const double* __restrict__ row, const double* vec_s, int k_lo, int k_hi) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int k = k_lo + lane; k < k_hi; k += 32) s = fma(__ldg(row + k), vec_s[k], s);
+  return warp_sum(s);
+}
+
+struct SolveSmem {
+  double* vec;   // dp: p (PCG) or x (IHS)
+  double* vec2;  // dp: x_{t-1} (IHS) / r or z staging
+  double* wred;  // LSQ_WARPS * dp
+  double* qred;  // LSQ_WARPS
+  double* scal;  // 8
+};
+
+template <typename TA, int EPL>
+__global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
+  extern __shared__ __align__(16) double smem[];
+  const int dp = a.dp, d = a.d;
+  SolveSmem S;
+  S.vec = smem;
+  S.vec2 = S.vec + dp;
+  S.wred = S.vec2 + dp;
+  S.qred = S.wred + LSQ_WARPS * dp;
+  S.scal = S.qred + LSQ_WARPS;
+  double* stage = S.scal + 8;  // dp: r or z staging for the triangular products
+
+  const int P = gridDim.x, cta = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = cta * LSQ_WARPS + warp, nw = P * LSQ_WARPS;
+  const int64_t r0 = (int64_t)cta * a.rows_per_cta;
+  const int64_t r1 = min(a.n, r0 + a.rows_per_cta);
+  const TA* A = reinterpret_cast<const TA*>(a.A);
+  double* red_rho = a.red;
+  double* red_bx = a.red + P;
+  int passes = 0;
+  const bool pcg = a.method == LSQ_PCG;
+
+  // ---- H_S^{-1} applied to the vector `src` (global, dp), result into `dst` (global);
+  //      also returns (through red_rho) the CTA partial of src^T dst.
+  auto precond = [&](const double* src, double* dst) -> int {
+    for (int c = threadIdx.x; c < dp; c += blockDim.x) stage[c] = c < d ? src[c] : 0.0;
+    __syncthreads();
+    for (int i = gw; i < d; i += nw) {
+      const double zi = warp_row_dot(a.WT + (int64_t)i * d, stage, 0, i + 1);
+      if (lane == 0) a.z[i] = zi;
+    }
+    if (grid_barrier(a.bar, P, a.err)) return 1;
+    for (int c = threadIdx.x; c < dp; c += blockDim.x) stage[c] = c < d ? a.z[c] : 0.0;
+    __syncthreads();
+    double part_rho = 0.0;
+    for (int j = gw; j < d; j += nw) {
+      const double v = warp_row_dot(a.W + (int64_t)j * d, stage, j, d);
+      if (lane == 0) {
+        dst[j] = v;
+        part_rho += v * src[j];
+      }
+    }
+    if (lane == 0) S.qred[warp] = part_rho;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < LSQ_WARPS; ++w) s += S.qred[w];
+      red_rho[cta] = s;
+    }
+    return grid_barrier(a.bar, P, a.err);
+  };
+
+  // every CTA: the same fixed-order sums of the per-CTA scalars
+  auto total = [&](const double* red) -> double {
+    if (warp == 0) {
+      const double s = warp_sum_strip(red, P);
+      if (lane == 0) S.scal[7] = s;
+    }
+    __syncthreads();
+    const double s = S.scal[7];
+    __syncthreads();
+    return s;
+  };
+
+  // partial of <b, x> over the columns this CTA owns, x read from `xsrc`
+  auto bx_partial = [&](const double* xsrc) {
+    double s = 0.0;
+    for (int c = gw; c < d; c += nw)
+      if (lane == 0) s += a.b[c] * xsrc[c];
+    if (lane == 0) S.qred[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < LSQ_WARPS; ++w) t += S.qred[w];
+      red_bx[cta] = t;
+    }
+    __syncthreads();
+  };
+
+  int status = LSQ_ERR_MAXIT;
+  int it = 0;
+  double est = 0.0;
+
+  if (pcg) {
+    // r0 = b - H x0
+    if (!a.x0_zero) {
+      for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec[c] = c < d ? a.x[c] : 0.0;
+      __syncthreads();
+      fused_pass<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+      ++passes;
+      if (grid_barrier(a.bar, P, a.err)) return;
+    }
+    for (int c = gw; c < d; c += nw) {
+      const double v = a.x0_zero ? 0.0 : warp_sum_strip(a.part + (int64_t)c * P, P);
+      if (lane == 0) a.r[c] = a.b[c] - v;
+    }
+    bx_partial(a.x);
+    if (grid_barrier(a.bar, P, a.err)) return;
+    if (precond(a.r, a.rh)) return;
+    double rho = total(red_rho);
+    double bx = total(red_bx);
+    for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec[c] = c < d ? a.rh[c] : 0.0;
+    __syncthreads();
+    est = (bx > 0.0) ? sqrt(a.lam1 * rho / bx) : 0.0;
+    if (rho == 0.0 || rho <= a.tol2 * bx) status = LSQ_OK;
+    while (status == LSQ_ERR_MAXIT && it < a.maxit) {
+      fused_pass<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+      ++passes;
+      if (grid_barrier(a.bar, P, a.err)) return;
+      if (warp == 0) {
+        const double qq = warp_sum_strip(a.part + (int64_t)dp * P, P);
+        if (lane == 0) S.scal[0] = qq;
+      }
+      __syncthreads();
+      const double q = S.scal[0];
+      if (!(q > 0.0) || !isfinite(q) || !isfinite(rho)) {
+        status = LSQ_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = rho / q;
+      for (int c = gw; c < d; c += nw) {
+        const double v = warp_sum_strip(a.part + (int64_t)c * P, P);
+        if (lane == 0) {
+          a.x[c] += alpha * S.vec[c];
+          a.r[c] -= alpha * v;
+        }
+      }
+      bx_partial(a.x);
+      if (grid_barrier(a.bar, P, a.err)) return;
+      if (precond(a.r, a.rh)) return;
+      const double rho_new = total(red_rho);
+      bx = total(red_bx);
+      const double beta = rho_new / rho;
+      for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec[c] = c < d ? a.rh[c] + beta * S.vec[c] : 0.0;
+      __syncthreads();
+      rho = rho_new;
+      ++it;
+      est = (bx > 0.0) ? sqrt(a.lam1 * rho / bx) : 0.0;
+      if (!isfinite(rho)) status = LSQ_ERR_BREAKDOWN;
+      else if (rho == 0.0 || rho <= a.tol2 * bx) status = LSQ_OK;
+    }
+  } else {
+    // IHS / Polyak-IHS: x and x_{t-1} whole in every CTA
+    for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+      const double xc = c < d ? a.x[c] : 0.0;
+      S.vec[c] = xc;
+      S.vec2[c] = a.first_step ? xc : (c < d ? a.xprev[c] : 0.0);
+    }
+    __syncthreads();
+    while (it < a.maxit) {
+      fused_pass<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+      ++passes;
+      if (grid_barrier(a.bar, P, a.err)) return;
+      for (int c = gw; c < d; c += nw) {
+        const double v = warp_sum_strip(a.part + (int64_t)c * P, P);
+        if (lane == 0) a.g[c] = v - a.b[c];
+      }
+      bx_partial(S.vec);
+      if (grid_barrier(a.bar, P, a.err)) return;
+      if (precond(a.g, a.rh)) return;
+      const double gam = total(red_rho);
+      const double bx = total(red_bx);
+      est = (bx > 0.0) ? sqrt(a.lam1 * gam / bx) : 0.0;
+      if (!isfinite(gam)) { status = LSQ_ERR_BREAKDOWN; break; }
+      if (gam == 0.0 || gam <= a.tol2 * bx) { status = LSQ_OK; break; }
+      for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+        const double xc = S.vec[c];
+        const double xn = c < d ? xc - a.mu * a.rh[c] + a.beta * (xc - S.vec2[c]) : 0.0;
+        S.vec2[c] = xc;
+        S.vec[c] = xn;
+      }
+      __syncthreads();
+      ++it;
+    }
+    if (cta == 0) {
+      for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        a.x[c] = S.vec[c];
+        a.xprev[c] = S.vec2[c];
+      }
+    }
+  }
+  if (cta == 0 && threadIdx.x == 0) {
+    a.out[0] = (double)it;
+    a.out[1] = (double)status;
+    a.out[2] = (double)passes;
+    a.out[3] = est;
+  }
+}
+
+// standalone pass for lsq_hmatvec
+template <typename TA, int EPL>
+__global__ void __launch_bounds__(LSQ_THREADS, 1) hmatvec_kernel(const void* A, int64_t n, int d, int dp, int64_t ld,
+                                                                  int64_t rows_per_cta, const double* p, double* part) {
+  extern __shared__ __align__(16) double smem[];
+  double* vec = smem;
+  double* wred = vec + dp;
+  double* qred = wred + LSQ_WARPS * dp;
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) vec[c] = c < d ? p[c] : 0.0;
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = min(n, r0 + rows_per_cta);
+  fused_pass<TA, EPL>(reinterpret_cast<const TA*>(A), ld, d, dp, r0, r1, vec, wred, qred, part, gridDim.x,
+                      blockIdx.x);
+}
+
+__global__ void reduce_part_kernel(const double* part, int P, int d, int dp, double* v, double* q) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int c = gw; c <= d; c += nw) {
+    const int src = c < d ? c : dp;
+    const double s = warp_sum_strip(part + (int64_t)src * P, P);
+    if (lane == 0) {
+      if (c < d) v[c] = s;
+      else *q = s;
+    }
+  }
+}
+
+__global__ void transpose_kernel(const double* __restrict__ W, int d, double* __restrict__ WT) {
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = by + k, c = bx + threadIdx.x;
+    tile[k][threadIdx.x] = (r < d && c < d) ? W[(int64_t)r * d + c] : 0.0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = bx + k, c = by + threadIdx.x;
+    if (r < d && c < d) WT[(int64_t)r * d + c] = tile[threadIdx.x][k];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------
+typedef void (*solve_fn)(SolveArgs);
+
+static int epl_for(int d) {
+  int e = 1;
+  while (32 * e < d) e <<= 1;
+  return e;
+}
+
+template <typename TA>
+static void* pick_solve(int epl) {
+  switch (epl) {
+    case 1: return (void*)solve_kernel<TA, 1>;
+    case 2: return (void*)solve_kernel<TA, 2>;
+    case 4: return (void*)solve_kernel<TA, 4>;
+    case 8: return (void*)solve_kernel<TA, 8>;
+    case 16: return (void*)solve_kernel<TA, 16>;
+    default: return (void*)solve_kernel<TA, 32>;
+  }
+}
+
+template <typename TA>
+static void* pick_hmv(int epl) {
+  switch (epl) {
+    case 1: return (void*)hmatvec_kernel<TA, 1>;
+    case 2: return (void*)hmatvec_kernel<TA, 2>;
+    case 4: return (void*)hmatvec_kernel<TA, 4>;
+    case 8: return (void*)hmatvec_kernel<TA, 8>;
+    case 16: return (void*)hmatvec_kernel<TA, 16>;
+    default: return (void*)hmatvec_kernel<TA, 32>;
+  }
+}
+
+static lsq_status check_matrix(const lsq_matrix* A) {
+  if (!A || !A->data) return LSQ_ERR_ARG;
+  if (A->n < 1 || A->n >= (1ll << 31) || A->d < 1 || A->d > LSQ_MAX_D || A->ld < A->d) return LSQ_ERR_ARG;
+  if (A->dtype != LSQ_F64 && A->dtype != LSQ_F32) return LSQ_ERR_ARG;
+  const size_t es = A->dtype == LSQ_F64 ? 8 : 4;
+  if (((uintptr_t)A->data) % es) return LSQ_ERR_ARG;
+  return LSQ_OK;
+}
+
+static size_t solve_smem_bytes(int dp) { return (size_t)(dp * 2 + LSQ_WARPS * dp + LSQ_WARPS + 8 + dp) * 8; }
+
+static double theta_ratio(int type, double m, double d, double N) {
+  // mu = theta1 / theta2 for refreshed embeddings
+  if (type == LSQ_SKETCH_SRHT) {
+    const double t1 = (N - d) / (m - d) * (m / N);
+    const double t2 = (N - d) / ((m - d) * (m - d) * (m - d)) * (d * d + m * N - 2 * d * m) * (m / N) * (m / N);
+    return t1 / t2;
+  }
+  const double t1 = m / (m - d - 1);
+  const double t2 = m * m * (m - 1) / ((m - d) * (m - d - 1) * (m - d - 3));
+  return t1 / t2;
+}
+
+}  // namespace
+
+extern "C" void lsq_solve_opts_default(lsq_solve_opts* o) {
+  if (!o) return;
+  o->rho = 0.0;
+  o->mu = NAN;
+  o->beta = NAN;
+  o->refresh = 0;
+  o->sketch_type = LSQ_SKETCH_GAUSS;
+  o->m = 0;
+  o->seed = 0;
+  o->s = 8;
+  o->precision = LSQ_PREC_F64;
+  o->refresh_every = 8;
+  o->grid_blocks = 0;
+  o->x0_zero = 0;
+}
+
+extern "C" lsq_status lsq_hmatvec(lsq_ctx* ctx, const lsq_matrix* A, const double* p, double* v, double* q) {
+  if (!ctx || !p || !v || !q) return LSQ_ERR_ARG;
+  lsq_status st = check_matrix(A);
+  if (st != LSQ_OK) return st;
+  const int d = (int)A->d, epl = epl_for(d), dp = 32 * epl;
+  void* kern = A->dtype == LSQ_F64 ? pick_hmv<double>(epl) : pick_hmv<float>(epl);
+  const size_t smem = (size_t)(dp + LSQ_WARPS * dp + LSQ_WARPS) * 8;
+  LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LSQ_THREADS, smem));
+  int P = std::max(1, per_sm) * ctx->sm_count;
+  P = (int)std::min<int64_t>(P, (A->n + 31) / 32);
+  P = std::max(P, 1);
+  const int64_t rows_per_cta = (A->n + P - 1) / P;
+  P = (int)((A->n + rows_per_cta - 1) / rows_per_cta);
+  st = lsq_ensure_scratch(ctx, lsq_align256((size_t)(dp + 1) * P * 8));
+  if (st != LSQ_OK) return st;
+  double* part = reinterpret_cast<double*>(ctx->scratch);
+  const void* Ad = A->data;
+  int64_t n = A->n, ld = A->ld;
+  int di = d, dpi = dp;
+  void* args[] = {(void*)&Ad, &n, &di, &dpi, &ld, (void*)&rows_per_cta, (void*)&p, &part};
+  LSQ_CUDA_TRY(cudaLaunchKernel(kern, dim3(P), dim3(LSQ_THREADS), args, smem, ctx->stream));
+  lsq_count_launch();
+  reduce_part_kernel<<<std::max(1, (d + 1 + 7) / 8), 256, 0, ctx->stream>>>(part, P, d, dp, v, q);
+  LSQ_LAUNCH_CHECK();
+  return LSQ_OK;
+}
+
+extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double* b, int32_t method, const double* W,
+                                double* x, double tol, int32_t maxit, const lsq_solve_opts* opts_in,
+                                lsq_solve_info* info) {
+  if (!ctx || !b || !x) return LSQ_ERR_ARG;
+  lsq_status st = check_matrix(A);
+  if (st != LSQ_OK) return st;
+  if (method != LSQ_PCG && method != LSQ_IHS && method != LSQ_POLYAK_IHS) return LSQ_ERR_ARG;
+  if (!(tol >= 0.0) || maxit < 0) return LSQ_ERR_ARG;
+  lsq_solve_opts o;
+  lsq_solve_opts_default(&o);
+  if (opts_in) o = *opts_in;
+  if (o.precision != LSQ_PREC_F64) return LSQ_ERR_ARG;  // mixed precision: see below
+  const int d = (int)A->d;
+  const bool refresh = (method != LSQ_PCG) && o.refresh;
+  if (!refresh && !W) return LSQ_ERR_ARG;
+  if (refresh && (o.m < d || o.m > 65536)) return LSQ_ERR_ARG;
+  double rho = o.rho;
+  if (!(rho > 0.0)) {
+    if (o.m <= 0) return LSQ_ERR_ARG;
+    rho = (double)d / (double)o.m;
+  }
+  if (!(rho < 1.0)) return LSQ_ERR_ARG;
+  const double lam1 = (1.0 + sqrt(rho)) * (1.0 + sqrt(rho));
+  double mu = o.mu, beta = o.beta;
+  if (method == LSQ_PCG) {
+    mu = 0.0;
+    beta = 0.0;
+  } else if (!refresh) {
+    if (isnan(mu)) mu = method == LSQ_IHS ? (1 - rho) * (1 - rho) / (1 + rho) : (1 - rho) * (1 - rho);
+    if (isnan(beta)) beta = method == LSQ_IHS ? 0.0 : rho;
+  } else {
+    if (isnan(mu)) {
+      int64_t N = 1;
+      while (N < A->n) N <<= 1;
+      if (o.sketch_type != LSQ_SKETCH_SRHT && o.m < d + 4) return LSQ_ERR_ARG;
+      mu = theta_ratio(o.sketch_type, (double)o.m, (double)d, (double)N);
+    }
+    if (isnan(beta)) beta = method == LSQ_IHS ? 0.0 : 0.1;
+  }
+  if (method == LSQ_IHS) beta = 0.0;
+
+  const int epl = epl_for(d), dp = 32 * epl;
+  void* kern = A->dtype == LSQ_F64 ? pick_solve<double>(epl) : pick_solve<float>(epl);
+  const size_t smem = solve_smem_bytes(dp);
+  LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LSQ_THREADS, smem));
+  if (per_sm < 1) return LSQ_ERR_CUDA;
+  int P = per_sm * ctx->sm_count;
+  if (o.grid_blocks > 0) P = std::min(P, o.grid_blocks);
+  P = (int)std::min<int64_t>(P, std::max<int64_t>(1, (A->n + 31) / 32));
+  const int64_t rows_per_cta = (A->n + P - 1) / P;
+  P = (int)((A->n + rows_per_cta - 1) / rows_per_cta);
+
+  // scratch: part, red, r, z, rh, g, xprev, WT, bar, out, + (refresh) SA, R, W
+  const size_t mat = (size_t)d * d;
+  size_t need = lsq_align256((size_t)(dp + 1) * P * 8) + lsq_align256((size_t)4 * P * 8) + 5 * lsq_align256((size_t)dp * 8) +
+                lsq_align256(mat * 8) + lsq_align256(64) + lsq_align256(64);
+  size_t refresh_extra = 0;
+  if (refresh) refresh_extra = lsq_align256((size_t)o.m * d * 8) + 3 * lsq_align256(mat * 8);
+  st = lsq_ensure_state(ctx, need + refresh_extra);
+  if (st != LSQ_OK) return st;
+  Carver cv{reinterpret_cast<char*>(ctx->state), 0};
+  SolveArgs a;
+  a.part = cv.take<double>((size_t)(dp + 1) * P);
+  a.red = cv.take<double>((size_t)4 * P);
+  a.r = cv.take<double>(dp);
+  a.z = cv.take<double>(dp);
+  a.rh = cv.take<double>(dp);
+  a.g = cv.take<double>(dp);
+  a.xprev = cv.take<double>(dp);
+  double* WT = cv.take<double>(mat);
+  a.bar = cv.take<unsigned>(16);
+  a.err = reinterpret_cast<int*>(a.bar + 8);
+  a.out = cv.take<double>(8);
+  double* SA = refresh ? cv.take<double>((size_t)o.m * d) : nullptr;
+  double* Rr = refresh ? cv.take<double>(mat) : nullptr;
+  double* Wr = refresh ? cv.take<double>(mat) : nullptr;
+
+  a.A = A->data;
+  a.dtype = A->dtype;
+  a.n = A->n;
+  a.d = d;
+  a.dp = dp;
+  a.ld = A->ld;
+  a.rows_per_cta = rows_per_cta;
+  a.b = b;
+  a.x = x;
+  a.method = method;
+  a.mu = mu;
+  a.beta = beta;
+  a.lam1 = lam1;
+  a.tol2 = tol * tol / lam1;
+  a.maxit = maxit;
+  a.x0_zero = o.x0_zero ? 1 : 0;
+  a.first_step = 1;
+  cudaStream_t s = ctx->stream;
+  LSQ_CUDA_TRY(cudaEventRecord(ctx->ev0, s));
+
+  double ms_sketch = 0.0;
+  int iters = 0, passes = 0, status = LSQ_ERR_MAXIT;
+  double est = 0.0;
+  if (!refresh) {
+    a.W = W;
+    a.WT = WT;
+    transpose_kernel<<<dim3((d + 31) / 32, (d + 31) / 32), dim3(32, 8), 0, s>>>(W, d, WT);
+    LSQ_LAUNCH_CHECK();
+    LSQ_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, s));
+    void* args[] = {&a};
+    LSQ_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(P), dim3(LSQ_THREADS), args, smem, s));
+    lsq_count_launch();
+    LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status, a.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 8, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaEventRecord(ctx->ev1, s));
+    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    const double* o4 = reinterpret_cast<const double*>(ctx->host_status);
+    const int errc = ctx->host_status[8];
+    iters = (int)o4[0];
+    status = errc ? errc : (int)o4[1];
+    passes = (int)o4[2];
+    est = o4[3];
+  } else {
+    a.W = Wr;
+    a.WT = WT;
+    a.maxit = 1;
+    cudaEvent_t e_a, e_b;
+    LSQ_CUDA_TRY(cudaEventCreate(&e_a));
+    LSQ_CUDA_TRY(cudaEventCreate(&e_b));
+    lsq_sketch_opts so;
+    so.s = o.s > 0 ? o.s : 8;
+    so.precision = LSQ_SKETCH_F64;
+    for (int t = 0; t <= maxit; ++t) {
+      if (t == maxit) {
+        status = LSQ_ERR_MAXIT;
+        break;
+      }
+      so.t = (uint32_t)t;
+      cudaEventRecord(e_a, s);
+      st = lsq_sketch(ctx, A, o.sketch_type, o.m, o.seed, &so, SA);
+      if (st == LSQ_OK) st = lsq_factor(ctx, SA, o.m, d, Rr, Wr);
+      cudaEventRecord(e_b, s);
+      if (st != LSQ_OK) {
+        status = st;
+        break;
+      }
+      transpose_kernel<<<dim3((d + 31) / 32, (d + 31) / 32), dim3(32, 8), 0, s>>>(Wr, d, WT);
+      LSQ_LAUNCH_CHECK();
+      a.first_step = t == 0;
+      LSQ_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, s));
+      void* args[] = {&a};
+      LSQ_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(P), dim3(LSQ_THREADS), args, smem, s));
+      lsq_count_launch();
+    lsq_count_launch();
+      LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status, a.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 8, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e_a, e_b);
+      ms_sketch += ms;
+      const double* o4 = reinterpret_cast<const double*>(ctx->host_status);
+      const int errc = ctx->host_status[8];
+      passes += (int)o4[2];
+      est = o4[3];
+      const int stt = errc ? errc : (int)o4[1];
+      iters = t + (int)o4[0];
+      if (stt == LSQ_ERR_MAXIT) continue;  // the one step was taken
+      status = stt;
+      break;
+    }
+    cudaEventRecord(ctx->ev1, s);
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(e_a);
+    cudaEventDestroy(e_b);
+  }
+  float ms_total = 0.f;
+  cudaEventElapsedTime(&ms_total, ctx->ev0, ctx->ev1);
+  (void)cudaGetLastError();
+  if (info) {
+    info->iters = iters;
+    info->status = status;
+    info->passes = passes;
+    info->exact_passes = passes;
+    info->est_err = est;
+    info->ms_total = ms_total;
+    info->ms_sketch = ms_sketch;
+  }
+  return (lsq_status)status;
+}

@@ -1,0 +1,51 @@
+"""Parity of lsq_factor (H_S = R^T R, W = R^{-1}) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_util import rel_fro, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_1911_02675_gb300 as lib
+    return lib
+
+
+@pytest.fixture(scope="module")
+def ctx(L):
+    c = L.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("m,d,kappa", [(40, 1, 1.0), (70, 37, 1e2), (256, 64, 1e4), (300, 100, 1e3), (1024, 512, 1e6),
+                                       (1200, 1024, 1e2), (200, 190, 1e1)])
+def test_factor_matches_oracle(L, ctx, m, d, kappa):
+    SA = W.make_problem(m, d, kappa, seed=d)["A"]
+    R, Wm = L.lsq_factor(ctx, to_dev(SA))
+    R, Wm = R.cpu().numpy(), Wm.cpu().numpy()
+    Rref = O.factor(SA)
+    # columnwise relative error (the factor of a column-scaled matrix is column-scaled)
+    colscale = np.abs(Rref).max(axis=0)
+    assert np.max(np.abs(R - Rref) / colscale) < 1e-11
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    assert np.all(np.tril(Wm, -1) == 0)
+    np.testing.assert_allclose(Wm @ R, np.eye(d), atol=1e-9)
+    Wref = O.tri_inv_upper(Rref)
+    rowscale = np.abs(Wref).max(axis=1, keepdims=True)
+    assert np.max(np.abs(Wm - Wref) / rowscale) < 1e-9
+
+
+def test_rank_deficient_is_reported(L, ctx):
+    SA = np.random.default_rng(0).standard_normal((50, 8))
+    SA[:, 3] = 0.0
+    with pytest.raises(L.LsqError) as e:
+        L.lsq_factor(ctx, to_dev(SA))
+    assert e.value.status == L.LSQ_ERR_RANK
+    # the context stays usable
+    R, _ = L.lsq_factor(ctx, to_dev(np.eye(8) + 0.1))
+    assert np.isfinite(R.cpu().numpy()).all()

@@ -1,0 +1,100 @@
+"""Parity of lsq_sketch (Section 2) with the FP64 oracle.
+
+Bar: SRHT signs / sample indices and SJLT positions bit for bit (integer-valued A makes
+every sum exact, so SA must equal the oracle's SA exactly); SA in FP64 to 1e-12 relative
+Frobenius error; the FP32 variant within its own rounding bound."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from gpu_util import int_matrix, rel_fro, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_1911_02675_gb300 as lib
+    return lib
+
+
+@pytest.fixture(scope="module")
+def ctx(L):
+    c = L.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n,d,m,seed,t", [(1000, 37, 70, 3, 0), (4096, 64, 256, 0, 0), (777, 130, 129, 5, 2),
+                                          (33, 1, 2, 9, 1)])
+def test_gaussian_fp64(L, ctx, n, d, m, seed, t):
+    A = W.make_problem(n, d, 1e3, seed=seed + 1)["A"]
+    SA = L.lsq_sketch(ctx, to_dev(A), "gauss", m, seed, t=t).cpu().numpy()
+    assert rel_fro(SA, O.sketch_gauss(A, m, seed, t)) < 1e-12
+
+
+def test_gaussian_fp32_storage_and_arithmetic(L, ctx):
+    A32 = W.make_problem(3000, 48, 1e2, seed=2)["A"].astype(np.float32)
+    ref = O.sketch_gauss(A32.astype(np.float64), 96, 4)
+    SA = L.lsq_sketch(ctx, to_dev(A32), "gauss", 96, 4).cpu().numpy()
+    assert rel_fro(SA, ref) < 1e-12          # FP32 storage, FP64 arithmetic
+    SA32 = L.lsq_sketch(ctx, to_dev(A32), "gauss", 96, 4, precision="f32").cpu().numpy()
+    assert rel_fro(SA32, ref) < 5e-6         # FP32 arithmetic: u32 * sqrt-growth
+
+
+@pytest.mark.parametrize("n,d,m,seed,t", [(64, 5, 16, 1, 0), (1000, 7, 64, 2, 3), (5000, 33, 300, 7, 1),
+                                          (70000, 3, 1000, 4, 0), (2048, 16, 2048, 3, 0)])
+def test_srht_indices_and_signs_bit_exact(L, ctx, n, d, m, seed, t):
+    A = int_matrix(n, d, seed)
+    SA = L.lsq_sketch(ctx, to_dev(A), "srht", m, seed, t=t).cpu().numpy()
+    ref = O.sketch_srht(A, m, seed, t)
+    assert np.array_equal(SA, ref)
+
+
+@pytest.mark.parametrize("n,d,m,seed", [(3000, 40, 200, 1), (4096, 64, 256, 0), (20000, 130, 1024, 2)])
+def test_srht_fp64(L, ctx, n, d, m, seed):
+    A = W.make_problem(n, d, 1e4, seed=seed)["A"]
+    SA = L.lsq_sketch(ctx, to_dev(A), "srht", m, seed).cpu().numpy()
+    assert rel_fro(SA, O.sketch_srht(A, m, seed)) < 1e-12
+    SA32 = L.lsq_sketch(ctx, to_dev(A), "srht", m, seed, precision="f32").cpu().numpy()
+    assert rel_fro(SA32, O.sketch_srht(A, m, seed)) < 5e-6
+
+
+@pytest.mark.parametrize("n,d,m,s,seed,t", [(100, 4, 10, 3, 1, 0), (5000, 33, 64, 8, 2, 2), (20000, 130, 512, 8, 3, 0),
+                                            (3000, 9, 7, 7, 5, 1), (1000, 2, 40, 1, 6, 0)])
+def test_sjlt_positions_bit_exact(L, ctx, n, d, m, s, seed, t):
+    A = int_matrix(n, d, seed)
+    SA = L.lsq_sketch(ctx, to_dev(A), "sjlt", m, seed, t=t, s=s).cpu().numpy()
+    ref = O.sketch_sjlt(A, m, s, seed, t)
+    # sqrt(s) SA holds exact integer sums of +-A rows; the two sides round the scale in a
+    # different order (per term vs per sum), so compare the integers those sums must be
+    k_gpu, k_ref = SA * np.sqrt(s), ref * np.sqrt(s)
+    assert np.max(np.abs(k_gpu - np.rint(k_gpu))) < 1e-6 and np.max(np.abs(k_ref - np.rint(k_ref))) < 1e-6
+    assert np.array_equal(np.rint(k_gpu), np.rint(k_ref))
+    assert rel_fro(SA, ref) < 1e-14
+
+
+def test_sjlt_fp64_and_fp32(L, ctx):
+    A = W.make_problem(8000, 64, 1e4, seed=3)["A"]
+    ref = O.sketch_sjlt(A, 512, 8, 11)
+    assert rel_fro(L.lsq_sketch(ctx, to_dev(A), "sjlt", 512, 11, s=8).cpu().numpy(), ref) < 1e-12
+    assert rel_fro(L.lsq_sketch(ctx, to_dev(A), "sjlt", 512, 11, s=8, precision="f32").cpu().numpy(), ref) < 5e-6
+
+
+def test_strided_rows(L, ctx):
+    A = W.make_problem(2000, 24, 1e2, seed=4)["A"]
+    big = torch.zeros((2000, 40), dtype=torch.float64, device="cuda")
+    big[:, :24] = to_dev(A)
+    for kind in ("gauss", "srht", "sjlt"):
+        SA = L.lsq_sketch(ctx, big[:, :24], kind, 128, 1).cpu().numpy()
+        assert rel_fro(SA, O.sketch(A, kind, 128, 1)) < 1e-12
+
+
+def test_rejects_bad_arguments(L, ctx):
+    A = to_dev(np.ones((64, 4)))
+    with pytest.raises(L.LsqError):
+        L.lsq_sketch(ctx, A, "srht", 65, 0)       # m > N
+    with pytest.raises(L.LsqError):
+        L.lsq_sketch(ctx, A, "sjlt", 4, 0, s=5)   # s > m
