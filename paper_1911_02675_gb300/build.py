@@ -33,7 +33,8 @@ def _flags():
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "common.cuh"), os.path.join(ROOT, "include", "lsq.h")]
+    deps = [src, os.path.join(ROOT, "include", "lsq.h")]
+    deps += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     return any(os.path.getmtime(p) > os.path.getmtime(obj) for p in deps)
 
 

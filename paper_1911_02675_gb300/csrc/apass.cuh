@@ -1,0 +1,148 @@
+// apass.cuh -- the fused pass over A (v = A^T (A p), q = ||A p||^2, one read of each row)
+// shared by the solver and the standalone pass entry points.  Internal, not part of the ABI.
+#pragma once
+
+#include "common.cuh"
+
+namespace lsq_apass {
+
+template <typename TA>
+__device__ __forceinline__ double ld_elem(const TA* p) {
+  return (double)__ldg(p);
+}
+
+// ------------------------------------------------------------------------------------
+// Fused pass over the rows [r0, r1): per-warp accumulators of v = A^T (A p) in
+// registers (lane owns columns lane + 32 k), q = sum (a_i . p)^2; then a fixed-order
+// CTA reduction into part[c * P + cta].  The next row is loaded before the current
+// one is used so that each warp keeps two rows in flight.
+// ------------------------------------------------------------------------------------
+template <typename TA, int EPL>
+__device__ void fused_pass(const TA* __restrict__ A, int64_t ld, int d, int dp, int64_t r0, int64_t r1,
+                           const double* vec_s, double* wred, double* qred, double* part, int P, int cta) {
+  constexpr bool PV_REG = EPL <= 8;   // keep p in registers while they are plentiful
+  constexpr bool PREFETCH = EPL <= 16;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double pv[PV_REG ? EPL : 1], acc[EPL], cur[EPL], nxt[PREFETCH ? EPL : 1];
+  bool ok[EPL];
+#pragma unroll
+  for (int k = 0; k < EPL; ++k) {
+    const int c = lane + 32 * k;
+    ok[k] = c < d;
+    if (PV_REG) pv[k] = ok[k] ? vec_s[c] : 0.0;
+    acc[k] = 0.0;
+  }
+  double q = 0.0;
+  int64_t i = r0 + warp;
+  if (PREFETCH && i < r1) {
+    const TA* a = A + i * ld;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? ld_elem(a + lane + 32 * k) : 0.0;
+  }
+  for (; i < r1; i += LSQ_WARPS) {
+    if (PREFETCH) {
+      const int64_t inext = i + LSQ_WARPS;
+      if (inext < r1) {
+        const TA* a = A + inext * ld;
+#pragma unroll
+        for (int k = 0; k < (PREFETCH ? EPL : 1); ++k) nxt[k] = ok[k] ? ld_elem(a + lane + 32 * k) : 0.0;
+      }
+    } else {
+      const TA* a = A + i * ld;
+#pragma unroll
+      for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? ld_elem(a + lane + 32 * k) : 0.0;
+    }
+    double w = 0.0;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) w = fma(cur[k], PV_REG ? pv[PV_REG ? k : 0] : vec_s[lane + 32 * k], w);
+    w = warp_sum(w);
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) acc[k] = fma(w, cur[k], acc[k]);
+    q = fma(w, w, q);
+    if (PREFETCH) {
+#pragma unroll
+      for (int k = 0; k < EPL; ++k) cur[k] = nxt[PREFETCH ? k : 0];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < EPL; ++k) {
+    const int c = lane + 32 * k;
+    if (c < dp) wred[warp * dp + c] = acc[k];
+  }
+  if (lane == 0) qred[warp] = q;
+  __syncthreads();
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < LSQ_WARPS; ++w) s += wred[w * dp + c];
+    part[(int64_t)c * P + cta] = s;
+  }
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < LSQ_WARPS; ++w) s += qred[w];
+    part[(int64_t)dp * P + cta] = s;
+  }
+  __syncthreads();
+}
+
+// sum_{j < P} src[j] by one warp, fixed order
+__device__ __forceinline__ double warp_sum_strip(const double* src, int P) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int j = lane; j < P; j += 32) s += src[j];
+  return warp_sum(s);
+}
+
+// standalone pass: CTA b handles rows [b * rows_per_cta, (b + 1) * rows_per_cta)
+template <typename TA, int EPL>
+__global__ void __launch_bounds__(LSQ_THREADS, 1) hmatvec_kernel(const void* A, int64_t n, int d, int dp, int64_t ld,
+                                                                  int64_t rows_per_cta, const double* p, double* part) {
+  extern __shared__ __align__(16) double smem[];
+  double* vec = smem;
+  double* wred = vec + dp;
+  double* qred = wred + LSQ_WARPS * dp;
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) vec[c] = c < d ? p[c] : 0.0;
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = min(n, r0 + rows_per_cta);
+  fused_pass<TA, EPL>(reinterpret_cast<const TA*>(A), ld, d, dp, r0, r1, vec, wred, qred, part, gridDim.x,
+                      blockIdx.x);
+}
+
+// v[c] = sum_j part[c][j] (c < d), q = sum_j part[dp][j]; one warp per output, fixed order
+__global__ void reduce_part_kernel(const double* part, int P, int d, int dp, double* v, double* q) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int c = gw; c <= d; c += nw) {
+    const int src = c < d ? c : dp;
+    const double s = warp_sum_strip(part + (int64_t)src * P, P);
+    if (lane == 0) {
+      if (c < d) v[c] = s;
+      else *q = s;
+    }
+  }
+}
+
+// elements per lane: the smallest power of two with 32 * EPL >= d
+static inline int epl_for(int d) {
+  int e = 1;
+  while (32 * e < d) e <<= 1;
+  return e;
+}
+
+template <typename TA>
+static void* pick_hmv(int epl) {
+  switch (epl) {
+    case 1: return (void*)hmatvec_kernel<TA, 1>;
+    case 2: return (void*)hmatvec_kernel<TA, 2>;
+    case 4: return (void*)hmatvec_kernel<TA, 4>;
+    case 8: return (void*)hmatvec_kernel<TA, 8>;
+    case 16: return (void*)hmatvec_kernel<TA, 16>;
+    default: return (void*)hmatvec_kernel<TA, 32>;
+  }
+}
+
+static inline size_t hmatvec_smem_bytes(int dp) { return (size_t)(dp + LSQ_WARPS * dp + LSQ_WARPS) * 8; }
+
+}  // namespace lsq_apass

@@ -14,7 +14,10 @@
 #include <algorithm>
 #include <math.h>
 
+#include "apass.cuh"
 #include "common.cuh"
+
+using namespace lsq_apass;
 
 namespace {
 
@@ -48,93 +51,6 @@ struct SolveArgs {
   int* err;
   double* out;       // [0] iters, [1] status, [2] passes, [3] est_err
 };
-
-template <typename TA>
-__device__ __forceinline__ double ld_elem(const TA* p) {
-  return (double)__ldg(p);
-}
-
-// ------------------------------------------------------------------------------------
-// Fused pass over the rows [r0, r1): per-warp accumulators of v = A^T (A p) in
-// registers (lane owns columns lane + 32 k), q = sum (a_i . p)^2; then a fixed-order
-// CTA reduction into part[c * P + cta].  The next row is loaded before the current
-// one is used so that each warp keeps two rows in flight.
-// ------------------------------------------------------------------------------------
-template <typename TA, int EPL>
-__device__ void fused_pass(const TA* __restrict__ A, int64_t ld, int d, int dp, int64_t r0, int64_t r1,
-                           const double* vec_s, double* wred, double* qred, double* part, int P, int cta) {
-  constexpr bool PV_REG = EPL <= 8;   // keep p in registers while they are plentiful
-  constexpr bool PREFETCH = EPL <= 16;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double pv[PV_REG ? EPL : 1], acc[EPL], cur[EPL], nxt[PREFETCH ? EPL : 1];
-  bool ok[EPL];
-#pragma unroll
-  for (int k = 0; k < EPL; ++k) {
-    const int c = lane + 32 * k;
-    ok[k] = c < d;
-    if (PV_REG) pv[k] = ok[k] ? vec_s[c] : 0.0;
-    acc[k] = 0.0;
-  }
-  double q = 0.0;
-  int64_t i = r0 + warp;
-  if (PREFETCH && i < r1) {
-    const TA* a = A + i * ld;
-#pragma unroll
-    for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? ld_elem(a + lane + 32 * k) : 0.0;
-  }
-  for (; i < r1; i += LSQ_WARPS) {
-    if (PREFETCH) {
-      const int64_t inext = i + LSQ_WARPS;
-      if (inext < r1) {
-        const TA* a = A + inext * ld;
-#pragma unroll
-        for (int k = 0; k < (PREFETCH ? EPL : 1); ++k) nxt[k] = ok[k] ? ld_elem(a + lane + 32 * k) : 0.0;
-      }
-    } else {
-      const TA* a = A + i * ld;
-#pragma unroll
-      for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? ld_elem(a + lane + 32 * k) : 0.0;
-    }
-    double w = 0.0;
-#pragma unroll
-    for (int k = 0; k < EPL; ++k) w = fma(cur[k], PV_REG ? pv[PV_REG ? k : 0] : vec_s[lane + 32 * k], w);
-    w = warp_sum(w);
-#pragma unroll
-    for (int k = 0; k < EPL; ++k) acc[k] = fma(w, cur[k], acc[k]);
-    q = fma(w, w, q);
-    if (PREFETCH) {
-#pragma unroll
-      for (int k = 0; k < EPL; ++k) cur[k] = nxt[PREFETCH ? k : 0];
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < EPL; ++k) {
-    const int c = lane + 32 * k;
-    if (c < dp) wred[warp * dp + c] = acc[k];
-  }
-  if (lane == 0) qred[warp] = q;
-  __syncthreads();
-  for (int c = threadIdx.x; c < dp; c += blockDim.x) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < LSQ_WARPS; ++w) s += wred[w * dp + c];
-    part[(int64_t)c * P + cta] = s;
-  }
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < LSQ_WARPS; ++w) s += qred[w];
-    part[(int64_t)dp * P + cta] = s;
-  }
-  __syncthreads();
-}
-
-// sum_{j < P} src[j] by one warp, fixed order
-__device__ __forceinline__ double warp_sum_strip(const double* src, int P) {
-  const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  for (int j = lane; j < P; j += 32) s += src[j];
-  return warp_sum(s);
-}
 
 // out[i] = sum_k M[i*d + k] vec_s[k] for k in [k_lo(i), k_hi(i)), one warp per output
 __device__ __forceinline__ double warp_row_dot(const double* __restrict__ row, const double* vec_s, int k_lo, int k_hi) {
@@ -342,36 +258,6 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
   }
 }
 
-// standalone pass for lsq_hmatvec
-template <typename TA, int EPL>
-__global__ void __launch_bounds__(LSQ_THREADS, 1) hmatvec_kernel(const void* A, int64_t n, int d, int dp, int64_t ld,
-                                                                  int64_t rows_per_cta, const double* p, double* part) {
-  extern __shared__ __align__(16) double smem[];
-  double* vec = smem;
-  double* wred = vec + dp;
-  double* qred = wred + LSQ_WARPS * dp;
-  for (int c = threadIdx.x; c < dp; c += blockDim.x) vec[c] = c < d ? p[c] : 0.0;
-  __syncthreads();
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
-  const int64_t r1 = min(n, r0 + rows_per_cta);
-  fused_pass<TA, EPL>(reinterpret_cast<const TA*>(A), ld, d, dp, r0, r1, vec, wred, qred, part, gridDim.x,
-                      blockIdx.x);
-}
-
-__global__ void reduce_part_kernel(const double* part, int P, int d, int dp, double* v, double* q) {
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int c = gw; c <= d; c += nw) {
-    const int src = c < d ? c : dp;
-    const double s = warp_sum_strip(part + (int64_t)src * P, P);
-    if (lane == 0) {
-      if (c < d) v[c] = s;
-      else *q = s;
-    }
-  }
-}
-
 __global__ void transpose_kernel(const double* __restrict__ W, int d, double* __restrict__ WT) {
   __shared__ double tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
@@ -391,12 +277,6 @@ __global__ void transpose_kernel(const double* __restrict__ W, int d, double* __
 // ------------------------------------------------------------------------------------
 typedef void (*solve_fn)(SolveArgs);
 
-static int epl_for(int d) {
-  int e = 1;
-  while (32 * e < d) e <<= 1;
-  return e;
-}
-
 template <typename TA>
 static void* pick_solve(int epl) {
   switch (epl) {
@@ -406,18 +286,6 @@ static void* pick_solve(int epl) {
     case 8: return (void*)solve_kernel<TA, 8>;
     case 16: return (void*)solve_kernel<TA, 16>;
     default: return (void*)solve_kernel<TA, 32>;
-  }
-}
-
-template <typename TA>
-static void* pick_hmv(int epl) {
-  switch (epl) {
-    case 1: return (void*)hmatvec_kernel<TA, 1>;
-    case 2: return (void*)hmatvec_kernel<TA, 2>;
-    case 4: return (void*)hmatvec_kernel<TA, 4>;
-    case 8: return (void*)hmatvec_kernel<TA, 8>;
-    case 16: return (void*)hmatvec_kernel<TA, 16>;
-    default: return (void*)hmatvec_kernel<TA, 32>;
   }
 }
 
@@ -468,7 +336,7 @@ extern "C" lsq_status lsq_hmatvec(lsq_ctx* ctx, const lsq_matrix* A, const doubl
   if (st != LSQ_OK) return st;
   const int d = (int)A->d, epl = epl_for(d), dp = 32 * epl;
   void* kern = A->dtype == LSQ_F64 ? pick_hmv<double>(epl) : pick_hmv<float>(epl);
-  const size_t smem = (size_t)(dp + LSQ_WARPS * dp + LSQ_WARPS) * 8;
+  const size_t smem = hmatvec_smem_bytes(dp);
   LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LSQ_THREADS, smem));
