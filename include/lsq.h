@@ -204,6 +204,26 @@ LSQ_API lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double* b,
  * of Section 6), FP64 arithmetic.  p, v: device, d FP64; q: device, 1 FP64. */
 LSQ_API lsq_status lsq_hmatvec(lsq_ctx* ctx, const lsq_matrix* A, const double* p, double* v, double* q);
 
+/* ---------------------------------------------------------------------------------
+ * lsq_hmatvec_noalloc: the same fused pass as lsq_hmatvec (v = A^T (A p), q = ||A p||^2,
+ * FP64 arithmetic) for callers that cannot allocate device memory -- code whose device
+ * memory all belongs to its own pool allocator, or latency-bound loops that cannot take
+ * the synchronisation an allocation may cause.  The paper has no counterpart: this is a
+ * deployment variant of the pass, not a step of the method.
+ *   A, p, v, q : as lsq_hmatvec (device; p, v: d FP64; q: 1 FP64), caller-owned.
+ *   cuda_stream: the cudaStream_t to issue on (NULL = legacy default stream).
+ * Needs no context and calls no allocator.  Its only scratch is a fixed array of
+ * 160 x 1025 doubles (1.25 MiB) inside the library, present on every GPU that loads it
+ * until the process exits; the number of CTAs is chosen so that the partial sums fit,
+ * and d > 1024 (or any size that would not fit) is rejected with LSQ_ERR_ARG.
+ * The first call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (other streams, other host threads) race and give
+ * wrong results, so serialise them.  Nothing in the array needs clearing between calls.
+ * --------------------------------------------------------------------------------- */
+LSQ_API lsq_status lsq_hmatvec_noalloc(const lsq_matrix* A, const double* p, double* v, double* q,
+                                       void* cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 LSQ_API const char* lsq_status_str(int32_t status);
 

@@ -35,7 +35,8 @@ DTYPE = {torch.float64: 0, torch.float32: 1}
 
 # every symbol the header declares
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_sketch", "lsq_factor", "lsq_solve",
-           "lsq_solve_opts_default", "lsq_hmatvec", "lsq_status_str", "lsq_version", "lsq_launch_count")
+           "lsq_solve_opts_default", "lsq_hmatvec", "lsq_status_str", "lsq_version", "lsq_launch_count",
+           "lsq_hmatvec_noalloc")
 
 
 class LsqError(RuntimeError):
@@ -84,6 +85,8 @@ def _load():
     L.lsq_solve_opts_default.argtypes = [ctypes.POINTER(LsqSolveOpts)]
     L.lsq_solve_opts_default.restype = None
     L.lsq_hmatvec.argtypes = [P, ctypes.POINTER(LsqMatrix), P, P, P]
+    L.lsq_hmatvec_noalloc.argtypes = [ctypes.POINTER(LsqMatrix), P, P, P, P]
+    L.lsq_hmatvec_noalloc.restype = ctypes.c_int
     L.lsq_status_str.argtypes = [i32]
     L.lsq_status_str.restype = ctypes.c_char_p
     L.lsq_version.restype = ctypes.c_char_p

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblsq.so")
-SOURCES = ["ctx.cu", "sketch.cu", "factor.cu", "solve.cu"]
+SOURCES = ["ctx.cu", "sketch.cu", "factor.cu", "solve.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             if verbose and msg:
                 print(msg, file=sys.stderr)
     objs = [os.path.join(OUT, n.replace(".cu", ".o")) for n in SOURCES]
-    if force or jobs or not os.path.exists(LIB):
+    if force or jobs or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
         run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, LIB)

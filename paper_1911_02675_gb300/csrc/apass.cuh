@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) hmatvec_kernel(const void* A, 
 }
 
 // v[c] = sum_j part[c][j] (c < d), q = sum_j part[dp][j]; one warp per output, fixed order
-__global__ void reduce_part_kernel(const double* part, int P, int d, int dp, double* v, double* q) {
+static __global__ void reduce_part_kernel(const double* part, int P, int d, int dp, double* v, double* q) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
