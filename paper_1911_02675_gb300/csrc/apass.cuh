@@ -17,11 +17,11 @@ __device__ __forceinline__ double ld_elem(const TA* p) {
 // CTA reduction into part[c * P + cta].  The next row is loaded before the current
 // one is used so that each warp keeps two rows in flight.
 // ------------------------------------------------------------------------------------
-template <typename TA, int EPL>
+template <typename TA, int EPL, bool ALLOW_PREFETCH = true>
 __device__ void fused_pass(const TA* __restrict__ A, int64_t ld, int d, int dp, int64_t r0, int64_t r1,
                            const double* vec_s, double* wred, double* qred, double* part, int P, int cta) {
   constexpr bool PV_REG = EPL <= 8;   // keep p in registers while they are plentiful
-  constexpr bool PREFETCH = EPL <= 16;
+  constexpr bool PREFETCH = ALLOW_PREFETCH && EPL <= 16;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double pv[PV_REG ? EPL : 1], acc[EPL], cur[EPL], nxt[PREFETCH ? EPL : 1];
   bool ok[EPL];
@@ -80,6 +80,102 @@ __device__ void fused_pass(const TA* __restrict__ A, int64_t ld, int d, int dp, 
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < LSQ_WARPS; ++w) s += qred[w];
+    part[(int64_t)dp * P + cta] = s;
+  }
+  __syncthreads();
+}
+
+
+// ------------------------------------------------------------------------------------
+// FP32 arithmetic variant of the pass (the inner passes of the mixed-precision solve).
+// FP64 elements are narrowed to FP32 by integer operations on their bit pattern (the
+// FP64->FP32 conversion instruction runs at the FP64 rate, about 2 per clock per SM on
+// this part, below the ~3 elements per clock per SM that the HBM rate needs):
+// mantissa truncated to 23 bits, exponent clamped so that values below the FP32 normal
+// range become (tiny) subnormal-or-zero patterns and values above it become non-finite,
+// which the solver reports as a breakdown.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ float narrow_f32(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t lo = (uint32_t)u, hi = (uint32_t)(u >> 32);
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  const uint32_t ec = min(max(e, 896u), 1151u) - 896u;
+  const uint32_t mant = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;
+  return __uint_as_float((ec << 23) | mant | (hi & 0x80000000u));
+}
+
+__device__ __forceinline__ float narrow_f32(float x) { return x; }
+
+template <typename TA, int EPL>
+__device__ void fused_pass_f32(const TA* __restrict__ A, int64_t ld, int d, int dp, int64_t r0, int64_t r1,
+                               const double* vec_s, double* wred, double* qred, double* part, int P, int cta) {
+  // two rows in flight per warp while the registers allow it (raw FP64 rows are 2 registers
+  // per element); p from shared memory at the widest rows
+  constexpr bool PREFETCH = sizeof(TA) == 4 || EPL <= 16;
+  constexpr bool PV_REG = EPL <= 16;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float pv[PV_REG ? EPL : 1], acc[EPL];
+  TA cur[EPL], nxt[PREFETCH ? EPL : 1];
+  bool ok[EPL];
+#pragma unroll
+  for (int k = 0; k < EPL; ++k) {
+    const int c = lane + 32 * k;
+    ok[k] = c < d;
+    if (PV_REG) pv[PV_REG ? k : 0] = ok[k] ? (float)vec_s[c] : 0.0f;
+    acc[k] = 0.0f;
+  }
+  double q = 0.0;
+  int64_t i = r0 + warp;
+  if (PREFETCH && i < r1) {
+    const TA* a = A + i * ld;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
+  }
+  for (; i < r1; i += LSQ_WARPS) {
+    if (PREFETCH) {
+      const int64_t inext = i + LSQ_WARPS;
+      if (inext < r1) {
+        const TA* a = A + inext * ld;
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) nxt[PREFETCH ? k : 0] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
+      }
+    } else {
+      const TA* a = A + i * ld;
+#pragma unroll
+      for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
+    }
+    float af[EPL];
+    float w = 0.0f;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) {
+      af[k] = narrow_f32(cur[k]);
+      w = fmaf(af[k], PV_REG ? pv[PV_REG ? k : 0] : (float)vec_s[lane + 32 * k], w);
+    }
+    w = warp_sumf(w);
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) acc[k] = fmaf(w, af[k], acc[k]);
+    q = fma((double)w, (double)w, q);
+    if (PREFETCH) {
+#pragma unroll
+      for (int k = 0; k < EPL; ++k) cur[k] = nxt[PREFETCH ? k : 0];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < EPL; ++k) {
+    const int c = lane + 32 * k;
+    if (c < dp) wred[warp * dp + c] = (double)acc[k];
+  }
+  if (lane == 0) qred[warp] = q;
+  __syncthreads();
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w2 = 0; w2 < LSQ_WARPS; ++w2) s += wred[w2 * dp + c];
+    part[(int64_t)c * P + cta] = s;
+  }
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < LSQ_WARPS; ++w2) s += qred[w2];
     part[(int64_t)dp * P + cta] = s;
   }
   __syncthreads();

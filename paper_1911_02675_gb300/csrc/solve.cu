@@ -41,6 +41,10 @@ struct SolveArgs {
   int maxit;
   int x0_zero;       // PCG: skip the initial pass when x0 = 0
   int first_step;    // IHS single-step launches: 1 when x_{-1} = x_0
+  int force_exact;   // mixed IHS single-step launches: the gradient is already small, pass in FP64
+  int refresh_every; // mixed PCG: longest run of FP32 passes between exact residual replacements
+  double replace2;   // mixed PCG: replace when rho has dropped by this factor since the last one
+  double exact2;     // mixed IHS: passes in FP64 once gamma <= exact2 * <b, x>
   double* part;      // [(dp + 1)][P] pass partials
   double* red;       // [4][P] scalar partials
   double* r;         // dp each
@@ -49,7 +53,7 @@ struct SolveArgs {
   double* g;
   unsigned* bar;
   int* err;
-  double* out;       // [0] iters, [1] status, [2] passes, [3] est_err
+  double* out;       // [0] iters, [1] status, [2] passes, [3] est_err, [4] exact passes
 };
 
 // out[i] = sum_k M[i*d + k] vec_s[k] for k in [k_lo(i), k_hi(i)), one warp per output
@@ -68,7 +72,13 @@ struct SolveSmem {
   double* scal;  // 8
 };
 
-template <typename TA, int EPL>
+// MIXED = false: every pass in FP64 arithmetic.  MIXED = true: PCG's passes over A run in
+// FP32 arithmetic and the recursive residual is replaced by an exact b - H x (FP64 pass) when
+// it has dropped by `replace2` since the last replacement, after `refresh_every` iterations,
+// and whenever it passes the stopping test (so convergence is always declared on an exact
+// residual); IHS / Polyak-IHS compute the gradient in FP32 until it is small relative to
+// <b, x> and in FP64 after that (their update has no recursive residual to correct).
+template <typename TA, int EPL, bool MIXED>
 __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
   extern __shared__ __align__(16) double smem[];
   const int dp = a.dp, d = a.d;
@@ -88,7 +98,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
   const TA* A = reinterpret_cast<const TA*>(a.A);
   double* red_rho = a.red;
   double* red_bx = a.red + P;
-  int passes = 0;
+  int passes = 0, exact_passes = 0;
   const bool pcg = a.method == LSQ_PCG;
 
   // ---- H_S^{-1} applied to the vector `src` (global, dp), result into `dst` (global);
@@ -157,8 +167,9 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
     if (!a.x0_zero) {
       for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec[c] = c < d ? a.x[c] : 0.0;
       __syncthreads();
-      fused_pass<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+      fused_pass<TA, EPL, !MIXED>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
       ++passes;
+      ++exact_passes;
       if (grid_barrier(a.bar, P, a.err)) return;
     }
     for (int c = gw; c < d; c += nw) {
@@ -174,8 +185,15 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
     __syncthreads();
     est = (bx > 0.0) ? sqrt(a.lam1 * rho / bx) : 0.0;
     if (rho == 0.0 || rho <= a.tol2 * bx) status = LSQ_OK;
+    double rho_last = rho;  // rho at the last exact residual
+    int it_last = 0;
     while (status == LSQ_ERR_MAXIT && it < a.maxit) {
-      fused_pass<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+      if (MIXED) {
+        fused_pass_f32<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+      } else {
+        fused_pass<TA, EPL, !MIXED>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+        ++exact_passes;
+      }
       ++passes;
       if (grid_barrier(a.bar, P, a.err)) return;
       if (warp == 0) {
@@ -199,8 +217,28 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
       bx_partial(a.x);
       if (grid_barrier(a.bar, P, a.err)) return;
       if (precond(a.r, a.rh)) return;
-      const double rho_new = total(red_rho);
+      double rho_new = total(red_rho);
       bx = total(red_bx);
+      bool conv = rho_new == 0.0 || rho_new <= a.tol2 * bx;
+      if (MIXED && (conv || rho_new <= a.replace2 * rho_last || it + 1 - it_last >= a.refresh_every)) {
+        // replace the recursive residual by b - H x evaluated in FP64
+        for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec2[c] = c < d ? a.x[c] : 0.0;
+        __syncthreads();
+        fused_pass<TA, EPL, !MIXED>(A, a.ld, d, dp, r0, r1, S.vec2, S.wred, S.qred, a.part, P, cta);
+        ++passes;
+        ++exact_passes;
+        if (grid_barrier(a.bar, P, a.err)) return;
+        for (int c = gw; c < d; c += nw) {
+          const double v = warp_sum_strip(a.part + (int64_t)c * P, P);
+          if (lane == 0) a.r[c] = a.b[c] - v;
+        }
+        if (grid_barrier(a.bar, P, a.err)) return;
+        if (precond(a.r, a.rh)) return;
+        rho_new = total(red_rho);
+        conv = rho_new == 0.0 || rho_new <= a.tol2 * bx;
+        rho_last = rho_new;
+        it_last = it + 1;
+      }
       const double beta = rho_new / rho;
       for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec[c] = c < d ? a.rh[c] + beta * S.vec[c] : 0.0;
       __syncthreads();
@@ -208,7 +246,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
       ++it;
       est = (bx > 0.0) ? sqrt(a.lam1 * rho / bx) : 0.0;
       if (!isfinite(rho)) status = LSQ_ERR_BREAKDOWN;
-      else if (rho == 0.0 || rho <= a.tol2 * bx) status = LSQ_OK;
+      else if (conv) status = LSQ_OK;
     }
   } else {
     // IHS / Polyak-IHS: x and x_{t-1} whole in every CTA
@@ -218,8 +256,14 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
       S.vec2[c] = a.first_step ? xc : (c < d ? a.xprev[c] : 0.0);
     }
     __syncthreads();
+    bool exact = !MIXED || a.force_exact;
     while (it < a.maxit) {
-      fused_pass<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+      if (exact) {
+        fused_pass<TA, EPL, !MIXED>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+        ++exact_passes;
+      } else {
+        fused_pass_f32<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+      }
       ++passes;
       if (grid_barrier(a.bar, P, a.err)) return;
       for (int c = gw; c < d; c += nw) {
@@ -233,7 +277,12 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
       const double bx = total(red_bx);
       est = (bx > 0.0) ? sqrt(a.lam1 * gam / bx) : 0.0;
       if (!isfinite(gam)) { status = LSQ_ERR_BREAKDOWN; break; }
-      if (gam == 0.0 || gam <= a.tol2 * bx) { status = LSQ_OK; break; }
+      if (gam == 0.0 || gam <= a.tol2 * bx) {
+        if (exact) { status = LSQ_OK; break; }
+        exact = true;  // confirm on an FP64 gradient before stopping
+        continue;
+      }
+      if (!exact && gam <= a.exact2 * bx) exact = true;
       for (int c = threadIdx.x; c < dp; c += blockDim.x) {
         const double xc = S.vec[c];
         const double xn = c < d ? xc - a.mu * a.rh[c] + a.beta * (xc - S.vec2[c]) : 0.0;
@@ -255,6 +304,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
     a.out[1] = (double)status;
     a.out[2] = (double)passes;
     a.out[3] = est;
+    a.out[4] = (double)exact_passes;
   }
 }
 
@@ -277,15 +327,15 @@ __global__ void transpose_kernel(const double* __restrict__ W, int d, double* __
 // ------------------------------------------------------------------------------------
 typedef void (*solve_fn)(SolveArgs);
 
-template <typename TA>
+template <typename TA, bool MIXED>
 static void* pick_solve(int epl) {
   switch (epl) {
-    case 1: return (void*)solve_kernel<TA, 1>;
-    case 2: return (void*)solve_kernel<TA, 2>;
-    case 4: return (void*)solve_kernel<TA, 4>;
-    case 8: return (void*)solve_kernel<TA, 8>;
-    case 16: return (void*)solve_kernel<TA, 16>;
-    default: return (void*)solve_kernel<TA, 32>;
+    case 1: return (void*)solve_kernel<TA, 1, MIXED>;
+    case 2: return (void*)solve_kernel<TA, 2, MIXED>;
+    case 4: return (void*)solve_kernel<TA, 4, MIXED>;
+    case 8: return (void*)solve_kernel<TA, 8, MIXED>;
+    case 16: return (void*)solve_kernel<TA, 16, MIXED>;
+    default: return (void*)solve_kernel<TA, 32, MIXED>;
   }
 }
 
@@ -370,7 +420,8 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   lsq_solve_opts o;
   lsq_solve_opts_default(&o);
   if (opts_in) o = *opts_in;
-  if (o.precision != LSQ_PREC_F64) return LSQ_ERR_ARG;  // mixed precision: see below
+  if (o.precision != LSQ_PREC_F64 && o.precision != LSQ_PREC_MIXED) return LSQ_ERR_ARG;
+  const bool mixed = o.precision == LSQ_PREC_MIXED;
   const int d = (int)A->d;
   const bool refresh = (method != LSQ_PCG) && o.refresh;
   if (!refresh && !W) return LSQ_ERR_ARG;
@@ -401,7 +452,8 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   if (method == LSQ_IHS) beta = 0.0;
 
   const int epl = epl_for(d), dp = 32 * epl;
-  void* kern = A->dtype == LSQ_F64 ? pick_solve<double>(epl) : pick_solve<float>(epl);
+  void* kern = A->dtype == LSQ_F64 ? (mixed ? pick_solve<double, true>(epl) : pick_solve<double, false>(epl))
+                                   : (mixed ? pick_solve<float, true>(epl) : pick_solve<float, false>(epl));
   const size_t smem = solve_smem_bytes(dp);
   LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -455,11 +507,15 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   a.maxit = maxit;
   a.x0_zero = o.x0_zero ? 1 : 0;
   a.first_step = 1;
+  a.force_exact = 0;
+  a.refresh_every = o.refresh_every > 0 ? o.refresh_every : 8;
+  a.replace2 = 1e-6;  // replace after a 10^3 drop of the residual norm (FP32 passes err ~1e-6)
+  a.exact2 = 1e-8;    // IHS: FP64 gradients once the relative gradient is below 10^-4
   cudaStream_t s = ctx->stream;
   LSQ_CUDA_TRY(cudaEventRecord(ctx->ev0, s));
 
   double ms_sketch = 0.0;
-  int iters = 0, passes = 0, status = LSQ_ERR_MAXIT;
+  int iters = 0, passes = 0, exact_passes = 0, status = LSQ_ERR_MAXIT;
   double est = 0.0;
   if (!refresh) {
     a.W = W;
@@ -470,16 +526,17 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
     void* args[] = {&a};
     LSQ_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(P), dim3(LSQ_THREADS), args, smem, s));
     lsq_count_launch();
-    LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status, a.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 8, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status, a.out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 12, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     LSQ_CUDA_TRY(cudaEventRecord(ctx->ev1, s));
     LSQ_CUDA_TRY(cudaStreamSynchronize(s));
     const double* o4 = reinterpret_cast<const double*>(ctx->host_status);
-    const int errc = ctx->host_status[8];
+    const int errc = ctx->host_status[12];
     iters = (int)o4[0];
     status = errc ? errc : (int)o4[1];
     passes = (int)o4[2];
     est = o4[3];
+    exact_passes = (int)o4[4];
   } else {
     a.W = Wr;
     a.WT = WT;
@@ -507,20 +564,22 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
       transpose_kernel<<<dim3((d + 31) / 32, (d + 31) / 32), dim3(32, 8), 0, s>>>(Wr, d, WT);
       LSQ_LAUNCH_CHECK();
       a.first_step = t == 0;
+      a.force_exact = (t > 0 && est * est <= a.exact2 * a.lam1) ? 1 : 0;
       LSQ_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, s));
       void* args[] = {&a};
       LSQ_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(P), dim3(LSQ_THREADS), args, smem, s));
       lsq_count_launch();
     lsq_count_launch();
-      LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status, a.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 8, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status, a.out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 12, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
       LSQ_CUDA_TRY(cudaStreamSynchronize(s));
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e_a, e_b);
       ms_sketch += ms;
       const double* o4 = reinterpret_cast<const double*>(ctx->host_status);
-      const int errc = ctx->host_status[8];
+      const int errc = ctx->host_status[12];
       passes += (int)o4[2];
+      exact_passes += (int)o4[4];
       est = o4[3];
       const int stt = errc ? errc : (int)o4[1];
       iters = t + (int)o4[0];
@@ -540,7 +599,7 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
     info->iters = iters;
     info->status = status;
     info->passes = passes;
-    info->exact_passes = passes;
+    info->exact_passes = exact_passes;
     info->est_err = est;
     info->ms_total = ms_total;
     info->ms_sketch = ms_sketch;

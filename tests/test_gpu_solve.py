@@ -144,3 +144,48 @@ def test_maxit_and_breakdown_status(L, ctx):
     # zero right-hand side: x* = 0, converged at once
     x, info = L.lsq_solve(ctx, Ad, torch.zeros_like(bd), "pcg", Wm, tol=1e-10, maxit=50, m=120)
     assert info["status"] == 0 and info["iters"] == 0 and torch.all(x == 0)
+
+
+@pytest.mark.parametrize("kind,sketch_precision", [("srht", "f32"), ("sjlt", "f64"), ("gauss", "f32")])
+@pytest.mark.parametrize("tol", [1e-8, 1e-10, 1e-12])
+def test_mixed_pcg_reaches_tolerance(L, ctx, kind, sketch_precision, tol):
+    """FP32 inner passes + exact residual replacement reach the same tolerance as FP64."""
+    n, d, m = 20000, 128, 512
+    P = W.make_problem(n, d, 1e6, seed=3)
+    A, b = P["A"], P["b"]
+    xs = O.solve_direct(A, b)
+    Ad, bd = to_dev(A), to_dev(b)
+    _, Wm = L.lsq_factor(ctx, L.lsq_sketch(ctx, Ad, kind, m, 0, precision=sketch_precision))
+    x, info = L.lsq_solve(ctx, Ad, bd, "pcg", Wm, tol=tol, maxit=300, m=m, precision="mixed")
+    assert info["status"] == 0, info
+    assert O.rel_h_err(A, x.cpu().numpy(), xs) <= tol, info
+    assert 1 <= info["exact_passes"] < info["passes"]
+
+
+def test_mixed_pcg_fp32_storage(L, ctx):
+    P = W.make_problem(30000, 256, 1e5, seed=8, outlier_frac=0.05)
+    A32 = P["A"].astype(np.float32)
+    A64 = A32.astype(np.float64)
+    b = A64.T @ P["y"]
+    xs = O.solve_direct(A64, b)
+    Ad = to_dev(A32)
+    _, Wm = L.lsq_factor(ctx, L.lsq_sketch(ctx, Ad, "gauss", 1024, 0, precision="f32"))
+    x, info = L.lsq_solve(ctx, Ad, to_dev(b), "pcg", Wm, tol=1e-10, maxit=300, m=1024, precision="mixed")
+    assert info["status"] == 0 and O.rel_h_err(A64, x.cpu().numpy(), xs) <= 1e-10, info
+
+
+@pytest.mark.parametrize("method", ["ihs", "polyak"])
+def test_mixed_fixed_ihs(L, ctx, method):
+    A, b, xs, Ad, bd, Wm = _setup(L, ctx, 8000, 64, 1e4, "srht", 1024)
+    x, info = L.lsq_solve(ctx, Ad, bd, method, Wm, tol=1e-10, maxit=500, m=1024, precision="mixed")
+    assert info["status"] == 0 and O.rel_h_err(A, x.cpu().numpy(), xs) <= 1e-10, info
+    assert info["exact_passes"] < info["passes"]
+
+
+def test_mixed_refreshed_ihs(L, ctx):
+    P = W.make_problem(4096, 32, 1e3, seed=6)
+    A, b = P["A"], P["b"]
+    xs = O.solve_direct(A, b)
+    x, info = L.lsq_solve(ctx, to_dev(A), to_dev(b), "ihs", None, tol=1e-10, maxit=200, m=256, refresh=1,
+                          sketch_type="gauss", seed=3, precision="mixed")
+    assert info["status"] == 0 and O.rel_h_err(A, x.cpu().numpy(), xs) <= 1e-10, info
