@@ -112,16 +112,20 @@ __device__ void fused_pass_f32(const TA* __restrict__ A, int64_t ld, int d, int 
   // two rows in flight per warp while the registers allow it (raw FP64 rows are 2 registers
   // per element); p from shared memory at the widest rows
   constexpr bool PREFETCH = sizeof(TA) == 4 || EPL <= 16;
-  constexpr bool PV_REG = EPL <= 16;
+  constexpr bool PV_REG = EPL <= 8;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // FP32 copy of p in the (not yet used) reduction buffer: one conversion per entry per pass
+  float* pf = reinterpret_cast<float*>(wred);
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) pf[c] = (float)vec_s[c];
+  __syncthreads();
   float pv[PV_REG ? EPL : 1], acc[EPL];
-  TA cur[EPL], nxt[PREFETCH ? EPL : 1];
+  TA cur[EPL];
   bool ok[EPL];
 #pragma unroll
   for (int k = 0; k < EPL; ++k) {
     const int c = lane + 32 * k;
     ok[k] = c < d;
-    if (PV_REG) pv[PV_REG ? k : 0] = ok[k] ? (float)vec_s[c] : 0.0f;
+    if (PV_REG) pv[PV_REG ? k : 0] = ok[k] ? pf[c] : 0.0f;
     acc[k] = 0.0f;
   }
   double q = 0.0;
@@ -132,34 +136,32 @@ __device__ void fused_pass_f32(const TA* __restrict__ A, int64_t ld, int d, int 
     for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
   }
   for (; i < r1; i += LSQ_WARPS) {
+    if (!PREFETCH) {
+      const TA* a = A + i * ld;
+#pragma unroll
+      for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
+    }
+    // narrow the row first (its raw registers die here), then put the next row in flight
+    float af[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) af[k] = narrow_f32(cur[k]);
     if (PREFETCH) {
       const int64_t inext = i + LSQ_WARPS;
       if (inext < r1) {
         const TA* a = A + inext * ld;
 #pragma unroll
-        for (int k = 0; k < EPL; ++k) nxt[PREFETCH ? k : 0] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
+        for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
       }
-    } else {
-      const TA* a = A + i * ld;
-#pragma unroll
-      for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
     }
-    float af[EPL];
     float w = 0.0f;
 #pragma unroll
-    for (int k = 0; k < EPL; ++k) {
-      af[k] = narrow_f32(cur[k]);
-      w = fmaf(af[k], PV_REG ? pv[PV_REG ? k : 0] : (float)vec_s[lane + 32 * k], w);
-    }
+    for (int k = 0; k < EPL; ++k) w = fmaf(af[k], PV_REG ? pv[PV_REG ? k : 0] : pf[lane + 32 * k], w);
     w = warp_sumf(w);
 #pragma unroll
     for (int k = 0; k < EPL; ++k) acc[k] = fmaf(w, af[k], acc[k]);
     q = fma((double)w, (double)w, q);
-    if (PREFETCH) {
-#pragma unroll
-      for (int k = 0; k < EPL; ++k) cur[k] = nxt[PREFETCH ? k : 0];
-    }
   }
+  __syncthreads();  // every warp is done with pf before wred is overwritten
 #pragma unroll
   for (int k = 0; k < EPL; ++k) {
     const int c = lane + 32 * k;

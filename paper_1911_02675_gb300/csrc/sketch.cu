@@ -279,58 +279,120 @@ __global__ void select_write_kernel(const unsigned long long* __restrict__ keys,
   if (sel && pos < (unsigned long long)m) rows[pos] = i;
 }
 
-// two-level transform; TC = arithmetic type, DC columns per CTA, N2 = 2^logN2 rows per block
+// Two-level transform.  A CTA owns a tile of DC columns and a range of row blocks of
+// N2 = 2^logN2 rows.  Per block: the first (up to) 4 butterfly stages run in registers as
+// the block is loaded (16 consecutive rows of one column per unit, signs applied), the
+// remaining stages run as register radix-16 passes over a shared-memory copy, and the
+// sampled second level adds +-Z[k2(s)] into the CTA's partial of SA[s] for every sampled
+// row s.  Shared rows are DC elements (32 bytes) with 32 bytes of padding after every 16
+// rows, which keeps all three access patterns free of bank conflicts.
+constexpr int SRHT_THREADS = 512;
+
+__device__ __forceinline__ int zphys(int row, int dc) { return (row + (row >> 4)) * dc; }
+
+template <typename TC, int K>
+__device__ __forceinline__ void butterflies(TC* v) {
+#pragma unroll
+  for (int h = 1; h < (1 << K); h <<= 1)
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j)
+      if (!(j & h)) {
+        const TC a = v[j], b = v[j + h];
+        v[j] = a + b;
+        v[j + h] = a - b;
+      }
+}
+
+// stages over row bits [b, b + K) on the shared block
+template <typename TC, int DC, int K>
+__device__ __forceinline__ void radix_pass(TC* Z, int N2, int b) {
+  const int units = (N2 >> K) * DC;
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int c = u % DC, q = u / DC;
+    const int base = ((q >> b) << (b + K)) | (q & ((1 << b) - 1));
+    TC v[1 << K];
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j) v[j] = Z[zphys(base + (j << b), DC) + c];
+    butterflies<TC, K>(v);
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j) Z[zphys(base + (j << b), DC) + c] = v[j];
+  }
+}
+
+// load a block (signs applied, zero past n) with the stages over row bits [0, K)
+template <typename TC, int DC, int K>
+__device__ __forceinline__ void load_pass(TC* Z, const void* A, int dtype, int64_t n, int d, int64_t ld, int c0,
+                                          int64_t row0, int N2, const uint32_t* signbits) {
+  const int units = (N2 >> K) * DC;
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int c = u % DC, q = u / DC;
+    const int64_t r = row0 + ((int64_t)q << K);
+    const bool col_ok = c0 + c < d;
+    const uint32_t word = (r < n) ? signbits[r >> 5] : 0u;
+    const int sh = (int)(r & 31);
+    TC v[1 << K];
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j) {
+      const int64_t i = r + j;
+      TC x = (TC)0;
+      if (col_ok && i < n) {
+        x = load_as<TC>(A, i * ld + c0 + c, dtype);
+        if ((word >> (sh + j)) & 1u) x = -x;
+      }
+      v[j] = x;
+    }
+    butterflies<TC, K>(v);
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j) Z[zphys((q << K) + j, DC) + c] = v[j];
+  }
+}
+
 template <typename TC, int DC>
-__global__ void __launch_bounds__(256) srht_transform_kernel(const void* __restrict__ A, int dtype, int64_t n, int d,
-                                                             int64_t ld, int logN2, int64_t N1, int64_t blocks_per_group,
-                                                             const uint32_t* __restrict__ signbits,
-                                                             const int64_t* __restrict__ rows, int m,
-                                                             TC* __restrict__ part) {
+__global__ void __launch_bounds__(SRHT_THREADS, 1) srht_transform_kernel(
+    const void* __restrict__ A, int dtype, int64_t n, int d, int64_t ld, int logN2, int64_t N1,
+    int64_t blocks_per_group, const uint32_t* __restrict__ signbits, const int64_t* __restrict__ rows, int m,
+    TC* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N2 = 1 << logN2;
-  TC* Z = reinterpret_cast<TC*>(smem_raw);  // [N2][DC]
-  TC* Y = Z + (size_t)N2 * DC;              // [m][DC]
+  TC* Z = reinterpret_cast<TC*>(smem_raw);                   // padded [N2][DC]
+  TC* Y = Z + (size_t)zphys(N2, DC);                         // [m][DC]
+  uint32_t* k1s = reinterpret_cast<uint32_t*>(Y + (size_t)m * DC);  // [m]
+  uint16_t* k2s = reinterpret_cast<uint16_t*>(k1s + m);             // [m]
   const int c0 = blockIdx.x * DC;
   const int64_t b_begin = (int64_t)blockIdx.y * blocks_per_group;
   const int64_t b_end = min(N1, b_begin + blocks_per_group);
   for (int e = threadIdx.x; e < m * DC; e += blockDim.x) Y[e] = (TC)0;
-
+  for (int s = threadIdx.x; s < m; s += blockDim.x) {
+    const int64_t k = rows[s];
+    k1s[s] = (uint32_t)(k >> logN2);
+    k2s[s] = (uint16_t)(k & (N2 - 1));
+  }
+  const int k0 = logN2 < 4 ? logN2 : 4;
   for (int64_t i1 = b_begin; i1 < b_end; ++i1) {
-    __syncthreads();
+    __syncthreads();  // Z is free (previous block's second level is done)
     const int64_t row0 = i1 << logN2;
-    for (int e = threadIdx.x; e < N2 * DC; e += blockDim.x) {
-      const int k = e / DC, c = e % DC;
-      const int64_t i = row0 + k;
-      TC v = (TC)0;
-      if (i < n && c0 + c < d) {
-        v = load_as<TC>(A, i * ld + c0 + c, dtype);
-        if ((signbits[i >> 5] >> (i & 31)) & 1u) v = -v;
+    switch (k0) {
+      case 4: load_pass<TC, DC, 4>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
+      case 3: load_pass<TC, DC, 3>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
+      case 2: load_pass<TC, DC, 2>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
+      case 1: load_pass<TC, DC, 1>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
+      default: load_pass<TC, DC, 0>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
+    }
+    for (int b = k0; b < logN2; b += 4) {
+      __syncthreads();
+      switch (logN2 - b < 4 ? logN2 - b : 4) {
+        case 4: radix_pass<TC, DC, 4>(Z, N2, b); break;
+        case 3: radix_pass<TC, DC, 3>(Z, N2, b); break;
+        case 2: radix_pass<TC, DC, 2>(Z, N2, b); break;
+        default: radix_pass<TC, DC, 1>(Z, N2, b); break;
       }
-      Z[e] = v;
     }
     __syncthreads();
-    // unnormalised Sylvester butterflies, natural order
-    for (int h = 1; h < N2; h <<= 1) {
-      for (int e = threadIdx.x; e < (N2 >> 1) * DC; e += blockDim.x) {
-        const int p = e / DC, c = e % DC;
-        const int k = ((p / h) * 2 * h) + (p % h);
-        const TC u = Z[k * DC + c], v = Z[(k + h) * DC + c];
-        Z[k * DC + c] = u + v;
-        Z[(k + h) * DC + c] = u - v;
-      }
-      __syncthreads();
-    }
-    // second level, sampled rows only
-    for (int s = threadIdx.x; s < m; s += blockDim.x) {
-      const int64_t k = rows[s];
-      const int64_t k1 = k >> logN2;
-      const int k2 = (int)(k & (N2 - 1));
-      const bool neg = (__popcll((unsigned long long)(k1 & i1)) & 1) != 0;
-#pragma unroll
-      for (int c = 0; c < DC; ++c) {
-        const TC z = Z[k2 * DC + c];
-        Y[s * DC + c] += neg ? -z : z;
-      }
+    const uint32_t i1w = (uint32_t)i1;
+    for (int e = threadIdx.x; e < m * DC; e += blockDim.x) {
+      const int s = e / DC, c = e % DC;
+      const TC z = Z[zphys(k2s[s], DC) + c];
+      Y[e] += (__popc(k1s[s] & i1w) & 1) ? -z : z;
     }
   }
   __syncthreads();
@@ -373,11 +435,19 @@ __global__ void sjlt_hash_kernel(int64_t n, int m, int s, uint64_t seed, uint32_
   }
 }
 
+// The CTA owns a tile of DC columns and a range of rows.  512 threads cover 512/DC rows
+// at a time (DC threads per row, one column each); U such row sets are loaded (element,
+// sign word, s positions) before any of them is scattered, so that each thread keeps U
+// independent loads in flight.
+constexpr int SJLT_THREADS = 512;
+constexpr int SJLT_UNROLL = 4;
+
 template <typename TC, int DC>
-__global__ void __launch_bounds__(256) sjlt_scatter_kernel(const void* __restrict__ A, int dtype, int64_t n, int d,
-                                                           int64_t ld, int m, int s, const int32_t* __restrict__ h,
-                                                           const uint32_t* __restrict__ signs, int64_t rows_per_group,
-                                                           TC* __restrict__ part) {
+__global__ void __launch_bounds__(SJLT_THREADS, 1) sjlt_scatter_kernel(const void* __restrict__ A, int dtype,
+                                                                      int64_t n, int d, int64_t ld, int m, int s,
+                                                                      const int32_t* __restrict__ h,
+                                                                      const uint32_t* __restrict__ signs,
+                                                                      int64_t rows_per_group, TC* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* Y = reinterpret_cast<TC*>(smem_raw);  // [m][DC]
   const int c0 = blockIdx.x * DC;
@@ -385,15 +455,29 @@ __global__ void __launch_bounds__(256) sjlt_scatter_kernel(const void* __restric
   const int64_t i_end = min(n, i_begin + rows_per_group);
   for (int e = threadIdx.x; e < m * DC; e += blockDim.x) Y[e] = (TC)0;
   __syncthreads();
-  constexpr int RPI = 256 / DC;  // rows per step
+  constexpr int RPI = SJLT_THREADS / DC;  // rows per step
   const int rl = threadIdx.x / DC, c = threadIdx.x % DC;
   const bool col_ok = (c0 + c) < d;
-  for (int64_t i = i_begin + rl; i < i_end; i += RPI) {
-    const TC a = col_ok ? load_as<TC>(A, i * ld + c0 + c, dtype) : (TC)0;
-    const uint32_t sw = signs[i];
+  for (int64_t i0 = i_begin; i0 < i_end; i0 += (int64_t)RPI * SJLT_UNROLL) {
+    TC a[SJLT_UNROLL];
+    uint32_t sw[SJLT_UNROLL];
+#pragma unroll
+    for (int u = 0; u < SJLT_UNROLL; ++u) {
+      const int64_t i = i0 + rl + (int64_t)u * RPI;
+      const bool ok = i < i_end;
+      a[u] = (ok && col_ok) ? load_as<TC>(A, i * ld + c0 + c, dtype) : (TC)0;
+      sw[u] = ok ? __ldg(signs + i) : 0u;
+    }
     for (int k = 0; k < s; ++k) {
-      const int target = h[i * s + k];
-      atomicAdd(&Y[target * DC + c], ((sw >> k) & 1u) ? -a : a);
+      int32_t tgt[SJLT_UNROLL];
+#pragma unroll
+      for (int u = 0; u < SJLT_UNROLL; ++u) {
+        const int64_t i = i0 + rl + (int64_t)u * RPI;
+        tgt[u] = i < i_end ? __ldg(h + i * s + k) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < SJLT_UNROLL; ++u)
+        if (tgt[u] >= 0) atomicAdd(&Y[tgt[u] * DC + c], ((sw[u] >> k) & 1u) ? -a[u] : a[u]);
     }
   }
   __syncthreads();
@@ -447,17 +531,22 @@ static lsq_status gauss_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t s
   return LSQ_OK;
 }
 
+static size_t srht_smem_bytes(int logN2, int m, int dc, size_t es) {
+  const size_t N2 = (size_t)1 << logN2;
+  return (N2 + (N2 >> 4) + 1) * dc * es + (size_t)m * dc * es + (size_t)m * 6 + 64;
+}
+
 template <typename TC, int DC>
 static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN2, int64_t N1,
                               const uint32_t* signbits, const int64_t* rows, TC* part, int groups,
                               int64_t blocks_per_group) {
   const int d = (int)A->d;
-  const size_t smem = (size_t)((1 << logN2) + m) * DC * sizeof(TC);
+  const size_t smem = srht_smem_bytes(logN2, m, DC, sizeof(TC));
   auto kern = srht_transform_kernel<TC, DC>;
   LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(lsq_ceil_div(d, DC), groups);
-  kern<<<grid, 256, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, logN2, N1, blocks_per_group, signbits,
-                                          rows, m, part);
+  kern<<<grid, SRHT_THREADS, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, logN2, N1, blocks_per_group,
+                                                   signbits, rows, m, part);
   LSQ_LAUNCH_CHECK();
   return LSQ_OK;
 }
@@ -469,17 +558,19 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
   int logN = 0;
   while (N < A->n) { N <<= 1; ++logN; }
   if (m > N) return LSQ_ERR_ARG;
-  // shared memory budget: (N2 + m) * DC * sizeof(TC) <= 200 KB, DC as large as possible
-  const size_t budget = 200 * 1024;
-  int DC = (int)(sizeof(TC) == 8 ? 4 : 8);
+  // shared memory: padded block + sampled accumulators + sample positions <= 220 KB;
+  // 32-byte rows (DC * sizeof(TC) = 32) unless m forces narrower tiles
+  const size_t budget = 220 * 1024;
+  int DC = (int)(32 / sizeof(TC));
   int logN2 = std::min(logN, 11);
-  auto fits = [&](int dc, int l2) { return (size_t)((1ll << l2) + m) * dc * sizeof(TC) <= budget; };
+  auto fits = [&](int dc, int l2) { return srht_smem_bytes(l2, m, dc, sizeof(TC)) <= budget; };
   while (DC > 1 && !fits(DC, logN2)) DC >>= 1;
   while (logN2 > 0 && !fits(DC, logN2)) --logN2;
-  if (!fits(DC, logN2)) return LSQ_ERR_ARG;
+  if (!fits(DC, logN2) || logN2 > 16) return LSQ_ERR_ARG;
   const int64_t N1 = N >> logN2;
   const int tiles = lsq_ceil_div(d, DC);
-  int64_t groups = std::max<int64_t>(1, (ctx->sm_count + tiles - 1) / tiles);
+  // about eight waves of one CTA per SM, so the last partial wave costs little
+  int64_t groups = std::max<int64_t>(1, (8 * (int64_t)ctx->sm_count + tiles - 1) / tiles);
   groups = std::min(groups, N1);
   const int64_t cap = std::max<int64_t>(1, ((int64_t)256 << 20) / ((int64_t)m * d * (int64_t)sizeof(TC)));
   groups = std::min(groups, cap);
@@ -544,7 +635,8 @@ static lsq_status sjlt_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, c
   auto kern = sjlt_scatter_kernel<TC, DC>;
   LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(lsq_ceil_div(d, DC), groups);
-  kern<<<grid, 256, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, s, h, signs, rows_per_group, part);
+  kern<<<grid, SJLT_THREADS, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, s, h, signs, rows_per_group,
+                                                  part);
   LSQ_LAUNCH_CHECK();
   return LSQ_OK;
 }
@@ -558,8 +650,8 @@ static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint
   while (DC > 1 && (size_t)m * DC * sizeof(TC) > budget) DC >>= 1;
   if ((size_t)m * DC * sizeof(TC) > budget) return LSQ_ERR_ARG;
   const int tiles = lsq_ceil_div(d, DC);
-  int64_t groups = std::max<int64_t>(1, (2 * ctx->sm_count + tiles - 1) / tiles);
-  groups = std::min<int64_t>(groups, (n + 255) / 256);
+  int64_t groups = std::max<int64_t>(1, (8 * (int64_t)ctx->sm_count + tiles - 1) / tiles);
+  groups = std::min<int64_t>(groups, (n + 2047) / 2048);
   const int64_t cap = std::max<int64_t>(1, ((int64_t)256 << 20) / ((int64_t)m * d * (int64_t)sizeof(TC)));
   groups = std::max<int64_t>(1, std::min(groups, cap));
   const int64_t rows_per_group = (n + groups - 1) / groups;

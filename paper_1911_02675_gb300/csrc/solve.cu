@@ -79,7 +79,7 @@ struct SolveSmem {
 // residual); IHS / Polyak-IHS compute the gradient in FP32 until it is small relative to
 // <b, x> and in FP64 after that (their update has no recursive residual to correct).
 template <typename TA, int EPL, bool MIXED>
-__global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
+__global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel(SolveArgs a) {
   extern __shared__ __align__(16) double smem[];
   const int dp = a.dp, d = a.d;
   SolveSmem S;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
     if (!a.x0_zero) {
       for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec[c] = c < d ? a.x[c] : 0.0;
       __syncthreads();
-      fused_pass<TA, EPL, !MIXED>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+      fused_pass<TA, EPL, (!MIXED && EPL <= 4)>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
       ++passes;
       ++exact_passes;
       if (grid_barrier(a.bar, P, a.err)) return;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
       if (MIXED) {
         fused_pass_f32<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
       } else {
-        fused_pass<TA, EPL, !MIXED>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+        fused_pass<TA, EPL, (!MIXED && EPL <= 4)>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
         ++exact_passes;
       }
       ++passes;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
         // replace the recursive residual by b - H x evaluated in FP64
         for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec2[c] = c < d ? a.x[c] : 0.0;
         __syncthreads();
-        fused_pass<TA, EPL, !MIXED>(A, a.ld, d, dp, r0, r1, S.vec2, S.wred, S.qred, a.part, P, cta);
+        fused_pass<TA, EPL, (!MIXED && EPL <= 4)>(A, a.ld, d, dp, r0, r1, S.vec2, S.wred, S.qred, a.part, P, cta);
         ++passes;
         ++exact_passes;
         if (grid_barrier(a.bar, P, a.err)) return;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, 1) solve_kernel(SolveArgs a) {
     bool exact = !MIXED || a.force_exact;
     while (it < a.maxit) {
       if (exact) {
-        fused_pass<TA, EPL, !MIXED>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+        fused_pass<TA, EPL, (!MIXED && EPL <= 4)>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
         ++exact_passes;
       } else {
         fused_pass_f32<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
