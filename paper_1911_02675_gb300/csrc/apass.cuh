@@ -183,6 +183,143 @@ __device__ void fused_pass_f32(const TA* __restrict__ A, int64_t ld, int d, int 
   __syncthreads();
 }
 
+
+// ------------------------------------------------------------------------------------
+// Exact pass in double-FP32 arithmetic (the residual replacements of the mixed solve).
+// Each FP64 element a is split into a head of 21 significant bits and the FP32 rounding
+// of its remaining 32 mantissa bits (about 45 significant bits in all); products are made
+// error-free with an FMA (TwoProduct) and sums are carried as unevaluated (hi, lo) FP32
+// pairs with Knuth's TwoSum (Dekker 1971; Knuth, TAOCP vol. 2).  v = A^T (A x) comes out
+// with a relative error of a few 1e-14 per component, far below what the solver's
+// tolerance needs, at the throughput of the FP32 and integer pipes.
+// Elements with |a| < 2^-74 keep only their head (their tail would underflow FP32).
+// ------------------------------------------------------------------------------------
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void split_df(double x, float& head, float& tail) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t lo32 = (uint32_t)u, hi32 = (uint32_t)(u >> 32);
+  const uint32_t sign = hi32 & 0x80000000u;
+  const uint32_t e = (hi32 >> 20) & 0x7FFu;
+  const uint32_t ec = min(max(e, 896u), 1151u);
+  head = __uint_as_float(sign | ((ec - 896u) << 23) | ((hi32 & 0xFFFFFu) << 3));
+  // tail = lo32 * 2^(e - 1075), sign of x; zero when that scale leaves the FP32 range
+  const float scale = __uint_as_float(sign | ((e - 948u) << 23));
+  tail = (e >= 949u && e <= 1151u) ? __fmul_rn(__uint2float_rn(lo32), scale) : 0.0f;
+}
+
+__device__ __forceinline__ void split_df(float x, float& head, float& tail) {
+  head = x;
+  tail = 0.0f;
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (sh, sl) += (ah + al) * (bh + bl), dropping only al * bl
+__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float p = __fmul_rn(ah, bh);
+  const float pe = __fmaf_rn(ah, bh, -p);
+  const float cross = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, pe));
+  float s, e;
+  two_sum(sh, p, s, e);
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(e, cross));
+}
+
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  ah = s;
+  al = __fadd_rn(al, __fadd_rn(e, bl));
+}
+
+// v partials only (the residual needs no q); part[dp * P + cta] is written as 0
+template <typename TA, int EPL>
+__device__ void fused_pass_df(const TA* __restrict__ A, int64_t ld, int d, int dp, int64_t r0, int64_t r1,
+                              const double* vec_s, double* wred, double* qred, double* part, int P, int cta) {
+  constexpr bool PREFETCH = sizeof(TA) == 4 || EPL <= 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* xs = reinterpret_cast<float2*>(wred);  // (head, tail) of x, dp entries
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+    const double xv = vec_s[c];
+    const float xh = (float)xv;
+    xs[c] = make_float2(xh, (float)(xv - (double)xh));
+  }
+  __syncthreads();
+  float vh[EPL], vl[EPL];
+  TA cur[EPL];
+  bool ok[EPL];
+#pragma unroll
+  for (int k = 0; k < EPL; ++k) {
+    ok[k] = lane + 32 * k < d;
+    vh[k] = 0.0f;
+    vl[k] = 0.0f;
+  }
+  int64_t i = r0 + warp;
+  if (PREFETCH && i < r1) {
+    const TA* a = A + i * ld;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
+  }
+  for (; i < r1; i += LSQ_WARPS) {
+    if (!PREFETCH) {
+      const TA* a = A + i * ld;
+#pragma unroll
+      for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
+    }
+    float ah[EPL], al[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) split_df(cur[k], ah[k], al[k]);
+    if (PREFETCH) {
+      const int64_t inext = i + LSQ_WARPS;
+      if (inext < r1) {
+        const TA* a = A + inext * ld;
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
+      }
+    }
+    float wh = 0.0f, wl = 0.0f;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) {
+      const float2 xv = xs[lane + 32 * k];
+      df_fma(ah[k], al[k], xv.x, xv.y, wh, wl);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, wh, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, wl, o);
+      df_add(wh, wl, oh, ol);
+    }
+    // renormalise w to a clean (head, tail) pair
+    float nh, nl;
+    two_sum(wh, wl, nh, nl);
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) df_fma(ah[k], al[k], nh, nl, vh[k], vl[k]);
+  }
+  __syncthreads();  // every warp is done with xs before wred is overwritten
+#pragma unroll
+  for (int k = 0; k < EPL; ++k) {
+    const int c = lane + 32 * k;
+    if (c < dp) wred[warp * dp + c] = (double)vh[k] + (double)vl[k];
+  }
+  if (lane == 0) qred[warp] = 0.0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+    double sum = 0.0;
+#pragma unroll
+    for (int w2 = 0; w2 < LSQ_WARPS; ++w2) sum += wred[w2 * dp + c];
+    part[(int64_t)c * P + cta] = sum;
+  }
+  if (threadIdx.x == 0) part[(int64_t)dp * P + cta] = 0.0;
+  __syncthreads();
+}
+
 // sum_{j < P} src[j] by one warp, fixed order
 __device__ __forceinline__ double warp_sum_strip(const double* src, int P) {
   const int lane = threadIdx.x & 31;

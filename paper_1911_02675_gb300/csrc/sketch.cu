@@ -6,6 +6,7 @@
 // to run (SJLT: up to the order of its shared-memory additions).
 #include <math.h>
 
+#include "apass.cuh"
 #include "common.cuh"
 
 namespace {
@@ -17,6 +18,14 @@ template <typename T>
 __device__ __forceinline__ T load_as(const void* base, int64_t idx, int dtype) {
   if (dtype == LSQ_F64) return (T)__ldg(reinterpret_cast<const double*>(base) + idx);
   return (T)__ldg(reinterpret_cast<const float*>(base) + idx);
+}
+
+// FP32 arithmetic on FP64 data: narrow with integer operations (the FP64->FP32 conversion
+// instruction runs at the FP64 rate on this part)
+template <>
+__device__ __forceinline__ float load_as<float>(const void* base, int64_t idx, int dtype) {
+  if (dtype == LSQ_F64) return lsq_apass::narrow_f32(__ldg(reinterpret_cast<const double*>(base) + idx));
+  return __ldg(reinterpret_cast<const float*>(base) + idx);
 }
 
 // 53 random bits -> (k + 1/2) 2^-53 in the open unit interval
@@ -319,31 +328,48 @@ __device__ __forceinline__ void radix_pass(TC* Z, int N2, int b) {
   }
 }
 
-// load a block (signs applied, zero past n) with the stages over row bits [0, K)
+// load a block (signs applied, zero past n) with the stages over row bits [0, K); each
+// thread issues the loads of two units before it uses any of them
+template <typename TC, int DC, int K>
+__device__ __forceinline__ void load_unit(TC* v, const void* A, int dtype, int64_t n, int d, int64_t ld, int c0,
+                                          int64_t row0, const uint32_t* signbits, int u) {
+  const int c = u % DC, q = u / DC;
+  const int64_t r = row0 + ((int64_t)q << K);
+  const bool col_ok = c0 + c < d;
+  const uint32_t word = (r < n) ? __ldg(signbits + (r >> 5)) : 0u;
+  const int sh = (int)(r & 31);
+#pragma unroll
+  for (int j = 0; j < (1 << K); ++j) {
+    const int64_t i = r + j;
+    TC x = (TC)0;
+    if (col_ok && i < n) {
+      x = load_as<TC>(A, i * ld + c0 + c, dtype);
+      if ((word >> (sh + j)) & 1u) x = -x;
+    }
+    v[j] = x;
+  }
+}
+
+template <typename TC, int DC, int K>
+__device__ __forceinline__ void store_unit(TC* Z, TC* v, int u) {
+  const int c = u % DC, q = u / DC;
+  butterflies<TC, K>(v);
+#pragma unroll
+  for (int j = 0; j < (1 << K); ++j) Z[zphys((q << K) + j, DC) + c] = v[j];
+}
+
 template <typename TC, int DC, int K>
 __device__ __forceinline__ void load_pass(TC* Z, const void* A, int dtype, int64_t n, int d, int64_t ld, int c0,
                                           int64_t row0, int N2, const uint32_t* signbits) {
   const int units = (N2 >> K) * DC;
-  for (int u = threadIdx.x; u < units; u += blockDim.x) {
-    const int c = u % DC, q = u / DC;
-    const int64_t r = row0 + ((int64_t)q << K);
-    const bool col_ok = c0 + c < d;
-    const uint32_t word = (r < n) ? signbits[r >> 5] : 0u;
-    const int sh = (int)(r & 31);
-    TC v[1 << K];
-#pragma unroll
-    for (int j = 0; j < (1 << K); ++j) {
-      const int64_t i = r + j;
-      TC x = (TC)0;
-      if (col_ok && i < n) {
-        x = load_as<TC>(A, i * ld + c0 + c, dtype);
-        if ((word >> (sh + j)) & 1u) x = -x;
-      }
-      v[j] = x;
-    }
-    butterflies<TC, K>(v);
-#pragma unroll
-    for (int j = 0; j < (1 << K); ++j) Z[zphys((q << K) + j, DC) + c] = v[j];
+  const int T = blockDim.x;
+  for (int u = threadIdx.x; u < units; u += 2 * T) {
+    TC v0[1 << K], v1[1 << K];
+    const bool two = u + T < units;
+    load_unit<TC, DC, K>(v0, A, dtype, n, d, ld, c0, row0, signbits, u);
+    if (two) load_unit<TC, DC, K>(v1, A, dtype, n, d, ld, c0, row0, signbits, u + T);
+    store_unit<TC, DC, K>(Z, v0, u);
+    if (two) store_unit<TC, DC, K>(Z, v1, u + T);
   }
 }
 
@@ -436,13 +462,12 @@ __global__ void sjlt_hash_kernel(int64_t n, int m, int s, uint64_t seed, uint32_
 }
 
 // The CTA owns a tile of DC columns and a range of rows.  512 threads cover 512/DC rows
-// at a time (DC threads per row, one column each); U such row sets are loaded (element,
-// sign word, s positions) before any of them is scattered, so that each thread keeps U
-// independent loads in flight.
+// at a time (DC threads per row, one column each).  For U such row sets every load (the
+// element, the sign word and all s positions) is issued before the first shared-memory
+// addition, so each thread has U * (s + 2) independent loads in flight.
 constexpr int SJLT_THREADS = 512;
-constexpr int SJLT_UNROLL = 4;
 
-template <typename TC, int DC>
+template <typename TC, int DC, int SMAX, int U>
 __global__ void __launch_bounds__(SJLT_THREADS, 1) sjlt_scatter_kernel(const void* __restrict__ A, int dtype,
                                                                       int64_t n, int d, int64_t ld, int m, int s,
                                                                       const int32_t* __restrict__ h,
@@ -458,27 +483,24 @@ __global__ void __launch_bounds__(SJLT_THREADS, 1) sjlt_scatter_kernel(const voi
   constexpr int RPI = SJLT_THREADS / DC;  // rows per step
   const int rl = threadIdx.x / DC, c = threadIdx.x % DC;
   const bool col_ok = (c0 + c) < d;
-  for (int64_t i0 = i_begin; i0 < i_end; i0 += (int64_t)RPI * SJLT_UNROLL) {
-    TC a[SJLT_UNROLL];
-    uint32_t sw[SJLT_UNROLL];
+  for (int64_t i0 = i_begin; i0 < i_end; i0 += (int64_t)RPI * U) {
+    TC a[U];
+    uint32_t sw[U];
+    int32_t tgt[U][SMAX];
 #pragma unroll
-    for (int u = 0; u < SJLT_UNROLL; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int64_t i = i0 + rl + (int64_t)u * RPI;
       const bool ok = i < i_end;
       a[u] = (ok && col_ok) ? load_as<TC>(A, i * ld + c0 + c, dtype) : (TC)0;
       sw[u] = ok ? __ldg(signs + i) : 0u;
-    }
-    for (int k = 0; k < s; ++k) {
-      int32_t tgt[SJLT_UNROLL];
 #pragma unroll
-      for (int u = 0; u < SJLT_UNROLL; ++u) {
-        const int64_t i = i0 + rl + (int64_t)u * RPI;
-        tgt[u] = i < i_end ? __ldg(h + i * s + k) : -1;
-      }
-#pragma unroll
-      for (int u = 0; u < SJLT_UNROLL; ++u)
-        if (tgt[u] >= 0) atomicAdd(&Y[tgt[u] * DC + c], ((sw[u] >> k) & 1u) ? -a[u] : a[u]);
+      for (int k = 0; k < SMAX; ++k) tgt[u][k] = (ok && k < s) ? __ldg(h + i * s + k) : -1;
     }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < SMAX; ++k)
+        if (tgt[u][k] >= 0) atomicAdd(&Y[tgt[u][k] * DC + c], ((sw[u] >> k) & 1u) ? -a[u] : a[u]);
   }
   __syncthreads();
   TC* out = part + (int64_t)blockIdx.y * m * d;
@@ -558,9 +580,9 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
   int logN = 0;
   while (N < A->n) { N <<= 1; ++logN; }
   if (m > N) return LSQ_ERR_ARG;
-  // shared memory: padded block + sampled accumulators + sample positions <= 220 KB;
-  // 32-byte rows (DC * sizeof(TC) = 32) unless m forces narrower tiles
-  const size_t budget = 220 * 1024;
+  // shared memory: padded block + sampled accumulators + sample positions within the
+  // 227 KB a CTA may opt into; 32-byte rows (DC * sizeof(TC) = 32) unless m forces narrower
+  const size_t budget = 232448 - 1024;
   int DC = (int)(32 / sizeof(TC));
   int logN2 = std::min(logN, 11);
   auto fits = [&](int dc, int l2) { return srht_smem_bytes(l2, m, dc, sizeof(TC)) <= budget; };
@@ -632,11 +654,18 @@ static lsq_status sjlt_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, c
                               const uint32_t* signs, TC* part, int groups, int64_t rows_per_group) {
   const int d = (int)A->d;
   const size_t smem = (size_t)m * DC * sizeof(TC);
-  auto kern = sjlt_scatter_kernel<TC, DC>;
-  LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(lsq_ceil_div(d, DC), groups);
-  kern<<<grid, SJLT_THREADS, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, s, h, signs, rows_per_group,
-                                                  part);
+  if (s <= 8) {
+    auto kern = sjlt_scatter_kernel<TC, DC, 8, 4>;
+    LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, SJLT_THREADS, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, s, h, signs,
+                                                    rows_per_group, part);
+  } else {
+    auto kern = sjlt_scatter_kernel<TC, DC, 32, 1>;
+    LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, SJLT_THREADS, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, s, h, signs,
+                                                    rows_per_group, part);
+  }
   LSQ_LAUNCH_CHECK();
   return LSQ_OK;
 }

@@ -158,6 +158,12 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
     __syncthreads();
   };
 
+  // a pass whose v is accurate to (nearly) FP64: native FP64, or double-FP32 in MIXED mode
+  auto exact_pass = [&](const double* vec) {
+    if (MIXED) fused_pass_df<TA, EPL>(A, a.ld, d, dp, r0, r1, vec, S.wred, S.qred, a.part, P, cta);
+    else fused_pass<TA, EPL, (EPL <= 4)>(A, a.ld, d, dp, r0, r1, vec, S.wred, S.qred, a.part, P, cta);
+  };
+
   int status = LSQ_ERR_MAXIT;
   int it = 0;
   double est = 0.0;
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
     if (!a.x0_zero) {
       for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec[c] = c < d ? a.x[c] : 0.0;
       __syncthreads();
-      fused_pass<TA, EPL, (!MIXED && EPL <= 4)>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+      exact_pass(S.vec);
       ++passes;
       ++exact_passes;
       if (grid_barrier(a.bar, P, a.err)) return;
@@ -224,7 +230,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
         // replace the recursive residual by b - H x evaluated in FP64
         for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec2[c] = c < d ? a.x[c] : 0.0;
         __syncthreads();
-        fused_pass<TA, EPL, (!MIXED && EPL <= 4)>(A, a.ld, d, dp, r0, r1, S.vec2, S.wred, S.qred, a.part, P, cta);
+        exact_pass(S.vec2);
         ++passes;
         ++exact_passes;
         if (grid_barrier(a.bar, P, a.err)) return;
@@ -259,7 +265,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
     bool exact = !MIXED || a.force_exact;
     while (it < a.maxit) {
       if (exact) {
-        fused_pass<TA, EPL, (!MIXED && EPL <= 4)>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+        exact_pass(S.vec);
         ++exact_passes;
       } else {
         fused_pass_f32<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
