@@ -37,7 +37,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=os.environ.get("LSQ_BENCH_PRECISION", "f64"), choices=["f64", "mixed"])
     ap.add_argument("--sketch", default="srht", choices=["srht", "sjlt", "gauss"])
-    ap.add_argument("--sketch-precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--sketch-precision", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--a-dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--outlier-frac", type=float, default=0.0)
     ap.add_argument("--m", type=int, default=4096)
     ap.add_argument("--n-log2", type=int, default=20)
     ap.add_argument("--d", type=int, default=512)
@@ -123,6 +125,8 @@ def dist_info():
 
 def make_inputs(args, seed):
     n = 1 << args.n_log2
+    if args.a_dtype == "f32":
+        return None  # drawn on the device (run_ours)
     P = WL.make_problem(n, args.d, args.sigma_max, seed=seed)
     return P
 
@@ -186,11 +190,11 @@ def run_reference(args):
 
 def workload_config(args, parallelism):
     n = 1 << args.n_log2
-    return {"workload": f"fp64_{n}x{args.d}_{args.sketch}{args.m}_pcg",
+    return {"workload": f"{'fp64' if args.a_dtype == 'f64' else 'fp32'}_{n}x{args.d}_{args.sketch}{args.m}_pcg",
             "n": n, "d": args.d, "sigma_max": args.sigma_max, "sketch": args.sketch, "m": args.m,
             "sketch_precision": args.sketch_precision, "precision": args.precision, "method": "pcg",
-            "tol": args.tol, "A_dtype": "f64", "l2": "inputs larger than L2 (A = "
-            f"{n * args.d * 8 / 2**30:.1f} GiB), no flush", "parallelism": parallelism}
+            "tol": args.tol, "A_dtype": args.a_dtype, "l2": "inputs larger than L2 (A = "
+            f"{n * args.d * (8 if args.a_dtype == 'f64' else 4) / 2**30:.1f} GiB), no flush", "parallelism": parallelism}
 
 
 # ------------------------------------------------------------------------------ our arm
@@ -208,10 +212,17 @@ def run_ours(args):
 
     hbm, _, peak_kind = peaks()
     P = make_inputs(args, seed=1 + rank)
-    A_host = torch.from_numpy(P["A"])
-    b_host = torch.from_numpy(P["b"])
-    A = A_host.to(dev)
-    b = b_host.to(dev)
+    if P is None:
+        Pd = WL.make_problem_cuda(1 << args.n_log2, args.d, args.sigma_max, seed=1 + rank, dtype=torch.float32,
+                                  outlier_frac=args.outlier_frac, device=dev)
+        A, b = Pd["A"], Pd["b"]
+        A_host, b_host = None, b.cpu()
+        args.no_e2e = True
+    else:
+        A_host = torch.from_numpy(P["A"])
+        b_host = torch.from_numpy(P["b"])
+        A = A_host.to(dev)
+        b = b_host.to(dev)
     n, d = A.shape
     ctx = L.Context(dev)
     stream = torch.cuda.current_stream(dev)
@@ -283,7 +294,7 @@ def run_ours(args):
                "d2h_bytes_per_step": d * 8}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and args.a_dtype == "f64":
         ms, sample, cores = oracle_estimate(args, min(n, 1 << 16))
         cpu = {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
 

@@ -65,10 +65,12 @@ typedef enum {
 
 /* Arithmetic used for the passes over A inside lsq_solve.
  *   LSQ_PREC_F64:   native FP64 for every operation (the plain FP64 method).
- *   LSQ_PREC_MIXED: passes over A in FP32 arithmetic, with the residual b - H x
- *                   re-evaluated in emulated double-FP32 (about 48 significant bits)
- *                   every `refresh_every` iterations and at the end; x, r and the
- *                   preconditioner stay FP64.  Reaches the same tolerance as F64. */
+ *   LSQ_PREC_MIXED: passes over A in FP32 arithmetic; the recursive residual is
+ *                   replaced by b - H x evaluated in double-FP32 arithmetic (about 45
+ *                   significant bits per element, TwoProduct/TwoSum accumulation) after
+ *                   every 10^4 drop of its norm, every `refresh_every` iterations and
+ *                   before convergence is declared; x, r and the preconditioner stay
+ *                   FP64.  Reaches the same tolerance as LSQ_PREC_F64. */
 typedef enum { LSQ_PREC_F64 = 0, LSQ_PREC_MIXED = 1 } lsq_precision;
 
 /* A dense matrix in device memory (row-major, stride ld elements). */
@@ -98,8 +100,12 @@ LSQ_API lsq_status lsq_set_stream(lsq_ctx* ctx, void* cuda_stream);
  *                   evaluation of S A to rounding).
  *   LSQ_SKETCH_F32: A rounded to FP32 on load, FP32 arithmetic, FP64 output.  A sketch
  *                   only has to be a subspace embedding; the preconditioner it yields is
- *                   as good, and the solve still reaches its tolerance against FP64 x*. */
-typedef enum { LSQ_SKETCH_F64 = 0, LSQ_SKETCH_F32 = 1 } lsq_sketch_precision;
+ *                   as good, and the solve still reaches its tolerance against FP64 x*.
+ *   LSQ_SKETCH_BF16: Gaussian only.  S is generated in FP32 from the same Philox words
+ *                   (each uniform keeps the top 24 of its 53 bits), S and A are rounded to
+ *                   BF16 and multiplied on the tensor cores (tcgen05) with FP32
+ *                   accumulation; FP64 output.  Relative error of SA ~ 1e-3. */
+typedef enum { LSQ_SKETCH_F64 = 0, LSQ_SKETCH_F32 = 1, LSQ_SKETCH_BF16 = 2 } lsq_sketch_precision;
 
 typedef struct {
   uint32_t t;        /* sketch instance (Philox counter word 2): 0 for a fixed embedding,
@@ -162,7 +168,9 @@ typedef struct {
   uint64_t seed;       /* refreshed embeddings: Philox key (instance t = iteration index) */
   int32_t s;           /* refreshed SJLT: nonzeros per column (default 8) */
   int32_t precision;   /* lsq_precision (default LSQ_PREC_F64) */
-  int32_t refresh_every; /* MIXED only: iterations between exact residual replacements (default 8) */
+  int32_t refresh_every; /* MIXED only: most iterations between exact residual replacements
+                            (default 12; a replacement also follows every 10^4 drop of the
+                            residual norm and every recursive convergence) */
   int32_t grid_blocks; /* 0 = automatic; else the number of resident CTAs of the solve kernel */
   int32_t x0_zero;     /* 1: x0 is zero, so the initial residual b - H x0 = b needs no pass over A */
 } lsq_solve_opts;
@@ -205,6 +213,19 @@ LSQ_API lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double* b,
 LSQ_API lsq_status lsq_hmatvec(lsq_ctx* ctx, const lsq_matrix* A, const double* p, double* v, double* q);
 
 /* ---------------------------------------------------------------------------------
+ * lsq_grad_a: the gradient with respect to A of a loss L(x*), x* = H^{-1} b, given x*
+ * and lambda = H^{-1} dL/dx* (a second lsq_solve with the forward's W):
+ *     dL/dA = -(A x*) lambda^T - (A lambda) x*^T          (dL/db = lambda).
+ * Derived from the problem statement of Section 1 (implicit differentiation of H x* = b).
+ *   A      : the data matrix (device, FP64 or FP32).
+ *   x, lam : device, d FP64.
+ *   gA     : device, n x d output with row stride ldg >= d, same dtype as A, caller-owned.
+ * One pass over A (u = A x*, w = A lambda per row in FP64) and one write of gA.
+ * --------------------------------------------------------------------------------- */
+LSQ_API lsq_status lsq_grad_a(lsq_ctx* ctx, const lsq_matrix* A, const double* x, const double* lam, void* gA,
+                              int64_t ldg);
+
+/* ---------------------------------------------------------------------------------
  * lsq_hmatvec_noalloc: the same fused pass as lsq_hmatvec (v = A^T (A p), q = ||A p||^2,
  * FP64 arithmetic) for callers that cannot allocate device memory -- code whose device
  * memory all belongs to its own pool allocator, or latency-bound loops that cannot take
@@ -223,6 +244,29 @@ LSQ_API lsq_status lsq_hmatvec(lsq_ctx* ctx, const lsq_matrix* A, const double* 
  * --------------------------------------------------------------------------------- */
 LSQ_API lsq_status lsq_hmatvec_noalloc(const lsq_matrix* A, const double* p, double* v, double* q,
                                        void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------
+ * lsq_advise_sketch_size: host-only advisor of Section 6 (optimized sketch size).
+ *   Gaussian (theorem theoremoptimalcomplexitygaussian):
+ *       m* = d exp(W0((n/d^2) log(1/eps))),  cost ratio = 1 / log(n/d^2);
+ *   SRHT (theorem theoremoptimalcomplexitysrht), for n > d^2:
+ *       (i)  sqrt(log 1/eps) < log(n/d^2): m* = e^{sqrt(log 1/eps)} d log d,
+ *            cost ratio = (log d + sqrt(log 1/eps)) / (log d + log 1/eps);
+ *       (ii) otherwise: m* = (n/d) max(log d, log(1/eps)/log(n/d^2)),
+ *            cost ratio = (log d + log(1/eps)/log(n/d^2)) / (log d + log 1/eps).
+ * The cost ratios are the paper's flop models with constants dropped, against the
+ * classical m = O(d) (Gaussian) or O(d log d) (SRHT).  predicted_iters is
+ * ceil(log(4/eps) / log(m_star / m_delta)) with m_delta = d (Gaussian) or d log d (SRHT).
+ * LSQ_ERR_ARG for n <= d^2, eps outside (0,1), or an SJLT (no result in the paper).
+ * --------------------------------------------------------------------------------- */
+typedef struct {
+  double m_star;          /* optimized sketch size (real; round as needed) */
+  double cost_ratio;      /* model cost at m* over the classical cost */
+  double predicted_iters; /* PCG iterations predicted at m_star (-1 if m_star <= m_delta) */
+  int32_t regime;         /* 0 Gaussian; 1, 2: SRHT cases (i), (ii) */
+} lsq_advice;
+
+LSQ_API lsq_status lsq_advise_sketch_size(int64_t n, int64_t d, double eps, int32_t sketch_type, lsq_advice* out);
 
 /* Human-readable name of a status code (static storage). */
 LSQ_API const char* lsq_status_str(int32_t status);

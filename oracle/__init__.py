@@ -19,10 +19,12 @@ Functions and the passages they follow:
   pcg                     PCG with a fixed embedding                     Section 1, eq. (PCG)
   ihs                     IHS / Polyak-IHS, fixed or refreshed           Section 1, eqs. eqnihs / eqnpolyakihs
   solve_direct, solve_refined   x* (QR + double-double refinement)     Section 1 (definition of x*)
+  grad_a, solve_grads     gradients of L(x*) w.r.t. A and b              implicit differentiation of H x* = b
   theta_gaussian, theta_srht   inverse moments                           Section 2, eqs. eqngaussianmoments, eqnsrhtmoments
   ihs_fixed_params, polyak_fixed_params                                  Section 3, theorem theoremihsfixed
   refreshed_rate                                                         Section 4, theorem theoremexacterrorrefreshed
   pcg_iterations_bound                                                   Section 6 (T = ceil(log(4/eps)/log(1/rho)))
+  optimal_sketch_size                                                    Section 6, theorems theoremoptimalcomplexitysrht / -gaussian
 """
 from __future__ import annotations
 
@@ -72,6 +74,7 @@ def lib():
             "orc_solve_direct": (i32, [P, i64, i64, i64, P, P]),
             "orc_solve_refined": (i32, [P, i64, i64, i64, P, P, dbl, P, i32]),
             "orc_rel_h_err": (dbl, [P, i64, i64, i64, P, P]),
+            "orc_grad_a": (None, [P, i64, i64, i64, P, P, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -324,6 +327,21 @@ def rel_h_err(A, x, xstar) -> float:
     return lib().orc_rel_h_err(_ptr(A), n, d, ld, _ptr(_f64(x)), _ptr(_f64(xstar)))
 
 
+def grad_a(A, x, lam) -> np.ndarray:
+    """dL/dA = -(A x) lam^T - (A lam) x^T for x = H^{-1} b, lam = H^{-1} dL/dx."""
+    A, n, d, ld = _mat(A)
+    gA = np.empty((n, d))
+    lib().orc_grad_a(_ptr(A), n, d, ld, _ptr(_f64(x)), _ptr(_f64(lam)), _ptr(gA))
+    return gA
+
+
+def solve_grads(A, b, g):
+    """(x*, dL/dA, dL/db) of L with dL/dx* = g, by the definitions (direct solves)."""
+    xs = solve_direct(A, b)
+    lam = solve_direct(A, g)
+    return xs, grad_a(A, xs, lam), lam
+
+
 # ----------------------------------------------------------------------------- closed forms
 def theta_gaussian(m: int, d: int):
     """E[C_S^-1] = theta1 I, E[C_S^-2] = theta2 I for Gaussian S, m >= d + 4
@@ -365,6 +383,25 @@ def ihs_fixed_params(rho: float):
 def polyak_fixed_params(rho: float):
     """Polyak-IHS with a fixed embedding: mu = (1-rho)^2, beta = rho (same theorem)."""
     return (1 - rho) ** 2, rho
+
+
+def optimal_sketch_size(n: int, d: int, eps: float, kind: str):
+    """Section 6: (m*, cost ratio) of the flop model with constants dropped.
+    Gaussian (theorem theoremoptimalcomplexitygaussian): alpha* log alpha* = (n/d^2) log(1/eps),
+    m* = d alpha* = d exp(W0(.)), ratio = 1/log(n/d^2).  SRHT (theorem
+    theoremoptimalcomplexitysrht): cases (i) / (ii) by sqrt(log 1/eps) vs log(n/d^2)."""
+    from scipy.special import lambertw
+
+    L, Lr = math.log(1 / eps), math.log(n / d**2)
+    if n <= d * d:
+        raise ValueError("the analysis assumes n > d^2")
+    if kind == "gauss":
+        return d * math.exp(lambertw((n / d**2) * L).real), 1.0 / Lr
+    if kind == "srht":
+        if math.sqrt(L) < Lr:
+            return math.exp(math.sqrt(L)) * d * math.log(d), (math.log(d) + math.sqrt(L)) / (math.log(d) + L)
+        return (n / d) * max(math.log(d), L / Lr), (math.log(d) + L / Lr) / (math.log(d) + L)
+    raise ValueError(kind)
 
 
 def pcg_iterations_bound(eps: float, rho: float) -> int:

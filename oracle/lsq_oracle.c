@@ -681,6 +681,18 @@ int orc_solve_refined(const double* A, int64_t n, int64_t d, int64_t ld, const d
   return status;
 }
 
+/* gradient of L(x*) with respect to A, x* = H^{-1} b, lam = H^{-1} dL/dx*:
+   dL/dA = -(A x*) lam^T - (A lam) x*^T (implicit differentiation of H x* = b, H = A^T A) */
+void orc_grad_a(const double* A, int64_t n, int64_t d, int64_t ld, const double* x, const double* lam, double* gA) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    const double* a = A + i * ld;
+    double u = 0.0, w = 0.0;
+    for (int64_t c = 0; c < d; ++c) { u += a[c] * x[c]; w += a[c] * lam[c]; }
+    for (int64_t c = 0; c < d; ++c) gA[i * d + c] = -(u * lam[c] + w * x[c]);
+  }
+}
+
 /* relative H-norm error ||x - x*||_H / ||x*||_H = ||A e|| / ||A x*||, e = x - x* */
 double orc_rel_h_err(const double* A, int64_t n, int64_t d, int64_t ld, const double* x, const double* xstar) {
   double* e = (double*)malloc(sizeof(double) * (size_t)d);

@@ -30,13 +30,13 @@ LSQ_OK, LSQ_ERR_ARG, LSQ_ERR_RANK, LSQ_ERR_BREAKDOWN, LSQ_ERR_MAXIT, LSQ_ERR_TIM
 SKETCH = {"gauss": 0, "srht": 1, "sjlt": 2}
 METHOD = {"pcg": 0, "ihs": 1, "polyak": 2}
 PRECISION = {"f64": 0, "mixed": 1}
-SKETCH_PRECISION = {"f64": 0, "f32": 1}
+SKETCH_PRECISION = {"f64": 0, "f32": 1, "bf16": 2}
 DTYPE = {torch.float64: 0, torch.float32: 1}
 
 # every symbol the header declares
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_sketch", "lsq_factor", "lsq_solve",
            "lsq_solve_opts_default", "lsq_hmatvec", "lsq_status_str", "lsq_version", "lsq_launch_count",
-           "lsq_hmatvec_noalloc")
+           "lsq_hmatvec_noalloc", "lsq_grad_a", "lsq_advise_sketch_size")
 
 
 class LsqError(RuntimeError):
@@ -59,6 +59,11 @@ class LsqSolveOpts(ctypes.Structure):
                 ("refresh", ctypes.c_int32), ("sketch_type", ctypes.c_int32), ("m", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("s", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("refresh_every", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("x0_zero", ctypes.c_int32)]
+
+
+class LsqAdvice(ctypes.Structure):
+    _fields_ = [("m_star", ctypes.c_double), ("cost_ratio", ctypes.c_double), ("predicted_iters", ctypes.c_double),
+                ("regime", ctypes.c_int32)]
 
 
 class LsqSolveInfo(ctypes.Structure):
@@ -87,6 +92,10 @@ def _load():
     L.lsq_hmatvec.argtypes = [P, ctypes.POINTER(LsqMatrix), P, P, P]
     L.lsq_hmatvec_noalloc.argtypes = [ctypes.POINTER(LsqMatrix), P, P, P, P]
     L.lsq_hmatvec_noalloc.restype = ctypes.c_int
+    L.lsq_grad_a.argtypes = [P, ctypes.POINTER(LsqMatrix), P, P, P, i64]
+    L.lsq_grad_a.restype = ctypes.c_int
+    L.lsq_advise_sketch_size.argtypes = [i64, i64, dbl, i32, ctypes.POINTER(LsqAdvice)]
+    L.lsq_advise_sketch_size.restype = ctypes.c_int
     L.lsq_status_str.argtypes = [i32]
     L.lsq_status_str.restype = ctypes.c_char_p
     L.lsq_version.restype = ctypes.c_char_p
@@ -240,6 +249,64 @@ def lsq_hmatvec(ctx: Context, A: torch.Tensor, p: torch.Tensor):
     if st:
         raise LsqError(st, "lsq_hmatvec")
     return v, q
+
+
+def lsq_grad_a(ctx: Context, A: torch.Tensor, x: torch.Tensor, lam: torch.Tensor,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+    """dL/dA = -(A x) lam^T - (A lam) x^T (same dtype as A)."""
+    ctx.sync_stream()
+    M = as_matrix(A)
+    d = A.shape[1]
+    _check_vec(x, d, "x")
+    _check_vec(lam, d, "lam")
+    gA = out if out is not None else torch.empty(A.shape, dtype=A.dtype, device=A.device)
+    st = _L.lsq_grad_a(ctx.handle, ctypes.byref(M), _ptr(x), _ptr(lam), _ptr(gA), gA.stride(0))
+    if st:
+        raise LsqError(st, "lsq_grad_a")
+    return gA
+
+
+class LeastSquaresSolve(torch.autograd.Function):
+    """x* = argmin 1/2 <x, A^T A x> - <b, x> as a differentiable op.
+
+    forward: sketch (SRHT by default), factor, PCG to `tol`.  backward: lambda = H^{-1} g by
+    PCG with the forward's preconditioner W (no stored iterates), grad_b = lambda,
+    grad_A = -(A x*) lambda^T - (A lambda) x*^T (lsq_grad_a)."""
+
+    @staticmethod
+    def forward(fctx, A, b, lsq: Context, sketch: str = "srht", m: int = 1024, seed: int = 0, tol: float = 1e-10,
+                precision: str = "mixed", maxit: int = 1000):
+        SA = lsq_sketch(lsq, A, sketch, m, seed, precision="f32" if precision == "mixed" else "f64")
+        _, W = lsq_factor(lsq, SA)
+        x, info = lsq_solve(lsq, A, b.contiguous(), "pcg", W, tol=tol, maxit=maxit, m=m, precision=precision,
+                            raise_on_maxit=True)
+        fctx.lsq, fctx.m, fctx.tol, fctx.precision, fctx.maxit = lsq, m, tol, precision, maxit
+        fctx.save_for_backward(A, x, W)
+        return x
+
+    @staticmethod
+    def backward(fctx, g):
+        A, x, W = fctx.saved_tensors
+        lam, _ = lsq_solve(fctx.lsq, A, g.contiguous().to(torch.float64), "pcg", W, tol=fctx.tol, maxit=fctx.maxit,
+                           m=fctx.m, precision=fctx.precision, raise_on_maxit=True)
+        gA = lsq_grad_a(fctx.lsq, A, x, lam) if fctx.needs_input_grad[0] else None
+        gb = lam if fctx.needs_input_grad[1] else None
+        return gA, gb, None, None, None, None, None, None, None
+
+
+def lstsq_solve(A: torch.Tensor, b: torch.Tensor, lsq: Context, **kw) -> torch.Tensor:
+    """Differentiable x* = H^{-1} b (see LeastSquaresSolve)."""
+    return LeastSquaresSolve.apply(A, b, lsq, kw.get("sketch", "srht"), kw.get("m", 1024), kw.get("seed", 0),
+                                   kw.get("tol", 1e-10), kw.get("precision", "mixed"), kw.get("maxit", 1000))
+
+
+def lsq_advise_sketch_size(n: int, d: int, eps: float, kind: str = "srht") -> dict:
+    """Section 6's optimized sketch size m*, the model cost ratio and the predicted iterations."""
+    out = LsqAdvice()
+    st = _L.lsq_advise_sketch_size(n, d, eps, SKETCH[kind], ctypes.byref(out))
+    if st:
+        raise LsqError(st, "lsq_advise_sketch_size")
+    return {k: getattr(out, k) for k, _ in out._fields_}
 
 
 def default_rho(d: int, m: int) -> float:

@@ -88,31 +88,47 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int splits, 
 // X(r, k) = Xm[r*ld + k] (or Xm[k*ld + r] when transX), Y(k, c) = Ym[k*ld + c], k < K.
 // ------------------------------------------------------------------------------------
 struct TileSmem {
-  double X[32][33];
-  double Y[32][8];
+  double X[2][32][33];
+  double Y[2][32][8];
 };
 
+// 8-byte asynchronous copies global -> shared (the thread does not wait for the data)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void tile_load(TileSmem& sm, int buf, const double* Xm, bool transX, const double* Ym,
+                                          int k0, int ld) {
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    if (transX) {
+      const int kk = e >> 5, rr = e & 31;
+      cp_async8(&sm.X[buf][rr][kk], Xm + (int64_t)(k0 + kk) * ld + rr);
+    } else {
+      const int rr = e >> 5, kk = e & 31;
+      cp_async8(&sm.X[buf][rr][kk], Xm + (int64_t)rr * ld + k0 + kk);
+    }
+  }
+  const int kk = threadIdx.x >> 3, cc = threadIdx.x & 7;
+  cp_async8(&sm.Y[buf][kk][cc], Ym + (int64_t)(k0 + kk) * ld + cc);
+  cp_async_commit();
+}
+
+// the next 32-deep block is loaded while the current one is multiplied
 __device__ void tile_task(TileSmem& sm, double* out, const double* Xm, bool transX, const double* Ym, int K, int ld,
                           double alpha, bool acc) {
   const int r = threadIdx.x >> 3, c = threadIdx.x & 7;
   double sum = 0.0;
-  for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int e = threadIdx.x; e < 1024; e += 256) {
-      if (transX) {
-        const int kk = e >> 5, rr = e & 31;
-        sm.X[rr][kk] = Xm[(int64_t)(k0 + kk) * ld + rr];
-      } else {
-        const int rr = e >> 5, kk = e & 31;
-        sm.X[rr][kk] = Xm[(int64_t)rr * ld + k0 + kk];
-      }
-    }
-    {
-      const int kk = threadIdx.x >> 3, cc = threadIdx.x & 7;
-      sm.Y[kk][cc] = Ym[(int64_t)(k0 + kk) * ld + cc];
-    }
-    __syncthreads();
+  tile_load(sm, 0, Xm, transX, Ym, 0, ld);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int k0 = 0, buf = 0; k0 < K; k0 += 32, buf ^= 1) {
+    if (k0 + 32 < K) tile_load(sm, buf ^ 1, Xm, transX, Ym, k0 + 32, ld);
 #pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) sum = fma(sm.X[r][kk], sm.Y[kk][c], sum);
+    for (int kk = 0; kk < 32; ++kk) sum = fma(sm.X[buf][r][kk], sm.Y[buf][kk][c], sum);
+    cp_async_wait_all();
     __syncthreads();
   }
   double* o = out + (int64_t)r * ld + c;
@@ -122,9 +138,12 @@ __device__ void tile_task(TileSmem& sm, double* out, const double* Xm, bool tran
 // Cholesky of one 32 x 32 diagonal block (one warp) and the inverse of its factor.
 // Returns false (and sets *err) on a non-positive or non-finite pivot.
 __device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, int* err) {
+  __shared__ double Gs[32][33];
   __shared__ double Rs[32][33];
   __shared__ double Ws[32][33];
   __shared__ int bad;
+  // stage the block (one round trip for the whole CTA, not one per step of the loop below)
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) Gs[e >> 5][e & 31] = Gkk[(int64_t)(e >> 5) * ld + (e & 31)];
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -132,7 +151,7 @@ __device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, 
     for (int i = 0; i < 32; ++i) Rs[i][l] = 0.0;
     __syncwarp();
     for (int j = 0; j < 32; ++j) {
-      double t = Gkk[(int64_t)j * ld + l];
+      double t = Gs[j][l];
       for (int i = 0; i < j; ++i) t -= Rs[i][j] * Rs[i][l];
       const double piv = __shfl_sync(0xffffffffu, t, j);
       if (!(piv > 0.0) || !isfinite(piv)) {
@@ -155,12 +174,12 @@ __device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, 
       }
     }
     __syncwarp();
-    for (int i = 0; i < 32; ++i) {
-      Rkk[(int64_t)i * ld + l] = Rs[i][l];
-      Wkk[(int64_t)i * ld + l] = Ws[i][l];
-    }
   }
   __syncthreads();
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    Rkk[(int64_t)(e >> 5) * ld + (e & 31)] = Rs[e >> 5][e & 31];
+    Wkk[(int64_t)(e >> 5) * ld + (e & 31)] = Ws[e >> 5][e & 31];
+  }
   if (threadIdx.x == 0 && bad) atomicCAS(err, 0, (int)LSQ_ERR_RANK);
   __syncthreads();
 }
@@ -172,10 +191,13 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(double* __restrict__ G, d
   __shared__ TileSmem sm;
   const int dp = nblk * 32;
   const unsigned nb = gridDim.x;
+  // Look-ahead: CTA 0 applies the trailing update to the next diagonal block first and
+  // factors it at once, while the other CTAs update the rest of the trailing matrix; each
+  // panel then needs two grid barriers.
+  if (blockIdx.x == 0) diag_block(G, Rf, Wf, dp, err);
+  if (grid_barrier(bar, nb, err)) return;
   for (int k = 0; k < nblk; ++k) {
     const int64_t kk = (int64_t)k * 32;
-    if (blockIdx.x == 0) diag_block(G + kk * dp + kk, Rf + kk * dp + kk, Wf + kk * dp + kk, dp, err);
-    if (grid_barrier(bar, nb, err)) return;
     const int rest = nblk - 1 - k;
     // panel: R[k][j] = W[k][k]^T G[k][j]
     for (int task = blockIdx.x; task < rest * 4; task += nb) {
@@ -184,17 +206,31 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(double* __restrict__ G, d
       tile_task(sm, Rf + kk * dp + col, Wf + kk * dp + kk, true, G + kk * dp + col, 32, dp, 1.0, false);
     }
     if (grid_barrier(bar, nb, err)) return;
-    // trailing update: G[i][j] -= R[k][i]^T R[k][j], k < i <= j
+    if (rest == 0) break;
+    // trailing update: G[i][j] -= R[k][i]^T R[k][j], k < i <= j; pair 0 is the next
+    // diagonal block (k+1, k+1)
     const int pairs = rest * (rest + 1) / 2;
-    for (int task = blockIdx.x; task < pairs * 4; task += nb) {
-      int p = task / 4;
-      const int q = task % 4;
-      int i = 0;
-      while (p >= rest - i) { p -= rest - i; ++i; }
-      const int bi = k + 1 + i, bj = bi + p;
-      const int64_t col = (int64_t)bj * 32 + q * 8;
-      tile_task(sm, G + (int64_t)bi * 32 * dp + col, Rf + kk * dp + (int64_t)bi * 32, true, Rf + kk * dp + col, 32, dp,
-                -1.0, true);
+    const int64_t k1 = (int64_t)(k + 1) * 32;
+    if (blockIdx.x == 0) {
+      for (int q = 0; q < 4; ++q)
+        tile_task(sm, G + k1 * dp + k1 + q * 8, Rf + kk * dp + k1, true, Rf + kk * dp + k1 + q * 8, 32, dp, -1.0,
+                  true);
+      __syncthreads();
+      diag_block(G + k1 * dp + k1, Rf + k1 * dp + k1, Wf + k1 * dp + k1, dp, err);
+    }
+    const int others = nb > 1 ? (int)nb - 1 : 1;
+    const int first = nb > 1 ? (int)blockIdx.x - 1 : 0;
+    if (nb == 1 || blockIdx.x > 0) {
+      for (int task = 4 + first; task < pairs * 4; task += others) {
+        int p = task / 4;
+        const int q = task % 4;
+        int i = 0;
+        while (p >= rest - i) { p -= rest - i; ++i; }
+        const int bi = k + 1 + i, bj = bi + p;
+        const int64_t col = (int64_t)bj * 32 + q * 8;
+        tile_task(sm, G + (int64_t)bi * 32 * dp + col, Rf + kk * dp + (int64_t)bi * 32, true, Rf + kk * dp + col, 32,
+                  dp, -1.0, true);
+      }
     }
     if (grid_barrier(bar, nb, err)) return;
   }

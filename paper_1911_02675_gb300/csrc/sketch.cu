@@ -394,15 +394,41 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_transform_kernel(
     k2s[s] = (uint16_t)(k & (N2 - 1));
   }
   const int k0 = logN2 < 4 ? logN2 : 4;
+  const int T = blockDim.x;
+  const int units = (N2 >> k0) * DC;
+  // Common case: 16-row units and at most two per thread.  The next block's loads are put
+  // in flight as soon as the current block sits in shared memory, so they overlap the
+  // remaining butterfly passes and the sampled second level.
+  // (FP32 only: FP64 blocks are bound by the FP64 pipe and the registers are better spent)
+  constexpr bool PIPE = sizeof(TC) == 4;
+  constexpr int VB = PIPE ? 16 : 1;
+  const bool pipelined = PIPE && k0 == 4 && units <= 2 * T;
+  TC v0[VB], v1[VB];
+  const bool has0 = threadIdx.x < units, has1 = threadIdx.x + T < units;
+  if constexpr (PIPE) if (pipelined && b_begin < b_end) {
+    if (has0) load_unit<TC, DC, 4>(v0, A, dtype, n, d, ld, c0, b_begin << logN2, signbits, threadIdx.x);
+    if (has1) load_unit<TC, DC, 4>(v1, A, dtype, n, d, ld, c0, b_begin << logN2, signbits, threadIdx.x + T);
+  }
   for (int64_t i1 = b_begin; i1 < b_end; ++i1) {
     __syncthreads();  // Z is free (previous block's second level is done)
     const int64_t row0 = i1 << logN2;
-    switch (k0) {
-      case 4: load_pass<TC, DC, 4>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
-      case 3: load_pass<TC, DC, 3>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
-      case 2: load_pass<TC, DC, 2>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
-      case 1: load_pass<TC, DC, 1>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
-      default: load_pass<TC, DC, 0>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
+    if constexpr (PIPE) if (pipelined) {
+      if (has0) store_unit<TC, DC, 4>(Z, v0, threadIdx.x);
+      if (has1) store_unit<TC, DC, 4>(Z, v1, threadIdx.x + T);
+      if (i1 + 1 < b_end) {
+        const int64_t next0 = (i1 + 1) << logN2;
+        if (has0) load_unit<TC, DC, 4>(v0, A, dtype, n, d, ld, c0, next0, signbits, threadIdx.x);
+        if (has1) load_unit<TC, DC, 4>(v1, A, dtype, n, d, ld, c0, next0, signbits, threadIdx.x + T);
+      }
+    }
+    if (!pipelined) {
+      switch (k0) {
+        case 4: load_pass<TC, DC, 4>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
+        case 3: load_pass<TC, DC, 3>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
+        case 2: load_pass<TC, DC, 2>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
+        case 1: load_pass<TC, DC, 1>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
+        default: load_pass<TC, DC, 0>(Z, A, dtype, n, d, ld, c0, row0, N2, signbits); break;
+      }
     }
     for (int b = k0; b < logN2; b += 4) {
       __syncthreads();
@@ -415,10 +441,27 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_transform_kernel(
     }
     __syncthreads();
     const uint32_t i1w = (uint32_t)i1;
-    for (int e = threadIdx.x; e < m * DC; e += blockDim.x) {
-      const int s = e / DC, c = e % DC;
-      const TC z = Z[zphys(k2s[s], DC) + c];
-      Y[e] += (__popc(k1s[s] & i1w) & 1) ? -z : z;
+    // one sampled row per thread: its k1/k2 and sign once, then the DC columns as 16-byte
+    // vectors (a 32-byte row of the block and of the accumulator)
+    for (int s = threadIdx.x; s < m; s += blockDim.x) {
+      const bool neg = (__popc(k1s[s] & i1w) & 1) != 0;
+      const TC* zr = Z + zphys(k2s[s], DC);
+      TC* yr = Y + (size_t)s * DC;
+      if constexpr (DC * sizeof(TC) % 16 == 0) {
+#pragma unroll
+        for (int c = 0; c < DC * (int)sizeof(TC) / 16; ++c) {
+          uint4 zv = reinterpret_cast<const uint4*>(zr)[c];
+          uint4 yv = reinterpret_cast<uint4*>(yr)[c];
+          TC* zt = reinterpret_cast<TC*>(&zv);
+          TC* yt = reinterpret_cast<TC*>(&yv);
+#pragma unroll
+          for (int q = 0; q < 16 / (int)sizeof(TC); ++q) yt[q] += neg ? -zt[q] : zt[q];
+          reinterpret_cast<uint4*>(yr)[c] = yv;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < DC; ++c) yr[c] += neg ? -zr[c] : zr[c];
+      }
     }
   }
   __syncthreads();
@@ -461,13 +504,40 @@ __global__ void sjlt_hash_kernel(int64_t n, int m, int s, uint64_t seed, uint32_
   }
 }
 
-// The CTA owns a tile of DC columns and a range of rows.  512 threads cover 512/DC rows
-// at a time (DC threads per row, one column each).  For U such row sets every load (the
-// element, the sign word and all s positions) is issued before the first shared-memory
-// addition, so each thread has U * (s + 2) independent loads in flight.
+// The CTA owns a tile of DC columns (8 for FP32 arithmetic, 4 for FP64) and a range of
+// rows; each thread takes whole rows of the tile: it loads
+// the row's s positions, sign word and DC elements once and makes s * DC shared-memory
+// additions.  Lane l visits the columns rotated by l, so the 32 lanes of an atomic spread
+// over the banks instead of piling onto the DC banks of their targets.  The next row of
+// each thread is loaded while the current one is scattered.
 constexpr int SJLT_THREADS = 512;
 
-template <typename TC, int DC, int SMAX, int U>
+template <typename TC, int DC>
+__device__ __forceinline__ void rotate_by(TC (&a)[DC], int r) {
+#pragma unroll
+  for (int b = 1; b < DC; b <<= 1) {
+    if (r & b) {
+      TC t[DC];
+#pragma unroll
+      for (int c = 0; c < DC; ++c) t[c] = a[(c + b) & (DC - 1)];
+#pragma unroll
+      for (int c = 0; c < DC; ++c) a[c] = t[c];
+    }
+  }
+}
+
+template <typename TC, int DC, int SMAX>
+__device__ __forceinline__ void sjlt_load_row(const void* A, int dtype, int64_t ld, int c0, int d, int s,
+                                              const int32_t* h, const uint32_t* signs, int64_t i, bool ok, TC (&a)[DC],
+                                              int32_t (&tg)[SMAX], uint32_t& sw) {
+#pragma unroll
+  for (int c = 0; c < DC; ++c) a[c] = (ok && c0 + c < d) ? load_as<TC>(A, i * ld + c0 + c, dtype) : (TC)0;
+#pragma unroll
+  for (int k = 0; k < SMAX; ++k) tg[k] = (ok && k < s) ? __ldg(h + i * s + k) : -1;
+  sw = ok ? __ldg(signs + i) : 0u;
+}
+
+template <typename TC, int DC, int SMAX>
 __global__ void __launch_bounds__(SJLT_THREADS, 1) sjlt_scatter_kernel(const void* __restrict__ A, int dtype,
                                                                       int64_t n, int d, int64_t ld, int m, int s,
                                                                       const int32_t* __restrict__ h,
@@ -480,27 +550,29 @@ __global__ void __launch_bounds__(SJLT_THREADS, 1) sjlt_scatter_kernel(const voi
   const int64_t i_end = min(n, i_begin + rows_per_group);
   for (int e = threadIdx.x; e < m * DC; e += blockDim.x) Y[e] = (TC)0;
   __syncthreads();
-  constexpr int RPI = SJLT_THREADS / DC;  // rows per step
-  const int rl = threadIdx.x / DC, c = threadIdx.x % DC;
-  const bool col_ok = (c0 + c) < d;
-  for (int64_t i0 = i_begin; i0 < i_end; i0 += (int64_t)RPI * U) {
-    TC a[U];
-    uint32_t sw[U];
-    int32_t tgt[U][SMAX];
+  const int rot = (threadIdx.x & 31) & (DC - 1);
+  TC a[DC], an[DC];
+  int32_t tg[SMAX], tn[SMAX];
+  uint32_t sw = 0, swn = 0;
+  int64_t i = i_begin + threadIdx.x;
+  sjlt_load_row<TC, DC, SMAX>(A, dtype, ld, c0, d, s, h, signs, i, i < i_end, a, tg, sw);
+  for (; i < i_end; i += SJLT_THREADS) {
+    const int64_t inext = i + SJLT_THREADS;
+    sjlt_load_row<TC, DC, SMAX>(A, dtype, ld, c0, d, s, h, signs, inext, inext < i_end, an, tn, swn);
+    rotate_by<TC, DC>(a, rot);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t i = i0 + rl + (int64_t)u * RPI;
-      const bool ok = i < i_end;
-      a[u] = (ok && col_ok) ? load_as<TC>(A, i * ld + c0 + c, dtype) : (TC)0;
-      sw[u] = ok ? __ldg(signs + i) : 0u;
+    for (int k = 0; k < SMAX; ++k) {
+      if (k >= s) break;
+      TC* yr = Y + (size_t)tg[k] * DC;
+      const bool neg = (sw >> k) & 1u;
 #pragma unroll
-      for (int k = 0; k < SMAX; ++k) tgt[u][k] = (ok && k < s) ? __ldg(h + i * s + k) : -1;
+      for (int c = 0; c < DC; ++c) atomicAdd(yr + ((c + rot) & (DC - 1)), neg ? -a[c] : a[c]);
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int c = 0; c < DC; ++c) a[c] = an[c];
 #pragma unroll
-      for (int k = 0; k < SMAX; ++k)
-        if (tgt[u][k] >= 0) atomicAdd(&Y[tgt[u][k] * DC + c], ((sw[u] >> k) & 1u) ? -a[u] : a[u]);
+    for (int k = 0; k < SMAX; ++k) tg[k] = tn[k];
+    sw = swn;
   }
   __syncthreads();
   TC* out = part + (int64_t)blockIdx.y * m * d;
@@ -656,12 +728,12 @@ static lsq_status sjlt_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, c
   const size_t smem = (size_t)m * DC * sizeof(TC);
   dim3 grid(lsq_ceil_div(d, DC), groups);
   if (s <= 8) {
-    auto kern = sjlt_scatter_kernel<TC, DC, 8, 4>;
+    auto kern = sjlt_scatter_kernel<TC, DC, 8>;
     LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, SJLT_THREADS, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, s, h, signs,
                                                     rows_per_group, part);
   } else {
-    auto kern = sjlt_scatter_kernel<TC, DC, 32, 1>;
+    auto kern = sjlt_scatter_kernel<TC, DC, 32>;
     LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, SJLT_THREADS, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, s, h, signs,
                                                     rows_per_group, part);
@@ -711,6 +783,40 @@ static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint
 
 }  // namespace
 
+lsq_status lsq_gauss_tc_partials(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, float* part,
+                                 int splits, int64_t rows_per_split, int nt, int* err);
+
+namespace {
+
+// BF16 tensor-core Gaussian sketch: split-K over the rows of A, FP32 partials, fixed-order
+// reduction with the 1/sqrt(m) scale
+lsq_status gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA) {
+  const int d = (int)A->d;
+  const int nt = d > 256 ? 512 : 256;
+  const int tiles = lsq_ceil_div(m, 128) * lsq_ceil_div(d, nt);
+  const int64_t ksteps = (A->n + 63) / 64;
+  int64_t splits = std::max<int64_t>(1, (4 * (int64_t)ctx->sm_count + tiles - 1) / tiles);
+  const int64_t cap = std::max<int64_t>(1, ((int64_t)512 << 20) / ((int64_t)m * d * 4));
+  splits = std::max<int64_t>(1, std::min(std::min(splits, ksteps), cap));
+  const int64_t rows_per_split = ((ksteps + splits - 1) / splits) * 64;
+  splits = (A->n + rows_per_split - 1) / rows_per_split;
+  lsq_status st = lsq_ensure_scratch(ctx, lsq_align256((size_t)splits * m * d * 4) + 256);
+  if (st != LSQ_OK) return st;
+  Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};
+  float* part = cv.take<float>((size_t)splits * m * d);
+  int* err = cv.take<int>(1);
+  LSQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  st = lsq_gauss_tc_partials(ctx, A, m, seed, t, part, (int)splits, rows_per_split, nt, err);
+  if (st != LSQ_OK) return st;
+  const int64_t md = (int64_t)m * d;
+  reduce_splits_kernel<float><<<grid_for(md, 256, 4 * ctx->sm_count), 256, 0, ctx->stream>>>(
+      part, (int)splits, md, 1.0 / sqrt((double)m), SA);
+  LSQ_LAUNCH_CHECK();
+  return LSQ_OK;
+}
+
+}  // namespace
+
 extern "C" lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, int64_t m, uint64_t seed,
                                  const lsq_sketch_opts* opts, double* SA) {
   if (!ctx || !SA) return LSQ_ERR_ARG;
@@ -720,10 +826,12 @@ extern "C" lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type
   const uint32_t t = opts ? opts->t : 0u;
   const int s = (opts && opts->s > 0) ? opts->s : 8;
   const int prec = opts ? opts->precision : LSQ_SKETCH_F64;
-  if (prec != LSQ_SKETCH_F64 && prec != LSQ_SKETCH_F32) return LSQ_ERR_ARG;
+  if (prec != LSQ_SKETCH_F64 && prec != LSQ_SKETCH_F32 && prec != LSQ_SKETCH_BF16) return LSQ_ERR_ARG;
+  if (prec == LSQ_SKETCH_BF16 && type != LSQ_SKETCH_GAUSS) return LSQ_ERR_ARG;
   const bool f64 = prec == LSQ_SKETCH_F64;
   switch (type) {
     case LSQ_SKETCH_GAUSS:
+      if (prec == LSQ_SKETCH_BF16) return gauss_tc_run(ctx, A, (int)m, seed, t, SA);
       return f64 ? gauss_run<double>(ctx, A, (int)m, seed, t, SA) : gauss_run<float>(ctx, A, (int)m, seed, t, SA);
     case LSQ_SKETCH_SRHT:
       return f64 ? srht_run<double>(ctx, A, (int)m, seed, t, SA) : srht_run<float>(ctx, A, (int)m, seed, t, SA);

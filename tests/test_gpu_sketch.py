@@ -98,3 +98,30 @@ def test_rejects_bad_arguments(L, ctx):
         L.lsq_sketch(ctx, A, "srht", 65, 0)       # m > N
     with pytest.raises(L.LsqError):
         L.lsq_sketch(ctx, A, "sjlt", 4, 0, s=5)   # s > m
+
+
+@pytest.mark.parametrize("n,m", [(256, 256), (512, 128), (300, 200)])
+def test_gaussian_bf16_tensor_core_layout(L, ctx, n, m):
+    """A = I_n makes SA = S: every entry of the tensor-core product must be the BF16 rounding of
+    z(j, i) (up to one BF16 step where FP32 and FP64 evaluations straddle a rounding boundary),
+    so any error in the operand layouts or descriptors shows up entry by entry.  The kernel is
+    also deterministic: a second run agrees bit for bit."""
+    A = np.eye(n)
+    SA = L.lsq_sketch(ctx, to_dev(A), "gauss", m, 7, t=1, precision="bf16").cpu().numpy() * np.sqrt(m)
+    SA2 = L.lsq_sketch(ctx, to_dev(A), "gauss", m, 7, t=1, precision="bf16").cpu().numpy() * np.sqrt(m)
+    assert np.array_equal(SA, SA2)
+    Z = O.gauss_matrix(m, n, 7, 1) * np.sqrt(m)
+    Zb = torch.from_numpy(Z).to(torch.bfloat16).to(torch.float64).numpy()
+    # FP32 generation (24-bit uniforms, fast sin/cos) moves tiny |z| by up to ~1e-4 absolute
+    assert np.all(np.abs(SA - Zb) <= 2.0 ** -7 * np.abs(Zb) + 1e-4)
+    # equal up to the rounding of the final 1/sqrt(m) scale, except at straddled boundaries
+    assert np.mean(np.isclose(SA, Zb, rtol=1e-12, atol=0)) > 0.99
+
+
+@pytest.mark.parametrize("n,d,m,dtype", [(20000, 256, 512, np.float32), (9000, 700, 384, np.float64),
+                                         (4096, 64, 256, np.float32)])
+def test_gaussian_bf16_accuracy(L, ctx, n, d, m, dtype):
+    A = W.make_problem(n, d, 1e2, seed=5)["A"].astype(dtype)
+    SA = L.lsq_sketch(ctx, to_dev(A), "gauss", m, 3, precision="bf16").cpu().numpy()
+    ref = O.sketch_gauss(A.astype(np.float64), m, 3)
+    assert rel_fro(SA, ref) < 1e-2  # BF16 operands: about 2^-9 per product, random signs

@@ -189,3 +189,16 @@ def test_mixed_refreshed_ihs(L, ctx):
     x, info = L.lsq_solve(ctx, to_dev(A), to_dev(b), "ihs", None, tol=1e-10, maxit=200, m=256, refresh=1,
                           sketch_type="gauss", seed=3, precision="mixed")
     assert info["status"] == 0 and O.rel_h_err(A, x.cpu().numpy(), xs) <= 1e-10, info
+
+
+def test_mixed_pcg_with_bf16_gaussian_sketch(L, ctx):
+    """FP32-stored A with outliers, tensor-core BF16 Gaussian sketch, mixed-precision PCG."""
+    P = W.make_problem(50000, 256, 1e5, seed=9, outlier_frac=0.05)
+    A32 = P["A"].astype(np.float32)
+    A64 = A32.astype(np.float64)
+    b = A64.T @ P["y"]
+    xs = O.solve_direct(A64, b)
+    Ad = to_dev(A32)
+    _, Wm = L.lsq_factor(ctx, L.lsq_sketch(ctx, Ad, "gauss", 1024, 0, precision="bf16"))
+    x, info = L.lsq_solve(ctx, Ad, to_dev(b), "pcg", Wm, tol=1e-10, maxit=300, m=1024, precision="mixed")
+    assert info["status"] == 0 and O.rel_h_err(A64, x.cpu().numpy(), xs) <= 1e-10, info

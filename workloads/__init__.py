@@ -76,6 +76,35 @@ def make_problem(n: int, d: int, sigma_max: float, seed: int = 1, noise: float =
     return {"A": A, "b": np.ascontiguousarray(b), "x_true": x_true, "y": y}
 
 
+def make_problem_cuda(n: int, d: int, sigma_max: float, seed: int = 1, noise: float = 0.1, dtype=None,
+                      outlier_frac: float = 0.0, outlier_scale: float = 100.0, device="cuda", chunk: int = 1 << 18):
+    """The same recipe drawn directly in device memory with torch's CUDA generator (for
+    workloads too large to draw on the host; the draws differ from make_problem's).
+    y and b = A^T y are accumulated in FP64 over row chunks.  Returns dict(A, b) on device."""
+    import torch
+
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    A = torch.empty((n, d), dtype=dtype, device=device)
+    sig = torch.tensor(sigma(d, sigma_max), dtype=torch.float64, device=device)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        blk = torch.randn((r1 - r0, d), generator=g, dtype=torch.float64, device=device) * sig
+        A[r0:r1] = blk.to(dtype)
+    if outlier_frac > 0:
+        u = torch.rand(n, generator=g, device=device)
+        A[u < outlier_frac] *= outlier_scale
+    x_true = torch.randn(d, generator=g, dtype=torch.float64, device=device)
+    b = torch.zeros(d, dtype=torch.float64, device=device)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        blk = A[r0:r1].to(torch.float64)
+        y = blk @ x_true + noise * torch.randn(r1 - r0, generator=g, dtype=torch.float64, device=device)
+        b += blk.T @ y
+    return {"A": A, "b": b}
+
+
 def small_problem(n: int, d: int, kappa: float = 1e2, seed: int = 7):
     """Small dense test problem with column scales log-spaced 1..kappa."""
     return make_problem(n, d, kappa, seed=seed)
