@@ -18,6 +18,7 @@ Functions and the passages they follow:
   hmatvec, residual_dd    H p = A^T A p, b - H x                         Section 1 (problem)
   pcg                     PCG with a fixed embedding                     Section 1, eq. (PCG)
   ihs                     IHS / Polyak-IHS, fixed or refreshed           Section 1, eqs. eqnihs / eqnpolyakihs
+  fcg                     GCC / FCG / IPCG, refreshed                    Section 1, eqs. eqnconjugatedirectionsrefreshed / eqnflexiblecg
   solve_direct, solve_refined   x* (QR + double-double refinement)     Section 1 (definition of x*)
   grad_a, solve_grads     gradients of L(x*) w.r.t. A and b              implicit differentiation of H x* = b
   theta_gaussian, theta_srht   inverse moments                           Section 2, eqs. eqngaussianmoments, eqnsrhtmoments
@@ -75,6 +76,7 @@ def lib():
             "orc_solve_refined": (i32, [P, i64, i64, i64, P, P, dbl, P, i32]),
             "orc_rel_h_err": (dbl, [P, i64, i64, i64, P, P]),
             "orc_grad_a": (None, [P, i64, i64, i64, P, P, P]),
+            "orc_fcg": (i32, [P, i64, i64, i64, P, i32, i64, i32, u64, i32, P, dbl, i32, dbl, P, P, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -298,6 +300,20 @@ def ihs(A, b, *, R=None, kind="gauss", m=None, s=8, seed=0, mu, beta=0.0, x0=Non
     xs = _f64(xstar) if xstar is not None else None
     st = lib().orc_ihs(_ptr(A), n, d, ld, _ptr(b), _ptr(Rp) if Rp is not None else None,
                        SKETCH_TYPES[kind], int(m or 0), s, seed, mu, beta, _ptr(x), tol, maxit, rho_hat,
+                       _ptr(xs) if xs is not None else None, ctypes.byref(it), _ptr(hist))
+    return x, it.value, st, hist[: it.value + 1]
+
+
+def fcg(A, b, *, kind="gauss", m, s=8, seed=0, kmax=-1, x0=None, tol=1e-10, maxit=100, rho_hat, xstar=None):
+    """Flexible CG with refreshed embeddings: kmax = -1 GCC, kmax = 1 IPCG (Sections 1, 4).
+    Returns (x, iters, status, hist)."""
+    A, n, d, ld = _mat(A)
+    b = _f64(b)
+    x = np.zeros(d) if x0 is None else _f64(x0).copy()
+    hist = np.full(maxit + 1, np.nan)
+    it = ctypes.c_int(0)
+    xs = _f64(xstar) if xstar is not None else None
+    st = lib().orc_fcg(_ptr(A), n, d, ld, _ptr(b), SKETCH_TYPES[kind], m, s, seed, kmax, _ptr(x), tol, maxit, rho_hat,
                        _ptr(xs) if xs is not None else None, ctypes.byref(it), _ptr(hist))
     return x, it.value, st, hist[: it.value + 1]
 

@@ -625,6 +625,70 @@ int orc_ihs(const double* A, int64_t n, int64_t d, int64_t ld, const double* b, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Flexible CG with refreshed embeddings (Section 1, eqs. eqnconjugatedirections- */
+/* refreshed (GCC) and eqnflexiblecg (FCG); Section 4): at iteration t, with a     */
+/* fresh sketch S_t (instance t) and r_t = b - H x_t,                             */
+/*   v_t = H_{S_t}^{-1} r_t,                                                      */
+/*   p_t = v_t - sum_{j = t-k_t}^{t-1} <v_t, H p_j> / <p_j, H p_j> p_j,           */
+/*   x_{t+1} = x_t + <p_t, r_t> / <p_t, H p_t> p_t,  r_{t+1} = r_t - alpha H p_t,   */
+/* k_t = min(t, kmax); kmax < 0 keeps every earlier direction (GCC), kmax = 1 is  */
+/* IPCG.  The step <p_t, r_t>/<p_t, H p_t> is the paper's <p_t, b>/<p_t, H p_t>   */
+/* for x_0 = 0 and conjugate directions, written for any x_0.  Convergence is     */
+/* tested on r_t^T v_t before the update, as for IHS.                            */
+/* ------------------------------------------------------------------------ */
+int orc_fcg(const double* A, int64_t n, int64_t d, int64_t ld, const double* b, int sketch_type, int64_t m, int s,
+            uint64_t seed, int kmax, double* x, double tol, int maxit, double rho_hat, const double* xstar,
+            int* iters_out, double* hist) {
+  double* r = (double*)malloc(sizeof(double) * (size_t)d);
+  double* v = (double*)malloc(sizeof(double) * (size_t)d);
+  double* p = (double*)malloc(sizeof(double) * (size_t)d);
+  double* Hp = (double*)malloc(sizeof(double) * (size_t)d);
+  double* P = (double*)malloc(sizeof(double) * (size_t)(d * (maxit + 1)));
+  double* HP = (double*)malloc(sizeof(double) * (size_t)(d * (maxit + 1)));
+  double* qs = (double*)malloc(sizeof(double) * (size_t)(maxit + 1));
+  double* SA = (double*)malloc(sizeof(double) * (size_t)(m * d));
+  double* G = (double*)malloc(sizeof(double) * (size_t)(d * d));
+  double* R = (double*)malloc(sizeof(double) * (size_t)(d * d));
+  double* e1 = (double*)malloc(sizeof(double) * (size_t)d);
+  double* e2 = (double*)malloc(sizeof(double) * (size_t)d);
+  double q;
+  orc_hmatvec(A, n, d, ld, x, v, &q);
+  for (int64_t c = 0; c < d; ++c) r[c] = b[c] - v[c];
+  if (hist) hist[0] = xstar ? half_h_err2(A, n, d, ld, x, xstar, e1, e2) : 0.0;
+  int status = ORC_ERR_MAXIT, t = 0;
+  for (t = 0; t < maxit; ++t) {
+    int st = ORC_OK;
+    if (sketch_type == 0) orc_sketch_gauss(A, n, d, ld, m, seed, (uint32_t)t, SA);
+    else if (sketch_type == 1) st = orc_sketch_srht(A, n, d, ld, m, seed, (uint32_t)t, SA);
+    else st = orc_sketch_sjlt(A, n, d, ld, m, s, seed, (uint32_t)t, SA);
+    if (st != ORC_OK) { status = st; break; }
+    orc_gram(SA, m, d, G);
+    if (orc_cholesky_upper(G, d, R) != 0) { status = ORC_ERR_RANK; break; }
+    orc_precond_solve(R, d, r, v);
+    double rv = dot(r, v, d);
+    if (!isfinite(rv)) { status = ORC_ERR_BREAKDOWN; break; }
+    if (rv == 0.0 || converged(rv, rho_hat, tol, dot(b, x, d))) { status = ORC_OK; break; }
+    int kt = (kmax < 0 || kmax > t) ? t : kmax;
+    for (int64_t c = 0; c < d; ++c) p[c] = v[c];
+    for (int j = t - kt; j < t; ++j) {
+      double coef = dot(v, HP + (int64_t)j * d, d) / qs[j];
+      for (int64_t c = 0; c < d; ++c) p[c] -= coef * P[(int64_t)j * d + c];
+    }
+    orc_hmatvec(A, n, d, ld, p, Hp, &q);
+    if (!(q > 0.0) || !isfinite(q)) { status = ORC_ERR_BREAKDOWN; break; }
+    double alpha = dot(p, r, d) / q;
+    for (int64_t c = 0; c < d; ++c) { x[c] += alpha * p[c]; r[c] -= alpha * Hp[c]; }
+    memcpy(P + (int64_t)t * d, p, sizeof(double) * (size_t)d);
+    memcpy(HP + (int64_t)t * d, Hp, sizeof(double) * (size_t)d);
+    qs[t] = q;
+    if (hist) hist[t + 1] = xstar ? half_h_err2(A, n, d, ld, x, xstar, e1, e2) : rv;
+  }
+  *iters_out = t;
+  free(r); free(v); free(p); free(Hp); free(P); free(HP); free(qs); free(SA); free(G); free(R); free(e1); free(e2);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* x* by its definition, H x* = b: Householder QR of A (so H = R_A^T R_A),     */
 /* then iterative refinement with the residual b - A^T A x in double-double   */
 /* until the correction is below 1e-17 of x (at most 10 steps).               */
