@@ -35,9 +35,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("LSQ_BENCH_PRECISION", "f64"), choices=["f64", "mixed"])
+    ap.add_argument("--precision", default=os.environ.get("LSQ_BENCH_PRECISION", "mixed"), choices=["f64", "mixed"])
     ap.add_argument("--sketch", default="srht", choices=["srht", "sjlt", "gauss"])
-    ap.add_argument("--sketch-precision", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--sketch-precision", default="f32", choices=["f64", "f32", "bf16"])
     ap.add_argument("--a-dtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--outlier-frac", type=float, default=0.0)
     ap.add_argument("--m", type=int, default=4096)
@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing plain FP64 PCG beside the build")
     return ap.parse_args()
 
 
@@ -269,6 +270,28 @@ def run_ours(args):
     pass_bytes = n * d * A.element_size()
     achieved = passes * pass_bytes / (solve_ms * 1e-3) / 1e9
 
+    # plain FP64 PCG on the same inputs (FP64 sketch, FP64 passes), the metric's comparison
+    plain = None
+    if not args.no_plain and (args.precision != "f64" or args.sketch_precision != "f64"):
+        def plain_once():
+            SA = L.lsq_sketch(ctx, A, args.sketch, args.m, 0, precision="f64")
+            _, Wm = L.lsq_factor(ctx, SA)
+            return L.lsq_solve(ctx, A, b, "pcg", Wm, tol=args.tol, maxit=1000, m=args.m, precision="f64")
+
+        plain_once()
+        p_ms, p_info = [], None
+        for _ in range(max(1, args.steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            _, p_info = plain_once()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            p_ms.append(e0.elapsed_time(e1))
+        pm = statistics.median(p_ms)
+        plain = {"ms": pm, "iters": p_info["iters"], "est_err": p_info["est_err"], "status": p_info["status"],
+                 "speedup": pm / statistics.median(step_ms)}
+
     # end to end: pinned host A and b -> device, solve, x -> host, every step
     e2e = None
     if not args.no_e2e:
@@ -303,7 +326,8 @@ def run_ours(args):
         line = {
             "metric": "time-to-1e-10 H-norm error per solve", "value": ms_per_solve, "unit": "ms",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "f64" else "f32+f64",
             "data": "synthetic (seeded; A = G diag(sigma), replicas on distinct seeds)",
             "config": workload_config(args, f"replicas{world}"),
             "phases": {"solve_ms": solve_ms, "iters": iters, "passes": passes,
@@ -313,6 +337,7 @@ def run_ours(args):
                          "frac": achieved / hbm, "traffic": None,
                          "kernel": SOLVE_KERNEL, "peak_kind": f"{peak_kind} (burst copy)",
                          "algorithmic_bytes_per_launch": passes * pass_bytes},
+            "plain_fp64_pcg": plain,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)

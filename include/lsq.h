@@ -60,7 +60,10 @@ typedef enum {
 typedef enum {
   LSQ_PCG = 0,        /* Section 1, eq. (PCG); fixed embedding */
   LSQ_IHS = 1,        /* Section 1, eq. eqnihs */
-  LSQ_POLYAK_IHS = 2  /* Section 1, eq. eqnpolyakihs */
+  LSQ_POLYAK_IHS = 2, /* Section 1, eq. eqnpolyakihs */
+  LSQ_FCG = 3         /* Section 1, eqs. eqnconjugatedirectionsrefreshed / eqnflexiblecg:
+                         conjugate directions against the last fcg_k directions, a fresh
+                         embedding per iteration (GCC: fcg_k < 0, IPCG: fcg_k = 1) */
 } lsq_method;
 
 /* Arithmetic used for the passes over A inside lsq_solve.
@@ -173,6 +176,8 @@ typedef struct {
                             residual norm and every recursive convergence) */
   int32_t grid_blocks; /* 0 = automatic; else the number of resident CTAs of the solve kernel */
   int32_t x0_zero;     /* 1: x0 is zero, so the initial residual b - H x0 = b needs no pass over A */
+  int32_t fcg_k;       /* LSQ_FCG: directions kept for orthogonalisation; < 0 (default) keeps
+                          all of them (GCC), 1 gives IPCG, k gives FCG(k) */
 } lsq_solve_opts;
 
 /* Results of lsq_solve. */
@@ -194,7 +199,10 @@ LSQ_API void lsq_solve_opts_default(lsq_solve_opts* opts);
  *   b      : device, d FP64.
  *   method : lsq_method.
  *   W      : device, d x d FP64, W = R^{-1} from lsq_factor (fixed embedding); NULL
- *            with opts->refresh = 1 draws a new embedding every iteration (IHS/Polyak).
+ *            with opts->refresh = 1 draws a new embedding every iteration (IHS, Polyak,
+ *            FCG; the sketches of LSQ_FCG are FP32 under LSQ_PREC_MIXED, FP64 otherwise).
+ *            LSQ_FCG takes every H p_t from a full-precision pass (FP64, or double-FP32
+ *            under LSQ_PREC_MIXED) since its orthogonalisation uses the stored H p_j.
  *   x      : device, d FP64; in: x0, out: the last iterate.
  *   tol    : stop when (1+sqrt(rho))^2 r^T H_S^{-1} r <= tol^2 <b, x>, which bounds the
  *            relative H-norm error ||x - x*||_H / ||x*||_H by tol on the event E_rho

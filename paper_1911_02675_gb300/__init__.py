@@ -28,7 +28,7 @@ STATUS = {0: "LSQ_OK", 1: "LSQ_ERR_ARG", 2: "LSQ_ERR_RANK", 3: "LSQ_ERR_BREAKDOW
           5: "LSQ_ERR_TIMEOUT", 6: "LSQ_ERR_CUDA", 7: "LSQ_ERR_ALLOC"}
 LSQ_OK, LSQ_ERR_ARG, LSQ_ERR_RANK, LSQ_ERR_BREAKDOWN, LSQ_ERR_MAXIT, LSQ_ERR_TIMEOUT, LSQ_ERR_CUDA, LSQ_ERR_ALLOC = range(8)
 SKETCH = {"gauss": 0, "srht": 1, "sjlt": 2}
-METHOD = {"pcg": 0, "ihs": 1, "polyak": 2}
+METHOD = {"pcg": 0, "ihs": 1, "polyak": 2, "fcg": 3}
 PRECISION = {"f64": 0, "mixed": 1}
 SKETCH_PRECISION = {"f64": 0, "f32": 1, "bf16": 2}
 DTYPE = {torch.float64: 0, torch.float32: 1}
@@ -58,7 +58,8 @@ class LsqSolveOpts(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("mu", ctypes.c_double), ("beta", ctypes.c_double),
                 ("refresh", ctypes.c_int32), ("sketch_type", ctypes.c_int32), ("m", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("s", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("refresh_every", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("x0_zero", ctypes.c_int32)]
+                ("refresh_every", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("x0_zero", ctypes.c_int32),
+                ("fcg_k", ctypes.c_int32)]
 
 
 class LsqAdvice(ctypes.Structure):

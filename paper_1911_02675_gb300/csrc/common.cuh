@@ -52,6 +52,10 @@ void lsq_count_launch();
 lsq_status lsq_ensure_scratch(lsq_ctx* ctx, size_t bytes);
 lsq_status lsq_ensure_state(lsq_ctx* ctx, size_t bytes);
 
+// LSQ_FCG behind lsq_solve (arguments already checked; W_fixed = NULL refreshes)
+lsq_status lsq_fcg_solve(lsq_ctx* ctx, const lsq_matrix* A, const double* b, const double* W_fixed, double* x,
+                         double tol, int maxit, const lsq_solve_opts& o, double lam1, lsq_solve_info* info);
+
 static inline size_t lsq_align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Carves consecutive 256-byte aligned regions out of a base pointer.

@@ -2,18 +2,27 @@
 // BF16 operands and FP32 accumulation in tensor memory (Section 2: a Gaussian embedding is
 // a dense m x n matrix, so S A is a true dense contraction).
 //
-// A CTA owns a 128 x NT tile of SA (NT = 256 or 512 accumulator columns in TMEM) and a
-// contiguous range of rows of A (split-K).  Per stage of 64 rows:
-//   * all threads generate the 128 x 64 tile of S from Philox4x32-10 + Box-Muller (FP32,
-//     rounded to BF16) and narrow the 64 x NT tile of A to BF16, writing both into shared
-//     memory in the canonical K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per
-//     core matrix; K-adjacent core matrices 128 bytes apart, 8-row groups 256 bytes apart);
-//   * one thread issues the tcgen05.mma instructions (M = 128, N = 256, K = 16 each) and
-//     commits them to the stage's mbarrier, which the producers wait on (bounded) before
-//     they overwrite the stage.
-// The epilogue reads the accumulator with tcgen05.ld and writes FP32 partials; a fixed-order
-// reduction over the splits (sketch.cu) scales by 1/sqrt(m) and writes SA in FP64.
+// Two kernels per chunk of rows of A:
+//   * pack_kernel narrows the chunk to BF16 and writes it in the tensor core's canonical
+//     K-major, no-swizzle core-matrix layout, one contiguous blob of 64 rows x NT columns
+//     per (64-row block, column tile): core matrices of 8 columns x 8 rows (16 bytes per
+//     column), K-adjacent core matrices 128 bytes apart, 8-column groups 256 bytes apart,
+//     16-row K-steps NT * 32 bytes apart.  A blob is then one bulk copy (cp.async.bulk).
+//   * gauss_tc_kernel: a CTA owns a 128 x NT tile of SA (NT = 256 or 512 FP32 accumulator
+//     columns in TMEM) and a contiguous range of 64-row blocks (split-K).  Per stage, one
+//     thread starts the bulk copy of the blob into shared memory (completion counted in
+//     bytes on the stage's `full` mbarrier) while every thread generates the 128 x 64 tile
+//     of S from Philox4x32-10 + Box-Muller (FP32, rounded to BF16) in the same layout; then
+//     one thread issues the tcgen05.mma instructions (M = 128, N = 256, K = 16) and
+//     commits them to the stage's `empty` mbarrier, which the generators wait on before
+//     they overwrite the stage.  Every wait is bounded and records LSQ_ERR_TIMEOUT.
+// The epilogue reads the accumulator with tcgen05.ld and adds it into FP32 partials per
+// split; a fixed-order reduction over the splits scales by 1/sqrt(m) and writes SA in FP64.
 // S is never stored in global memory.
+//
+// Sketch rows j0 + 2 q' (cosine of pair q') sit in tile row q', rows j0 + 2 q' + 1 (sine)
+// in tile row q' + 64, so that one thread's Philox call fills both halves and a warp's
+// shared stores cover 512 contiguous bytes.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -25,7 +34,6 @@ namespace {
 
 constexpr int TC_M = 128;
 constexpr int TC_KS = 64;  // rows of A per stage (4 MMAs of K = 16)
-constexpr int TC_THREADS = 256;
 constexpr uint32_t TC_SPIN = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -54,6 +62,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
   }
   return true;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// one bulk global -> shared copy (16-byte aligned ends, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
@@ -112,11 +132,42 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// z(j, i) pair for j = 2q (cosine) and 2q + 1 (sine) in FP32, from the same Philox words as
-// the FP64 definition; the uniforms keep the top 24 of their 53 bits (BF16 keeps 8)
-__device__ __forceinline__ void gauss_pair_f32(uint64_t seed, uint32_t i, uint32_t q, uint32_t t, float& zc,
+// Philox4x32-10 with the ten round keys computed once per thread (the same function as
+// philox4x32_10: key k_r = k_0 + r * increment)
+struct RoundKeys {
+  uint32_t a[10], b[10];
+};
+
+__device__ __forceinline__ RoundKeys round_keys(uint64_t seed) {
+  RoundKeys k;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    k.a[r] = k0;
+    k.b[r] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return k;
+}
+
+__device__ __forceinline__ uint4 philox_keyed(uint4 c, const RoundKeys& k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.a[r], lo1, hi0 ^ c.w ^ k.b[r], lo0);
+  }
+  return c;
+}
+
+// z(2q, i) (cosine) and z(2q + 1, i) (sine) in FP32 from the same Philox words as the FP64
+// definition; the uniforms keep the top 24 of their 53 bits (BF16 keeps 8)
+__device__ __forceinline__ void gauss_pair_f32(const RoundKeys& k, uint32_t i, uint32_t q, uint32_t t, float& zc,
                                                float& zs) {
-  const uint4 w = philox_at(seed, i, q, t, TAG_GAUSS);
+  const uint4 w = philox_keyed(make_uint4(i, q, t, TAG_GAUSS), k);
   const float u1 = __fmaf_rn((float)(w.x >> 8), 0x1p-24f, 0x1p-25f);
   const float u2 = __fmaf_rn((float)(w.z >> 8), 0x1p-24f, 0x1p-25f);
   const float rad = sqrtf(-2.0f * __logf(u1));
@@ -126,35 +177,69 @@ __device__ __forceinline__ void gauss_pair_f32(uint64_t seed, uint32_t i, uint32
   zs = rad * s;
 }
 
-// byte offset of element (row r, k) of a K-major operand tile with R rows and TC_KS columns
-// (K-step kk = k / 16 occupies R * 32 bytes)
-__device__ __forceinline__ uint32_t core_offset(int R, int r, int kgroup) {
-  const int kk = kgroup >> 1, kc = kgroup & 1;  // 8-wide K groups: 2 per K-step
+// byte offset of element (row r, k-group kg of 8) of a K-major operand tile with R rows and
+// TC_KS columns (K-step kk = kg / 2 occupies R * 32 bytes)
+__host__ __device__ __forceinline__ uint32_t core_offset(int R, int r, int kgroup) {
+  const int kk = kgroup >> 1, kc = kgroup & 1;
   return (uint32_t)(kk * R * 32 + (r >> 3) * 256 + kc * 128 + (r & 7) * 16);
 }
 
-template <typename TA, int NT, int STAGES>
-__global__ void __launch_bounds__(TC_THREADS, 1) gauss_tc_kernel(const TA* __restrict__ A, int64_t n, int d,
-                                                                 int64_t ld, int m, uint64_t seed, uint32_t t,
-                                                                 int64_t rows_per_split, float* __restrict__ part,
-                                                                 int* err) {
+// ------------------------------------------------------------------------------------
+// Rows [row0, row0 + rows) of A -> BF16 blobs; blob (kb, ct) at byte ((kb * nct + ct) * NT * 128).
+// Unit = 8 consecutive rows of one column (one 16-byte store); zero outside n x d.
+// ------------------------------------------------------------------------------------
+template <typename TA>
+__global__ void __launch_bounds__(256) pack_kernel(const TA* __restrict__ A, int64_t n, int d, int64_t ld,
+                                                   int64_t row0, int64_t nkb, int nt, int nct,
+                                                   uint8_t* __restrict__ out) {
+  const int dpad = nt * nct;
+  const int64_t units = nkb * 8 * (int64_t)dpad;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(u % dpad);
+    const int64_t rest = u / dpad;
+    const int kg = (int)(rest & 7);
+    const int64_t kb = rest >> 3;
+    const int64_t i0 = row0 + kb * TC_KS + kg * 8;
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t i = i0 + q;
+      v[q] = (i < n && c < d) ? lsq_apass::narrow_f32(__ldg(A + i * ld + c)) : 0.f;
+    }
+    const int ct = c / nt, nn = c - ct * nt;
+    uint8_t* blob = out + ((size_t)kb * nct + ct) * (size_t)nt * 128;
+    *reinterpret_cast<uint4*>(blob + core_offset(nt, nn, kg)) =
+        make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+  }
+}
+
+template <int NT, int STAGES, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
+    gauss_tc_kernel(const uint8_t* __restrict__ pk, int64_t nkb, int nct, int d, int m, uint64_t seed, uint32_t t,
+                    int64_t row0, int64_t kb_per_split, int accumulate, float* __restrict__ part, int* err) {
   constexpr int A_BYTES = TC_M * TC_KS * 2;
   constexpr int B_BYTES = NT * TC_KS * 2;
   constexpr uint32_t IDESC = idesc_bf16(TC_M, 256);
+  constexpr int UNITS = (TC_M / 2) * (TC_KS / 8);  // 512 (pair of rows, k-group) per stage
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
-  __shared__ __align__(8) uint64_t mbar[STAGES];
+  __shared__ __align__(8) uint64_t full[STAGES];
+  __shared__ __align__(8) uint64_t empty[STAGES];
   __shared__ uint32_t tmem_base_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int j0 = blockIdx.x * TC_M, c0 = blockIdx.y * NT;
-  const int64_t i_begin = (int64_t)blockIdx.z * rows_per_split;
-  const int64_t i_end = min(n, i_begin + rows_per_split);
-  const int64_t nsteps = i_end > i_begin ? (i_end - i_begin + TC_KS - 1) / TC_KS : 0;
+  const int j0 = blockIdx.x * TC_M, ct = blockIdx.y;
+  const int64_t kb_begin = (int64_t)blockIdx.z * kb_per_split;
+  const int64_t kb_end = min(nkb, kb_begin + kb_per_split);
+  const int64_t nsteps = kb_end > kb_begin ? kb_end - kb_begin : 0;
+  const RoundKeys keys = round_keys(seed);
 
   if (warp == 0) tmem_alloc(&tmem_base_s, NT);
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(&mbar[s], 1);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -162,86 +247,123 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gauss_tc_kernel(const TA* __res
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
   bool ok = true;
+  int64_t copies = 0;  // bulk copies started (thread 0)
 
-  for (int64_t step = 0; step < nsteps && ok; ++step) {
+  for (int64_t step = 0; step < nsteps; ++step) {
     const int s = (int)(step % STAGES);
     if (step >= STAGES) {
       // the MMAs that read this stage STAGES steps ago have completed
-      ok = mbar_wait_bounded(&mbar[s], (uint32_t)(((step / STAGES) - 1) & 1), err);
-      if (__syncthreads_or(!ok)) {
-        ok = false;
-        break;
-      }
+      ok = ok && mbar_wait_bounded(&empty[s], (uint32_t)(((step / STAGES) - 1) & 1), err);
     }
-    const int64_t k0 = i_begin + step * TC_KS;
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+    const int64_t kb = kb_begin + step;
     uint8_t* stA = sA + s * A_BYTES;
     uint8_t* stB = sB + s * B_BYTES;
-    // S tile: 64 pairs of sketch rows x 8 groups of 8 rows of A
-    for (int u = tid; u < (TC_M / 2) * (TC_KS / 8); u += TC_THREADS) {
-      const int jp = u >> 3, kg = u & 7;
+    if (tid == 0) {
+      mbar_expect_tx(&full[s], (uint32_t)B_BYTES);
+      bulk_g2s(stB, pk + ((size_t)kb * nct + ct) * (size_t)B_BYTES, (uint32_t)B_BYTES, &full[s]);
+      ++copies;
+    }
+    // S tile: unit u -> pair jp (tile rows jp and jp + 64), k-group kg; a warp's 32 stores
+    // fill 512 contiguous bytes
+    const uint32_t i_base = (uint32_t)(row0 + kb * TC_KS);
+#pragma unroll 1
+    for (int u = tid; u < UNITS; u += THREADS) {
+      const int ln = u & 31, blk = u >> 5;
+      const int kk = blk & 3, gpair = blk >> 2;
+      const int r8 = ln & 7, kc = (ln >> 3) & 1, gsub = ln >> 4;
+      const int jp = 8 * (2 * gpair + gsub) + r8;
+      const int kg = 2 * kk + kc;
       uint32_t ev[4], od[4];
 #pragma unroll
       for (int q = 0; q < 8; q += 2) {
-        float c_a = 0.f, s_a = 0.f, c_b = 0.f, s_b = 0.f;
-        const int64_t ia = k0 + kg * 8 + q;
-        if (ia < i_end) gauss_pair_f32(seed, (uint32_t)ia, (uint32_t)((j0 >> 1) + jp), t, c_a, s_a);
-        if (ia + 1 < i_end) gauss_pair_f32(seed, (uint32_t)(ia + 1), (uint32_t)((j0 >> 1) + jp), t, c_b, s_b);
+        float c_a, s_a, c_b, s_b;
+        const uint32_t ia = i_base + (uint32_t)(kg * 8 + q);
+        gauss_pair_f32(keys, ia, (uint32_t)((j0 >> 1) + jp), t, c_a, s_a);
+        gauss_pair_f32(keys, ia + 1, (uint32_t)((j0 >> 1) + jp), t, c_b, s_b);
         ev[q >> 1] = pack_bf16(c_a, c_b);
         od[q >> 1] = pack_bf16(s_a, s_b);
       }
-      *reinterpret_cast<uint4*>(stA + core_offset(TC_M, 2 * jp, kg)) = make_uint4(ev[0], ev[1], ev[2], ev[3]);
-      *reinterpret_cast<uint4*>(stA + core_offset(TC_M, 2 * jp + 1, kg)) = make_uint4(od[0], od[1], od[2], od[3]);
-    }
-    // A tile: NT columns x 8 groups of 8 rows, narrowed to BF16
-    for (int u = tid; u < NT * (TC_KS / 8); u += TC_THREADS) {
-      const int nn = u % NT, kg = u / NT;
-      const int col = c0 + nn;
-      float v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int64_t i = k0 + kg * 8 + q;
-        v[q] = (i < i_end && col < d) ? lsq_apass::narrow_f32(__ldg(A + i * ld + col)) : 0.f;
-      }
-      *reinterpret_cast<uint4*>(stB + core_offset(NT, nn, kg)) =
-          make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+      *reinterpret_cast<uint4*>(stA + core_offset(TC_M, jp, kg)) = make_uint4(ev[0], ev[1], ev[2], ev[3]);
+      *reinterpret_cast<uint4*>(stA + core_offset(TC_M, jp + 64, kg)) = make_uint4(od[0], od[1], od[2], od[3]);
     }
     // generic-proxy writes -> visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
-      tc_fence_after();
+      ok = mbar_wait_bounded(&full[s], (uint32_t)((step / STAGES) & 1), err);
+      if (ok) {
+        tc_fence_after();
 #pragma unroll
-      for (int kk = 0; kk < TC_KS / 16; ++kk) {
-        const uint64_t ad = smem_desc(smem_u32(stA + kk * TC_M * 32), 128, 256);
+        for (int kk = 0; kk < TC_KS / 16; ++kk) {
+          const uint64_t ad = smem_desc(smem_u32(stA + kk * TC_M * 32), 128, 256);
 #pragma unroll
-        for (int h = 0; h < NT / 256; ++h) {
-          const uint64_t bd = smem_desc(smem_u32(stB + kk * NT * 32 + h * (256 / 8) * 256), 128, 256);
-          mma_bf16(tmem + h * 256, ad, bd, IDESC, (step > 0 || kk > 0) ? 1u : 0u);
+          for (int h = 0; h < NT / 256; ++h) {
+            const uint64_t bd = smem_desc(smem_u32(stB + kk * NT * 32 + h * (256 / 8) * 256), 128, 256);
+            mma_bf16(tmem + h * 256, ad, bd, IDESC, (step > 0 || kk > 0) ? 1u : 0u);
+          }
         }
+        mma_commit(&empty[s]);
       }
-      mma_commit(&mbar[s]);
     }
   }
   // all MMAs done: the last commit tracks every earlier one
+  ok = !__syncthreads_or(!ok);
   if (ok && nsteps > 0) {
     const int64_t last = nsteps - 1;
-    ok = mbar_wait_bounded(&mbar[last % STAGES], (uint32_t)((last / STAGES) & 1), err);
+    ok = mbar_wait_bounded(&empty[last % STAGES], (uint32_t)((last / STAGES) & 1), err);
   }
   ok = !__syncthreads_or(!ok);
+  if (!ok && tid == 0) {
+    // a failed run may leave bulk copies in flight: wait (bounded) for each stage's last one
+    for (int64_t c = (copies > STAGES ? copies - STAGES : 0); c < copies; ++c)
+      (void)mbar_wait_bounded(&full[c % STAGES], (uint32_t)((c / STAGES) & 1), err);
+  }
   tc_fence_after();
-  if (warp < 4) {
-    const int j = j0 + 32 * warp + lane;
+  if (ok && nsteps > 0) {
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31; the warps sharing a lane group split the columns
+    constexpr int GROUPS = THREADS / 128;
+    const int lg = warp & 3, cg = warp >> 2;
+    const int L = 32 * lg + lane;
+    const int j = j0 + (L < 64 ? 2 * L : 2 * (L - 64) + 1);
     float* out = part + (int64_t)blockIdx.z * m * d;
-    for (int cb = 0; cb < NT; cb += 16) {
+    for (int cb = 16 * cg; cb < NT; cb += 16 * GROUPS) {
       uint32_t r[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb, r);
-      if (j < m) {
+      tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)cb, r);
+      const int col0 = ct * NT + cb;
+      if (j < m && col0 < d) {
+        float* o = out + (int64_t)j * d + col0;
+        if ((d & 3) == 0 && col0 + 16 <= d) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int col = c0 + cb + q;
-          if (col < d) out[(int64_t)j * d + col] = (ok && nsteps > 0) ? __uint_as_float(r[q]) : 0.f;
+          for (int q = 0; q < 16; q += 4) {
+            float4 v = make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]), __uint_as_float(r[q + 2]),
+                                   __uint_as_float(r[q + 3]));
+            if (accumulate) {
+              const float4 p = *reinterpret_cast<const float4*>(o + q);
+              v.x += p.x;
+              v.y += p.y;
+              v.z += p.z;
+              v.w += p.w;
+            }
+            *reinterpret_cast<float4*>(o + q) = v;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (col0 + q < d) o[q] = (accumulate ? o[q] : 0.f) + __uint_as_float(r[q]);
         }
       }
+    }
+  } else if (!accumulate) {
+    // nothing accumulated (no rows, or a failed run): the partial tile is zero
+    float* out = part + (int64_t)blockIdx.z * m * d;
+    for (int e = tid; e < TC_M * NT; e += THREADS) {
+      const int row = e / NT, col = ct * NT + e % NT;
+      const int jj = j0 + (row < 64 ? 2 * row : 2 * (row - 64) + 1);
+      if (jj < m && col < d) out[(int64_t)jj * d + col] = 0.f;
     }
   }
   tc_fence_before();
@@ -249,43 +371,93 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gauss_tc_kernel(const TA* __res
   if (warp == 0) tmem_dealloc(tmem, NT);
 }
 
-}  // namespace
-
-// entry from sketch.cu: FP32 partials [splits][m][d] of the Gaussian sketch (unscaled)
-lsq_status lsq_gauss_tc_partials(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, float* part,
-                                 int splits, int64_t rows_per_split, int nt, int* err) {
-  const int d = (int)A->d;
-  const int gx = (m + TC_M - 1) / TC_M, gy = (d + nt - 1) / nt;
-  dim3 grid(gx, gy, splits);
-  if (nt == 512) {
-    constexpr int STAGES = 2;
-    const size_t smem = (size_t)STAGES * (TC_M * TC_KS * 2 + 512 * TC_KS * 2);
-    if (A->dtype == LSQ_F64) {
-      auto k = gauss_tc_kernel<double, 512, STAGES>;
-      LSQ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k<<<grid, TC_THREADS, smem, ctx->stream>>>(reinterpret_cast<const double*>(A->data), A->n, d, A->ld, m, seed, t,
-                                                 rows_per_split, part, err);
-    } else {
-      auto k = gauss_tc_kernel<float, 512, STAGES>;
-      LSQ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k<<<grid, TC_THREADS, smem, ctx->stream>>>(reinterpret_cast<const float*>(A->data), A->n, d, A->ld, m, seed, t,
-                                                 rows_per_split, part, err);
-    }
-  } else {
-    constexpr int STAGES = 3;
-    const size_t smem = (size_t)STAGES * (TC_M * TC_KS * 2 + 256 * TC_KS * 2);
-    if (A->dtype == LSQ_F64) {
-      auto k = gauss_tc_kernel<double, 256, STAGES>;
-      LSQ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k<<<grid, TC_THREADS, smem, ctx->stream>>>(reinterpret_cast<const double*>(A->data), A->n, d, A->ld, m, seed, t,
-                                                 rows_per_split, part, err);
-    } else {
-      auto k = gauss_tc_kernel<float, 256, STAGES>;
-      LSQ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k<<<grid, TC_THREADS, smem, ctx->stream>>>(reinterpret_cast<const float*>(A->data), A->n, d, A->ld, m, seed, t,
-                                                 rows_per_split, part, err);
-    }
+// out[e] = scale * sum_g part[g][e], fixed order in g
+__global__ void reduce_tc_kernel(const float* __restrict__ part, int splits, int64_t md, double scale,
+                                 double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < md; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < splits; ++g) s += (double)part[(int64_t)g * md + e];
+    out[e] = scale * s;
   }
+}
+
+template <int NT, int STAGES, int THREADS>
+lsq_status launch_tc(lsq_ctx* ctx, dim3 grid, const uint8_t* pk, int64_t nkb, int nct, int d, int m, uint64_t seed,
+                     uint32_t t, int64_t row0, int64_t kb_per_split, int accumulate, float* part, int* err) {
+  const size_t smem = (size_t)STAGES * (TC_M * TC_KS * 2 + NT * TC_KS * 2);
+  auto k = gauss_tc_kernel<NT, STAGES, THREADS>;
+  LSQ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k<<<grid, THREADS, smem, ctx->stream>>>(pk, nkb, nct, d, m, seed, t, row0, kb_per_split, accumulate, part, err);
   LSQ_LAUNCH_CHECK();
   return LSQ_OK;
+}
+
+// split count whose CTA count fills whole waves best (one CTA per SM)
+int pick_splits(int tiles, int sms, int64_t kb_total, int64_t cap) {
+  int best = 1;
+  double best_eff = -1.0;
+  for (int s = 1; s <= 64 && s <= kb_total && s <= cap; ++s) {
+    const int64_t ctas = (int64_t)tiles * s;
+    const int64_t waves = (ctas + sms - 1) / sms;
+    double eff = (double)ctas / (double)(waves * sms);
+    if (waves < 2) eff *= 0.9;  // prefer at least two waves' worth of CTAs
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  return best;
+}
+
+}  // namespace
+
+// BF16 tensor-core Gaussian sketch into SA (FP64, m x d); called by lsq_sketch
+lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA) {
+  const int d = (int)A->d;
+  const int nt = d > 256 ? 512 : 256;
+  const int nct = (d + nt - 1) / nt;
+  const int tiles_m = (m + TC_M - 1) / TC_M;
+  const int tiles = tiles_m * nct;
+  const size_t blob = (size_t)nt * TC_KS * 2;
+  // chunks of at most 1 GiB of packed A
+  int64_t kb_chunk = std::max<int64_t>(1, ((int64_t)1 << 30) / (int64_t)(blob * nct));
+  const int64_t kb_total = (A->n + TC_KS - 1) / TC_KS;
+  kb_chunk = std::min(kb_chunk, kb_total);
+  const int64_t cap = std::max<int64_t>(1, ((int64_t)512 << 20) / ((int64_t)m * d * 4));
+  const int splits = pick_splits(tiles, ctx->sm_count, kb_chunk, cap);
+  const int64_t kb_per_split = (kb_chunk + splits - 1) / splits;
+  const size_t need = lsq_align256((size_t)kb_chunk * nct * blob) + lsq_align256((size_t)splits * m * d * 4) + 256;
+  lsq_status st = lsq_ensure_scratch(ctx, need);
+  if (st != LSQ_OK) return st;
+  Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};
+  uint8_t* pk = cv.take<uint8_t>((size_t)kb_chunk * nct * blob);
+  float* part = cv.take<float>((size_t)splits * m * d);
+  int* err = cv.take<int>(1);
+  LSQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  const dim3 grid(tiles_m, nct, splits);
+  for (int64_t kb0 = 0; kb0 < kb_total; kb0 += kb_chunk) {
+    const int64_t nkb = std::min(kb_chunk, kb_total - kb0);
+    const int64_t row0 = kb0 * TC_KS;
+    const int64_t units = nkb * 8 * (int64_t)nt * nct;
+    const int pgrid = (int)std::min<int64_t>((units + 255) / 256, 16 * (int64_t)ctx->sm_count);
+    if (A->dtype == LSQ_F64)
+      pack_kernel<double><<<pgrid, 256, 0, ctx->stream>>>(reinterpret_cast<const double*>(A->data), A->n, d, A->ld,
+                                                          row0, nkb, nt, nct, pk);
+    else
+      pack_kernel<float><<<pgrid, 256, 0, ctx->stream>>>(reinterpret_cast<const float*>(A->data), A->n, d, A->ld,
+                                                         row0, nkb, nt, nct, pk);
+    LSQ_LAUNCH_CHECK();
+    const int acc = kb0 > 0 ? 1 : 0;
+    st = nt == 512 ? launch_tc<512, 2, 512>(ctx, grid, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, acc, part, err)
+                   : launch_tc<256, 4, 512>(ctx, grid, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, acc, part, err);
+    if (st != LSQ_OK) return st;
+  }
+  const int64_t md = (int64_t)m * d;
+  const int rgrid = (int)std::min<int64_t>((md + 255) / 256, 4 * (int64_t)ctx->sm_count);
+  reduce_tc_kernel<<<rgrid, 256, 0, ctx->stream>>>(part, splits, md, 1.0 / sqrt((double)m), SA);
+  LSQ_LAUNCH_CHECK();
+  // a timed-out wait inside the tensor-core kernel is reported here
+  LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 13, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  LSQ_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ctx->host_status[13] ? (lsq_status)ctx->host_status[13] : LSQ_OK;
 }

@@ -783,39 +783,7 @@ static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint
 
 }  // namespace
 
-lsq_status lsq_gauss_tc_partials(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, float* part,
-                                 int splits, int64_t rows_per_split, int nt, int* err);
-
-namespace {
-
-// BF16 tensor-core Gaussian sketch: split-K over the rows of A, FP32 partials, fixed-order
-// reduction with the 1/sqrt(m) scale
-lsq_status gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA) {
-  const int d = (int)A->d;
-  const int nt = d > 256 ? 512 : 256;
-  const int tiles = lsq_ceil_div(m, 128) * lsq_ceil_div(d, nt);
-  const int64_t ksteps = (A->n + 63) / 64;
-  int64_t splits = std::max<int64_t>(1, (4 * (int64_t)ctx->sm_count + tiles - 1) / tiles);
-  const int64_t cap = std::max<int64_t>(1, ((int64_t)512 << 20) / ((int64_t)m * d * 4));
-  splits = std::max<int64_t>(1, std::min(std::min(splits, ksteps), cap));
-  const int64_t rows_per_split = ((ksteps + splits - 1) / splits) * 64;
-  splits = (A->n + rows_per_split - 1) / rows_per_split;
-  lsq_status st = lsq_ensure_scratch(ctx, lsq_align256((size_t)splits * m * d * 4) + 256);
-  if (st != LSQ_OK) return st;
-  Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};
-  float* part = cv.take<float>((size_t)splits * m * d);
-  int* err = cv.take<int>(1);
-  LSQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
-  st = lsq_gauss_tc_partials(ctx, A, m, seed, t, part, (int)splits, rows_per_split, nt, err);
-  if (st != LSQ_OK) return st;
-  const int64_t md = (int64_t)m * d;
-  reduce_splits_kernel<float><<<grid_for(md, 256, 4 * ctx->sm_count), 256, 0, ctx->stream>>>(
-      part, (int)splits, md, 1.0 / sqrt((double)m), SA);
-  LSQ_LAUNCH_CHECK();
-  return LSQ_OK;
-}
-
-}  // namespace
+lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA);
 
 extern "C" lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, int64_t m, uint64_t seed,
                                  const lsq_sketch_opts* opts, double* SA) {
@@ -831,7 +799,7 @@ extern "C" lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type
   const bool f64 = prec == LSQ_SKETCH_F64;
   switch (type) {
     case LSQ_SKETCH_GAUSS:
-      if (prec == LSQ_SKETCH_BF16) return gauss_tc_run(ctx, A, (int)m, seed, t, SA);
+      if (prec == LSQ_SKETCH_BF16) return lsq_gauss_tc_run(ctx, A, (int)m, seed, t, SA);
       return f64 ? gauss_run<double>(ctx, A, (int)m, seed, t, SA) : gauss_run<float>(ctx, A, (int)m, seed, t, SA);
     case LSQ_SKETCH_SRHT:
       return f64 ? srht_run<double>(ctx, A, (int)m, seed, t, SA) : srht_run<float>(ctx, A, (int)m, seed, t, SA);

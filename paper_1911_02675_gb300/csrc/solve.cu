@@ -384,6 +384,7 @@ extern "C" void lsq_solve_opts_default(lsq_solve_opts* o) {
   o->refresh_every = 12;
   o->grid_blocks = 0;
   o->x0_zero = 0;
+  o->fcg_k = -1;
 }
 
 extern "C" lsq_status lsq_hmatvec(lsq_ctx* ctx, const lsq_matrix* A, const double* p, double* v, double* q) {
@@ -421,7 +422,7 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   if (!ctx || !b || !x) return LSQ_ERR_ARG;
   lsq_status st = check_matrix(A);
   if (st != LSQ_OK) return st;
-  if (method != LSQ_PCG && method != LSQ_IHS && method != LSQ_POLYAK_IHS) return LSQ_ERR_ARG;
+  if (method != LSQ_PCG && method != LSQ_IHS && method != LSQ_POLYAK_IHS && method != LSQ_FCG) return LSQ_ERR_ARG;
   if (!(tol >= 0.0) || maxit < 0) return LSQ_ERR_ARG;
   lsq_solve_opts o;
   lsq_solve_opts_default(&o);
@@ -439,6 +440,7 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   }
   if (!(rho < 1.0)) return LSQ_ERR_ARG;
   const double lam1 = (1.0 + sqrt(rho)) * (1.0 + sqrt(rho));
+  if (method == LSQ_FCG) return lsq_fcg_solve(ctx, A, b, refresh ? nullptr : W, x, tol, maxit, o, lam1, info);
   double mu = o.mu, beta = o.beta;
   if (method == LSQ_PCG) {
     mu = 0.0;
@@ -575,7 +577,6 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
       void* args[] = {&a};
       LSQ_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(P), dim3(LSQ_THREADS), args, smem, s));
       lsq_count_launch();
-    lsq_count_launch();
       LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status, a.out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
       LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 12, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
       LSQ_CUDA_TRY(cudaStreamSynchronize(s));
