@@ -28,11 +28,29 @@ import workloads as WL  # noqa: E402
 
 SOLVE_KERNEL = "solve_kernel"
 
+# DRAM traffic of solve_kernel<double, 16, MIXED> from one ncu capture (n = 2^18, d = 512, SRHT m = 4096,
+# 26 passes; profiles/solve_kernel_mixed_262144x512_srht4096.md): dram__bytes_read.sum +
+# dram__bytes_write.sum of the launch divided by its algorithmic bytes.  Scaled to a launch of the
+# bench by its algorithmic bytes (units processed: passes x rows); reported only while the kernel's
+# sources hash to the captured ones.
+SOLVE_TRAFFIC = {"ratio": 28.013047e9 / 27917287424, "sources_sha256":
+                 "a2dff6f59512d4f86876957b4f784bf340e7c4c6aa39e9ae70ba1c5d71789cff"}
+
+
+def solve_sources_sha256() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("solve.cu", "apass.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1911_02675_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=os.environ.get("LSQ_BENCH_PRECISION", "mixed"), choices=["f64", "mixed"])
@@ -61,7 +79,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -77,7 +95,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -133,12 +151,13 @@ def make_inputs(args, seed):
 
 
 # ------------------------------------------------------------------------------ oracle arm
-def oracle_solve_sample(args, n_sample, seed=1):
+def oracle_solve_sample(args, n_sample, P=None, seed=1):
     """One solve of the oracle (sketch + factor + PCG) on the first n_sample rows of the
-    workload recipe.  Returns phase times (s) and the iteration count."""
+    workload recipe (or on the given problem P).  Returns phase times (s) and iterations."""
     import oracle as O
 
-    P = WL.make_problem(n_sample, args.d, args.sigma_max, seed=seed)
+    if P is None or P["A"].shape[0] != n_sample:
+        P = WL.make_problem(n_sample, args.d, args.sigma_max, seed=seed)
     A, b = P["A"], P["b"]
     m = min(args.m, O.next_pow2(n_sample))
     t0 = time.perf_counter()
@@ -151,17 +170,24 @@ def oracle_solve_sample(args, n_sample, seed=1):
     return {"sketch": t1 - t0, "factor": t2 - t1, "iters_s": t3 - t2, "iters": it, "status": st, "n": n_sample, "m": m}
 
 
-def oracle_estimate(args, n_sample):
-    """Oracle time per solve at the full workload, from a bounded sample: the O(n) phases
-    (sketch, passes over A) scale by n_full / n_sample; the factor does not depend on n."""
+def oracle_n_sample(args):
+    """The whole workload up to 2^20 rows (seconds of CPU work); above that the first 2^20 rows."""
+    return min(1 << args.n_log2, 1 << 20)
+
+
+def oracle_estimate(args, n_sample, P=None):
+    """Oracle time per solve at the full workload: measured on the whole workload when it has at
+    most 2^20 rows; otherwise the O(n) phases (sketch, passes over A) of an n_sample-row solve
+    are scaled by n_full / n_sample and the factor, which does not depend on n, is not."""
     import oracle as O
 
-    r = oracle_solve_sample(args, n_sample)
+    r = oracle_solve_sample(args, n_sample, P)
     scale = (1 << args.n_log2) / r["n"]
     est = r["sketch"] * scale + r["factor"] + r["iters_s"] * scale
-    sample = (f"oracle on the first {r['n']} rows of the same recipe (d={args.d}, {args.sketch} m={r['m']}, "
-              f"PCG to {args.tol:g}, {r['iters']} iterations); sketch and passes scaled by {scale:g}, "
-              f"factor unscaled; measured {r['sketch'] + r['factor'] + r['iters_s']:.2f} s")
+    what = "the whole workload" if scale == 1 else f"the first {r['n']} rows of the same recipe"
+    sample = (f"oracle on {what} (d={args.d}, {args.sketch} m={r['m']}, PCG to {args.tol:g}, {r['iters']} "
+              f"iterations)" + ("" if scale == 1 else f"; sketch and passes scaled by {scale:g}, factor unscaled")
+              + f"; measured {r['sketch'] + r['factor'] + r['iters_s']:.2f} s")
     return est * 1e3, sample, O.num_threads()
 
 
@@ -169,13 +195,14 @@ def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    n_sample = min(1 << args.n_log2, 1 << 16)
+    n_sample = oracle_n_sample(args)
+    P = WL.make_problem(n_sample, args.d, args.sigma_max, seed=1)
     times = []
     for _ in range(args.warmup):
-        oracle_estimate(args, n_sample)
+        oracle_estimate(args, n_sample, P)
     sample, cores = "", 0
     for _ in range(args.steps):
-        ms, sample, cores = oracle_estimate(args, n_sample)
+        ms, sample, cores = oracle_estimate(args, n_sample, P)
         times.append(ms)
     value = statistics.median(times)
     line = {
@@ -318,8 +345,13 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and args.a_dtype == "f64":
-        ms, sample, cores = oracle_estimate(args, min(n, 1 << 16))
+        ms, sample, cores = oracle_estimate(args, oracle_n_sample(args), P)
         cpu = {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
+
+    traffic = None
+    if (args.precision == "mixed" and args.a_dtype == "f64" and d == 512
+            and solve_sources_sha256() == SOLVE_TRAFFIC["sources_sha256"]):
+        traffic = SOLVE_TRAFFIC["ratio"] * passes * pass_bytes
 
     if rank == 0:
         clocks = clk.summary()
@@ -334,7 +366,7 @@ def run_ours(args):
                        "sketch_factor_ms": statistics.median(step_ms) - solve_ms,
                        "status": infos[-1]["status"], "est_err": infos[-1]["est_err"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm, "traffic": traffic,
                          "kernel": SOLVE_KERNEL, "peak_kind": f"{peak_kind} (burst copy)",
                          "algorithmic_bytes_per_launch": passes * pass_bytes},
             "plain_fp64_pcg": plain,
