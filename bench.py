@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing plain FP64 PCG beside the build")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="time the batched solve of this many uneven problems instead (k right-hand sides each)")
+    ap.add_argument("--batch-seed", type=int, default=1)
     return ap.parse_args()
 
 
@@ -378,9 +381,138 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------------------------------ batched workload
+def batch_config(args, parallelism):
+    return {"workload": f"batch{args.batch}_fp32_sjlt_m4d_pcg", "nprob": args.batch,
+            "n_range": [1 << 12, 1 << 18], "d_range": [32, 512], "k_range": [1, 16], "scale_max": 1e4,
+            "sketch": "sjlt", "s": 8, "m_factor": 4.0, "sketch_precision": args.sketch_precision,
+            "precision": args.precision, "method": "pcg (per right-hand side)", "tol": args.tol, "A_dtype": "f32",
+            "l2": "inputs larger than L2", "parallelism": parallelism}
+
+
+def oracle_batch_estimate(args, shapes):
+    """Oracle time for the whole batch from the problems of a bounded prefix (about 10 s of CPU
+    work), scaled by the share of sum(n d k) they carry."""
+    import oracle as O
+
+    total = sum(n * d * k for n, d, k in shapes)
+    done, t_acc, used = 0, 0.0, 0
+    for p, (n, d, k) in enumerate(shapes):
+        q = WL.make_batch([(n, d, k)], seed=args.batch_seed * 7919 + p, scale_max=1e4, dtype=np.float32)[0]
+        t0 = time.perf_counter()
+        O.solve_batched([(q["A"], q["B"])], kind="sjlt", s=8, m_factor=4.0, seed=0, tol=args.tol)
+        t_acc += time.perf_counter() - t0
+        done += n * d * k
+        used += 1
+        if t_acc > 10.0:
+            break
+    est = t_acc * total / done
+    sample = (f"oracle on the first {used} of {len(shapes)} problems ({100.0 * done / total:.1f} % of sum n d k), "
+              f"scaled by sum n d k; measured {t_acc:.2f} s")
+    return est * 1e3, sample, O.num_threads()
+
+
+def run_batch(args):
+    import torch
+
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        shapes = WL.batch_shapes(args.batch, seed=args.batch_seed)
+        times, sample, cores = [], "", 0
+        for _ in range(max(1, args.steps)):
+            ms, sample, cores = oracle_batch_estimate(args, shapes)
+            times.append(ms)
+        value = statistics.median(times)
+        print(json.dumps({
+            "impl": "reference", "metric": "time-to-1e-10 H-norm error per batch", "value": value, "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": 0, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": batch_config(args, "oracle"),
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1911_02675_gb300 as L
+
+    hbm, _, peak_kind = peaks()
+    shapes = WL.batch_shapes(args.batch, seed=args.batch_seed + rank)
+    probs = WL.make_batch_cuda(shapes, seed=args.batch_seed + rank, device=dev)
+    a_bytes = [n * d * 4 for n, d, _ in shapes]
+    ctx = L.Context(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve_once():
+        return L.lsq_solve_batched(ctx, probs, tol=args.tol, maxit=1000, precision=args.precision,
+                                   sketch_precision=args.sketch_precision, seed=0)
+
+    for _ in range(args.warmup):
+        solve_once()
+    torch.cuda.synchronize(dev)
+    launches0 = L.lsq_launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    infos, step_ms, pers = [], [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            X, per, info = solve_once()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            step_ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+            pers.append(per)
+    launches = L.lsq_launch_count() - launches0
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_batch = total_ms / (args.steps * world)
+    info = infos[-1]
+    per = pers[-1]
+    solve_ms = statistics.median(i["ms_solve"] for i in infos)
+    # algorithmic bytes of the persistent launch: one read of A_p per iteration the problem took
+    pass_bytes = sum(b * it for b, (it, _) in zip(a_bytes, per))
+    achieved = pass_bytes / (solve_ms * 1e-3) / 1e9
+    statuses = sorted(set(st for _, st in per))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        ms, sample, cores = oracle_batch_estimate(args, shapes)
+        cpu = {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "time-to-1e-10 H-norm error per batch", "value": ms_per_batch, "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "f64" else "f32+f64",
+            "data": "synthetic (seeded shapes; A drawn on the device, column scales 1..1e4)",
+            "config": batch_config(args, f"replicas{world}"),
+            "phases": {"sketch_ms": info["ms_sketch"], "factor_ms": info["ms_factor"], "solve_ms": solve_ms,
+                       "iters_max": info["iters_max"], "passes": info["passes"], "exact_passes": info["exact_passes"],
+                       "statuses": statuses, "rhs": sum(k for _, _, k in shapes),
+                       "A_GiB": sum(a_bytes) / 2 ** 30},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "batch_kernel", "peak_kind": f"{peak_kind} (burst copy)",
+                         "algorithmic_bytes_per_launch": pass_bytes},
+            "cpu_baseline": cpu, "e2e": None, "clocks": clk.summary(), "gpu_launches": launches}), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.batch > 0:
+        run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -276,6 +276,63 @@ typedef struct {
 
 LSQ_API lsq_status lsq_advise_sketch_size(int64_t n, int64_t d, double eps, int32_t sketch_type, lsq_advice* out);
 
+/* ---------------------------------------------------------------------------------
+ * Batched solves: many independent problems of uneven n, d and numbers of right-hand
+ * sides, each solved by PCG with its own fixed embedding (Section 1, eq. (PCG), applied
+ * per right-hand side; the iterations of all problems share one persistent launch).
+ * --------------------------------------------------------------------------------- */
+#define LSQ_MAX_RHS 16
+
+typedef struct {
+  lsq_matrix A;      /* n x d (device), d <= 512 */
+  const double* B;   /* device, k right-hand sides of length d: entry c of b_j at B[j * d + c] */
+  double* X;         /* device, same layout: in x0 (ignored when x0_zero), out the iterates */
+  int32_t k;         /* right-hand sides, 1 .. LSQ_MAX_RHS */
+  int32_t iters;     /* out: iterations until the last right-hand side of the problem stopped */
+  int32_t status;    /* out: LSQ_OK, LSQ_ERR_MAXIT, LSQ_ERR_BREAKDOWN or LSQ_ERR_RANK */
+  int32_t reserved;
+} lsq_problem;
+
+typedef struct {
+  int32_t sketch_type;      /* default LSQ_SKETCH_SJLT */
+  int32_t s;                /* SJLT nonzeros per column (default 8; at most m of a problem) */
+  double m_factor;          /* sketch size m = ceil(m_factor * d) (default 4; m >= d enforced) */
+  uint64_t seed;            /* problem p draws sketch instance t = p of this seed */
+  int32_t sketch_precision; /* lsq_sketch_precision (default LSQ_SKETCH_F32) */
+  int32_t precision;        /* lsq_precision (default LSQ_PREC_MIXED) */
+  double rho;               /* stopping-rule deviation parameter; default (<= 0): d/m per problem */
+  int32_t x0_zero;          /* 1 (default): every x0 is zero and X is overwritten */
+  int32_t refresh_every;    /* MIXED: most iterations between exact residual replacements (12) */
+  int32_t chunk_rows;       /* rows of A per work unit of the pass (0: tuned) */
+  int32_t grid_blocks;      /* resident CTAs of the persistent launch (0: one per SM) */
+} lsq_batch_opts;
+
+typedef struct {
+  int32_t iters_max;     /* iterations of the slowest right-hand side */
+  int32_t status;        /* LSQ_OK if every right-hand side converged, else the first error */
+  int32_t passes;        /* passes of the persistent launch over the active problems */
+  int32_t exact_passes;  /* of which exact (FP64 or double-FP32) residual passes */
+  double ms_total;       /* device time of the call (ms) */
+  double ms_sketch;      /* sketches of all problems */
+  double ms_factor;      /* factorisations of all problems */
+  double ms_solve;       /* the persistent PCG launch */
+} lsq_batch_info;
+
+LSQ_API void lsq_batch_opts_default(lsq_batch_opts* opts);
+
+/* lsq_solve_batched: for every problem p (host array `probs` of nprob entries, device data),
+ * draws its sketch (instance t = p), factors it (Cholesky of the Gram matrix, W = R^{-1}),
+ * then runs PCG on all right-hand sides of all problems in one persistent cooperative launch:
+ * each iteration makes one pass over A_p per active problem that yields A_p^T (A_p P) for all
+ * of its search directions at once, then the vector updates and W W^T per right-hand side.
+ * A right-hand side stops by rule (1+sqrt(rho))^2 r^T H_S^{-1} r <= tol^2 <b, x> (as in
+ * lsq_solve); a problem stops when all of its right-hand sides have. Under LSQ_PREC_MIXED the
+ * passes run in FP32 with exact (double-FP32) residual replacement as in lsq_solve.
+ * Returns LSQ_OK, LSQ_ERR_MAXIT, LSQ_ERR_BREAKDOWN, LSQ_ERR_RANK (see probs[p].status),
+ * LSQ_ERR_TIMEOUT, LSQ_ERR_ARG or LSQ_ERR_CUDA. Synchronises before returning. */
+LSQ_API lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem* probs, double tol, int32_t maxit,
+                                     const lsq_batch_opts* opts, lsq_batch_info* info);
+
 /* Human-readable name of a status code (static storage). */
 LSQ_API const char* lsq_status_str(int32_t status);
 

@@ -318,6 +318,28 @@ def fcg(A, b, *, kind="gauss", m, s=8, seed=0, kmax=-1, x0=None, tol=1e-10, maxi
     return x, it.value, st, hist[: it.value + 1]
 
 
+def solve_batched(problems, *, kind="sjlt", s=8, m_factor=4.0, seed=0, tol=1e-10, maxit=1000, X0=None):
+    """Batched PCG (Section 1, eq. (PCG)) done problem by problem and right-hand side by
+    right-hand side: problem p draws sketch instance t = p of `seed` with m = max(d, ceil(m_factor d))
+    rows (an SJLT with min(s, m) nonzeros per column), factors it, and runs the oracle's PCG (rho_hat = d / m) from x0 (zero by default) on
+    each right-hand side.  problems: list of (A (n x d), B (k x d)).
+    Returns a list of (X (k x d), iters (k,), status (k,))."""
+    out = []
+    for p, (A, B) in enumerate(problems):
+        A64 = np.ascontiguousarray(A, dtype=np.float64)
+        n, d = A64.shape
+        m = max(d, int(math.ceil(m_factor * d)))
+        R = factor(sketch(A64, kind, m, seed, t=p, s=min(s, m)))
+        X = np.zeros((B.shape[0], d))
+        its = np.zeros(B.shape[0], dtype=np.int64)
+        sts = np.zeros(B.shape[0], dtype=np.int64)
+        for j in range(B.shape[0]):
+            x0 = None if X0 is None else X0[p][j]
+            X[j], its[j], sts[j], _ = pcg(A64, B[j], R, x0=x0, tol=tol, maxit=maxit, rho_hat=d / m)
+        out.append((X, its, sts))
+    return out
+
+
 def solve_direct(A, b) -> np.ndarray:
     A, n, d, ld = _mat(A)
     b = _f64(b)

@@ -12,6 +12,7 @@ Entry points (same names as the C ABI):
     lsq_factor(ctx, SA) -> (R, W)                                           (Section 1, PCG; Section 6)
     lsq_solve(ctx, A, b, method, W, x0=None, tol=1e-10, maxit=..., **opts)  (Section 1; Sections 3-4)
     lsq_hmatvec(ctx, A, p) -> (v, q)                                        (one fused pass over A)
+    lsq_solve_batched(ctx, [(A_p, B_p), ...], tol, maxit, **opts)            (many problems, k_p RHS each)
 """
 from __future__ import annotations
 
@@ -36,7 +37,8 @@ DTYPE = {torch.float64: 0, torch.float32: 1}
 # every symbol the header declares
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_sketch", "lsq_factor", "lsq_solve",
            "lsq_solve_opts_default", "lsq_hmatvec", "lsq_status_str", "lsq_version", "lsq_launch_count",
-           "lsq_hmatvec_noalloc", "lsq_grad_a", "lsq_advise_sketch_size")
+           "lsq_hmatvec_noalloc", "lsq_grad_a", "lsq_advise_sketch_size", "lsq_batch_opts_default",
+           "lsq_solve_batched")
 
 
 class LsqError(RuntimeError):
@@ -60,6 +62,27 @@ class LsqSolveOpts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("s", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("refresh_every", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("x0_zero", ctypes.c_int32),
                 ("fcg_k", ctypes.c_int32)]
+
+
+class LsqProblem(ctypes.Structure):
+    _fields_ = [("A", LsqMatrix), ("B", ctypes.c_void_p), ("X", ctypes.c_void_p), ("k", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class LsqBatchOpts(ctypes.Structure):
+    _fields_ = [("sketch_type", ctypes.c_int32), ("s", ctypes.c_int32), ("m_factor", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("sketch_precision", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("rho", ctypes.c_double), ("x0_zero", ctypes.c_int32), ("refresh_every", ctypes.c_int32),
+                ("chunk_rows", ctypes.c_int32), ("grid_blocks", ctypes.c_int32)]
+
+
+class LsqBatchInfo(ctypes.Structure):
+    _fields_ = [("iters_max", ctypes.c_int32), ("status", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("exact_passes", ctypes.c_int32), ("ms_total", ctypes.c_double), ("ms_sketch", ctypes.c_double),
+                ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class LsqAdvice(ctypes.Structure):
@@ -97,6 +120,11 @@ def _load():
     L.lsq_grad_a.restype = ctypes.c_int
     L.lsq_advise_sketch_size.argtypes = [i64, i64, dbl, i32, ctypes.POINTER(LsqAdvice)]
     L.lsq_advise_sketch_size.restype = ctypes.c_int
+    L.lsq_batch_opts_default.argtypes = [ctypes.POINTER(LsqBatchOpts)]
+    L.lsq_batch_opts_default.restype = None
+    L.lsq_solve_batched.argtypes = [P, i32, ctypes.POINTER(LsqProblem), dbl, i32, ctypes.POINTER(LsqBatchOpts),
+                                    ctypes.POINTER(LsqBatchInfo)]
+    L.lsq_solve_batched.restype = ctypes.c_int
     L.lsq_status_str.argtypes = [i32]
     L.lsq_status_str.restype = ctypes.c_char_p
     L.lsq_version.restype = ctypes.c_char_p
@@ -299,6 +327,54 @@ def lstsq_solve(A: torch.Tensor, b: torch.Tensor, lsq: Context, **kw) -> torch.T
     """Differentiable x* = H^{-1} b (see LeastSquaresSolve)."""
     return LeastSquaresSolve.apply(A, b, lsq, kw.get("sketch", "srht"), kw.get("m", 1024), kw.get("seed", 0),
                                    kw.get("tol", 1e-10), kw.get("precision", "mixed"), kw.get("maxit", 1000))
+
+
+def batch_opts(**kw) -> LsqBatchOpts:
+    o = LsqBatchOpts()
+    _L.lsq_batch_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "sketch_type" and isinstance(v, str):
+            v = SKETCH[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        if k == "sketch_precision" and isinstance(v, str):
+            v = SKETCH_PRECISION[v]
+        setattr(o, k, v)
+    return o
+
+
+def lsq_solve_batched(ctx: Context, problems, tol: float = 1e-10, maxit: int = 1000, X0=None, **opts):
+    """Solves every problem (A_p, B_p) of the list: A_p an n_p x d_p CUDA tensor (FP64 or FP32, one
+    type for the batch), B_p a k_p x d_p FP64 CUDA tensor of right-hand sides (row j = b_j).
+    Returns (X list (k_p x d_p FP64), per-problem (iters, status) list, info dict).  Raises
+    LsqError for errors other than LSQ_ERR_MAXIT / LSQ_ERR_BREAKDOWN / LSQ_ERR_RANK, which
+    are reported per problem."""
+    ctx.sync_stream()
+    n = len(problems)
+    arr = (LsqProblem * n)()
+    Xs = []
+    for p, (A, B) in enumerate(problems):
+        M = as_matrix(A)
+        d = A.shape[1]
+        if B.dim() != 2 or B.shape[1] != d or B.dtype != torch.float64 or not B.is_cuda or not B.is_contiguous():
+            raise ValueError("B must be a contiguous CUDA float64 tensor of shape (k, d)")
+        if X0 is not None:
+            X = X0[p].clone()
+        else:
+            X = torch.zeros_like(B)
+        Xs.append(X)
+        arr[p] = LsqProblem(M, B.data_ptr(), X.data_ptr(), B.shape[0], 0, 0, 0)
+    if X0 is None:
+        opts.setdefault("x0_zero", 1)
+    else:
+        opts.setdefault("x0_zero", 0)
+    o = batch_opts(**opts)
+    info = LsqBatchInfo()
+    st = _L.lsq_solve_batched(ctx.handle, n, arr, float(tol), int(maxit), ctypes.byref(o), ctypes.byref(info))
+    if st not in (LSQ_OK, LSQ_ERR_MAXIT, LSQ_ERR_BREAKDOWN, LSQ_ERR_RANK):
+        raise LsqError(st, "lsq_solve_batched")
+    per = [(arr[p].iters, arr[p].status) for p in range(n)]
+    return Xs, per, info.as_dict()
 
 
 def lsq_advise_sketch_size(n: int, d: int, eps: float, kind: str = "srht") -> dict:

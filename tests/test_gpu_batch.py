@@ -1,0 +1,104 @@
+"""Parity of lsq_solve_batched (many problems, k right-hand sides each, one persistent launch)
+with the FP64 oracle.
+
+Bar: every right-hand side of every problem reaches relative H-norm error <= 1e-10 against
+x* (QR + double-double refinement of the oracle); in the FP64 mode, with FP64 sketches, the
+iterates follow the oracle's PCG (same sketch instance t = p per problem).  Shapes are uneven
+(d not a multiple of 32, n not a multiple of the 32-row tile, problems smaller than one work
+unit, k from 1 to 16, d up to the 512 limit)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from gpu_util import rel_fro, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_1911_02675_gb300 as lib
+    return lib
+
+
+@pytest.fixture(scope="module")
+def ctx(L):
+    c = L.Context(0)
+    yield c
+    c.close()
+
+
+SHAPES = [(700, 5, 1), (3001, 37, 3), (5000, 64, 16), (1200, 130, 7), (20000, 96, 2), (4100, 200, 9),
+          (999, 33, 4), (6000, 250, 12), (2500, 31, 16), (1500, 300, 5)]
+
+
+def _dev(probs, dtype):
+    return [(to_dev(q["A"].astype(dtype)), to_dev(q["B"])) for q in probs]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_batch_reaches_xstar(L, ctx, precision):
+    probs = W.make_batch(SHAPES, seed=11, scale_max=1e4, dtype=np.float32)
+    X, per, info = L.lsq_solve_batched(ctx, _dev(probs, np.float32), tol=1e-10, maxit=300, precision=precision,
+                                       seed=4)
+    assert info["status"] == 0, (info, per)
+    for q, Xp, (it, st) in zip(probs, X, per):
+        A64 = q["A"].astype(np.float64)
+        assert st == 0 and it > 0
+        Xh = Xp.cpu().numpy()
+        for j in range(q["B"].shape[0]):
+            xs = O.solve_direct(A64, q["B"][j])
+            assert O.rel_h_err(A64, Xh[j], xs) <= 1e-10, (q["A"].shape, j)
+
+
+def test_batch_f64_follows_oracle(L, ctx):
+    shapes = SHAPES[:6]
+    probs = W.make_batch(shapes, seed=12, scale_max=1e3, dtype=np.float64)
+    for T in (1, 4):
+        X, per, info = L.lsq_solve_batched(ctx, _dev(probs, np.float64), tol=0.0, maxit=T, precision="f64",
+                                           sketch_precision="f64", seed=7, s=8)
+        ref = O.solve_batched([(q["A"], q["B"]) for q in probs], kind="sjlt", s=8, m_factor=4.0, seed=7, tol=0.0,
+                              maxit=T)
+        for Xp, (Xr, its, sts), (it, st) in zip(X, ref, per):
+            assert it == T and st == L.LSQ_ERR_MAXIT
+            assert rel_fro(Xp.cpu().numpy(), Xr) < 1e-10
+    # converged iteration counts agree with the oracle's (same sketches, same rule)
+    X, per, info = L.lsq_solve_batched(ctx, _dev(probs, np.float64), tol=1e-10, maxit=300, precision="f64",
+                                       sketch_precision="f64", seed=7)
+    ref = O.solve_batched([(q["A"], q["B"]) for q in probs], kind="sjlt", s=8, m_factor=4.0, seed=7, tol=1e-10)
+    for (it, st), (Xr, its, sts) in zip(per, ref):
+        assert st == 0 and abs(it - int(its.max())) <= 1
+
+
+def test_batch_nonzero_x0_and_statuses(L, ctx):
+    shapes = [(2000, 40, 3), (3000, 64, 1), (1000, 20, 5)]
+    probs = W.make_batch(shapes, seed=13, scale_max=1e2, dtype=np.float32)
+    rng = np.random.default_rng(1)
+    X0 = [to_dev(rng.standard_normal(q["B"].shape)) for q in probs]
+    X, per, info = L.lsq_solve_batched(ctx, _dev(probs, np.float32), X0=X0, tol=1e-10, maxit=300, seed=2)
+    assert info["status"] == 0
+    for q, Xp in zip(probs, X):
+        A64 = q["A"].astype(np.float64)
+        for j in range(q["B"].shape[0]):
+            assert O.rel_h_err(A64, Xp[j].cpu().numpy(), O.solve_direct(A64, q["B"][j])) <= 1e-10
+    # zero right-hand sides converge at once; a tight tolerance with 2 iterations hits maxit
+    dev = _dev(probs, np.float32)
+    dev[1] = (dev[1][0], torch.zeros_like(dev[1][1]))
+    X, per, info = L.lsq_solve_batched(ctx, dev, tol=1e-10, maxit=300, seed=2)
+    assert per[1] == (0, 0) and not X[1].abs().sum().item()
+    X, per, info = L.lsq_solve_batched(ctx, _dev(probs, np.float32), tol=1e-15, maxit=2, seed=2)
+    assert all(st == L.LSQ_ERR_MAXIT and it == 2 for it, st in per)
+    assert info["status"] == L.LSQ_ERR_MAXIT
+
+
+def test_batch_largest_shape(L, ctx):
+    shapes = [(6000, 512, 16), (4096, 1, 1), (3000, 512, 2)]
+    probs = W.make_batch(shapes, seed=14, scale_max=1e4, dtype=np.float32)
+    X, per, info = L.lsq_solve_batched(ctx, _dev(probs, np.float32), tol=1e-10, maxit=400, seed=1)
+    assert info["status"] == 0, per
+    for q, Xp in zip(probs, X):
+        A64 = q["A"].astype(np.float64)
+        for j in range(q["B"].shape[0]):
+            assert O.rel_h_err(A64, Xp[j].cpu().numpy(), O.solve_direct(A64, q["B"][j])) <= 1e-10

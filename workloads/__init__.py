@@ -105,6 +105,56 @@ def make_problem_cuda(n: int, d: int, sigma_max: float, seed: int = 1, noise: fl
     return {"A": A, "b": b}
 
 
+def batch_shapes(nprob: int, seed: int, n_range=(1 << 12, 1 << 18), d_range=(32, 512), k_range=(1, 16)):
+    """Shapes of an uneven batch: n and d log-uniform in their ranges, k uniform in k_range."""
+    g = _gen(seed, 10)
+    u = g.random((nprob, 2))
+    n = np.floor(np.exp(np.log(n_range[0]) + u[:, 0] * (np.log(n_range[1]) - np.log(n_range[0])))).astype(np.int64)
+    d = np.floor(np.exp(np.log(d_range[0]) + u[:, 1] * (np.log(d_range[1]) - np.log(d_range[0])))).astype(np.int64)
+    k = g.integers(k_range[0], k_range[1] + 1, size=nprob)
+    return [(int(a), int(b), int(c)) for a, b, c in zip(n, d, k)]
+
+
+def make_batch(shapes, seed: int = 1, scale_max: float = 1e4, dtype=np.float32, noise: float = 0.1):
+    """One problem per (n, d, k): A = G diag(sigma) (sigma log-spaced 1..scale_max), rounded to
+    `dtype`; k right-hand sides b_j = A^T (A x_j + noise eps_j) formed from the rounded A in FP64.
+    Returns a list of dicts (A (n x d), B (k x d FP64), X_true (k x d))."""
+    out = []
+    for p, (n, d, k) in enumerate(shapes):
+        A = np.empty((n, d), dtype=np.float64)
+        _fill_normal(A, seed * 1000003 + p, 0, 1)
+        A = (A * sigma(d, scale_max)).astype(dtype)
+        A64 = A.astype(np.float64)
+        g = _gen(seed * 1000003 + p, 4)
+        Xt = g.standard_normal((k, d))
+        E = g.standard_normal((k, n))
+        Y = Xt @ A64.T + noise * E
+        B = np.ascontiguousarray(Y @ A64)
+        out.append({"A": A, "B": B, "X_true": Xt})
+    return out
+
+
+def make_batch_cuda(shapes, seed: int = 1, scale_max: float = 1e4, dtype=None, noise: float = 0.1, device="cuda"):
+    """The same recipe drawn in device memory with torch's CUDA generator (draws differ from
+    make_batch's).  Returns a list of (A, B) CUDA tensors."""
+    import torch
+
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    out = []
+    for n, d, k in shapes:
+        sig = torch.tensor(sigma(d, scale_max), dtype=torch.float64, device=device)
+        A = (torch.randn((n, d), generator=g, dtype=torch.float64, device=device) * sig).to(dtype)
+        A64 = A.to(torch.float64)
+        Xt = torch.randn((k, d), generator=g, dtype=torch.float64, device=device)
+        Y = Xt @ A64.T + noise * torch.randn((k, n), generator=g, dtype=torch.float64, device=device)
+        B = (Y @ A64).contiguous()
+        del A64, Y
+        out.append((A, B))
+    return out
+
+
 def small_problem(n: int, d: int, kappa: float = 1e2, seed: int = 7):
     """Small dense test problem with column scales log-spaced 1..kappa."""
     return make_problem(n, d, kappa, seed=seed)
@@ -121,6 +171,11 @@ WORKLOADS = {
     # FP32-stored A with outliers, Gaussian m=4096.
     "fp32_4194304x1024": dict(n=1 << 22, d=1024, sigma_max=1e5, dtype="f32", sketch="gauss", m=4096,
                               outlier_frac=0.05, seed_data=1, seed_sketch=0, tol=1e-10),
+    # Batch: 256 problems, n in [2^12, 2^18], d in [32, 512] (log-uniform), k in 1..16 right-hand
+    # sides, A FP32 with column scales 1..1e4; SJLT (s = 8), m = 4d; PCG per right-hand side.
+    "batch256_fp32": dict(nprob=256, n_range=(1 << 12, 1 << 18), d_range=(32, 512), k_range=(1, 16),
+                          scale_max=1e4, dtype="f32", sketch="sjlt", s=8, m_factor=4.0, seed_data=1,
+                          seed_sketch=0, tol=1e-10),
 }
 
 
