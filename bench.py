@@ -498,6 +498,7 @@ def run_batch(args):
             "phases": {"sketch_ms": info["ms_sketch"], "factor_ms": info["ms_factor"], "solve_ms": solve_ms,
                        "iters_max": info["iters_max"], "passes": info["passes"], "exact_passes": info["exact_passes"],
                        "statuses": statuses, "rhs": sum(k for _, _, k in shapes),
+                       "launch_phases_ms": info["ms_phase"],
                        "A_GiB": sum(a_bytes) / 2 ** 30},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": None, "kernel": "batch_kernel", "peak_kind": f"{peak_kind} (burst copy)",

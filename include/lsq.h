@@ -302,9 +302,13 @@ typedef struct {
   int32_t precision;        /* lsq_precision (default LSQ_PREC_MIXED) */
   double rho;               /* stopping-rule deviation parameter; default (<= 0): d/m per problem */
   int32_t x0_zero;          /* 1 (default): every x0 is zero and X is overwritten */
-  int32_t refresh_every;    /* MIXED: most iterations between exact residual replacements (12) */
-  int32_t chunk_rows;       /* rows of A per work unit of the pass (0: tuned) */
-  int32_t grid_blocks;      /* resident CTAs of the persistent launch (0: one per SM) */
+  int32_t refresh_every;    /* MIXED: most iterations between exact residual replacements (40);
+                               a replacement also follows a 10^5 drop of the residual norm and
+                               every convergence of the recursive residual */
+  int32_t chunk_rows;       /* rows of A per work unit of the pass (0: about 2^20 elements of A) */
+  int32_t grid_blocks;      /* CTAs of the pass kernel (0: as many as are resident) */
+  int32_t profile_phases;   /* 1: run the iterations without the CUDA graph and time each kernel
+                               into lsq_batch_info.ms_phase (slower; for tuning) */
 } lsq_batch_opts;
 
 typedef struct {
@@ -316,15 +320,17 @@ typedef struct {
   double ms_sketch;      /* sketches of all problems */
   double ms_factor;      /* factorisations of all problems */
   double ms_solve;       /* the persistent PCG launch */
+  double ms_phase[8];    /* with opts.profile_phases: time in the pass, update, W^T r, W t and
+                            direction kernels of the iterations ([5..7] unused); else zero */
 } lsq_batch_info;
 
 LSQ_API void lsq_batch_opts_default(lsq_batch_opts* opts);
 
 /* lsq_solve_batched: for every problem p (host array `probs` of nprob entries, device data),
  * draws its sketch (instance t = p), factors it (Cholesky of the Gram matrix, W = R^{-1}),
- * then runs PCG on all right-hand sides of all problems in one persistent cooperative launch:
- * each iteration makes one pass over A_p per active problem that yields A_p^T (A_p P) for all
- * of its search directions at once, then the vector updates and W W^T per right-hand side.
+ * then runs PCG on all right-hand sides of all problems in lockstep iterations, each a CUDA graph
+ * of kernels replayed from the host: one pass over A_p per active problem yields A_p^T (A_p P) for
+ * all of its search directions at once, then the vector updates and W W^T per right-hand side.
  * A right-hand side stops by rule (1+sqrt(rho))^2 r^T H_S^{-1} r <= tol^2 <b, x> (as in
  * lsq_solve); a problem stops when all of its right-hand sides have. Under LSQ_PREC_MIXED the
  * passes run in FP32 with exact (double-FP32) residual replacement as in lsq_solve.

@@ -1,21 +1,24 @@
 // batch.cu -- many independent least-squares problems of uneven n, d and numbers of
 // right-hand sides k, each solved by PCG (Section 1, eq. (PCG)) per right-hand side with
-// the problem's own fixed embedding; the iterations of every problem run in one persistent
-// cooperative launch.
+// the problem's own fixed embedding; all problems advance in lockstep iterations.
 //
-// Per iteration (all problems in lockstep, converged right-hand sides masked out):
-//   pass      one read of every active A_p, in chunks of rows scheduled over the CTAs, gives
-//             V = A_p^T (A_p P_p) and q_j = ||A_p p_j||^2 for all k_p directions at once: a tile
-//             of 32 rows is staged in shared memory, Y = A_tile P (rows x k) and then
-//             V += A_tile^T Y (register tiles), FP32 under LSQ_PREC_MIXED, FP64 otherwise;
-//   update    alpha_j = r_j^T z_j / q_j, x_j += alpha_j p_j, r_j -= alpha_j v_j;
-//   precond   t = W^T r, then z = W t (W = R^{-1}), one warp per 32 rows of W;
-//   direction beta_j = r_j^T z_j / (previous), p_j = z_j + beta_j p_j, stopping rule.
-// Under LSQ_PREC_MIXED a right-hand side whose recursive residual should be replaced (as in
-// lsq_solve: convergence, a 10^4 drop since the last exact residual, or refresh_every
-// iterations) makes its problem take an exact pass in double-FP32 arithmetic, r = b - A^T A x,
-// before the direction update. Phases are separated by bounded grid barriers.
-// Work units and per-unit partial sums are reduced in a fixed order (deterministic results).
+// One iteration is a CUDA graph of six kernels (replayed; the iteration index lives in device
+// memory):
+//   pass      one read of every active A_p gives V = A_p^T (A_p P_p) and q_j = ||A_p p_j||^2 for
+//             all k_p directions at once; chunks of rows are taken from a queue (costliest
+//             first) by 512-thread CTAs; a tile of rows is staged in shared memory,
+//             Y = A_tile P (rows x k) and then V += A_tile^T Y (register tiles), FP32 under
+//             LSQ_PREC_MIXED, FP64 otherwise;
+//   update    alpha_j = r_j^T z_j / q_j, x_j += alpha_j p_j, r_j -= alpha_j v_j (a warp per 32
+//             columns);
+//   precond   t = W^T r, then z = W t (W = R^{-1}), a CTA per 32 rows of W whose warps split the
+//             columns, so a problem's FP64 work spreads over many SMs;
+//   direction beta_j, p_j = z_j + beta_j p_j, the stopping rule; then a one-thread tick.
+// Under LSQ_PREC_MIXED a right-hand side whose recursive residual should be replaced (a 10^5
+// drop of its norm since the last exact residual, refresh_every iterations, or convergence)
+// makes its problem spend its next iteration on an exact residual r = b - A^T A x from a pass
+// in double-FP32 arithmetic, before its directions are updated.  Partial sums are reduced in a
+// fixed order (deterministic results).
 #include <algorithm>
 #include <math.h>
 #include <vector>
@@ -30,7 +33,7 @@ using lsq_apass::split_df;
 
 namespace {
 
-constexpr int BT = 256;      // threads per CTA
+constexpr int BT = 256;      // threads per CTA of the block kernels
 constexpr int BW = BT / 32;  // warps per CTA
 constexpr int KPMAX = 16;
 
@@ -40,7 +43,7 @@ constexpr int F_ACTIVE = 1;
 struct BProb {
   const void* A;
   int64_t n, ld;
-  int d, dp, k, kp, nblk, chunk0, nchunk;
+  int d, dp, k, kp, nblk, chunk0, nchunk, vec;  // vec: rows of A allow 16-byte loads
   const double* B;
   double* X;
   const double* W;
@@ -59,27 +62,30 @@ struct BProb {
   int* its;        // [kp] iterations taken
   int* st;         // [kp] status
   int* it_last;    // [kp] iteration of the last exact residual
-  int* pstate;     // [2 * par] right-hand sides left and [2 * par + 1] the iteration this count is
-                   // for, by iteration parity par; [4] needs an exact pass this iteration
+  int* pstate;     // by iteration parity par: [2 * par] right-hand sides left, [2 * par + 1] the
+                   // iteration this count is for, [4 + par] this iteration is an exact residual step
   double lam1, tol2;
 };
 
 struct BatchArgs {
   BProb* probs;
-  const int4* chunks;     // (problem, row0, row1, 0)
+  int nprob;
+  const int4* chunks;       // (problem, row0, row1, 0)
   const int64_t* part_off;  // chunk -> offset of its partials (kp * dp + kp doubles)
-  const int* sched;       // chunk indices, CTA by CTA
-  const int* sched_off;   // [P + 1]
-  const int2* blocks;     // (problem, block of 32 columns / rows)
+  const int* order;         // chunks by decreasing cost (the queue)
+  int nchunks;
+  const int2* blocks;       // (problem, block of 32 columns / rows)
   int nblocks;
   double* part;
-  unsigned* bar;
-  int* err;
-  int* cnt;               // [3] problems still active, rotating by iteration
-  int* anyx;              // [3] some problem needs an exact pass, rotating
+  int* iter;                // the current iteration
+  int* qhead;               // [3] queue heads, rotating by iteration
+  int* cnt;                 // [4] problems active in the next iteration, rotating; [3] unused
+  int* anyx;                // [3] some problem takes an exact residual step, rotating
+  int* stats;               // [0] iterations run, [1] iterations with an exact residual step
+  int* err;                 // first error of a kernel
+  int smem_bytes;           // dynamic shared memory of the pass kernel
   int maxit, mixed, x0_zero, refresh_every;
   double replace2;
-  int* out;               // [0] iterations, [1] passes, [2] exact passes
 };
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -94,6 +100,8 @@ __device__ __forceinline__ bool prob_active(const BProb& pr, int it) {
   return pr.pstate[2 * par + 1] == it && pr.pstate[2 * par] > 0;
 }
 
+__device__ __forceinline__ bool exact_step(const BProb& pr, int it) { return pr.pstate[4 + (it & 1)] != 0; }
+
 __device__ __forceinline__ void set_left(const BProb& pr, int it, int left) {
   const int par = it & 1;
   pr.pstate[2 * par] = left;
@@ -103,17 +111,28 @@ __device__ __forceinline__ void set_left(const BProb& pr, int it, int left) {
 // ------------------------------------------------------------------------------------
 // The pass over one chunk of rows in FP32 (TT = float) or FP64 (TT = double):
 // part[j * dp + c] = sum_rows a_c (a . p_j),  part[kp * dp + j] = sum_rows (a . p_j)^2.
-// Shared memory: As[TR][dp + 1] (tile), Ps[dp][KP] (directions), Yp[BW][KP][TR], Ys[TR][KP].
+// A tile holds TE elements: tr = TE / dp rows (dp a power of two >= 32), so narrow problems
+// take tall tiles.  Stage 1, Y = A_tile P: each of the 256 lanes owns one row and a slice of
+// the columns (S = 256 / tr slices; for tr > 256 a lane owns tr / 256 whole rows); stage 2,
+// V += A_tile^T Y: a warp owns 32 columns (or 64) and every KP accumulator of them, warps
+// sharing columns split the rows.  Shared memory: As[tr][dp] (XOR-swizzled), Ps[dp][KP],
+// Yp[S][KP][tr] (S > 1), Ys[tr][KP].
 // ------------------------------------------------------------------------------------
-template <typename TA, typename TT, int TR, int KP>
-__device__ void pass_chunk(const BProb& pr, int64_t r0, int64_t r1, double* __restrict__ out, uint8_t* smem) {
+template <typename TA, typename TT, int TE, int KP, int PT>
+__device__ __forceinline__ void pass_chunk(const BProb& pr, int64_t r0, int64_t r1, double* __restrict__ out,
+                                           uint8_t* smem) {
+  constexpr int BT = PT, BW = PT / 32;
+  constexpr int CPWMAX = 16 / BW > 1 ? 16 / BW : 1;  // column groups per warp at dp = 512
   const int dp = pr.dp, d = pr.d, kp = pr.kp;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int lda = dp + 1;
+  const int lgdp = 31 - __clz(dp);
+  const int tr = TE >> lgdp;                 // rows per tile
+  const int S = tr >= BT ? 1 : BT / tr;      // column slices of stage 1
+  const int RPL = tr > BT ? tr / BT : 1;     // rows per lane of stage 1 (<= 2)
   TT* As = reinterpret_cast<TT*>(smem);
-  TT* Ps = As + TR * lda;
+  TT* Ps = As + TE;
   TT* Yp = Ps + dp * KP;
-  TT* Ys = Yp + BW * KP * TR;
+  TT* Ys = Yp + (S > 1 ? S * KP * tr : 0);
   const TA* A = reinterpret_cast<const TA*>(pr.A);
   // directions (padding columns j >= kp are zero)
   for (int e = tid; e < dp * KP; e += BT) {
@@ -131,118 +150,167 @@ __device__ void pass_chunk(const BProb& pr, int64_t r0, int64_t r1, double* __re
   const int rsplit = NC >= BW ? 1 : BW / NC;   // warps sharing a column group
   const int g0 = NC >= BW ? warp : warp % NC;
   const int rphase = NC >= BW ? 0 : warp / NC;
-  TT acc[2][KP];
+  TT acc[CPWMAX][KP];
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
+  for (int h = 0; h < CPWMAX; ++h)
 #pragma unroll
     for (int j = 0; j < KP; ++j) acc[h][j] = 0;
-  TT qacc[2] = {0, 0};
-  // register prefetch of the next tile: TR * dp / BT elements per thread (<= 64)
-  constexpr int PFN = TR * 512 / BT;
-  TA pf[PFN];
-  const int per = TR * dp;
-  auto load_tile = [&](int64_t t0) {
+  TT qacc[KP];
 #pragma unroll
-    for (int u = 0; u < PFN; ++u) {
-      const int e = tid + u * BT;
-      TA v = 0;
-      if (e < per) {
-        const int r = e / dp, c = e - r * dp;
-        const int64_t row = t0 + r;
-        if (row < r1 && c < d) v = __ldg(A + row * pr.ld + c);
-      }
-      pf[u] = v;
-    }
-  };
-  load_tile(r0);
-  for (int64_t t0 = r0; t0 < r1; t0 += TR) {
+  for (int j = 0; j < KP; ++j) qacc[j] = 0;
+  // stage-1 ownership: global lane g -> row g % tr (+ BT i) and slice g / tr
+  const int g = tid;
+  const int s_row = tr >= BT ? g : g % tr;
+  const int s_slice = tr >= BT ? 0 : g / tr;
+  const int cs = dp / S;
+  // Tile element (r, c) sits at As[r * dp + (c ^ (r & 31))]: a column read by 32 consecutive
+  // rows and a row read by 32 consecutive columns both hit 32 distinct banks.  Loads are
+  // 16-byte vectors (V elements) when A allows; the next tile waits in registers.
+  constexpr int V = sizeof(TA) == 4 ? 4 : 2;
+  using VT = typename std::conditional<sizeof(TA) == 4, float4, double2>::type;
+  constexpr int NU = TE / (V * BT);
+  const int lgu = lgdp - (V == 4 ? 2 : 1);  // log2 of the vectors per row
+  const int units = tr << lgu;
+  const bool vec_ok = pr.vec != 0;
+  TA pf[NU * V];
+#define LSQ_LOAD_TILE(t0_)                                                                   \
+  _Pragma("unroll") for (int i = 0; i < NU; ++i) {                                           \
+    const int u = tid + i * BT;                                                              \
+    const int r = u >> lgu, c = (u & ((1 << lgu) - 1)) * V;                                  \
+    const int64_t row = (t0_) + r;                                                           \
+    const bool in_ = u < units && row < r1;                                                  \
+    const TA* src = A + (in_ ? row * pr.ld + c : 0);                                         \
+    if (in_ && vec_ok && c + V <= d) {                                                       \
+      const VT x = __ldg(reinterpret_cast<const VT*>(src));                                  \
+      pf[i * V + 0] = x.x;                                                                   \
+      pf[i * V + 1] = x.y;                                                                   \
+      if constexpr (V == 4) {                                                                \
+        pf[i * V + 2] = reinterpret_cast<const float4&>(x).z;                                \
+        pf[i * V + 3] = reinterpret_cast<const float4&>(x).w;                                \
+      }                                                                                      \
+    } else {                                                                                 \
+      _Pragma("unroll") for (int q = 0; q < V; ++q) pf[i * V + q] =                          \
+          (in_ && c + q < d) ? __ldg(src + q) : (TA)0;                                       \
+    }                                                                                        \
+  }
+  LSQ_LOAD_TILE(r0)
+  for (int64_t t0 = r0; t0 < r1; t0 += tr) {
     __syncthreads();  // the previous tile is no longer read
 #pragma unroll
-    for (int u = 0; u < PFN; ++u) {
-      const int e = tid + u * BT;
-      if (e < per) {
-        const int r = e / dp, c = e - r * dp;
-        if constexpr (sizeof(TT) == 4) As[r * lda + c] = narrow_f32(pf[u]);
-        else As[r * lda + c] = (TT)pf[u];
+    for (int i = 0; i < NU; ++i) {
+      const int u = tid + i * BT;
+      if (u < units) {
+        const int r = u >> lgu, c = (u & ((1 << lgu) - 1)) * V;
+        const int sw = r & 31;
+        if constexpr (sizeof(TT) == 4 && V == 4) {
+          // position p of the swizzled group holds element p ^ (r & 3)
+          float e0 = narrow_f32(pf[i * V + 0]), e1 = narrow_f32(pf[i * V + 1]);
+          float e2 = narrow_f32(pf[i * V + 2]), e3 = narrow_f32(pf[i * V + 3]);
+          if (sw & 1) { float t = e0; e0 = e1; e1 = t; t = e2; e2 = e3; e3 = t; }
+          if (sw & 2) { float t = e0; e0 = e2; e2 = t; t = e1; e1 = e3; e3 = t; }
+          *reinterpret_cast<float4*>(As + r * dp + ((c ^ sw) & ~3)) = make_float4(e0, e1, e2, e3);
+        } else {
+#pragma unroll
+          for (int q = 0; q < V; ++q) {
+            if constexpr (sizeof(TT) == 4) As[r * dp + ((c + q) ^ sw)] = narrow_f32(pf[i * V + q]);
+            else As[r * dp + ((c + q) ^ sw)] = (TT)pf[i * V + q];
+          }
+        }
       }
     }
     __syncthreads();
-    if (t0 + TR < r1) load_tile(t0 + TR);
-    // stage 1: Y[r][j] = sum_c As[r][c] Ps[c][j]; warp w takes a slice of the columns, lane = row
-    if (lane < TR) {
-      TT y[KP];
+    if (t0 + tr < r1) {
+      LSQ_LOAD_TILE(t0 + tr)
+    }
+    // stage 1
 #pragma unroll
-      for (int j = 0; j < KP; ++j) y[j] = 0;
-      const int cs = dp / BW, c0 = warp * cs;
-      for (int c = c0; c < c0 + cs; ++c) {
-        const TT a = As[lane * lda + c];
-        const TT* pc = Ps + c * KP;
+    for (int i = 0; i < 2; ++i) {
+      if (i < RPL) {
+        const int r = s_row + i * BT;
+        TT y[KP];
 #pragma unroll
-        for (int j = 0; j < KP; ++j) y[j] = fma(a, pc[j], y[j]);
+        for (int j = 0; j < KP; ++j) y[j] = 0;
+        const int c0 = s_slice * cs;
+        const TT* arow = As + r * dp;
+        const int sw = r & 31;
+        for (int c = c0; c < c0 + cs; ++c) {
+          const TT a = arow[c ^ sw];
+          const TT* pc = Ps + c * KP;
+#pragma unroll
+          for (int j = 0; j < KP; ++j) y[j] = fma(a, pc[j], y[j]);
+        }
+        if (S == 1) {
+#pragma unroll
+          for (int j = 0; j < KP; ++j) {
+            Ys[r * KP + j] = y[j];
+            qacc[j] = fma(y[j], y[j], qacc[j]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < KP; ++j) Yp[(s_slice * KP + j) * tr + r] = y[j];
+        }
       }
-#pragma unroll
-      for (int j = 0; j < KP; ++j) Yp[(warp * KP + j) * TR + lane] = y[j];
     }
     __syncthreads();
-    for (int e = tid; e < TR * KP; e += BT) {
-      const int j = e / TR, r = e - j * TR;
-      TT s = 0;
+    if (S > 1 && tid < tr) {
+      const int r = tid;
 #pragma unroll
-      for (int w = 0; w < BW; ++w) s += Yp[(w * KP + j) * TR + r];
-      Ys[r * KP + j] = s;
-      qacc[e / BT] = fma(s, s, qacc[e / BT]);
+      for (int j = 0; j < KP; ++j) {
+        TT sum = 0;
+        for (int q = 0; q < S; ++q) sum += Yp[(q * KP + j) * tr + r];
+        Ys[r * KP + j] = sum;
+        qacc[j] = fma(sum, sum, qacc[j]);
+      }
     }
-    __syncthreads();
+    if (S > 1) __syncthreads();
     // stage 2: acc[h][j] += As[r][c] Ys[r][j] for the warp's column groups and row phase
-    for (int r = rphase; r < TR; r += rsplit) {
+    for (int r = rphase; r < tr; r += rsplit) {
       const TT* yr = Ys + r * KP;
+      const int sw = r & 31;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < CPWMAX; ++h) {
         if (h < cpw) {
-          const TT a = As[r * lda + ((g0 + h * BW) << 5) + lane];
+          const TT a = As[r * dp + ((((g0 + h * BW) << 5) + lane) ^ sw)];
 #pragma unroll
           for (int j = 0; j < KP; ++j) acc[h][j] = fma(a, yr[j], acc[h][j]);
         }
       }
     }
   }
+#undef LSQ_LOAD_TILE
   __syncthreads();
   // combine the row phases (reuse the tile area), then write the chunk's partials in FP64
   double* red = reinterpret_cast<double*>(smem);
   if (rsplit > 1) {
+#pragma unroll
     for (int j = 0; j < KP; ++j) red[(rphase * KP + j) * (NC * 32) + (g0 << 5) + lane] = (double)acc[0][j];
     __syncthreads();
     for (int e = tid; e < kp * dp; e += BT) {
       const int j = e / dp, c = e - j * dp;
-      double s = 0.0;
-      for (int ph = 0; ph < rsplit; ++ph) s += red[(ph * KP + j) * (NC * 32) + c];
-      out[e] = s;
+      double sum = 0.0;
+      for (int ph = 0; ph < rsplit; ++ph) sum += red[(ph * KP + j) * (NC * 32) + c];
+      out[e] = sum;
     }
   } else {
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int h = 0; h < CPWMAX; ++h)
       if (h < cpw)
-        for (int j = 0; j < kp; ++j) out[j * dp + ((g0 + h * BW) << 5) + lane] = (double)acc[h][j];
-  }
-  // q_j: thread e of the reduction handled j = e / TR (TR = 32: warp w -> j = w, w + 8)
-  __syncthreads();
-  if (TR == 32) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = warp + h * BW;
-      const double qs = warp_sum_d((double)qacc[h]);
-      if (lane == 0 && j < kp && j < KP) out[kp * dp + j] = qs;
-    }
-  } else {
-    // TR = 16: e = j * 16 + r, thread e -> j = e / 16 (threads 0..255 cover KP * 16 = 256 entries)
-    double* qr = red;
-    qr[tid] = (double)qacc[0];
-    __syncthreads();
-    if (tid < kp) {
-      double s = 0.0;
-      for (int r = 0; r < 16; ++r) s += qr[tid * 16 + r];
-      out[kp * dp + tid] = s;
-    }
+        for (int j = 0; j < KP; ++j)
+          if (j < kp) out[j * dp + ((g0 + h * BW) << 5) + lane] = (double)acc[h][j];
+  }
+  __syncthreads();
+  // q_j = sum of the per-thread sums of squares: warp sums, then the warps in order
+#pragma unroll
+  for (int j = 0; j < KP; ++j) {
+    const double w = warp_sum_d((double)qacc[j]);
+    if (lane == 0) red[warp * KP + j] = w;
+  }
+  __syncthreads();
+  if (tid < kp) {
+    double sum = 0.0;
+    for (int w = 0; w < BW; ++w) sum += red[w * KP + tid];
+    out[kp * dp + tid] = sum;
   }
   __syncthreads();
 }
@@ -251,16 +319,20 @@ __device__ void pass_chunk(const BProb& pr, int64_t r0, int64_t r1, double* __re
 // Exact pass in double-FP32: part[j * dp + c] = sum_rows a_c (a . x_j) for every column of
 // X (heads and tails of x, and of A when it is FP64); 16-row tiles.
 // ------------------------------------------------------------------------------------
-template <typename TA, int KP>
-__device__ void pass_chunk_df(const BProb& pr, int64_t r0, int64_t r1, double* __restrict__ out, uint8_t* smem) {
+template <typename TA, int KP, int PT>
+__device__ __forceinline__ void pass_chunk_df(const BProb& pr, int64_t r0, int64_t r1, double* __restrict__ out,
+                                              uint8_t* smem) {
+  constexpr int BT = PT, BW = PT / 32;
+  constexpr int CPWMAX = 16 / BW > 1 ? 16 / BW : 1;
   constexpr int TR = 16;
   const int dp = pr.dp, d = pr.d, kp = pr.kp;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int lda = dp + 1;
   constexpr bool HASLO = sizeof(TA) == 8;
+  // tile element (r, c) at [r * dp + (c ^ 2r)]: a column read by 16 rows with the two
+  // half-warps on even / odd columns, and a row read by 32 lanes, both hit distinct banks
   float* Ah = reinterpret_cast<float*>(smem);
-  float* Al = Ah + TR * lda;
-  float* Xh = Al + (HASLO ? TR * lda : 0);
+  float* Al = Ah + TR * dp;
+  float* Xh = Al + (HASLO ? TR * dp : 0);
   float* Xl = Xh + dp * KP;
   float* Yph = Xl + dp * KP;
   float* Ypl = Yph + BW * KP * TR;
@@ -277,33 +349,35 @@ __device__ void pass_chunk_df(const BProb& pr, int64_t r0, int64_t r1, double* _
   const int rsplit = NC >= BW ? 1 : BW / NC;
   const int g0 = NC >= BW ? warp : warp % NC;
   const int rphase = NC >= BW ? 0 : warp / NC;
-  float ah_[2][KP], al_[2][KP];
+  float ah_[CPWMAX][KP], al_[CPWMAX][KP];
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
+  for (int h = 0; h < CPWMAX; ++h)
 #pragma unroll
     for (int j = 0; j < KP; ++j) ah_[h][j] = al_[h][j] = 0.f;
+  const int lg = 31 - __clz(dp);
   const int per = TR * dp;
   for (int64_t t0 = r0; t0 < r1; t0 += TR) {
     __syncthreads();
     for (int e = tid; e < per; e += BT) {
-      const int r = e / dp, c = e - r * dp;
+      const int r = e >> lg, c = e & (dp - 1);
       const int64_t row = t0 + r;
       float hh = 0.f, ll = 0.f;
       if (row < r1 && c < d) split_df(__ldg(A + row * pr.ld + c), hh, ll);
-      Ah[r * lda + c] = hh;
-      if (HASLO) Al[r * lda + c] = ll;
+      Ah[r * dp + (c ^ (2 * r))] = hh;
+      if (HASLO) Al[r * dp + (c ^ (2 * r))] = ll;
     }
     __syncthreads();
-    // stage 1 (lanes 0..15 = rows; two half-warps take adjacent column slices)
+    // stage 1 (lanes 0..15 = rows; the half-warps take the even / odd columns of the warp's slice)
     {
       const int r = lane & 15, half = lane >> 4;
       float yh[KP], yl[KP];
 #pragma unroll
       for (int j = 0; j < KP; ++j) yh[j] = yl[j] = 0.f;
-      const int cs = dp / (2 * BW), c0 = (2 * warp + half) * cs;
-      for (int c = c0; c < c0 + cs; ++c) {
-        const float a = Ah[r * lda + c];
-        const float al = HASLO ? Al[r * lda + c] : 0.f;
+      const int cs = dp / BW, c0 = warp * cs;
+      for (int c = c0 + half; c < c0 + cs; c += 2) {
+        const int sc = r * dp + (c ^ (2 * r));
+        const float a = Ah[sc];
+        const float al = HASLO ? Al[sc] : 0.f;
 #pragma unroll
         for (int j = 0; j < KP; ++j) df_fma(a, al, Xh[c * KP + j], Xl[c * KP + j], yh[j], yl[j]);
       }
@@ -334,11 +408,12 @@ __device__ void pass_chunk_df(const BProb& pr, int64_t r0, int64_t r1, double* _
     __syncthreads();
     for (int r = rphase; r < TR; r += rsplit) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < CPWMAX; ++h) {
         if (h < cpw) {
           const int c = ((g0 + h * BW) << 5) + lane;
-          const float a = Ah[r * lda + c];
-          const float al = HASLO ? Al[r * lda + c] : 0.f;
+          const int sc = r * dp + (c ^ (2 * r));
+          const float a = Ah[sc];
+          const float al = HASLO ? Al[sc] : 0.f;
 #pragma unroll
           for (int j = 0; j < KP; ++j) df_fma(a, al, Ysh[r * KP + j], Ysl[r * KP + j], ah_[h][j], al_[h][j]);
         }
@@ -359,116 +434,188 @@ __device__ void pass_chunk_df(const BProb& pr, int64_t r0, int64_t r1, double* _
     }
   } else {
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int h = 0; h < CPWMAX; ++h)
       if (h < cpw)
-        for (int j = 0; j < kp; ++j)
-          out[j * dp + ((g0 + h * BW) << 5) + lane] = (double)ah_[h][j] + (double)al_[h][j];
+#pragma unroll
+        for (int j = 0; j < KP; ++j)
+          if (j < kp) out[j * dp + ((g0 + h * BW) << 5) + lane] = (double)ah_[h][j] + (double)al_[h][j];
   }
   if (tid < kp) out[kp * dp + tid] = 0.0;
   __syncthreads();
 }
 
-// one pass over the chunks of this CTA; exact = double-FP32 (MIXED) pass over X for problems
-// that asked for one, else the pass over the search directions
+constexpr int PT = 512;  // threads of a pass CTA (the other kernels use BT)
+
+// shared memory of the passes for one problem shape (the launch takes the maximum); mirrors
+// the layouts of pass_chunk and pass_chunk_df with PT threads
+__host__ __device__ inline size_t pass_smem_shape(bool mixed, bool a_f64, int dp, int KP) {
+  constexpr int W = PT / 32;
+  auto tile = [&](size_t es, int TE) {
+    const int tr = TE / dp;
+    const int S = tr >= PT ? 1 : PT / tr;
+    return (size_t)(TE + dp * KP + (S > 1 ? S * KP * tr : 0) + tr * KP) * es;
+  };
+  size_t f = 0;
+  if (mixed) {
+    f = tile(4, a_f64 ? 8192 : 16384);
+    const int TRd = 16;
+    const size_t df = (size_t)(TRd * dp * (a_f64 ? 2 : 1) + 2 * dp * KP + 2 * W * KP * TRd + 2 * TRd * KP) * 4;
+    f = f > df ? f : df;
+  } else {
+    f = tile(8, 8192);
+  }
+  // the end-of-chunk reductions reuse the area: PT * KP doubles (row phases), W * KP (q)
+  const size_t red = (size_t)PT * KP * 8;
+  return f > red ? f : red;
+}
+
+
+// one chunk of the pass: for a problem in an exact residual step the double-FP32 (MIXED) or
+// FP64 pass over X, else the pass over the search directions
 template <typename TA, bool MIXED>
-__device__ void pass_phase(const BatchArgs& a, bool exact, int it, uint8_t* smem) {
+__device__ void pass_one(const BatchArgs& a, int ch, bool force_exact, int it, uint8_t* smem) {
   using TT = typename std::conditional<MIXED, float, double>::type;
-  constexpr int TRP = (MIXED && sizeof(TA) == 4) ? 32 : 16;
-  for (int u = a.sched_off[blockIdx.x]; u < a.sched_off[blockIdx.x + 1]; ++u) {
-    const int ch = a.sched[u];
-    const int4 cd = a.chunks[ch];
-    const BProb& pr = a.probs[cd.x];
-    if (!prob_active(pr, it)) continue;
-    if (exact && pr.pstate[4] == 0) continue;
-    double* out = a.part + a.part_off[ch];
-    if (exact) {
-      if (MIXED) {
-        switch (pr.kp) {
-          case 4: pass_chunk_df<TA, 4>(pr, cd.y, cd.z, out, smem); break;
-          case 8: pass_chunk_df<TA, 8>(pr, cd.y, cd.z, out, smem); break;
-          default: pass_chunk_df<TA, 16>(pr, cd.y, cd.z, out, smem); break;
-        }
-      } else {
-        // FP64 mode: the exact pass is the FP64 pass over X (stored as P's FP64 layout by the caller)
-        switch (pr.kp) {
-          case 4: pass_chunk<TA, double, 16, 4>(pr, cd.y, cd.z, out, smem); break;
-          case 8: pass_chunk<TA, double, 16, 8>(pr, cd.y, cd.z, out, smem); break;
-          default: pass_chunk<TA, double, 16, 16>(pr, cd.y, cd.z, out, smem); break;
-        }
+  // elements of a tile: 64 KB of FP32; 8192 when the tile or the prefetch is FP64
+  constexpr int TEP = (MIXED && sizeof(TA) == 4) ? 16384 : 8192;
+  const int4 cd = a.chunks[ch];
+  const BProb& pr = a.probs[cd.x];
+  if (!prob_active(pr, it)) return;
+  if (pass_smem_shape(MIXED, sizeof(TA) == 8, pr.dp, pr.kp) > (size_t)a.smem_bytes) {
+    // the launch's shared memory does not hold this shape (cannot happen with the host's sizing)
+    if (threadIdx.x == 0) atomicCAS(a.err, 0, (int)LSQ_ERR_ARG);
+    return;
+  }
+  const bool exact = force_exact || exact_step(pr, it);
+  double* out = a.part + a.part_off[ch];
+  if (exact) {
+    if constexpr (MIXED) {
+      switch (pr.kp) {
+        case 4: pass_chunk_df<TA, 4, PT>(pr, cd.y, cd.z, out, smem); break;
+        case 8: pass_chunk_df<TA, 8, PT>(pr, cd.y, cd.z, out, smem); break;
+        case 12: pass_chunk_df<TA, 12, PT>(pr, cd.y, cd.z, out, smem); break;
+        default: pass_chunk_df<TA, 16, PT>(pr, cd.y, cd.z, out, smem); break;
       }
     } else {
+      // FP64 mode: the exact pass is the FP64 pass over X (held in P's layout by the caller)
       switch (pr.kp) {
-        case 4: pass_chunk<TA, TT, TRP, 4>(pr, cd.y, cd.z, out, smem); break;
-        case 8: pass_chunk<TA, TT, TRP, 8>(pr, cd.y, cd.z, out, smem); break;
-        default: pass_chunk<TA, TT, TRP, 16>(pr, cd.y, cd.z, out, smem); break;
+        case 4: pass_chunk<TA, double, 8192, 4, PT>(pr, cd.y, cd.z, out, smem); break;
+        case 8: pass_chunk<TA, double, 8192, 8, PT>(pr, cd.y, cd.z, out, smem); break;
+        case 12: pass_chunk<TA, double, 8192, 12, PT>(pr, cd.y, cd.z, out, smem); break;
+        default: pass_chunk<TA, double, 8192, 16, PT>(pr, cd.y, cd.z, out, smem); break;
       }
+    }
+  } else {
+    switch (pr.kp) {
+      case 4: pass_chunk<TA, TT, TEP, 4, PT>(pr, cd.y, cd.z, out, smem); break;
+      case 8: pass_chunk<TA, TT, TEP, 8, PT>(pr, cd.y, cd.z, out, smem); break;
+      case 12: pass_chunk<TA, TT, TEP, 12, PT>(pr, cd.y, cd.z, out, smem); break;
+      default: pass_chunk<TA, TT, TEP, 16, PT>(pr, cd.y, cd.z, out, smem); break;
     }
   }
 }
 
-// sum of the chunk partials of problem pr at offset `off` within each chunk's block (fixed order)
+// the pass: CTAs take chunks from the iteration's queue (costliest first)
+template <typename TA, bool MIXED>
+__global__ void __launch_bounds__(PT, 1) bpass_kernel(BatchArgs a, int force_exact) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int next;
+  const int it = *(volatile int*)a.iter;
+  int* head = a.qhead + it % 3;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(head, 1);
+    __syncthreads();
+    const int u = next;
+    __syncthreads();
+    if (u >= a.nchunks) break;
+    pass_one<TA, MIXED>(a, a.order[u], force_exact != 0, it, smem);
+  }
+}
+
+// sum of the chunk partials of problem pr at offset `off` within each chunk's block (fixed
+// order); a problem's chunks are consecutive and their partial blocks equally spaced
 __device__ __forceinline__ double chunk_sum(const BatchArgs& a, const BProb& pr, int off) {
-  double s = 0.0;
-  for (int ch = pr.chunk0; ch < pr.chunk0 + pr.nchunk; ++ch) s += a.part[a.part_off[ch] + off];
-  return s;
+  const double* base = a.part + a.part_off[pr.chunk0] + off;
+  const int64_t stride = (int64_t)pr.kp * pr.dp + pr.kp;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int ch = 0;
+  for (; ch + 4 <= pr.nchunk; ch += 4) {
+    s0 += base[(ch + 0) * stride];
+    s1 += base[(ch + 1) * stride];
+    s2 += base[(ch + 2) * stride];
+    s3 += base[(ch + 3) * stride];
+  }
+  for (; ch < pr.nchunk; ++ch) s0 += base[ch * stride];
+  return (s0 + s1) + (s2 + s3);
 }
 
 __device__ __forceinline__ double chunk_sum_warp(const BatchArgs& a, const BProb& pr, int off) {
   const int lane = threadIdx.x & 31;
+  const double* base = a.part + a.part_off[pr.chunk0] + off;
+  const int64_t stride = (int64_t)pr.kp * pr.dp + pr.kp;
   double s = 0.0;
-  for (int ch = pr.chunk0 + lane; ch < pr.chunk0 + pr.nchunk; ch += 32) s += a.part[a.part_off[ch] + off];
+  for (int ch = lane; ch < pr.nchunk; ch += 32) s += base[ch * stride];
   return warp_sum_d(s);
 }
 
-// t = W^T r (phase 1) or z = W t and the block's partial r^T z (phase 2), rows of one block
-__device__ void precond_block(const BatchArgs& a, const BProb& pr, int blk, int phase, int cur) {
-  const int lane = threadIdx.x & 31;
-  const int d = pr.d, dp = pr.dp;
-  double rzp[KPMAX];
+// t = W^T r (phase 1) or z = W t and the block's partial r^T z (phase 2) for the 32 rows of one
+// block, one CTA: lane = row; t_i = sum_{c <= i} W[c][i] r_c reads rows of W, z_i =
+// sum_{c >= i} W^T[c][i] t_c reads rows of W^T (contiguous loads, broadcast vector entries); the
+// warps take consecutive slices of the columns and their sums are added in warp order.
+template <int PHASE>
+__global__ void __launch_bounds__(BT) bprec_kernel(BatchArgs a) {
+  __shared__ double red[BW][KPMAX][32];
+  const int it = *(volatile int*)a.iter;
+  const int cur = it & 1;
+  const int2 bk = a.blocks[blockIdx.x];
+  const BProb& pr = a.probs[bk.x];
+  if (!prob_active(pr, it)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int d = pr.d, dp = pr.dp, blk = bk.y;
+  const int i = blk * 32 + lane;
+  const bool row_ok = i < d;
+  unsigned act = 0;
+  for (int j = 0; j < pr.k; ++j)
+    if (pr.flags[cur * pr.kp + j] & F_ACTIVE) act |= 1u << j;
+  const double* M = PHASE == 1 ? pr.W : pr.WT;
+  const double* vin = PHASE == 1 ? pr.R : pr.T;
+  const int c_lo = PHASE == 1 ? 0 : blk * 32;
+  const int c_hi = PHASE == 1 ? min(d, blk * 32 + 32) : d;
+  const int span = (c_hi - c_lo + BW - 1) / BW;
+  const int w_lo = c_lo + warp * span, w_hi = min(c_hi, w_lo + span);
+  const int ic = row_ok ? i : 0;
+  double s[KPMAX];
 #pragma unroll
-  for (int j = 0; j < KPMAX; ++j) rzp[j] = 0.0;
-  const int i0 = blk * 32, i1 = min(d, i0 + 32);
-  for (int i = i0; i < i1; ++i) {
-    double s[KPMAX];
+  for (int j = 0; j < KPMAX; ++j) s[j] = 0.0;
+  for (int c = w_lo; c < w_hi; ++c) {
+    const double w = __ldg(M + (int64_t)c * d + ic);
 #pragma unroll
-    for (int j = 0; j < KPMAX; ++j) s[j] = 0.0;
-    if (phase == 1) {
-      const double* row = pr.WT + (int64_t)i * d;
-      for (int c = lane; c <= i; c += 32) {
-        const double w = __ldg(row + c);
+    for (int j = 0; j < KPMAX; ++j)
+      if (act & (1u << j)) s[j] = fma(w, vin[j * dp + c], s[j]);
+  }
 #pragma unroll
-        for (int j = 0; j < KPMAX; ++j)
-          if (j < pr.k && (pr.flags[cur * pr.kp + j] & F_ACTIVE)) s[j] = fma(w, pr.R[j * dp + c], s[j]);
-      }
-    } else {
-      const double* row = pr.W + (int64_t)i * d;
-      for (int c = i + lane; c < d; c += 32) {
-        const double w = __ldg(row + c);
-#pragma unroll
-        for (int j = 0; j < KPMAX; ++j)
-          if (j < pr.k && (pr.flags[cur * pr.kp + j] & F_ACTIVE)) s[j] = fma(w, pr.T[j * dp + c], s[j]);
-      }
-    }
+  for (int j = 0; j < KPMAX; ++j) red[warp][j][lane] = s[j];
+  __syncthreads();
+  if (warp == 0) {
 #pragma unroll
     for (int j = 0; j < KPMAX; ++j) {
-      if (j < pr.k && (pr.flags[cur * pr.kp + j] & F_ACTIVE)) {
-        const double v = warp_sum_d(s[j]);
-        if (phase == 1) {
-          if (lane == 0) pr.T[j * dp + i] = v;
-        } else {
-          if (lane == 0) pr.Z[j * dp + i] = v;
-          rzp[j] = fma(pr.R[j * dp + i], v, rzp[j]);
+      if (!(act & (1u << j))) continue;
+      double v = 0.0;
+      for (int w = 0; w < BW; ++w) v += red[w][j][lane];
+      if (PHASE == 1) {
+        if (row_ok) pr.T[j * dp + i] = v;
+      } else {
+        if (row_ok) pr.Z[j * dp + i] = v;
+        // a breakdown marked by the update survives in the block's r^T z slot
+        const double rz = warp_sum_d(row_ok ? pr.R[j * dp + i] * v : 0.0);
+        if (lane == 0) {
+          double* sl = pr.slot + (blk * 2 + 1) * pr.kp + j;
+          if (!isnan(*sl)) *sl = rz;
         }
       }
     }
   }
-  if (phase == 2 && lane == 0) {
-    for (int j = 0; j < pr.k; ++j)
-      if (pr.flags[cur * pr.kp + j] & F_ACTIVE) pr.slot[(blk * 2 + 1) * pr.kp + j] = rzp[j];
-  }
 }
 
-// split x into FP32 head and tail ([dp][kp] layout) for the columns of one block
 __device__ void split_x_block(const BProb& pr, int blk) {
   const int lane = threadIdx.x & 31;
   const int c = blk * 32 + lane;
@@ -518,12 +665,18 @@ __device__ void direction_block(const BatchArgs& a, const BProb& pr, int blk, in
     }
   }
   if (need) {
-    // the whole problem takes an exact residual before its directions are updated
+    // the problem's next iteration replaces its residuals by b - H x before the directions
+    // are updated
     split_x_block(pr, blk);
     if (blk == 0 && lane == 0) {
-      pr.pstate[4] = 1;
-      atomicOr(any_exact, 1);
+      for (int j = 0; j < kp; ++j) {  // the state carries over unchanged into the exact step
+        pr.flags[nxt * kp + j] = pr.flags[cur * kp + j];
+        pr.rz[nxt * kp + j] = pr.rz[cur * kp + j];
+      }
+      pr.pstate[4 + nxt] = 1;
+      set_left(pr, it + 1, 1);
       atomicAdd(active_cnt, 1);
+      atomicOr(any_exact, 1);
     }
     return;
   }
@@ -545,7 +698,6 @@ __device__ void direction_block(const BatchArgs& a, const BProb& pr, int blk, in
       if (w0) {
         pr.st[j] = !fin[j] ? LSQ_ERR_BREAKDOWN : (conv[j] ? LSQ_OK : LSQ_ERR_MAXIT);
         pr.flags[nxt * kp + j] = 0;
-        pr.its[j] = it + 1;
         pr.rz[nxt * kp + j] = rzn[j];
       }
       continue;
@@ -560,7 +712,6 @@ __device__ void direction_block(const BatchArgs& a, const BProb& pr, int blk, in
     if (w0) {
       pr.flags[nxt * kp + j] = F_ACTIVE;
       pr.rz[nxt * kp + j] = rzn[j];
-      pr.its[j] = it + 1;
       if (after_exact) {
         pr.rz_rep[j] = rzn[j];
         pr.it_last[j] = it + 1;
@@ -569,274 +720,180 @@ __device__ void direction_block(const BatchArgs& a, const BProb& pr, int blk, in
   }
   if (blk == 0 && lane == 0) {
     set_left(pr, it + 1, left);
-    if (!after_exact) pr.pstate[4] = 0;
-    if (left && !after_exact) atomicAdd(active_cnt, 1);
+    pr.pstate[4 + nxt] = 0;
+    if (left) atomicAdd(active_cnt, 1);
   }
 }
 
-template <typename TA, bool MIXED>
-__global__ void __launch_bounds__(BT, 1) batch_kernel(BatchArgs a) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  const int P = gridDim.x;
+
+// set-up per block: r = b (x0 = 0) or the split of x0 for the exact pass; state of iteration 0
+template <bool MIXED>
+__global__ void __launch_bounds__(BT) binit_kernel(BatchArgs a) {
   const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * BW + (threadIdx.x >> 5), nw = P * BW;
-  int passes = 0, exact_passes = 0;
-#define BAR()                                        \
-  do {                                               \
-    if (grid_barrier(a.bar, P, a.err)) return;       \
-  } while (0)
-
-  // ---- initial residual r = b - A^T A x0 (or b), z = W W^T r, p = z
-  for (int w = gw; w < a.nblocks; w += nw) {
-    const int2 bk = a.blocks[w];
-    const BProb& pr = a.probs[bk.x];
-    const int c = bk.y * 32 + lane;
+  const int w = blockIdx.x * BW + (threadIdx.x >> 5);
+  if (w >= a.nblocks) return;
+  const int2 bk = a.blocks[w];
+  const BProb& pr = a.probs[bk.x];
+  const int c = bk.y * 32 + lane;
+  for (int j = 0; j < pr.kp; ++j) {
+    if (c < pr.dp) {
+      const bool in = c < pr.d && j < pr.k;
+      if (in && a.x0_zero) pr.X[j * pr.d + c] = 0.0;
+      pr.R[j * pr.dp + c] = in ? pr.B[j * pr.d + c] : 0.0;
+      pr.P[j * pr.dp + c] = (in && !MIXED) ? pr.X[j * pr.d + c] : 0.0;  // the FP64 exact pass reads P
+      pr.Pf[c * pr.kp + j] = 0.f;
+      pr.Z[j * pr.dp + c] = 0.0;
+      pr.T[j * pr.dp + c] = 0.0;
+    }
+  }
+  if (!a.x0_zero && MIXED) split_x_block(pr, bk.y);
+  // <b, x0>, and r^T z slots cleared
+  for (int j = 0; j < pr.k; ++j) {
+    const double bx = warp_sum_d(c < pr.d ? pr.B[j * pr.d + c] * pr.X[j * pr.d + c] : 0.0);
+    if (lane == 0) {
+      pr.slot[(bk.y * 2 + 0) * pr.kp + j] = bx;
+      pr.slot[(bk.y * 2 + 1) * pr.kp + j] = 0.0;
+    }
+  }
+  if (bk.y == 0 && lane == 0) {
+    set_left(pr, 0, 1);
+    pr.pstate[2] = 0;
+    pr.pstate[3] = -1;
+    pr.pstate[4] = 0;
+    pr.pstate[5] = 0;
     for (int j = 0; j < pr.kp; ++j) {
-      if (c < pr.dp) {
-        const bool in = c < pr.d && j < pr.k;
-        if (in && a.x0_zero) pr.X[j * pr.d + c] = 0.0;
-        pr.R[j * pr.dp + c] = in ? pr.B[j * pr.d + c] : 0.0;
-        pr.P[j * pr.dp + c] = (in && !MIXED) ? pr.X[j * pr.d + c] : 0.0;  // FP64 exact pass reads P
-        pr.Pf[c * pr.kp + j] = 0.f;
-        pr.Z[j * pr.dp + c] = 0.0;
-        pr.T[j * pr.dp + c] = 0.0;
-      }
+      pr.flags[j] = j < pr.k ? F_ACTIVE : 0;  // parity 0: iteration 0 reads it
+      pr.flags[pr.kp + j] = 0;
+      pr.its[j] = 0;
+      pr.st[j] = LSQ_ERR_MAXIT;
+      pr.it_last[j] = 0;
     }
-    if (!a.x0_zero && MIXED) split_x_block(pr, bk.y);
+  }
+}
+
+// r0 = b - A^T A x0 from the exact pass
+template <bool MIXED>
+__global__ void __launch_bounds__(BT) bresid_kernel(BatchArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * BW + (threadIdx.x >> 5);
+  if (w >= a.nblocks) return;
+  const int2 bk = a.blocks[w];
+  const BProb& pr = a.probs[bk.x];
+  const int c = bk.y * 32 + lane;
+  for (int j = 0; j < pr.k; ++j) {
+    const double v = c < pr.d ? chunk_sum(a, pr, j * pr.dp + c) : 0.0;
+    if (c < pr.d) {
+      pr.R[j * pr.dp + c] = pr.B[j * pr.d + c] - v;
+      if (!MIXED) pr.P[j * pr.dp + c] = 0.0;
+    }
+  }
+}
+
+// p = z, r^T z and the stopping rule at x0
+__global__ void __launch_bounds__(BT) binitdir_kernel(BatchArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * BW + (threadIdx.x >> 5);
+  if (w >= a.nblocks) return;
+  const int2 bk = a.blocks[w];
+  const BProb& pr = a.probs[bk.x];
+  const int c = bk.y * 32 + lane;
+  int left = 0;
+  for (int j = 0; j < pr.k; ++j) {
+    double rz = 0.0, bx = 0.0;
+    for (int b = 0; b < pr.nblk; ++b) {
+      rz += pr.slot[(b * 2 + 1) * pr.kp + j];
+      bx += pr.slot[(b * 2 + 0) * pr.kp + j];
+    }
+    const bool conv = rz == 0.0 || rz <= pr.tol2 * bx;
+    const bool stop = conv || !isfinite(rz) || a.maxit == 0;
+    if (c < pr.d) {
+      const double z = pr.Z[j * pr.dp + c];
+      pr.P[j * pr.dp + c] = stop ? 0.0 : z;
+      pr.Pf[c * pr.kp + j] = stop ? 0.f : (float)z;
+    }
+    if (!stop) ++left;
     if (bk.y == 0 && lane == 0) {
-      set_left(pr, 0, 1);
-      pr.pstate[2] = 0;
-      pr.pstate[3] = -1;
-      pr.pstate[4] = a.x0_zero ? 0 : 1;
-      for (int j = 0; j < pr.kp; ++j) {
-        pr.flags[j] = j < pr.k ? F_ACTIVE : 0;  // parity 0: iteration 0 reads it
-        pr.flags[pr.kp + j] = 0;
-        pr.its[j] = 0;
-        pr.st[j] = LSQ_ERR_MAXIT;
-        pr.it_last[j] = 0;
+      pr.rz[j] = rz;
+      pr.rz_rep[j] = rz;
+      if (stop) {
+        pr.flags[j] = 0;  // parity 0 (no other block reads it in this kernel)
+        pr.st[j] = conv ? LSQ_OK : (isfinite(rz) ? LSQ_ERR_MAXIT : LSQ_ERR_BREAKDOWN);
       }
     }
   }
-  BAR();
-  if (!a.x0_zero) {
-    pass_phase<TA, MIXED>(a, true, 0, smem);
-    ++passes;
-    ++exact_passes;
-    BAR();
-    for (int w = gw; w < a.nblocks; w += nw) {
-      const int2 bk = a.blocks[w];
-      const BProb& pr = a.probs[bk.x];
-      const int c = bk.y * 32 + lane;
-      for (int j = 0; j < pr.k; ++j) {
-        const double v = c < pr.d ? chunk_sum(a, pr, j * pr.dp + c) : 0.0;
-        if (c < pr.d) pr.R[j * pr.dp + c] = pr.B[j * pr.d + c] - v;
-      }
-    }
-    BAR();
-  }
-  // <b, x0> per block
-  for (int w = gw; w < a.nblocks; w += nw) {
-    const int2 bk = a.blocks[w];
-    const BProb& pr = a.probs[bk.x];
-    const int c = bk.y * 32 + lane;
-    for (int j = 0; j < pr.k; ++j) {
-      const double bx = warp_sum_d(c < pr.d ? pr.B[j * pr.d + c] * pr.X[j * pr.d + c] : 0.0);
-      if (lane == 0) pr.slot[(bk.y * 2 + 0) * pr.kp + j] = bx;
-    }
-    if (!MIXED) {
-      for (int j = 0; j < pr.k; ++j)
-        if (c < pr.d) pr.P[j * pr.dp + c] = 0.0;
-    }
-  }
-  BAR();
-  for (int w = gw; w < a.nblocks; w += nw) precond_block(a, a.probs[a.blocks[w].x], a.blocks[w].y, 1, 0);
-  BAR();
-  for (int w = gw; w < a.nblocks; w += nw) precond_block(a, a.probs[a.blocks[w].x], a.blocks[w].y, 2, 0);
-  BAR();
-  // p = z, rz, stopping rule at x0
-  {
-    int* cnt = a.cnt + 0;
-    for (int w = gw; w < a.nblocks; w += nw) {
-      const int2 bk = a.blocks[w];
-      const BProb& pr = a.probs[bk.x];
-      const int c = bk.y * 32 + lane;
-      int left = 0;
-      for (int j = 0; j < pr.k; ++j) {
-        double rz = 0.0, bx = 0.0;
-        for (int b = 0; b < pr.nblk; ++b) {
-          rz += pr.slot[(b * 2 + 1) * pr.kp + j];
-          bx += pr.slot[(b * 2 + 0) * pr.kp + j];
-        }
-        const bool conv = rz == 0.0 || rz <= pr.tol2 * bx;
-        const bool stop = conv || !isfinite(rz) || a.maxit == 0;
-        if (c < pr.d) {
-          const double z = pr.Z[j * pr.dp + c];
-          pr.P[j * pr.dp + c] = stop ? 0.0 : z;
-          pr.Pf[c * pr.kp + j] = stop ? 0.f : (float)z;
-        }
-        if (!stop) ++left;
-        if (bk.y == 0 && lane == 0) {
-          pr.rz[j] = rz;
-          pr.rz_rep[j] = rz;
-          if (stop) {
-            pr.flags[j] = 0;  // parity 0 (no other block reads it in this phase)
-            pr.st[j] = conv ? LSQ_OK : (isfinite(rz) ? LSQ_ERR_MAXIT : LSQ_ERR_BREAKDOWN);
-          }
-        }
-      }
-      if (bk.y == 0 && lane == 0) {
-        set_left(pr, 0, left);
-        pr.pstate[4] = 0;
-        if (left) atomicAdd(cnt, 1);
-      }
-    }
-  }
-  BAR();
-  int it = 0;
-  while (it < a.maxit) {
-    const int slot = it % 3, cur = it & 1;
-    if (*(volatile int*)(a.cnt + slot) == 0) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      a.cnt[(it + 1) % 3] = 0;
-      a.anyx[(it + 1) % 3] = 0;
-    }
-    // ---- pass over the search directions
-    pass_phase<TA, MIXED>(a, false, it, smem);
-    ++passes;
-    if (!MIXED) ++exact_passes;
-    BAR();
-    // ---- x += alpha p, r -= alpha v, <b, x>
-    for (int w = gw; w < a.nblocks; w += nw) {
-      const int2 bk = a.blocks[w];
-      const BProb& pr = a.probs[bk.x];
-      if (!prob_active(pr, it)) continue;
-      const int c = bk.y * 32 + lane;
-      for (int j = 0; j < pr.k; ++j) {
-        if (!(pr.flags[cur * pr.kp + j] & F_ACTIVE)) continue;
-        const double q = chunk_sum_warp(a, pr, pr.kp * pr.dp + j);
-        const double rz = pr.rz[cur * pr.kp + j];
-        if (!(q > 0.0) || !isfinite(q)) {
-          // breakdown: stop this right-hand side (the direction phase sees rz = NaN)
-          if (lane == 0) pr.slot[(bk.y * 2 + 1) * pr.kp + j] = NAN;
-          continue;
-        }
-        const double alpha = rz / q;
-        double bxp = 0.0;
-        if (c < pr.d) {
-          const double v = chunk_sum(a, pr, j * pr.dp + c);
-          const double x = pr.X[j * pr.d + c] + alpha * pr.P[j * pr.dp + c];
-          pr.X[j * pr.d + c] = x;
-          pr.R[j * pr.dp + c] -= alpha * v;
-          bxp = pr.B[j * pr.d + c] * x;
-        }
-        bxp = warp_sum_d(bxp);
-        if (lane == 0) pr.slot[(bk.y * 2 + 0) * pr.kp + j] = bxp;
-      }
-    }
-    BAR();
-    for (int w = gw; w < a.nblocks; w += nw) {
-      const BProb& pr = a.probs[a.blocks[w].x];
-      if (prob_active(pr, it)) precond_block(a, pr, a.blocks[w].y, 1, cur);
-    }
-    BAR();
-    for (int w = gw; w < a.nblocks; w += nw) {
-      const BProb& pr = a.probs[a.blocks[w].x];
-      if (!prob_active(pr, it)) continue;
-      // a breakdown marked in the update phase survives in the block's r^T z slot
-      const int2 bk = a.blocks[w];
-      unsigned nanmask = 0;
-#pragma unroll
-      for (int j = 0; j < KPMAX; ++j)
-        if (j < pr.k && isnan(pr.slot[(bk.y * 2 + 1) * pr.kp + j])) nanmask |= 1u << j;
-      precond_block(a, pr, bk.y, 2, cur);
-      if (lane == 0)
-        for (int j = 0; j < pr.k; ++j)
-          if (nanmask & (1u << j)) pr.slot[(bk.y * 2 + 1) * pr.kp + j] = NAN;
-    }
-    BAR();
-    int* cnt_next = a.cnt + (it + 1) % 3;
-    int* anyx = a.anyx + (it + 1) % 3;
-    for (int w = gw; w < a.nblocks; w += nw) {
-      const BProb& pr = a.probs[a.blocks[w].x];
-      if (prob_active(pr, it)) direction_block(a, pr, a.blocks[w].y, it, false, anyx, cnt_next);
-    }
-    BAR();
-    if (MIXED && *(volatile int*)anyx) {
-      // ---- exact residual for the problems that asked for one
-      pass_phase<TA, MIXED>(a, true, it, smem);
-      ++passes;
-      ++exact_passes;
-      BAR();
-      for (int w = gw; w < a.nblocks; w += nw) {
-        const int2 bk = a.blocks[w];
-        const BProb& pr = a.probs[bk.x];
-        if (!prob_active(pr, it) || !pr.pstate[4]) continue;
-        const int c = bk.y * 32 + lane;
-        for (int j = 0; j < pr.k; ++j) {
-          if (!(pr.flags[cur * pr.kp + j] & F_ACTIVE)) continue;
-          if (c < pr.d) pr.R[j * pr.dp + c] = pr.B[j * pr.d + c] - chunk_sum(a, pr, j * pr.dp + c);
-        }
-      }
-      BAR();
-      for (int w = gw; w < a.nblocks; w += nw) {
-        const BProb& pr = a.probs[a.blocks[w].x];
-        if (prob_active(pr, it) && pr.pstate[4]) precond_block(a, pr, a.blocks[w].y, 1, cur);
-      }
-      BAR();
-      for (int w = gw; w < a.nblocks; w += nw) {
-        const BProb& pr = a.probs[a.blocks[w].x];
-        if (prob_active(pr, it) && pr.pstate[4]) precond_block(a, pr, a.blocks[w].y, 2, cur);
-      }
-      BAR();
-      // the problem-wide counter of this iteration already counted these problems once
-      for (int w = gw; w < a.nblocks; w += nw) {
-        const BProb& pr = a.probs[a.blocks[w].x];
-        if (prob_active(pr, it) && pr.pstate[4]) direction_block(a, pr, a.blocks[w].y, it, true, anyx, a.cnt + 3);
-      }
-      BAR();
-    }
-    ++it;
-  }
-#undef BAR
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.out[0] = it;
-    a.out[1] = passes;
-    a.out[2] = exact_passes;
+  if (bk.y == 0 && lane == 0) {
+    set_left(pr, 0, left);
+    if (left) atomicAdd(a.cnt, 1);
   }
 }
 
-__global__ void transpose_batch_kernel(const double* __restrict__ W, int d, double* __restrict__ WT) {
-  __shared__ double tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int r = by + k, c = bx + threadIdx.x;
-    tile[k][threadIdx.x] = (r < d && c < d) ? W[(int64_t)r * d + c] : 0.0;
-  }
-  __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int r = bx + k, c = by + threadIdx.x;
-    if (r < d && c < d) WT[(int64_t)r * d + c] = tile[threadIdx.x][k];
+// x += alpha p, r -= alpha v, <b, x>; or r = b - H x in an exact residual step
+__global__ void __launch_bounds__(BT) bupdate_kernel(BatchArgs a) {
+  const int it = *(volatile int*)a.iter;
+  const int cur = it & 1;
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * BW + (threadIdx.x >> 5);
+  if (w >= a.nblocks) return;
+  const int2 bk = a.blocks[w];
+  const BProb& pr = a.probs[bk.x];
+  if (!prob_active(pr, it)) return;
+  const int c = bk.y * 32 + lane;
+  const bool exact = exact_step(pr, it);
+  for (int j = 0; j < pr.k; ++j) {
+    if (!(pr.flags[cur * pr.kp + j] & F_ACTIVE)) continue;
+    if (exact) {
+      if (c < pr.d) pr.R[j * pr.dp + c] = pr.B[j * pr.d + c] - chunk_sum(a, pr, j * pr.dp + c);
+      if (lane == 0) pr.slot[(bk.y * 2 + 1) * pr.kp + j] = 0.0;
+      continue;
+    }
+    const double q = chunk_sum_warp(a, pr, pr.kp * pr.dp + j);
+    const double rz = pr.rz[cur * pr.kp + j];
+    if (!(q > 0.0) || !isfinite(q)) {
+      // breakdown: stop this right-hand side (the direction kernel sees r^T z = NaN)
+      if (lane == 0) pr.slot[(bk.y * 2 + 1) * pr.kp + j] = NAN;
+      continue;
+    }
+    const double alpha = rz / q;
+    double bxp = 0.0;
+    if (c < pr.d) {
+      const double v = chunk_sum(a, pr, j * pr.dp + c);
+      const double x = pr.X[j * pr.d + c] + alpha * pr.P[j * pr.dp + c];
+      pr.X[j * pr.d + c] = x;
+      pr.R[j * pr.dp + c] -= alpha * v;
+      bxp = pr.B[j * pr.d + c] * x;
+    }
+    bxp = warp_sum_d(bxp);
+    if (lane == 0) {
+      pr.slot[(bk.y * 2 + 0) * pr.kp + j] = bxp;
+      pr.slot[(bk.y * 2 + 1) * pr.kp + j] = 0.0;
+      if (bk.y == 0) pr.its[j] += 1;
+    }
   }
 }
 
-template <typename TA>
-size_t pass_smem(bool mixed, int dp, int kp) {
-  const int KP = kp <= 4 ? 4 : (kp <= 8 ? 8 : 16);
-  size_t f32 = 0, df = 0, f64 = 0;
-  if (mixed) {
-    const int TR = sizeof(TA) == 4 ? 32 : 16;
-    f32 = (size_t)(TR * (dp + 1) + dp * KP + BW * KP * TR + TR * KP) * 4;
-    const int TRd = 16;
-    df = (size_t)(TRd * (dp + 1) * (sizeof(TA) == 8 ? 2 : 1) + 2 * dp * KP + 2 * BW * KP * TRd + 2 * TRd * KP) * 4;
-  } else {
-    f64 = (size_t)(16 * (dp + 1) + dp * KP + BW * KP * 16 + 16 * KP) * 8;
-  }
-  // the row-phase reduction reuses the area: rsplit * KP * dp = 256 * KP doubles for dp < 256
-  const size_t red = (size_t)(dp >= 256 ? 0 : 256) * KP * 8;
-  return std::max(std::max(f32, df), std::max(f64, red));
+__global__ void __launch_bounds__(BT) bdir_kernel(BatchArgs a) {
+  const int it = *(volatile int*)a.iter;
+  const int w = blockIdx.x * BW + (threadIdx.x >> 5);
+  if (w >= a.nblocks) return;
+  const int2 bk = a.blocks[w];
+  const BProb& pr = a.probs[bk.x];
+  if (prob_active(pr, it))
+    direction_block(a, pr, bk.y, it, exact_step(pr, it), a.anyx + (it + 1) % 3, a.cnt + (it + 1) % 3);
 }
 
-int kp_of(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : 16); }
+// end of an iteration: counters of the next one, then the iteration index
+__global__ void btick_kernel(BatchArgs a) {
+  const int it = *a.iter;
+  a.stats[0] += 1;
+  if (a.anyx[it % 3]) a.stats[1] += 1;
+  const int nx = it + 1;
+  a.qhead[nx % 3] = 0;
+  a.cnt[(nx + 1) % 3] = 0;
+  a.anyx[(nx + 1) % 3] = 0;
+  *a.iter = nx;
+}
+
+int kp_of(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 12 ? 12 : 16)); }
 int dp_of(int d) {
   int e = 1;
   while (32 * e < d) e <<= 1;
@@ -855,9 +912,10 @@ extern "C" void lsq_batch_opts_default(lsq_batch_opts* o) {
   o->precision = LSQ_PREC_MIXED;
   o->rho = 0.0;
   o->x0_zero = 1;
-  o->refresh_every = 12;
+  o->refresh_every = 40;
   o->chunk_rows = 0;
   o->grid_blocks = 0;
+  o->profile_phases = 0;
 }
 
 extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem* probs, double tol, int32_t maxit,
@@ -870,8 +928,6 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   if (!(o.m_factor >= 1.0)) return LSQ_ERR_ARG;
   const bool mixed = o.precision == LSQ_PREC_MIXED;
   int dtype = -1;
-  int max_d = 1, max_kp = 4;
-  int64_t max_md = 1;
   for (int p = 0; p < nprob; ++p) {
     const lsq_problem& q = probs[p];
     if (!q.A.data || !q.B || !q.X) return LSQ_ERR_ARG;
@@ -881,12 +937,13 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     dtype = q.A.dtype;
     if (q.k < 1 || q.k > LSQ_MAX_RHS) return LSQ_ERR_ARG;
     const int64_t m = std::max<int64_t>(q.A.d, (int64_t)ceil(o.m_factor * (double)q.A.d));
-    max_d = std::max<int>(max_d, (int)q.A.d);
-    max_kp = std::max(max_kp, kp_of(q.k));
-    max_md = std::max<int64_t>(max_md, m * q.A.d);
   }
-  const int max_dp = dp_of(max_d);
-  const int chunk_rows = o.chunk_rows > 0 ? ((o.chunk_rows + 31) / 32) * 32 : 2048;
+  // work unit of the pass: about 2^20 elements of A (4 MB of FP32), at least 256 rows, so narrow
+  // problems do not spread over thousands of partial sums
+  auto chunk_rows_of = [&](int d) {
+    if (o.chunk_rows > 0) return ((o.chunk_rows + 31) / 32) * 32;
+    return std::max(256, (1 << 20) / dp_of(d));
+  };
 
   // ---- layout of the state arena
   std::vector<int4> chunks;
@@ -925,6 +982,7 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     f.it_last = add((size_t)kp * 4);
     f.pstate = add(32);
     chunk0[p] = (int)chunks.size();
+    const int chunk_rows = chunk_rows_of(d);
     for (int64_t r0 = 0; r0 < probs[p].A.n; r0 += chunk_rows) {
       chunks.push_back(make_int4(p, (int)r0, (int)std::min<int64_t>(probs[p].A.n, r0 + chunk_rows), 0));
       part_off.push_back(part_total);
@@ -935,20 +993,25 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   }
   const int nch = (int)chunks.size();
 
-  // ---- persistent launch shape
-  void* kern = dtype == LSQ_F64 ? (mixed ? (void*)batch_kernel<double, true> : (void*)batch_kernel<double, false>)
-                                : (mixed ? (void*)batch_kernel<float, true> : (void*)batch_kernel<float, false>);
-  const size_t smem = dtype == LSQ_F64 ? pass_smem<double>(mixed, max_dp, max_kp) : pass_smem<float>(mixed, max_dp, max_kp);
+  // ---- the pass kernel: dynamic shared memory for the largest problem shape
+  void* kpass = dtype == LSQ_F64 ? (mixed ? (void*)bpass_kernel<double, true> : (void*)bpass_kernel<double, false>)
+                                 : (mixed ? (void*)bpass_kernel<float, true> : (void*)bpass_kernel<float, false>);
+  size_t smem = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const int dpp = dp_of((int)probs[p].A.d), kpp = kp_of(probs[p].k);
+    smem = std::max(smem, pass_smem_shape(mixed, dtype == LSQ_F64, dpp, kpp));
+  }
   if (smem > 227 * 1024) return LSQ_ERR_ARG;
-  LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LSQ_CUDA_TRY(cudaFuncSetAttribute(kpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, smem));
+  LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpass, PT, smem));
   if (per_sm < 1) return LSQ_ERR_CUDA;
   int G = per_sm * ctx->sm_count;
   if (o.grid_blocks > 0) G = std::min(G, o.grid_blocks);
-  G = std::max(1, std::min(G, std::max(nch, (int)blocks.size() / BW + 1)));
+  G = std::max(1, std::min(G, nch));
 
-  // ---- static schedule of the chunks: longest first onto the least-loaded CTA
+  // ---- the queue: chunks by decreasing cost (rows x columns, scaled by the directions per
+  // element under the FP32 arithmetic)
   std::vector<int> order(nch);
   std::vector<double> cost(nch);
   for (int c = 0; c < nch; ++c) {
@@ -959,48 +1022,36 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     cost[c] = rows * (double)dp_of((int)q.A.d) * std::max(1.0, kp / (mixed ? 6.0 : 1.0));
   }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-  std::vector<double> load(G, 0.0);
-  std::vector<std::vector<int>> lists(G);
-  for (int c : order) {
-    int best = 0;
-    for (int g = 1; g < G; ++g)
-      if (load[g] < load[best]) best = g;
-    load[best] += cost[c];
-    lists[best].push_back(c);
-  }
-  std::vector<int> sched, sched_off(G + 1, 0);
-  for (int g = 0; g < G; ++g) {
-    std::sort(lists[g].begin(), lists[g].end());
-    sched_off[g] = (int)sched.size();
-    for (int c : lists[g]) sched.push_back(c);
-  }
-  sched_off[G] = (int)sched.size();
 
   const size_t o_probs = add(sizeof(BProb) * nprob);
   const size_t o_chunks = add(sizeof(int4) * nch);
   const size_t o_poff = add(sizeof(int64_t) * nch);
-  const size_t o_sched = add(sizeof(int) * std::max<size_t>(1, sched.size()));
-  const size_t o_soff = add(sizeof(int) * (G + 1));
+  const size_t o_order = add(sizeof(int) * nch);
   const size_t o_blocks = add(sizeof(int2) * blocks.size());
   const size_t o_part = add((size_t)part_total * 8);
-  const size_t o_bar = add(256);
-  const size_t o_SA = add((size_t)max_md * 8);
-  const size_t o_R = add((size_t)max_d * max_d * 8);
+  const size_t o_ctl = add(256);
+  std::vector<size_t> sa_off(nprob);
+  for (int p = 0; p < nprob; ++p) {
+    const int64_t dd = probs[p].A.d;
+    const int64_t m = std::max<int64_t>(dd, (int64_t)ceil(o.m_factor * (double)dd));
+    sa_off[p] = add((size_t)m * dd * 8);
+  }
   lsq_status st = lsq_ensure_state(ctx, need);
   if (st != LSQ_OK) return st;
   char* base = reinterpret_cast<char*>(ctx->state);
   cudaStream_t s = ctx->stream;
   LSQ_CUDA_TRY(cudaEventRecord(ctx->ev0, s));
 
-  // ---- sketch and factor every problem (instance t = p of the seed)
+  // ---- sketch every problem (instance t = p of the seed), then factor them all at once
   cudaEvent_t e1, e2;
   LSQ_CUDA_TRY(cudaEventCreate(&e1));
   LSQ_CUDA_TRY(cudaEventCreate(&e2));
-  float ms_sketch = 0.f, ms_factor = 0.f;
   std::vector<int> prob_status(nprob, LSQ_OK);
   lsq_status first_err = LSQ_OK;
-  double* SA = reinterpret_cast<double*>(base + o_SA);
-  double* Rtmp = reinterpret_cast<double*>(base + o_R);
+  std::vector<const double*> sa_ptr(nprob);
+  std::vector<double*> w_ptr(nprob), wt_ptr(nprob);
+  std::vector<int> m_of(nprob), d_of(nprob);
+  cudaEventRecord(e1, s);
   for (int p = 0; p < nprob; ++p) {
     const int d = (int)probs[p].A.d;
     const int64_t m = std::max<int64_t>(d, (int64_t)ceil(o.m_factor * (double)d));
@@ -1008,37 +1059,36 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     so.t = (uint32_t)p;
     so.s = (int)std::min<int64_t>(o.s > 0 ? o.s : 8, m);  // an SJLT column has at most m nonzeros
     so.precision = o.sketch_precision;
-    cudaEventRecord(e1, s);
+    double* SA = reinterpret_cast<double*>(base + sa_off[p]);
     st = lsq_sketch(ctx, &probs[p].A, o.sketch_type, m, o.seed, &so, SA);
     if (st != LSQ_OK) return st;
-    cudaEventRecord(e2, s);
-    double* W = reinterpret_cast<double*>(base + off[p].W);
-    st = lsq_factor(ctx, SA, m, d, Rtmp, W);  // synchronises (rank check)
-    float t1 = 0.f, t2 = 0.f;
-    cudaEventElapsedTime(&t1, e1, e2);
-    ms_sketch += t1;
-    cudaEventRecord(e1, s);
-    if (st == LSQ_ERR_RANK) {
-      prob_status[p] = LSQ_ERR_RANK;
-      if (first_err == LSQ_OK) first_err = st;
-      LSQ_CUDA_TRY(cudaMemsetAsync(W, 0, (size_t)d * d * 8, s));
-    } else if (st != LSQ_OK) {
-      return st;
-    }
-    transpose_batch_kernel<<<dim3((d + 31) / 32, (d + 31) / 32), dim3(32, 8), 0, s>>>(
-        W, d, reinterpret_cast<double*>(base + off[p].WT));
-    LSQ_LAUNCH_CHECK();
-    cudaEventRecord(e2, s);
-    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
-    cudaEventElapsedTime(&t2, e1, e2);
-    (void)t2;
+    sa_ptr[p] = SA;
+    w_ptr[p] = reinterpret_cast<double*>(base + off[p].W);
+    wt_ptr[p] = reinterpret_cast<double*>(base + off[p].WT);
+    m_of[p] = (int)m;
+    d_of[p] = d;
   }
+  cudaEventRecord(e2, s);
+  st = lsq_factor_batched(ctx, nprob, sa_ptr.data(), m_of.data(), d_of.data(), w_ptr.data(), wt_ptr.data(), mixed,
+                          prob_status.data());
+  if (st != LSQ_OK) return st;
+  for (int p = 0; p < nprob; ++p) {
+    if (prob_status[p] == LSQ_ERR_RANK) {
+      if (first_err == LSQ_OK) first_err = LSQ_ERR_RANK;
+      const size_t dd = (size_t)d_of[p] * d_of[p] * 8;
+      LSQ_CUDA_TRY(cudaMemsetAsync(w_ptr[p], 0, dd, s));
+      LSQ_CUDA_TRY(cudaMemsetAsync(wt_ptr[p], 0, dd, s));
+    }
+  }
+  float ms_sketch = 0.f, ms_factor = 0.f;
   {
-    float tt = 0.f;
-    cudaEventRecord(e1, s);
+    cudaEvent_t e3;
+    LSQ_CUDA_TRY(cudaEventCreate(&e3));
+    cudaEventRecord(e3, s);
     LSQ_CUDA_TRY(cudaStreamSynchronize(s));
-    cudaEventElapsedTime(&tt, ctx->ev0, e1);
-    ms_factor = tt - ms_sketch;
+    cudaEventElapsedTime(&ms_sketch, e1, e2);
+    cudaEventElapsedTime(&ms_factor, e2, e3);
+    cudaEventDestroy(e3);
   }
 
   // ---- device tables
@@ -1055,6 +1105,10 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     b.k = q.k;
     b.kp = kp_of(q.k);
     b.nblk = (b.d + 31) / 32;
+    {
+      const size_t es = q.A.dtype == LSQ_F64 ? 8 : 4;
+      b.vec = (((uintptr_t)q.A.data % 16) == 0 && ((size_t)q.A.ld * es) % 16 == 0) ? 1 : 0;
+    }
     b.chunk0 = chunk0[p];
     b.nchunk = nchunk[p];
     b.B = q.B;
@@ -1085,37 +1139,156 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   LSQ_CUDA_TRY(cudaMemcpy(base + o_probs, hp.data(), sizeof(BProb) * nprob, cudaMemcpyHostToDevice));
   LSQ_CUDA_TRY(cudaMemcpy(base + o_chunks, chunks.data(), sizeof(int4) * nch, cudaMemcpyHostToDevice));
   LSQ_CUDA_TRY(cudaMemcpy(base + o_poff, part_off.data(), sizeof(int64_t) * nch, cudaMemcpyHostToDevice));
-  if (!sched.empty())
-    LSQ_CUDA_TRY(cudaMemcpy(base + o_sched, sched.data(), sizeof(int) * sched.size(), cudaMemcpyHostToDevice));
-  LSQ_CUDA_TRY(cudaMemcpy(base + o_soff, sched_off.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice));
+  LSQ_CUDA_TRY(cudaMemcpy(base + o_order, order.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
   LSQ_CUDA_TRY(cudaMemcpy(base + o_blocks, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice));
-  LSQ_CUDA_TRY(cudaMemsetAsync(base + o_bar, 0, 256, s));
+  LSQ_CUDA_TRY(cudaMemsetAsync(base + o_ctl, 0, 256, s));
 
   BatchArgs a;
   a.probs = reinterpret_cast<BProb*>(base + o_probs);
+  a.nprob = nprob;
   a.chunks = reinterpret_cast<const int4*>(base + o_chunks);
   a.part_off = reinterpret_cast<const int64_t*>(base + o_poff);
-  a.sched = reinterpret_cast<const int*>(base + o_sched);
-  a.sched_off = reinterpret_cast<const int*>(base + o_soff);
+  a.order = reinterpret_cast<const int*>(base + o_order);
+  a.nchunks = nch;
   a.blocks = reinterpret_cast<const int2*>(base + o_blocks);
   a.nblocks = (int)blocks.size();
   a.part = reinterpret_cast<double*>(base + o_part);
-  a.bar = reinterpret_cast<unsigned*>(base + o_bar);
-  a.err = reinterpret_cast<int*>(base + o_bar + 64);
-  a.cnt = reinterpret_cast<int*>(base + o_bar + 96);    // [4]: 3 rotating + 1 sink
-  a.anyx = reinterpret_cast<int*>(base + o_bar + 128);  // [3]
-  a.out = reinterpret_cast<int*>(base + o_bar + 160);   // [3]
+  int* ctl = reinterpret_cast<int*>(base + o_ctl);
+  a.iter = ctl + 0;
+  a.qhead = ctl + 4;   // [3]
+  a.cnt = ctl + 8;     // [4]
+  a.anyx = ctl + 12;   // [3]
+  a.stats = ctl + 16;  // [2]
+  a.err = ctl + 20;
+  a.smem_bytes = (int)smem;
   a.maxit = maxit;
   a.mixed = mixed ? 1 : 0;
   a.x0_zero = o.x0_zero ? 1 : 0;
-  a.refresh_every = o.refresh_every > 0 ? o.refresh_every : 12;
-  a.replace2 = 1e-8;
+  a.refresh_every = o.refresh_every > 0 ? o.refresh_every : 40;
+  // one replacement after a 10^5 drop of the residual norm and one to confirm convergence:
+  // the FP32 passes' drift after the first (~1e-7 of that level) stays below 1e-10 overall
+  a.replace2 = 1e-10;
+
+  const int nbk = (int)blocks.size();
+  const int gblk = (nbk + BW - 1) / BW;
+  auto launch_pass = [&](int force_exact, bool count) -> lsq_status {
+    void* args[] = {&a, &force_exact};
+    LSQ_CUDA_TRY(cudaLaunchKernel(kpass, dim3(G), dim3(PT), args, smem, s));
+    if (count) lsq_count_launch();
+    return LSQ_OK;
+  };
+  // phase timers (opts.profile_phases): events around each kernel of the iteration, no graph
+  const bool prof = o.profile_phases != 0;
+  double ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  cudaEvent_t pe[7];
+  if (prof)
+    for (auto& e : pe) LSQ_CUDA_TRY(cudaEventCreate(&e));
+  // (LSQ_LAUNCH_CHECK counts the launch; in the captured iteration the replays are counted)
+#define ITER_CHECK()                                               \
+  do {                                                             \
+    if (cudaGetLastError() != cudaSuccess) return LSQ_ERR_CUDA;    \
+    if (timed) lsq_count_launch();                                 \
+  } while (0)
+  auto iteration = [&](bool timed) -> lsq_status {
+    if (timed) cudaEventRecord(pe[0], s);
+    lsq_status r = launch_pass(0, timed);
+    if (r != LSQ_OK) return r;
+    if (timed) cudaEventRecord(pe[1], s);
+    bupdate_kernel<<<gblk, BT, 0, s>>>(a);
+    ITER_CHECK();
+    if (timed) cudaEventRecord(pe[2], s);
+    bprec_kernel<1><<<nbk, BT, 0, s>>>(a);
+    ITER_CHECK();
+    if (timed) cudaEventRecord(pe[3], s);
+    bprec_kernel<2><<<nbk, BT, 0, s>>>(a);
+    ITER_CHECK();
+    if (timed) cudaEventRecord(pe[4], s);
+    bdir_kernel<<<gblk, BT, 0, s>>>(a);
+    ITER_CHECK();
+    btick_kernel<<<1, 1, 0, s>>>(a);
+    ITER_CHECK();
+    if (timed) cudaEventRecord(pe[5], s);
+    return LSQ_OK;
+  };
+
+#undef ITER_CHECK
   cudaEvent_t e3;
   LSQ_CUDA_TRY(cudaEventCreate(&e3));
   cudaEventRecord(e1, s);
-  void* args[] = {&a};
-  LSQ_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(G), dim3(BT), args, smem, s));
-  lsq_count_launch();
+  // ---- set-up: r0, z0, p0 and the stopping rule at x0
+  if (mixed) binit_kernel<true><<<gblk, BT, 0, s>>>(a);
+  else binit_kernel<false><<<gblk, BT, 0, s>>>(a);
+  LSQ_LAUNCH_CHECK();
+  int passes = 0, exact_passes = 0;
+  if (!o.x0_zero) {
+    st = launch_pass(1, true);
+    if (st != LSQ_OK) return st;
+    ++passes;
+    ++exact_passes;
+    LSQ_CUDA_TRY(cudaMemsetAsync(a.qhead, 0, sizeof(int), s));
+    if (mixed) bresid_kernel<true><<<gblk, BT, 0, s>>>(a);
+    else bresid_kernel<false><<<gblk, BT, 0, s>>>(a);
+    LSQ_LAUNCH_CHECK();
+  }
+  bprec_kernel<1><<<nbk, BT, 0, s>>>(a);
+  LSQ_LAUNCH_CHECK();
+  bprec_kernel<2><<<nbk, BT, 0, s>>>(a);
+  LSQ_LAUNCH_CHECK();
+  binitdir_kernel<<<gblk, BT, 0, s>>>(a);
+  LSQ_LAUNCH_CHECK();
+
+  // ---- iterations: one CUDA graph per iteration, replayed; the host looks at the count of
+  // active problems every `check` iterations
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  if (!prof && maxit > 0) {
+    // captured on the context's own non-blocking stream (the caller's may be the legacy
+    // default stream, which cannot be captured), replayed on the caller's stream
+    if (!ctx->capture) LSQ_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
+    const cudaStream_t s_user = s;
+    s = ctx->capture;
+    LSQ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    st = iteration(false);
+    cudaGraph_t g2 = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &g2);
+    s = s_user;
+    if (st != LSQ_OK || ce != cudaSuccess) {
+      if (g2) cudaGraphDestroy(g2);
+      (void)cudaGetLastError();
+      return st != LSQ_OK ? st : LSQ_ERR_CUDA;
+    }
+    graph = g2;
+    LSQ_CUDA_TRY(cudaGraphInstantiate(&gexec, graph, 0));
+  }
+  const int check = 4;
+  int it = 0;
+  int* host_cnt = ctx->host_status + 14;
+  while (it < maxit) {
+    // active problems for iteration it: cnt[it % 3]
+    if (it % check == 0) {
+      LSQ_CUDA_TRY(cudaMemcpyAsync(host_cnt, a.cnt + it % 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+      LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+      if (*host_cnt == 0) break;
+    }
+    if (prof) {
+      st = iteration(true);
+      if (st != LSQ_OK) return st;
+      LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+      float t = 0.f;
+      for (int q = 0; q < 5; ++q) {
+        cudaEventElapsedTime(&t, pe[q], pe[q + 1]);
+        ph[q] += t;
+      }
+    } else {
+      LSQ_CUDA_TRY(cudaGraphLaunch(gexec, s));
+      for (int q = 0; q < 6; ++q) lsq_count_launch();
+    }
+    ++it;
+  }
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  if (prof)
+    for (auto& e : pe) cudaEventDestroy(e);
   cudaEventRecord(e3, s);
   cudaEventRecord(ctx->ev1, s);
   LSQ_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1125,9 +1298,11 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   cudaEventDestroy(e1);
   cudaEventDestroy(e2);
   cudaEventDestroy(e3);
-  int hdr[48];
-  LSQ_CUDA_TRY(cudaMemcpy(hdr, base + o_bar, sizeof(hdr), cudaMemcpyDeviceToHost));
-  const int errc = hdr[16];
+  int hdr[24];
+  LSQ_CUDA_TRY(cudaMemcpy(hdr, ctl, sizeof(hdr), cudaMemcpyDeviceToHost));
+  passes += hdr[16];
+  exact_passes += mixed ? hdr[17] : hdr[16];
+  const int errc = hdr[20];
   // per-problem results
   int iters_max = 0;
   lsq_status overall = errc ? (lsq_status)errc : first_err;
@@ -1150,12 +1325,13 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   if (info) {
     info->iters_max = iters_max;
     info->status = overall;
-    info->passes = hdr[41];
-    info->exact_passes = hdr[42];
+    info->passes = passes;
+    info->exact_passes = exact_passes;
     info->ms_total = ms_total;
     info->ms_sketch = ms_sketch;
     info->ms_factor = ms_factor;
     info->ms_solve = ms_solve;
+    for (int q = 0; q < 8; ++q) info->ms_phase[q] = q < 5 ? ph[q] : 0.0;
   }
   return overall;
 }

@@ -26,6 +26,7 @@ struct lsq_ctx {
   void* state;             // device arena of the solver's iteration state (separate, so that a
   size_t state_bytes;      // refreshed solve can call the sketch and the factor between steps)
   int* host_status;        // pinned host word for status read-back
+  cudaStream_t capture;    // non-blocking stream on which CUDA graphs are captured (lazily)
   cudaEvent_t ev0, ev1;
 };
 
@@ -51,6 +52,11 @@ void lsq_count_launch();
 // Ensures the context arena holds at least `bytes` (256-byte aligned carving is the caller's).
 lsq_status lsq_ensure_scratch(lsq_ctx* ctx, size_t bytes);
 lsq_status lsq_ensure_state(lsq_ctx* ctx, size_t bytes);
+
+// Factorisations of many sketches (batched solves): W_p = R_p^{-1} and W_p^T; status_out[p]
+// (host) = LSQ_OK or LSQ_ERR_RANK; the Gram matrices in double-FP32 when df_gram.
+lsq_status lsq_factor_batched(lsq_ctx* ctx, int nprob, const double* const* SA, const int* m, const int* d,
+                              double* const* W, double* const* WT, bool df_gram, int* status_out);
 
 // LSQ_FCG behind lsq_solve (arguments already checked; W_fixed = NULL refreshes)
 lsq_status lsq_fcg_solve(lsq_ctx* ctx, const lsq_matrix* A, const double* b, const double* W_fixed, double* x,

@@ -35,6 +35,7 @@ extern "C" lsq_status lsq_destroy(lsq_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->scratch) cudaFree(c->scratch);
   if (c->state) cudaFree(c->state);
+  if (c->capture) cudaStreamDestroy(c->capture);
   cudaFreeHost(c->host_status);
   cudaEventDestroy(c->ev0);
   cudaEventDestroy(c->ev1);

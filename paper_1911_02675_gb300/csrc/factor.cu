@@ -184,23 +184,24 @@ __device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) chol_inv_kernel(double* __restrict__ G, double* __restrict__ Rf,
-                                                       double* __restrict__ Wf, double* __restrict__ Tb, int nblk,
-                                                       const int4* __restrict__ nodes, const int* __restrict__ level_start,
-                                                       int nlevels, unsigned* bar, int* err) {
+// The blocked Cholesky and inverse on a group of `nb` CTAs (this CTA has rank `rank`) that
+// synchronise through `bar`; the single-problem launch uses the whole grid as one group.
+__device__ void chol_inv_body(double* __restrict__ G, double* __restrict__ Rf, double* __restrict__ Wf,
+                              double* __restrict__ Tb, int nblk, const int4* __restrict__ nodes,
+                              const int* __restrict__ level_start, int nlevels, unsigned* bar, unsigned nb,
+                              unsigned rank, int* err) {
   __shared__ TileSmem sm;
   const int dp = nblk * 32;
-  const unsigned nb = gridDim.x;
   // Look-ahead: CTA 0 applies the trailing update to the next diagonal block first and
   // factors it at once, while the other CTAs update the rest of the trailing matrix; each
   // panel then needs two grid barriers.
-  if (blockIdx.x == 0) diag_block(G, Rf, Wf, dp, err);
+  if (rank == 0) diag_block(G, Rf, Wf, dp, err);
   if (grid_barrier(bar, nb, err)) return;
   for (int k = 0; k < nblk; ++k) {
     const int64_t kk = (int64_t)k * 32;
     const int rest = nblk - 1 - k;
     // panel: R[k][j] = W[k][k]^T G[k][j]
-    for (int task = blockIdx.x; task < rest * 4; task += nb) {
+    for (int task = rank; task < rest * 4; task += nb) {
       const int j = k + 1 + task / 4, q = task % 4;
       const int64_t col = (int64_t)j * 32 + q * 8;
       tile_task(sm, Rf + kk * dp + col, Wf + kk * dp + kk, true, G + kk * dp + col, 32, dp, 1.0, false);
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(double* __restrict__ G, d
     // diagonal block (k+1, k+1)
     const int pairs = rest * (rest + 1) / 2;
     const int64_t k1 = (int64_t)(k + 1) * 32;
-    if (blockIdx.x == 0) {
+    if (rank == 0) {
       for (int q = 0; q < 4; ++q)
         tile_task(sm, G + k1 * dp + k1 + q * 8, Rf + kk * dp + k1, true, Rf + kk * dp + k1 + q * 8, 32, dp, -1.0,
                   true);
@@ -219,8 +220,8 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(double* __restrict__ G, d
       diag_block(G + k1 * dp + k1, Rf + k1 * dp + k1, Wf + k1 * dp + k1, dp, err);
     }
     const int others = nb > 1 ? (int)nb - 1 : 1;
-    const int first = nb > 1 ? (int)blockIdx.x - 1 : 0;
-    if (nb == 1 || blockIdx.x > 0) {
+    const int first = nb > 1 ? (int)rank - 1 : 0;
+    if (nb == 1 || rank > 0) {
       for (int task = 4 + first; task < pairs * 4; task += others) {
         int p = task / 4;
         const int q = task % 4;
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(double* __restrict__ G, d
     for (int nd = n0; nd < n1; ++nd) {
       const int4 t = nodes[nd];
       const int rows = t.y - t.x, cols4 = (t.z - t.y) * 4;
-      for (int task = (int)((blockIdx.x + nb - (unsigned)(base % nb)) % nb); task < rows * cols4; task += nb) {
+      for (int task = (int)((rank + nb - (unsigned)(base % nb)) % nb); task < rows * cols4; task += nb) {
         const int rb = task / cols4, cs = task % cols4;
         const int64_t r0 = (int64_t)(t.x + rb) * 32, c0 = (int64_t)t.y * 32 + cs * 8;
         tile_task(sm, Tb + r0 * dp + c0, Rf + r0 * dp + (int64_t)t.y * 32, false, Wf + (int64_t)t.y * 32 * dp + c0,
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(double* __restrict__ G, d
     for (int nd = n0; nd < n1; ++nd) {
       const int4 t = nodes[nd];
       const int rows = t.y - t.x, cols4 = (t.z - t.y) * 4;
-      for (int task = (int)((blockIdx.x + nb - (unsigned)(base % nb)) % nb); task < rows * cols4; task += nb) {
+      for (int task = (int)((rank + nb - (unsigned)(base % nb)) % nb); task < rows * cols4; task += nb) {
         const int rb = task / cols4, cs = task % cols4;
         const int64_t r0 = (int64_t)(t.x + rb) * 32, c0 = (int64_t)t.y * 32 + cs * 8;
         tile_task(sm, Wf + r0 * dp + c0, Wf + r0 * dp + (int64_t)t.x * 32, false, Tb + (int64_t)t.x * 32 * dp + c0,
@@ -266,6 +267,13 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(double* __restrict__ G, d
     }
     if (grid_barrier(bar, nb, err)) return;
   }
+}
+
+__global__ void __launch_bounds__(256) chol_inv_kernel(double* __restrict__ G, double* __restrict__ Rf,
+                                                       double* __restrict__ Wf, double* __restrict__ Tb, int nblk,
+                                                       const int4* __restrict__ nodes, const int* __restrict__ level_start,
+                                                       int nlevels, unsigned* bar, int* err) {
+  chol_inv_body(G, Rf, Wf, Tb, nblk, nodes, level_start, nlevels, bar, gridDim.x, blockIdx.x, err);
 }
 
 __global__ void copy_out_kernel(const double* __restrict__ Rf, const double* __restrict__ Wf, int d, int dp,
@@ -372,4 +380,293 @@ extern "C" lsq_status lsq_factor(lsq_ctx* ctx, const double* SA, int64_t m, int6
   if (code == LSQ_ERR_RANK) return LSQ_ERR_RANK;
   if (code != 0) return (lsq_status)code;
   return LSQ_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Many factorisations at once (batched solves): one launch for every Gram matrix (a 64 x 64
+// tile of one problem per CTA, all rows of its SA; FP64, or double-FP32 under the mixed
+// precision), one cooperative launch in which each problem's Cholesky and inverse run on a
+// group of CTAs sized by its d^3 with a barrier of its own, one launch writing W and W^T.
+// ------------------------------------------------------------------------------------
+namespace {
+
+struct GramJob {
+  const double* SA;
+  double* G;
+  int m, d, dp;
+};
+
+struct CholJob {
+  double *G, *Rf, *Wf, *Tb;
+  const int4* nodes;
+  const int* level_start;
+  int nlevels, nblk, cta0, ncta;
+  unsigned* bar;
+  int* err;
+  double* W;   // d x d output
+  double* WT;  // d x d output
+  int d;
+};
+
+template <bool DF>
+__global__ void __launch_bounds__(256) gram_batched_kernel(const GramJob* __restrict__ jobs,
+                                                           const int4* __restrict__ units) {
+  const int4 u = units[blockIdx.x];
+  const GramJob jb = jobs[u.x];
+  const int a0 = u.y * TB, b0 = u.z * TB;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int d = jb.d, dp = jb.dp;
+  double res[4][4];
+  if constexpr (!DF) {
+    __shared__ double Xa[TK][TB];
+    __shared__ double Xb[TK][TB];
+    double acc[4][4] = {};
+    for (int r0 = 0; r0 < jb.m; r0 += TK) {
+      for (int e = threadIdx.x; e < TK * TB; e += 256) {
+        const int k = e / TB, c = e % TB;
+        const int r = r0 + k;
+        Xa[k][c] = (r < jb.m && a0 + c < d) ? jb.SA[(int64_t)r * d + a0 + c] : 0.0;
+        Xb[k][c] = (r < jb.m && b0 + c < d) ? jb.SA[(int64_t)r * d + b0 + c] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < TK; ++k) {
+        double x[4], y[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = Xa[k][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[j] = Xb[k][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(x[i], y[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) res[i][j] = acc[i][j];
+  } else {
+    // double-FP32: x = xh + xl (FP32 head and the FP32 rounding of the rest), products by
+    // FMA-exact TwoProduct plus the cross terms, sums by TwoSum (Dekker 1971; Knuth)
+    __shared__ float2 Xa[TK][TB];
+    __shared__ float2 Xb[TK][TB];
+    float ah[4][4] = {}, al[4][4] = {};
+    for (int r0 = 0; r0 < jb.m; r0 += TK) {
+      for (int e = threadIdx.x; e < TK * TB; e += 256) {
+        const int k = e / TB, c = e % TB;
+        const int r = r0 + k;
+        const double va = (r < jb.m && a0 + c < d) ? jb.SA[(int64_t)r * d + a0 + c] : 0.0;
+        const double vb = (r < jb.m && b0 + c < d) ? jb.SA[(int64_t)r * d + b0 + c] : 0.0;
+        const float ha = (float)va, hb = (float)vb;
+        Xa[k][c] = make_float2(ha, (float)(va - (double)ha));
+        Xb[k][c] = make_float2(hb, (float)(vb - (double)hb));
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int k = 0; k < TK; ++k) {
+        float2 x[4], y[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = Xa[k][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[j] = Xb[k][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float p = __fmul_rn(x[i].x, y[j].x);
+            const float pe = __fmaf_rn(x[i].x, y[j].x, -p);
+            const float cross = __fmaf_rn(x[i].x, y[j].y, __fmaf_rn(x[i].y, y[j].x, pe));
+            const float s = __fadd_rn(ah[i][j], p);
+            const float bb = __fsub_rn(s, ah[i][j]);
+            const float err = __fadd_rn(__fsub_rn(ah[i][j], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+            ah[i][j] = s;
+            al[i][j] = __fadd_rn(al[i][j], __fadd_rn(err, cross));
+          }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) res[i][j] = (double)ah[i][j] + (double)al[i][j];
+  }
+  // the tile and its mirror; the padding of the last block is the identity
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
+      if (a < dp && b < dp) {
+        const double v = (a < d && b < d) ? res[i][j] : (a == b ? 1.0 : 0.0);
+        jb.G[(int64_t)a * dp + b] = v;
+        jb.G[(int64_t)b * dp + a] = v;
+      }
+    }
+}
+
+__global__ void __launch_bounds__(256) chol_inv_batched_kernel(const CholJob* __restrict__ jobs,
+                                                               const int* __restrict__ cta_job) {
+  const CholJob& j = jobs[cta_job[blockIdx.x]];
+  chol_inv_body(j.G, j.Rf, j.Wf, j.Tb, j.nblk, j.nodes, j.level_start, j.nlevels, j.bar, (unsigned)j.ncta,
+                blockIdx.x - (unsigned)j.cta0, j.err);
+}
+
+// W (upper part of Wf) and W^T for problem blockIdx.y; rows strided over blockIdx.x
+__global__ void w_out_batched_kernel(const CholJob* __restrict__ jobs) {
+  const CholJob& j = jobs[blockIdx.y];
+  const int d = j.d, dp = j.nblk * 32;
+  for (int i = blockIdx.x; i < d; i += gridDim.x) {
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+      const double w = c >= i ? j.Wf[(int64_t)i * dp + c] : 0.0;
+      j.W[(int64_t)i * d + c] = w;
+      j.WT[(int64_t)c * d + i] = w;
+    }
+  }
+}
+
+}  // namespace
+
+// Factors the sketches SA_p (device, m_p x d_p) of nprob problems: W_p = R_p^{-1} and its
+// transpose into the caller's buffers; status_out[p] = LSQ_OK or LSQ_ERR_RANK (host array).
+lsq_status lsq_factor_batched(lsq_ctx* ctx, int nprob, const double* const* SA, const int* m, const int* d,
+                              double* const* W, double* const* WT, bool df_gram, int* status_out) {
+  cudaStream_t s = ctx->stream;
+  // the scratch arena is rewritten below by synchronous copies: earlier work must be done
+  LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+  // trees of the inverse, one per distinct block count
+  std::vector<int4> nodes;
+  std::vector<int> levels;
+  std::vector<int> tree_node0(33, -1), tree_lev0(33, -1), tree_nlev(33, 0);
+  for (int p = 0; p < nprob; ++p) {
+    const int nblk = (d[p] + 31) / 32;
+    if (tree_node0[nblk] >= 0) continue;
+    std::vector<std::vector<int4>> by_depth;
+    build_tree(0, nblk, 0, by_depth);
+    tree_node0[nblk] = (int)nodes.size();
+    tree_lev0[nblk] = (int)levels.size();
+    const int base = (int)nodes.size();
+    for (int dep = (int)by_depth.size() - 1; dep >= 0; --dep) {
+      levels.push_back((int)nodes.size() - base);
+      for (auto& t : by_depth[dep]) nodes.push_back(t);
+    }
+    levels.push_back((int)nodes.size() - base);
+    tree_nlev[nblk] = (int)by_depth.size();
+  }
+  // Gram units and the scratch layout
+  std::vector<int4> units;
+  size_t mats = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const int dp = ((d[p] + 31) / 32) * 32, nt = (dp + TB - 1) / TB;
+    for (int a = 0; a < nt; ++a)
+      for (int b = a; b < nt; ++b) units.push_back(make_int4(p, a, b, 0));
+    mats += lsq_align256((size_t)dp * dp * 8);
+  }
+  // CTA groups of the cooperative launch: sizes by d^3, at least one CTA each, problems in waves
+  int per_sm = 0;
+  LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_inv_batched_kernel, 256, 0));
+  if (per_sm < 1) return LSQ_ERR_CUDA;
+  const int gmax = std::min(per_sm, 2) * ctx->sm_count;
+  size_t need = 4 * mats + lsq_align256(sizeof(GramJob) * nprob) + lsq_align256(sizeof(CholJob) * nprob) +
+                lsq_align256(sizeof(int4) * units.size()) + lsq_align256(sizeof(int4) * std::max<size_t>(1, nodes.size())) +
+                lsq_align256(sizeof(int) * levels.size()) + lsq_align256(sizeof(int) * gmax) +
+                lsq_align256((size_t)nprob * 64);
+  lsq_status st = lsq_ensure_scratch(ctx, need);
+  if (st != LSQ_OK) return st;
+  Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};
+  char* mbase = cv.take<char>(4 * mats);
+  GramJob* d_gj = cv.take<GramJob>(nprob);
+  CholJob* d_cj = cv.take<CholJob>(nprob);
+  int4* d_units = cv.take<int4>(units.size());
+  int4* d_nodes = cv.take<int4>(std::max<size_t>(1, nodes.size()));
+  int* d_levels = cv.take<int>(levels.size());
+  int* d_ctajob = cv.take<int>(gmax);
+  unsigned* d_bars = cv.take<unsigned>((size_t)nprob * 16);
+  std::vector<GramJob> gj(nprob);
+  std::vector<CholJob> cj(nprob);
+  size_t off = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const int nblk = (d[p] + 31) / 32, dp = nblk * 32;
+    const size_t mb = lsq_align256((size_t)dp * dp * 8);
+    double* G = reinterpret_cast<double*>(mbase + off);
+    double* Rf = reinterpret_cast<double*>(mbase + mats + off);
+    double* Wf = reinterpret_cast<double*>(mbase + 2 * mats + off);
+    double* Tb = reinterpret_cast<double*>(mbase + 3 * mats + off);
+    off += mb;
+    gj[p] = GramJob{SA[p], G, m[p], d[p], dp};
+    cj[p].G = G;
+    cj[p].Rf = Rf;
+    cj[p].Wf = Wf;
+    cj[p].Tb = Tb;
+    cj[p].nodes = d_nodes + tree_node0[nblk];
+    cj[p].level_start = d_levels + tree_lev0[nblk];
+    cj[p].nlevels = tree_nlev[nblk];
+    cj[p].nblk = nblk;
+    cj[p].bar = d_bars + (size_t)p * 16;
+    cj[p].err = reinterpret_cast<int*>(d_bars + (size_t)p * 16 + 8);
+    cj[p].W = W[p];
+    cj[p].WT = WT[p];
+    cj[p].d = d[p];
+  }
+  LSQ_CUDA_TRY(cudaMemsetAsync(mbase + mats, 0, 2 * mats, s));  // Rf, Wf
+  LSQ_CUDA_TRY(cudaMemsetAsync(d_bars, 0, (size_t)nprob * 64, s));
+  LSQ_CUDA_TRY(cudaMemcpy(d_gj, gj.data(), sizeof(GramJob) * nprob, cudaMemcpyHostToDevice));
+  LSQ_CUDA_TRY(cudaMemcpy(d_units, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice));
+  if (!nodes.empty()) LSQ_CUDA_TRY(cudaMemcpy(d_nodes, nodes.data(), sizeof(int4) * nodes.size(), cudaMemcpyHostToDevice));
+  LSQ_CUDA_TRY(cudaMemcpy(d_levels, levels.data(), sizeof(int) * levels.size(), cudaMemcpyHostToDevice));
+  if (df_gram)
+    gram_batched_kernel<true><<<(unsigned)units.size(), 256, 0, s>>>(d_gj, d_units);
+  else
+    gram_batched_kernel<false><<<(unsigned)units.size(), 256, 0, s>>>(d_gj, d_units);
+  LSQ_LAUNCH_CHECK();
+  // waves of problems whose groups fit the cooperative grid
+  std::vector<int> order(nprob);
+  for (int p = 0; p < nprob; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return d[x] > d[y]; });
+  size_t next = 0;
+  while (next < order.size()) {
+    const size_t w0 = next;
+    size_t w1 = std::min(order.size(), w0 + (size_t)gmax);
+    double wsum = 0.0;
+    for (size_t i = w0; i < w1; ++i) {
+      const double nb = (d[order[i]] + 31) / 32;
+      wsum += nb * nb * nb + 4.0;
+    }
+    std::vector<int> ctajob;
+    int spare = gmax - (int)(w1 - w0);
+    for (size_t i = w0; i < w1; ++i) {
+      const int p = order[i];
+      const int nblk = (d[p] + 31) / 32;
+      const double wgt = (double)nblk * nblk * nblk + 4.0;
+      int g = 1 + (int)std::floor((double)spare * wgt / wsum);
+      g = std::min(g, std::max(1, 4 * nblk * nblk));
+      cj[p].cta0 = (int)ctajob.size();
+      cj[p].ncta = g;
+      for (int q = 0; q < g; ++q) ctajob.push_back(p);
+    }
+    LSQ_CUDA_TRY(cudaMemcpy(d_cj, cj.data(), sizeof(CholJob) * nprob, cudaMemcpyHostToDevice));
+    LSQ_CUDA_TRY(cudaMemcpy(d_ctajob, ctajob.data(), sizeof(int) * ctajob.size(), cudaMemcpyHostToDevice));
+    const CholJob* jp = d_cj;
+    const int* cp = d_ctajob;
+    void* args[] = {(void*)&jp, (void*)&cp};
+    LSQ_CUDA_TRY(cudaLaunchCooperativeKernel((void*)chol_inv_batched_kernel, dim3((unsigned)ctajob.size()), dim3(256),
+                                             args, 0, s));
+    lsq_count_launch();
+    LSQ_CUDA_TRY(cudaStreamSynchronize(s));  // the tables are rewritten for the next wave
+    next = w1;
+  }
+  LSQ_CUDA_TRY(cudaMemcpy(d_cj, cj.data(), sizeof(CholJob) * nprob, cudaMemcpyHostToDevice));
+  w_out_batched_kernel<<<dim3(64, (unsigned)nprob), 256, 0, s>>>(d_cj);
+  LSQ_LAUNCH_CHECK();
+  std::vector<unsigned> bars((size_t)nprob * 16);
+  LSQ_CUDA_TRY(cudaMemcpyAsync(bars.data(), d_bars, bars.size() * 4, cudaMemcpyDeviceToHost, s));
+  LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+  lsq_status overall = LSQ_OK;
+  for (int p = 0; p < nprob; ++p) {
+    const int code = (int)bars[(size_t)p * 16 + 8];
+    status_out[p] = code;
+    if (code != 0 && code != LSQ_ERR_RANK && overall == LSQ_OK) overall = (lsq_status)code;
+  }
+  return overall;
 }
