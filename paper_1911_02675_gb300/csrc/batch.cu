@@ -155,9 +155,13 @@ __device__ __forceinline__ void pass_chunk(const BProb& pr, int64_t r0, int64_t 
   for (int h = 0; h < CPWMAX; ++h)
 #pragma unroll
     for (int j = 0; j < KP; ++j) acc[h][j] = 0;
+  // sums of squares for q: S == 1, qacc[j] of the rows the thread owns; S > 1, qacc[h] of its
+  // entries h of the slice reduction (tr KP / BT <= KP / 2 of them)
   TT qacc[KP];
 #pragma unroll
   for (int j = 0; j < KP; ++j) qacc[j] = 0;
+  constexpr int QH = KP / 2 > 1 ? KP / 2 : 1;
+  const int lgtr = 31 - __clz(TE) - lgdp;
   // stage-1 ownership: global lane g -> row g % tr (+ BT i) and slice g / tr
   const int g = tid;
   const int s_row = tr >= BT ? g : g % tr;
@@ -252,17 +256,22 @@ __device__ __forceinline__ void pass_chunk(const BProb& pr, int64_t r0, int64_t 
       }
     }
     __syncthreads();
-    if (S > 1 && tid < tr) {
-      const int r = tid;
+    if (S > 1) {
+      // every thread: entries e = tid + BT h -> (j = e / tr, r = e % tr), summed over the slices;
+      // with tr | BT a thread sees j = tid / tr + h BT / tr and row tid % tr
 #pragma unroll
-      for (int j = 0; j < KP; ++j) {
-        TT sum = 0;
-        for (int q = 0; q < S; ++q) sum += Yp[(q * KP + j) * tr + r];
-        Ys[r * KP + j] = sum;
-        qacc[j] = fma(sum, sum, qacc[j]);
+      for (int h = 0; h < QH; ++h) {
+        const int e = tid + h * BT;
+        if (e < tr * KP) {
+          const int j = e >> lgtr, r = e & (tr - 1);
+          TT sum = 0;
+          for (int q = 0; q < S; ++q) sum += Yp[(q * KP + j) * tr + r];
+          Ys[r * KP + j] = sum;
+          qacc[h] = fma(sum, sum, qacc[h]);
+        }
       }
+      __syncthreads();
     }
-    if (S > 1) __syncthreads();
     // stage 2: acc[h][j] += As[r][c] Ys[r][j] for the warp's column groups and row phase
     for (int r = rphase; r < tr; r += rsplit) {
       const TT* yr = Ys + r * KP;
@@ -300,44 +309,63 @@ __device__ __forceinline__ void pass_chunk(const BProb& pr, int64_t r0, int64_t 
           if (j < kp) out[j * dp + ((g0 + h * BW) << 5) + lane] = (double)acc[h][j];
   }
   __syncthreads();
-  // q_j = sum of the per-thread sums of squares: warp sums, then the warps in order
+  if (S == 1) {
+    // q_j = sum of the per-thread sums of squares: warp sums, then the warps in order
 #pragma unroll
-  for (int j = 0; j < KP; ++j) {
-    const double w = warp_sum_d((double)qacc[j]);
-    if (lane == 0) red[warp * KP + j] = w;
-  }
-  __syncthreads();
-  if (tid < kp) {
-    double sum = 0.0;
-    for (int w = 0; w < BW; ++w) sum += red[w * KP + tid];
-    out[kp * dp + tid] = sum;
+    for (int j = 0; j < KP; ++j) {
+      const double w = warp_sum_d((double)qacc[j]);
+      if (lane == 0) red[warp * KP + j] = w;
+    }
+    __syncthreads();
+    if (tid < kp) {
+      double sum = 0.0;
+      for (int w = 0; w < BW; ++w) sum += red[w * KP + tid];
+      out[kp * dp + tid] = sum;
+    }
+  } else {
+    // q_j from the threads that summed rows of j: h = j / (BT / tr), threads (j % (BT / tr)) tr + r
+#pragma unroll
+    for (int h = 0; h < QH; ++h) red[h * BT + tid] = (double)qacc[h];
+    __syncthreads();
+    if (tid < kp) {
+      const int per_h = BT / tr;
+      const int h = tid / per_h, t0 = (tid % per_h) * tr;
+      double sum = 0.0;
+      for (int r = 0; r < tr; ++r) sum += red[h * BT + t0 + r];
+      out[kp * dp + tid] = sum;
+    }
   }
   __syncthreads();
 }
 
 // ------------------------------------------------------------------------------------
 // Exact pass in double-FP32: part[j * dp + c] = sum_rows a_c (a . x_j) for every column of
-// X (heads and tails of x, and of A when it is FP64); 16-row tiles.
+// X (heads and tails of x, and of A when it is FP64).  The structure of pass_chunk (tiles of
+// TE elements, tall for narrow problems; stage 1 with a lane per row and S column slices;
+// stage 2 with a warp per 32 columns) with every product and sum in double-FP32: products by
+// FMA-exact TwoProduct plus the cross terms, sums by TwoSum (Dekker 1971; Knuth).
 // ------------------------------------------------------------------------------------
 template <typename TA, int KP, int PT>
 __device__ __forceinline__ void pass_chunk_df(const BProb& pr, int64_t r0, int64_t r1, double* __restrict__ out,
                                               uint8_t* smem) {
   constexpr int BT = PT, BW = PT / 32;
   constexpr int CPWMAX = 16 / BW > 1 ? 16 / BW : 1;
-  constexpr int TR = 16;
+  constexpr int TE = 8192;
+  constexpr bool HASLO = sizeof(TA) == 8;
   const int dp = pr.dp, d = pr.d, kp = pr.kp;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr bool HASLO = sizeof(TA) == 8;
-  // tile element (r, c) at [r * dp + (c ^ 2r)]: a column read by 16 rows with the two
-  // half-warps on even / odd columns, and a row read by 32 lanes, both hit distinct banks
+  const int lgdp = 31 - __clz(dp);
+  const int tr = TE >> lgdp;
+  const int S = tr >= BT ? 1 : BT / tr;
+  const int RPL = tr > BT ? tr / BT : 1;
   float* Ah = reinterpret_cast<float*>(smem);
-  float* Al = Ah + TR * dp;
-  float* Xh = Al + (HASLO ? TR * dp : 0);
+  float* Al = Ah + TE;
+  float* Xh = Al + (HASLO ? TE : 0);
   float* Xl = Xh + dp * KP;
   float* Yph = Xl + dp * KP;
-  float* Ypl = Yph + BW * KP * TR;
-  float* Ysh = Ypl + BW * KP * TR;
-  float* Ysl = Ysh + TR * KP;
+  float* Ypl = Yph + (S > 1 ? S * KP * tr : 0);
+  float* Ysh = Ypl + (S > 1 ? S * KP * tr : 0);
+  float* Ysl = Ysh + tr * KP;
   const TA* A = reinterpret_cast<const TA*>(pr.A);
   for (int e = tid; e < dp * KP; e += BT) {
     const int c = e / KP, j = e - c * KP;
@@ -354,68 +382,81 @@ __device__ __forceinline__ void pass_chunk_df(const BProb& pr, int64_t r0, int64
   for (int h = 0; h < CPWMAX; ++h)
 #pragma unroll
     for (int j = 0; j < KP; ++j) ah_[h][j] = al_[h][j] = 0.f;
-  const int lg = 31 - __clz(dp);
-  const int per = TR * dp;
-  for (int64_t t0 = r0; t0 < r1; t0 += TR) {
+  const int s_row = tr >= BT ? tid : tid % tr;
+  const int s_slice = tr >= BT ? 0 : tid / tr;
+  const int cs = dp / S;
+  const int per = tr * dp;
+  for (int64_t t0 = r0; t0 < r1; t0 += tr) {
     __syncthreads();
     for (int e = tid; e < per; e += BT) {
-      const int r = e >> lg, c = e & (dp - 1);
+      const int r = e >> lgdp, c = e & (dp - 1);
       const int64_t row = t0 + r;
       float hh = 0.f, ll = 0.f;
       if (row < r1 && c < d) split_df(__ldg(A + row * pr.ld + c), hh, ll);
-      Ah[r * dp + (c ^ (2 * r))] = hh;
-      if (HASLO) Al[r * dp + (c ^ (2 * r))] = ll;
+      const int sc = r * dp + (c ^ (r & 31));
+      Ah[sc] = hh;
+      if (HASLO) Al[sc] = ll;
     }
     __syncthreads();
-    // stage 1 (lanes 0..15 = rows; the half-warps take the even / odd columns of the warp's slice)
-    {
-      const int r = lane & 15, half = lane >> 4;
-      float yh[KP], yl[KP];
+    // stage 1
 #pragma unroll
-      for (int j = 0; j < KP; ++j) yh[j] = yl[j] = 0.f;
-      const int cs = dp / BW, c0 = warp * cs;
-      for (int c = c0 + half; c < c0 + cs; c += 2) {
-        const int sc = r * dp + (c ^ (2 * r));
-        const float a = Ah[sc];
-        const float al = HASLO ? Al[sc] : 0.f;
+    for (int i = 0; i < 2; ++i) {
+      if (i < RPL) {
+        const int r = s_row + i * BT;
+        float yh[KP], yl[KP];
 #pragma unroll
-        for (int j = 0; j < KP; ++j) df_fma(a, al, Xh[c * KP + j], Xl[c * KP + j], yh[j], yl[j]);
-      }
-      // combine the two halves in double-FP32, then one entry per (warp, j, row)
+        for (int j = 0; j < KP; ++j) yh[j] = yl[j] = 0.f;
+        const int c0 = s_slice * cs;
+        const int sw = r & 31;
+        for (int c = c0; c < c0 + cs; ++c) {
+          const int sc = r * dp + (c ^ sw);
+          const float av = Ah[sc];
+          const float al = HASLO ? Al[sc] : 0.f;
 #pragma unroll
-      for (int j = 0; j < KP; ++j) {
-        const float oh = __shfl_xor_sync(0xffffffffu, yh[j], 16);
-        const float ol = __shfl_xor_sync(0xffffffffu, yl[j], 16);
-        df_add(yh[j], yl[j], oh, ol);
-        if (half == 0) {
-          Yph[(warp * KP + j) * TR + r] = yh[j];
-          Ypl[(warp * KP + j) * TR + r] = yl[j];
+          for (int j = 0; j < KP; ++j) df_fma(av, al, Xh[c * KP + j], Xl[c * KP + j], yh[j], yl[j]);
+        }
+        if (S == 1) {
+#pragma unroll
+          for (int j = 0; j < KP; ++j) {
+            float h2, e2;
+            lsq_apass::two_sum(yh[j], yl[j], h2, e2);
+            Ysh[r * KP + j] = h2;
+            Ysl[r * KP + j] = e2;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < KP; ++j) {
+            Yph[(s_slice * KP + j) * tr + r] = yh[j];
+            Ypl[(s_slice * KP + j) * tr + r] = yl[j];
+          }
         }
       }
     }
     __syncthreads();
-    for (int e = tid; e < TR * KP; e += BT) {
-      const int j = e / TR, r = e - j * TR;
-      float sh = 0.f, sl = 0.f;
-#pragma unroll
-      for (int w = 0; w < BW; ++w) df_add(sh, sl, Yph[(w * KP + j) * TR + r], Ypl[(w * KP + j) * TR + r]);
-      // renormalise so that the head carries the sum
-      float h2, e2;
-      lsq_apass::two_sum(sh, sl, h2, e2);
-      Ysh[r * KP + j] = h2;
-      Ysl[r * KP + j] = e2;
+    if (S > 1) {
+      for (int e = tid; e < tr * KP; e += BT) {
+        const int j = e / tr, r = e - j * tr;
+        float sh = 0.f, sl = 0.f;
+        for (int q = 0; q < S; ++q) df_add(sh, sl, Yph[(q * KP + j) * tr + r], Ypl[(q * KP + j) * tr + r]);
+        float h2, e2;
+        lsq_apass::two_sum(sh, sl, h2, e2);
+        Ysh[r * KP + j] = h2;
+        Ysl[r * KP + j] = e2;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int r = rphase; r < TR; r += rsplit) {
+    // stage 2
+    for (int r = rphase; r < tr; r += rsplit) {
+      const int sw = r & 31;
 #pragma unroll
       for (int h = 0; h < CPWMAX; ++h) {
         if (h < cpw) {
           const int c = ((g0 + h * BW) << 5) + lane;
-          const int sc = r * dp + (c ^ (2 * r));
-          const float a = Ah[sc];
+          const int sc = r * dp + (c ^ sw);
+          const float av = Ah[sc];
           const float al = HASLO ? Al[sc] : 0.f;
 #pragma unroll
-          for (int j = 0; j < KP; ++j) df_fma(a, al, Ysh[r * KP + j], Ysl[r * KP + j], ah_[h][j], al_[h][j]);
+          for (int j = 0; j < KP; ++j) df_fma(av, al, Ysh[r * KP + j], Ysl[r * KP + j], ah_[h][j], al_[h][j]);
         }
       }
     }
@@ -423,14 +464,15 @@ __device__ __forceinline__ void pass_chunk_df(const BProb& pr, int64_t r0, int64
   __syncthreads();
   double* red = reinterpret_cast<double*>(smem);
   if (rsplit > 1) {
+#pragma unroll
     for (int j = 0; j < KP; ++j)
       red[(rphase * KP + j) * (NC * 32) + (g0 << 5) + lane] = (double)ah_[0][j] + (double)al_[0][j];
     __syncthreads();
     for (int e = tid; e < kp * dp; e += BT) {
       const int j = e / dp, c = e - j * dp;
-      double s = 0.0;
-      for (int ph = 0; ph < rsplit; ++ph) s += red[(ph * KP + j) * (NC * 32) + c];
-      out[e] = s;
+      double sum = 0.0;
+      for (int ph = 0; ph < rsplit; ++ph) sum += red[(ph * KP + j) * (NC * 32) + c];
+      out[e] = sum;
     }
   } else {
 #pragma unroll
@@ -458,8 +500,9 @@ __host__ __device__ inline size_t pass_smem_shape(bool mixed, bool a_f64, int dp
   size_t f = 0;
   if (mixed) {
     f = tile(4, a_f64 ? 8192 : 16384);
-    const int TRd = 16;
-    const size_t df = (size_t)(TRd * dp * (a_f64 ? 2 : 1) + 2 * dp * KP + 2 * W * KP * TRd + 2 * TRd * KP) * 4;
+    const int TEd = 8192, trd = TEd / dp, Sd = trd >= PT ? 1 : PT / trd;
+    const size_t df =
+        (size_t)(TEd * (a_f64 ? 2 : 1) + 2 * dp * KP + (Sd > 1 ? 2 * Sd * KP * trd : 0) + 2 * trd * KP) * 4;
     f = f > df ? f : df;
   } else {
     f = tile(8, 8192);
@@ -536,16 +579,14 @@ __global__ void __launch_bounds__(PT, 1) bpass_kernel(BatchArgs a, int force_exa
 __device__ __forceinline__ double chunk_sum(const BatchArgs& a, const BProb& pr, int off) {
   const double* base = a.part + a.part_off[pr.chunk0] + off;
   const int64_t stride = (int64_t)pr.kp * pr.dp + pr.kp;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int ch = 0;
-  for (; ch + 4 <= pr.nchunk; ch += 4) {
-    s0 += base[(ch + 0) * stride];
-    s1 += base[(ch + 1) * stride];
-    s2 += base[(ch + 2) * stride];
-    s3 += base[(ch + 3) * stride];
+  for (; ch + 8 <= pr.nchunk; ch += 8) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[q] += base[(ch + q) * stride];
   }
-  for (; ch < pr.nchunk; ++ch) s0 += base[ch * stride];
-  return (s0 + s1) + (s2 + s3);
+  for (; ch < pr.nchunk; ++ch) s[0] += base[ch * stride];
+  return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
 __device__ __forceinline__ double chunk_sum_warp(const BatchArgs& a, const BProb& pr, int off) {
@@ -827,19 +868,19 @@ __global__ void __launch_bounds__(BT) binitdir_kernel(BatchArgs a) {
   }
 }
 
-// x += alpha p, r -= alpha v, <b, x>; or r = b - H x in an exact residual step
+// x += alpha p, r -= alpha v, <b, x>; or r = b - H x in an exact residual step.  One CTA per
+// block of 32 columns; warp w takes the right-hand sides j = w, w + 8, ... (lane = column), so
+// the sums over a problem's chunk partials run on all warps.
 __global__ void __launch_bounds__(BT) bupdate_kernel(BatchArgs a) {
   const int it = *(volatile int*)a.iter;
   const int cur = it & 1;
-  const int lane = threadIdx.x & 31;
-  const int w = blockIdx.x * BW + (threadIdx.x >> 5);
-  if (w >= a.nblocks) return;
-  const int2 bk = a.blocks[w];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int2 bk = a.blocks[blockIdx.x];
   const BProb& pr = a.probs[bk.x];
   if (!prob_active(pr, it)) return;
   const int c = bk.y * 32 + lane;
   const bool exact = exact_step(pr, it);
-  for (int j = 0; j < pr.k; ++j) {
+  for (int j = warp; j < pr.k; j += BW) {
     if (!(pr.flags[cur * pr.kp + j] & F_ACTIVE)) continue;
     if (exact) {
       if (c < pr.d) pr.R[j * pr.dp + c] = pr.B[j * pr.d + c] - chunk_sum(a, pr, j * pr.dp + c);
@@ -1194,7 +1235,7 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     lsq_status r = launch_pass(0, timed);
     if (r != LSQ_OK) return r;
     if (timed) cudaEventRecord(pe[1], s);
-    bupdate_kernel<<<gblk, BT, 0, s>>>(a);
+    bupdate_kernel<<<nbk, BT, 0, s>>>(a);
     ITER_CHECK();
     if (timed) cudaEventRecord(pe[2], s);
     bprec_kernel<1><<<nbk, BT, 0, s>>>(a);

@@ -472,6 +472,111 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_transform_kernel(
   }
 }
 
+// The common case of the transform (FP32 arithmetic, 8-column tiles, 2048-row blocks) in a
+// kernel of its own: a thread owns 16 consecutive rows x 2 adjacent columns of every block
+// (512 units = 512 threads).  The next block's elements are loaded as raw 8- or 16-byte
+// vectors and kept as loaded until the block is stored, so the loads stay in flight through
+// the radix passes and the sampled second level; narrowing, signs and the first 4 butterfly
+// stages happen at the store.  Same arithmetic, in the same order, as the general kernel.
+template <typename TA>
+__device__ __forceinline__ void srht_fast_load(TA (&r0)[16], TA (&r1)[16], uint32_t& sw, const TA* __restrict__ A,
+                                               int64_t n, int64_t ld, int64_t row, int c, bool c_ok0, bool c_ok1,
+                                               bool vec, const uint32_t* __restrict__ signbits) {
+  using T2 = typename std::conditional<sizeof(TA) == 8, double2, float2>::type;
+  sw = row < n ? (__ldg(signbits + (row >> 5)) >> (row & 31)) : 0u;
+  const TA* src = A + (row < n ? row * ld + c : 0);
+  if (vec && row + 15 < n) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const T2 x = __ldg(reinterpret_cast<const T2*>(src + j * ld));
+      r0[j] = x.x;
+      r1[j] = x.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const bool ok = row + j < n;
+      r0[j] = (ok && c_ok0) ? __ldg(src + j * ld) : (TA)0;
+      r1[j] = (ok && c_ok1) ? __ldg(src + j * ld + 1) : (TA)0;
+    }
+  }
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(SRHT_THREADS, 1) srht_fast_kernel(
+    const TA* __restrict__ A, int64_t n, int d, int64_t ld, int64_t N1, int64_t blocks_per_group, int vec_ok,
+    const uint32_t* __restrict__ signbits, const int64_t* __restrict__ rows, int m, float* __restrict__ part) {
+  constexpr int DC = 8, LOGN2 = 11, N2 = 1 << LOGN2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Z = reinterpret_cast<float*>(smem_raw);                        // padded [N2][DC]
+  float* Y = Z + (size_t)zphys(N2, DC);                                 // [m][DC]
+  uint32_t* k1s = reinterpret_cast<uint32_t*>(Y + (size_t)m * DC);      // [m]
+  uint16_t* k2s = reinterpret_cast<uint16_t*>(k1s + m);                 // [m]
+  const int c0 = blockIdx.x * DC;
+  const int64_t b_begin = (int64_t)blockIdx.y * blocks_per_group;
+  const int64_t b_end = min(N1, b_begin + blocks_per_group);
+  for (int e = threadIdx.x; e < m * DC; e += blockDim.x) Y[e] = 0.f;
+  for (int s = threadIdx.x; s < m; s += blockDim.x) {
+    const int64_t k = rows[s];
+    k1s[s] = (uint32_t)(k >> LOGN2);
+    k2s[s] = (uint16_t)(k & (N2 - 1));
+  }
+  const int q = threadIdx.x >> 2, pc = threadIdx.x & 3;  // 16-row group, column pair
+  const int c = c0 + 2 * pc;
+  const bool c_ok0 = c < d, c_ok1 = c + 1 < d;
+  const bool vec = vec_ok != 0 && c_ok1;
+  TA r0[16], r1[16];
+  uint32_t sw = 0;
+  if (b_begin < b_end)
+    srht_fast_load<TA>(r0, r1, sw, A, n, ld, (b_begin << LOGN2) + (q << 4), c, c_ok0, c_ok1, vec, signbits);
+  for (int64_t i1 = b_begin; i1 < b_end; ++i1) {
+    __syncthreads();  // Z is free (previous block's second level is done)
+    {
+      float v0[16], v1[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const uint32_t neg = ((sw >> j) & 1u) << 31;
+        v0[j] = __uint_as_float(__float_as_uint(lsq_apass::narrow_f32(r0[j])) ^ neg);
+        v1[j] = __uint_as_float(__float_as_uint(lsq_apass::narrow_f32(r1[j])) ^ neg);
+      }
+      butterflies<float, 4>(v0);
+      butterflies<float, 4>(v1);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        *reinterpret_cast<float2*>(Z + zphys((q << 4) + j, DC) + 2 * pc) = make_float2(v0[j], v1[j]);
+    }
+    if (i1 + 1 < b_end)
+      srht_fast_load<TA>(r0, r1, sw, A, n, ld, ((i1 + 1) << LOGN2) + (q << 4), c, c_ok0, c_ok1, vec, signbits);
+    __syncthreads();
+    radix_pass<float, DC, 4>(Z, N2, 4);
+    __syncthreads();
+    radix_pass<float, DC, 3>(Z, N2, 8);
+    __syncthreads();
+    const uint32_t i1w = (uint32_t)i1;
+    for (int s = threadIdx.x; s < m; s += blockDim.x) {
+      const bool neg = (__popc(k1s[s] & i1w) & 1) != 0;
+      const float4* zr = reinterpret_cast<const float4*>(Z + zphys(k2s[s], DC));
+      float4* yr = reinterpret_cast<float4*>(Y + (size_t)s * DC);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 z = zr[h];
+        float4 y = yr[h];
+        y.x += neg ? -z.x : z.x;
+        y.y += neg ? -z.y : z.y;
+        y.z += neg ? -z.z : z.z;
+        y.w += neg ? -z.w : z.w;
+        yr[h] = y;
+      }
+    }
+  }
+  __syncthreads();
+  float* out = part + (int64_t)blockIdx.y * m * d;
+  for (int e = threadIdx.x; e < m * DC; e += blockDim.x) {
+    const int s = e / DC, cc = e % DC;
+    if (c0 + cc < d) out[(int64_t)s * d + c0 + cc] = Y[e];
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // SJLT: s distinct rows per column of S by Lemire's method on successive Philox words,
 // then a shared-memory scatter of each data row into its s target rows.
@@ -636,9 +741,31 @@ static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN
                               int64_t blocks_per_group) {
   const int d = (int)A->d;
   const size_t smem = srht_smem_bytes(logN2, m, DC, sizeof(TC));
+  dim3 grid(lsq_ceil_div(d, DC), groups);
+  if constexpr (sizeof(TC) == 4 && DC == 8) {
+    if (logN2 == 11) {
+      const size_t es = A->dtype == LSQ_F64 ? 8 : 4;
+      const size_t vb = 2 * es;  // bytes of one column pair
+      const int vec_ok = (((uintptr_t)A->data % vb) == 0 && ((size_t)A->ld * es) % vb == 0) ? 1 : 0;
+      if (A->dtype == LSQ_F64) {
+        auto kf = srht_fast_kernel<double>;
+        LSQ_CUDA_TRY(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kf<<<grid, SRHT_THREADS, smem, ctx->stream>>>(reinterpret_cast<const double*>(A->data), A->n, d, A->ld, N1,
+                                                      blocks_per_group, vec_ok, signbits, rows, m,
+                                                      reinterpret_cast<float*>(part));
+      } else {
+        auto kf = srht_fast_kernel<float>;
+        LSQ_CUDA_TRY(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kf<<<grid, SRHT_THREADS, smem, ctx->stream>>>(reinterpret_cast<const float*>(A->data), A->n, d, A->ld, N1,
+                                                      blocks_per_group, vec_ok, signbits, rows, m,
+                                                      reinterpret_cast<float*>(part));
+      }
+      LSQ_LAUNCH_CHECK();
+      return LSQ_OK;
+    }
+  }
   auto kern = srht_transform_kernel<TC, DC>;
   LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(lsq_ceil_div(d, DC), groups);
   kern<<<grid, SRHT_THREADS, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, logN2, N1, blocks_per_group,
                                                    signbits, rows, m, part);
   LSQ_LAUNCH_CHECK();
