@@ -71,7 +71,7 @@ typedef enum {
  *   LSQ_PREC_MIXED: passes over A in FP32 arithmetic; the recursive residual is
  *                   replaced by b - H x evaluated in double-FP32 arithmetic (about 45
  *                   significant bits per element, TwoProduct/TwoSum accumulation) after
- *                   every 10^4 drop of its norm, every `refresh_every` iterations and
+ *                   every 10^5 drop of its norm, every `refresh_every` iterations and
  *                   before convergence is declared; x, r and the preconditioner stay
  *                   FP64.  Reaches the same tolerance as LSQ_PREC_F64. */
 typedef enum { LSQ_PREC_F64 = 0, LSQ_PREC_MIXED = 1 } lsq_precision;
@@ -172,7 +172,7 @@ typedef struct {
   int32_t s;           /* refreshed SJLT: nonzeros per column (default 8) */
   int32_t precision;   /* lsq_precision (default LSQ_PREC_F64) */
   int32_t refresh_every; /* MIXED only: most iterations between exact residual replacements
-                            (default 12; a replacement also follows every 10^4 drop of the
+                            (default 40; a replacement also follows every 10^5 drop of the
                             residual norm and every recursive convergence) */
   int32_t grid_blocks; /* 0 = automatic; else the number of resident CTAs of the solve kernel */
   int32_t x0_zero;     /* 1: x0 is zero, so the initial residual b - H x0 = b needs no pass over A */

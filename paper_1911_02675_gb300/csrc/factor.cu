@@ -135,47 +135,60 @@ __device__ void tile_task(TileSmem& sm, double* out, const double* Xm, bool tran
   *o = (acc ? *o : 0.0) + alpha * sum;
 }
 
-// Cholesky of one 32 x 32 diagonal block (one warp) and the inverse of its factor.
-// Returns false (and sets *err) on a non-positive or non-finite pivot.
+// Cholesky of one 32 x 32 diagonal block and the inverse of its factor, by the whole CTA:
+// lane l owns column l; the dot products of each step are split over 4 warps (one per SM
+// sub-partition, so 4 FP64 pipes work on them) and added in warp order by warp 0.
+// Sets *err to LSQ_ERR_RANK on a non-positive or non-finite pivot.
 __device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, int* err) {
   __shared__ double Gs[32][33];
   __shared__ double Rs[32][33];
   __shared__ double Ws[32][33];
+  __shared__ double part[4][32];
   __shared__ int bad;
-  // stage the block (one round trip for the whole CTA, not one per step of the loop below)
-  for (int e = threadIdx.x; e < 1024; e += blockDim.x) Gs[e >> 5][e & 31] = Gkk[(int64_t)(e >> 5) * ld + (e & 31)];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  // stage the block (one round trip for the whole CTA)
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    Gs[e >> 5][e & 31] = Gkk[(int64_t)(e >> 5) * ld + (e & 31)];
+    Rs[e >> 5][e & 31] = 0.0;
+    Ws[e >> 5][e & 31] = 0.0;
+  }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int l = threadIdx.x;
-    for (int i = 0; i < 32; ++i) Rs[i][l] = 0.0;
-    __syncwarp();
-    for (int j = 0; j < 32; ++j) {
-      double t = Gs[j][l];
-      for (int i = 0; i < j; ++i) t -= Rs[i][j] * Rs[i][l];
+  // left-looking by columns: t_l = G[j][l] - sum_{i < j} R[i][j] R[i][l] for l >= j
+  for (int j = 0; j < 32; ++j) {
+    if (w < 4) {
+      double t = 0.0;
+      for (int i = w; i < j; i += 4) t = fma(Rs[i][j], Rs[i][l], t);
+      part[w][l] = t;
+    }
+    __syncthreads();
+    if (w == 0) {
+      const double t = Gs[j][l] - ((part[0][l] + part[1][l]) + (part[2][l] + part[3][l]));
       const double piv = __shfl_sync(0xffffffffu, t, j);
       if (!(piv > 0.0) || !isfinite(piv)) {
         if (l == 0) bad = 1;
-        break;
-      }
-      const double rjj = sqrt(piv);
-      if (l == j) Rs[j][j] = rjj;
-      else if (l > j) Rs[j][l] = t / rjj;
-      __syncwarp();
-    }
-    __syncwarp();
-    // column l of the inverse by back substitution
-    for (int i = 0; i < 32; ++i) Ws[i][l] = 0.0;
-    if (!bad) {
-      for (int i = l; i >= 0; --i) {
-        double s = (i == l) ? 1.0 : 0.0;
-        for (int k = i + 1; k <= l; ++k) s -= Rs[i][k] * Ws[k][l];
-        Ws[i][l] = s / Rs[i][i];
+      } else {
+        const double rjj = sqrt(piv);
+        if (l == j) Rs[j][j] = rjj;
+        else if (l > j) Rs[j][l] = t / rjj;
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
-  __syncthreads();
+  // the inverse row by row from the bottom: W[i][l] = (delta_il - sum_{i < k <= l} R[i][k] W[k][l]) / R[i][i]
+  if (!bad) {
+    for (int i = 31; i >= 0; --i) {
+      if (w < 4) {
+        double t = 0.0;
+        for (int k = i + 1 + w; k <= l; k += 4) t = fma(Rs[i][k], Ws[k][l], t);
+        part[w][l] = t;
+      }
+      __syncthreads();
+      if (w == 0 && l >= i)
+        Ws[i][l] = ((i == l ? 1.0 : 0.0) - ((part[0][l] + part[1][l]) + (part[2][l] + part[3][l]))) / Rs[i][i];
+      __syncthreads();
+    }
+  }
   for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
     Rkk[(int64_t)(e >> 5) * ld + (e & 31)] = Rs[e >> 5][e & 31];
     Wkk[(int64_t)(e >> 5) * ld + (e & 31)] = Ws[e >> 5][e & 31];
