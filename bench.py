@@ -58,9 +58,9 @@ def parse():
     ap.add_argument("--sketch-precision", default="f32", choices=["f64", "f32", "bf16"])
     ap.add_argument("--a-dtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--outlier-frac", type=float, default=0.0)
-    ap.add_argument("--m", type=int, default=4096)
+    ap.add_argument("--m", "--sketch-rows", dest="m", type=int, default=4096)
     ap.add_argument("--n-log2", type=int, default=20)
-    ap.add_argument("--d", type=int, default=512)
+    ap.add_argument("--d", "--dim", dest="d", type=int, default=512)
     ap.add_argument("--sigma-max", type=float, default=1e6)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-e2e", action="store_true")
@@ -136,6 +136,19 @@ class ClockSampler:
         if sm:
             out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
         return out
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's); the value itself
+    when there is one rank.  Uses the initialised process group (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_info():
@@ -285,11 +298,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
     launches = L.lsq_launch_count() - launches0
     step_ms = [a.elapsed_time(b_) for a, b_ in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_solve = total_ms / (args.steps * world)
 
     # accuracy of the last solve against the oracle-free residual check is in the tests;
@@ -470,11 +479,7 @@ def run_batch(args):
             infos.append(info)
             pers.append(per)
     launches = L.lsq_launch_count() - launches0
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_batch = total_ms / (args.steps * world)
     info = infos[-1]
     per = pers[-1]
