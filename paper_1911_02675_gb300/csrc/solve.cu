@@ -226,7 +226,10 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
       double rho_new = total(red_rho);
       bx = total(red_bx);
       bool conv = rho_new == 0.0 || rho_new <= a.tol2 * bx;
-      if (MIXED && (conv || rho_new <= a.replace2 * rho_last || it + 1 - it_last >= a.refresh_every)) {
+      // a drop-triggered replacement within 10^2 (in norm) of the tolerance is left to the one
+      // that confirms convergence a few iterations later
+      const bool near = rho_new <= 1e4 * a.tol2 * bx;
+      if (MIXED && (conv || (!near && rho_new <= a.replace2 * rho_last) || it + 1 - it_last >= a.refresh_every)) {
         // replace the recursive residual by b - H x evaluated in FP64
         for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec2[c] = c < d ? a.x[c] : 0.0;
         __syncthreads();
