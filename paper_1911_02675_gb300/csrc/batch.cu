@@ -167,8 +167,9 @@ __device__ __forceinline__ void pass_chunk(const BProb& pr, int64_t r0, int64_t 
   const int s_row = tr >= BT ? g : g % tr;
   const int s_slice = tr >= BT ? 0 : g / tr;
   const int cs = dp / S;
-  // Tile element (r, c) sits at As[r * dp + (c ^ (r & 31))]: a column read by 32 consecutive
-  // rows and a row read by 32 consecutive columns both hit 32 distinct banks.  Loads are
+  // Tile element (r, c) sits at As[r * dp + (c ^ 4 (r & 7))]: aligned groups of 4 columns move
+  // together, so a 16-byte read of 4 columns by 8 consecutive rows (a quarter warp) and a read
+  // of 32 consecutive columns of one row both hit distinct banks.  Loads are
   // 16-byte vectors (V elements) when A allows; the next tile waits in registers.
   constexpr int V = sizeof(TA) == 4 ? 4 : 2;
   using VT = typename std::conditional<sizeof(TA) == 4, float4, double2>::type;
@@ -205,14 +206,12 @@ __device__ __forceinline__ void pass_chunk(const BProb& pr, int64_t r0, int64_t 
       const int u = tid + i * BT;
       if (u < units) {
         const int r = u >> lgu, c = (u & ((1 << lgu) - 1)) * V;
-        const int sw = r & 31;
+        const int sw = (r & 7) << 2;
         if constexpr (sizeof(TT) == 4 && V == 4) {
-          // position p of the swizzled group holds element p ^ (r & 3)
-          float e0 = narrow_f32(pf[i * V + 0]), e1 = narrow_f32(pf[i * V + 1]);
-          float e2 = narrow_f32(pf[i * V + 2]), e3 = narrow_f32(pf[i * V + 3]);
-          if (sw & 1) { float t = e0; e0 = e1; e1 = t; t = e2; e2 = e3; e3 = t; }
-          if (sw & 2) { float t = e0; e0 = e2; e2 = t; t = e1; e1 = e3; e3 = t; }
-          *reinterpret_cast<float4*>(As + r * dp + ((c ^ sw) & ~3)) = make_float4(e0, e1, e2, e3);
+          // the swizzle moves whole aligned groups of 4 columns: one 16-byte store
+          *reinterpret_cast<float4*>(As + r * dp + (c ^ sw)) =
+              make_float4(narrow_f32(pf[i * V + 0]), narrow_f32(pf[i * V + 1]), narrow_f32(pf[i * V + 2]),
+                          narrow_f32(pf[i * V + 3]));
         } else {
 #pragma unroll
           for (int q = 0; q < V; ++q) {
@@ -236,12 +235,28 @@ __device__ __forceinline__ void pass_chunk(const BProb& pr, int64_t r0, int64_t 
         for (int j = 0; j < KP; ++j) y[j] = 0;
         const int c0 = s_slice * cs;
         const TT* arow = As + r * dp;
-        const int sw = r & 31;
-        for (int c = c0; c < c0 + cs; ++c) {
-          const TT a = arow[c ^ sw];
-          const TT* pc = Ps + c * KP;
+        const int sw = (r & 7) << 2;
+        if constexpr (sizeof(TT) == 4 && TE == 16384) {
+          // cs = TE / BT = 32 columns: 8 groups of 4, each one 16-byte load of the row
 #pragma unroll
-          for (int j = 0; j < KP; ++j) y[j] = fma(a, pc[j], y[j]);
+          for (int g = 0; g < 8; ++g) {
+            const int c = c0 + 4 * g;
+            const float4 a4 = *reinterpret_cast<const float4*>(arow + (c ^ sw));
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const TT* pc = Ps + (c + q) * KP;
+#pragma unroll
+              for (int j = 0; j < KP; ++j) y[j] = fma(av[q], pc[j], y[j]);
+            }
+          }
+        } else {
+          for (int c = c0; c < c0 + cs; ++c) {
+            const TT a = arow[c ^ sw];
+            const TT* pc = Ps + c * KP;
+#pragma unroll
+            for (int j = 0; j < KP; ++j) y[j] = fma(a, pc[j], y[j]);
+          }
         }
         if (S == 1) {
 #pragma unroll
@@ -275,7 +290,7 @@ __device__ __forceinline__ void pass_chunk(const BProb& pr, int64_t r0, int64_t 
     // stage 2: acc[h][j] += As[r][c] Ys[r][j] for the warp's column groups and row phase
     for (int r = rphase; r < tr; r += rsplit) {
       const TT* yr = Ys + r * KP;
-      const int sw = r & 31;
+      const int sw = (r & 7) << 2;
 #pragma unroll
       for (int h = 0; h < CPWMAX; ++h) {
         if (h < cpw) {
@@ -700,8 +715,11 @@ __device__ void direction_block(const BatchArgs& a, const BProb& pr, int blk, in
       rzn[j] = rz;
       fin[j] = isfinite(rz);
       conv[j] = fin[j] && (rz == 0.0 || rz <= pr.tol2 * bx);
+      // a drop-triggered replacement within 10^2 (in norm) of the tolerance is left to the one
+      // that confirms convergence a few iterations later
+      const bool near = rz <= 1e4 * pr.tol2 * bx;
       if (a.mixed && !after_exact && fin[j] &&
-          (conv[j] || rz <= a.replace2 * pr.rz_rep[j] || it + 1 - pr.it_last[j] >= a.refresh_every))
+          (conv[j] || (!near && rz <= a.replace2 * pr.rz_rep[j]) || it + 1 - pr.it_last[j] >= a.refresh_every))
         need = true;
     }
   }
