@@ -155,6 +155,18 @@ LSQ_API lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
  * --------------------------------------------------------------------------------- */
 LSQ_API lsq_status lsq_factor(lsq_ctx* ctx, const double* SA, int64_t m, int64_t d, double* R, double* W);
 
+/* lsq_factor_ex: lsq_factor with the arithmetic of the Gram matrix chosen.
+ *   gram_precision : LSQ_PREC_F64 (= lsq_factor) or LSQ_PREC_MIXED, which forms
+ *                    H_S = (SA)^T (SA) in double-FP32 on the FP32 pipe: each entry of SA is
+ *                    split into a 21-bit head and the FP32 rounding of the rest (about 45
+ *                    significant bits), products are exact (TwoProduct by FMA) and sums are
+ *                    (head, tail) pairs (TwoSum), a relative error near 1e-13 per entry,
+ *                    far below what an FP32 sketch (LSQ_SKETCH_F32) already carries.  The
+ *                    Cholesky factor and the inverse stay FP64.
+ * Other arguments, results and status as lsq_factor; LSQ_ERR_ARG for another precision. */
+LSQ_API lsq_status lsq_factor_ex(lsq_ctx* ctx, const double* SA, int64_t m, int64_t d, double* R, double* W,
+                                 int32_t gram_precision);
+
 /* Options of lsq_solve; lsq_solve_opts_default fills the defaults noted below. */
 typedef struct {
   double rho;          /* deviation parameter rho in (0,1) of the event E_rho (Section 3);
@@ -178,6 +190,13 @@ typedef struct {
   int32_t x0_zero;     /* 1: x0 is zero, so the initial residual b - H x0 = b needs no pass over A */
   int32_t fcg_k;       /* LSQ_FCG: directions kept for orthogonalisation; < 0 (default) keeps
                           all of them (GCC), 1 gives IPCG, k gives FCG(k) */
+  int32_t a32_copy;    /* MIXED PCG / IHS with FP64 A and maxit >= 3: 1 (default) makes an FP32
+                          copy of A once per call (n x ceil32(d) x 4 bytes of device memory,
+                          kept by the context for later calls) that the FP32 passes read
+                          instead of A, halving their bytes; it holds the values those passes
+                          compute with, so results are bit-identical with 0 (every pass
+                          narrows A itself).  Where the memory cannot be had the solve runs as
+                          with 0. */
 } lsq_solve_opts;
 
 /* Results of lsq_solve. */
@@ -189,6 +208,8 @@ typedef struct {
   double est_err;       /* final stopping quantity sqrt((1+sqrt(rho))^2 r^T H_S^-1 r / <b,x>) */
   double ms_total;      /* device time of the whole call (ms), CUDA events */
   double ms_sketch;     /* refreshed only: time in sketch + factor (ms) */
+  int32_t a32_copy;     /* 1 when the FP32 passes read an FP32 copy of A (opts->a32_copy) */
+  int32_t reserved;
 } lsq_solve_info;
 
 LSQ_API void lsq_solve_opts_default(lsq_solve_opts* opts);

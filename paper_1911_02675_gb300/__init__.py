@@ -9,7 +9,7 @@ is no CPU path.
 
 Entry points (same names as the C ABI):
     lsq_sketch(ctx, A, kind, m, seed, t=0, s=8, precision="f64") -> SA      (Section 2)
-    lsq_factor(ctx, SA) -> (R, W)                                           (Section 1, PCG; Section 6)
+    lsq_factor(ctx, SA, precision) -> (R, W)                                (Section 1, PCG; Section 6)
     lsq_solve(ctx, A, b, method, W, x0=None, tol=1e-10, maxit=..., **opts)  (Section 1; Sections 3-4)
     lsq_hmatvec(ctx, A, p) -> (v, q)                                        (one fused pass over A)
     lsq_solve_batched(ctx, [(A_p, B_p), ...], tol, maxit, **opts)            (many problems, k_p RHS each)
@@ -35,7 +35,7 @@ SKETCH_PRECISION = {"f64": 0, "f32": 1, "bf16": 2}
 DTYPE = {torch.float64: 0, torch.float32: 1}
 
 # every symbol the header declares
-EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_sketch", "lsq_factor", "lsq_solve",
+EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_sketch", "lsq_factor", "lsq_factor_ex", "lsq_solve",
            "lsq_solve_opts_default", "lsq_hmatvec", "lsq_status_str", "lsq_version", "lsq_launch_count",
            "lsq_hmatvec_noalloc", "lsq_grad_a", "lsq_advise_sketch_size", "lsq_batch_opts_default",
            "lsq_solve_batched")
@@ -61,7 +61,7 @@ class LsqSolveOpts(ctypes.Structure):
                 ("refresh", ctypes.c_int32), ("sketch_type", ctypes.c_int32), ("m", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("s", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("refresh_every", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("x0_zero", ctypes.c_int32),
-                ("fcg_k", ctypes.c_int32)]
+                ("fcg_k", ctypes.c_int32), ("a32_copy", ctypes.c_int32)]
 
 
 class LsqProblem(ctypes.Structure):
@@ -95,7 +95,7 @@ class LsqAdvice(ctypes.Structure):
 class LsqSolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("exact_passes", ctypes.c_int32), ("est_err", ctypes.c_double), ("ms_total", ctypes.c_double),
-                ("ms_sketch", ctypes.c_double)]
+                ("ms_sketch", ctypes.c_double), ("a32_copy", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -111,6 +111,7 @@ def _load():
     L.lsq_set_stream.argtypes = [P, P]
     L.lsq_sketch.argtypes = [P, ctypes.POINTER(LsqMatrix), i32, i64, u64, ctypes.POINTER(LsqSketchOpts), P]
     L.lsq_factor.argtypes = [P, P, i64, i64, P, P]
+    L.lsq_factor_ex.argtypes = [P, P, i64, i64, P, P, i32]
     L.lsq_solve.argtypes = [P, ctypes.POINTER(LsqMatrix), P, i32, P, P, dbl, i32, ctypes.POINTER(LsqSolveOpts),
                             ctypes.POINTER(LsqSolveInfo)]
     L.lsq_solve_opts_default.argtypes = [ctypes.POINTER(LsqSolveOpts)]
@@ -131,7 +132,8 @@ def _load():
     L.lsq_status_str.restype = ctypes.c_char_p
     L.lsq_version.restype = ctypes.c_char_p
     L.lsq_launch_count.restype = ctypes.c_uint64
-    for name in ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_sketch", "lsq_factor", "lsq_solve", "lsq_hmatvec"):
+    for name in ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_sketch", "lsq_factor", "lsq_factor_ex", "lsq_solve",
+                 "lsq_hmatvec"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -221,14 +223,16 @@ def lsq_sketch(ctx: Context, A: torch.Tensor, kind: str, m: int, seed: int, t: i
     return SA
 
 
-def lsq_factor(ctx: Context, SA: torch.Tensor, R: torch.Tensor | None = None, W: torch.Tensor | None = None):
+def lsq_factor(ctx: Context, SA: torch.Tensor, R: torch.Tensor | None = None, W: torch.Tensor | None = None,
+               precision: str = "f64"):
+    """(R, W) with R^T R = SA^T SA and W = R^{-1}; precision "mixed" forms the Gram in double-FP32."""
     ctx.sync_stream()
     if SA.dtype != torch.float64 or not SA.is_contiguous() or not SA.is_cuda:
         raise ValueError("SA must be a contiguous CUDA float64 matrix")
     m, d = SA.shape
     R = R if R is not None else torch.empty((d, d), dtype=torch.float64, device=SA.device)
     W = W if W is not None else torch.empty((d, d), dtype=torch.float64, device=SA.device)
-    st = _L.lsq_factor(ctx.handle, _ptr(SA), m, d, _ptr(R), _ptr(W))
+    st = _L.lsq_factor_ex(ctx.handle, _ptr(SA), m, d, _ptr(R), _ptr(W), PRECISION[precision])
     if st:
         raise LsqError(st, "lsq_factor")
     return R, W

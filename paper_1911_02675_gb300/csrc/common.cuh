@@ -25,6 +25,8 @@ struct lsq_ctx {
   size_t scratch_bytes;
   void* state;             // device arena of the solver's iteration state (separate, so that a
   size_t state_bytes;      // refreshed solve can call the sketch and the factor between steps)
+  void* a32;               // FP32 copy of an FP64 A that a mixed-precision solve streams
+  size_t a32_bytes;
   int* host_status;        // pinned host word for status read-back
   cudaStream_t capture;    // non-blocking stream on which CUDA graphs are captured (lazily)
   cudaEvent_t ev0, ev1;
@@ -52,6 +54,7 @@ void lsq_count_launch();
 // Ensures the context arena holds at least `bytes` (256-byte aligned carving is the caller's).
 lsq_status lsq_ensure_scratch(lsq_ctx* ctx, size_t bytes);
 lsq_status lsq_ensure_state(lsq_ctx* ctx, size_t bytes);
+lsq_status lsq_ensure_a32(lsq_ctx* ctx, size_t bytes);
 
 // Factorisations of many sketches (batched solves): W_p = R_p^{-1} and W_p^T; status_out[p]
 // (host) = LSQ_OK or LSQ_ERR_RANK; the Gram matrices in double-FP32 when df_gram.

@@ -35,6 +35,7 @@ extern "C" lsq_status lsq_destroy(lsq_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->scratch) cudaFree(c->scratch);
   if (c->state) cudaFree(c->state);
+  if (c->a32) cudaFree(c->a32);
   if (c->capture) cudaStreamDestroy(c->capture);
   cudaFreeHost(c->host_status);
   cudaEventDestroy(c->ev0);
@@ -72,6 +73,8 @@ static lsq_status grow(lsq_ctx* c, void** buf, size_t* have, size_t bytes) {
 lsq_status lsq_ensure_scratch(lsq_ctx* c, size_t bytes) { return grow(c, &c->scratch, &c->scratch_bytes, bytes); }
 
 lsq_status lsq_ensure_state(lsq_ctx* c, size_t bytes) { return grow(c, &c->state, &c->state_bytes, bytes); }
+
+lsq_status lsq_ensure_a32(lsq_ctx* c, size_t bytes) { return grow(c, &c->a32, &c->a32_bytes, bytes); }
 
 extern "C" const char* lsq_status_str(int32_t s) {
   switch (s) {

@@ -9,46 +9,90 @@
 //     diagonal blocks: for R = [[A, B], [0, C]], R^{-1} = [[A^-1, -A^-1 B C^-1], [0, C^-1]].
 //     Phases are separated by bounded grid barriers.
 #include <algorithm>
+#include <type_traits>
 #include <math.h>
 #include <vector>
 
+#include "apass.cuh"
 #include "common.cuh"
 
 namespace {
 
 constexpr int TB = 64, TK = 16;
 
-// part[split][dp][dp] (upper tiles only) = sum over the split's rows of SA^T SA
+// One TK-row step of a 64 x 64 Gram tile in double-FP32 (DF): each thread's 4 x 4 outputs are
+// (head, tail) FP32 pairs; the operands were split into a 21-bit head and the FP32 rounding of
+// the rest (about 45 significant bits), products are exact through an FMA (TwoProduct) and the
+// sums are carried with TwoSum (Dekker 1971; Knuth) -- on the FP32 pipe, which does ~70x the
+// FP64 pipe's FMA rate on this part.
+__device__ __forceinline__ void df_gram_step(const float2 (*Xa)[TB], const float2 (*Xb)[TB], int ty, int tx,
+                                             float (&ah)[4][4], float (&al)[4][4]) {
+#pragma unroll 4
+  for (int k = 0; k < TK; ++k) {
+    float2 x[4], y[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = Xa[k][ty + 16 * i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) y[j] = Xb[k][tx + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) lsq_apass::df_fma(x[i].x, x[i].y, y[j].x, y[j].y, ah[i][j], al[i][j]);
+  }
+}
+
+__device__ __forceinline__ float2 df_split(double v) {
+  float h, t;
+  lsq_apass::split_df(v, h, t);
+  return make_float2(h, t);
+}
+
+// part[split][dp][dp] (upper tiles only) = sum over the split's rows of SA^T SA, in FP64 or,
+// with DF, in double-FP32
+template <bool DF>
 __global__ void __launch_bounds__(256) gram_kernel(const double* __restrict__ SA, int m, int d, int dp,
                                                    int rows_per_split, const int2* __restrict__ tiles,
                                                    double* __restrict__ part) {
-  __shared__ double Xa[TK][TB];
-  __shared__ double Xb[TK][TB];
+  using E = typename std::conditional<DF, float2, double>::type;
+  __shared__ E Xa[TK][TB];
+  __shared__ E Xb[TK][TB];
   const int2 tl = tiles[blockIdx.x];
   const int a0 = tl.x * TB, b0 = tl.y * TB;
   const int r_begin = blockIdx.y * rows_per_split;
   const int r_end = min(m, r_begin + rows_per_split);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double acc[4][4] = {};
+  float ah[4][4] = {}, al[4][4] = {};
   for (int r0 = r_begin; r0 < r_end; r0 += TK) {
     for (int e = threadIdx.x; e < TK * TB; e += 256) {
       const int k = e / TB, c = e % TB;
       const int r = r0 + k;
-      Xa[k][c] = (r < r_end && a0 + c < d) ? SA[(int64_t)r * d + a0 + c] : 0.0;
-      Xb[k][c] = (r < r_end && b0 + c < d) ? SA[(int64_t)r * d + b0 + c] : 0.0;
+      const double va = (r < r_end && a0 + c < d) ? SA[(int64_t)r * d + a0 + c] : 0.0;
+      const double vb = (r < r_end && b0 + c < d) ? SA[(int64_t)r * d + b0 + c] : 0.0;
+      if constexpr (DF) {
+        Xa[k][c] = df_split(va);
+        Xb[k][c] = df_split(vb);
+      } else {
+        Xa[k][c] = va;
+        Xb[k][c] = vb;
+      }
     }
     __syncthreads();
+    if constexpr (DF) {
+      df_gram_step(Xa, Xb, ty, tx, ah, al);
+    } else {
 #pragma unroll
-    for (int k = 0; k < TK; ++k) {
-      double x[4], y[4];
+      for (int k = 0; k < TK; ++k) {
+        double x[4], y[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) x[i] = Xa[k][ty + 16 * i];
+        for (int i = 0; i < 4; ++i) x[i] = Xa[k][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) y[j] = Xb[k][tx + 16 * j];
+        for (int j = 0; j < 4; ++j) y[j] = Xb[k][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(x[i], y[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(x[i], y[j], acc[i][j]);
+      }
     }
     __syncthreads();
   }
@@ -58,7 +102,8 @@ __global__ void __launch_bounds__(256) gram_kernel(const double* __restrict__ SA
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
-      if (a < dp && b < dp) out[(int64_t)a * dp + b] = acc[i][j];
+      const double v = DF ? (double)ah[i][j] + (double)al[i][j] : acc[i][j];
+      if (a < dp && b < dp) out[(int64_t)a * dp + b] = v;
     }
 }
 
@@ -137,13 +182,17 @@ __device__ void tile_task(TileSmem& sm, double* out, const double* Xm, bool tran
 
 // Cholesky of one 32 x 32 diagonal block and the inverse of its factor, by the whole CTA:
 // lane l owns column l; the dot products of each step are split over 4 warps (one per SM
-// sub-partition, so 4 FP64 pipes work on them) and added in warp order by warp 0.
+// sub-partition, so 4 FP64 pipes work on them) and added in warp order by warp 0.  FP64
+// instructions are costly on this part (a warp instruction holds a sub-partition's FP64 unit
+// for ~70 cycles), so each pivot takes one reciprocal square root and the rest are products:
+// R[j][j] = piv * rsqrt(piv), R[j][l] = t_l * rsqrt(piv); the inverse reuses 1 / R[i][i].
 // Sets *err to LSQ_ERR_RANK on a non-positive or non-finite pivot.
 __device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, int* err) {
   __shared__ double Gs[32][33];
   __shared__ double Rs[32][33];
   __shared__ double Ws[32][33];
   __shared__ double part[4][32];
+  __shared__ double rinv[32];
   __shared__ int bad;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   // stage the block (one round trip for the whole CTA)
@@ -168,9 +217,13 @@ __device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, 
       if (!(piv > 0.0) || !isfinite(piv)) {
         if (l == 0) bad = 1;
       } else {
-        const double rjj = sqrt(piv);
-        if (l == j) Rs[j][j] = rjj;
-        else if (l > j) Rs[j][l] = t / rjj;
+        const double ri = rsqrt(piv);
+        if (l == j) {
+          Rs[j][j] = piv * ri;
+          rinv[j] = ri;
+        } else if (l > j) {
+          Rs[j][l] = t * ri;
+        }
       }
     }
     __syncthreads();
@@ -185,7 +238,7 @@ __device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, 
       }
       __syncthreads();
       if (w == 0 && l >= i)
-        Ws[i][l] = ((i == l ? 1.0 : 0.0) - ((part[0][l] + part[1][l]) + (part[2][l] + part[3][l]))) / Rs[i][i];
+        Ws[i][l] = ((i == l ? 1.0 : 0.0) - ((part[0][l] + part[1][l]) + (part[2][l] + part[3][l]))) * rinv[i];
       __syncthreads();
     }
   }
@@ -225,12 +278,37 @@ __device__ void chol_inv_body(double* __restrict__ G, double* __restrict__ Rf, d
     // diagonal block (k+1, k+1)
     const int pairs = rest * (rest + 1) / 2;
     const int64_t k1 = (int64_t)(k + 1) * 32;
-    if (rank == 0) {
-      for (int q = 0; q < 4; ++q)
+    // the next diagonal block's update is split over `nd` CTAs (one 32 x 8 tile each: it is
+    // 32^3 FP64 FMAs, ~9 us on one SM); CTAs 1 .. nd-1 count themselves done on bar[4] and
+    // CTA 0 waits for them (bounded) before it factors the block
+    const unsigned nd = nb >= 4 ? 4u : 1u;
+    if (rank < nd) {
+      for (unsigned q = rank; q < 4; q += nd)
         tile_task(sm, G + k1 * dp + k1 + q * 8, Rf + kk * dp + k1, true, Rf + kk * dp + k1 + q * 8, 32, dp, -1.0,
                   true);
       __syncthreads();
-      diag_block(G + k1 * dp + k1, Rf + k1 * dp + k1, Wf + k1 * dp + k1, dp, err);
+      if (rank > 0 && threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar + 4, 1u);
+      }
+    }
+    if (rank == 0) {
+      if (nd > 1 && threadIdx.x == 0) {
+        const unsigned target = (unsigned)(k + 1) * (nd - 1);
+        const uint64_t t0 = global_ns();
+        unsigned spins = 0;
+        while (ld_acquire_u32(bar + 4) < target) {
+          if (*(volatile int*)err != 0) break;
+          if (++spins > LSQ_SPIN_LIMIT || global_ns() - t0 > LSQ_WAIT_NS) {
+            atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      if (*(volatile int*)err == 0) diag_block(G + k1 * dp + k1, Rf + k1 * dp + k1, Wf + k1 * dp + k1, dp, err);
     }
     const int others = nb > 1 ? (int)nb - 1 : 1;
     const int first = nb > 1 ? (int)rank - 1 : 0;
@@ -312,7 +390,13 @@ static void build_tree(int a, int b, int depth, std::vector<std::vector<int4>>& 
 }  // namespace
 
 extern "C" lsq_status lsq_factor(lsq_ctx* ctx, const double* SA, int64_t m, int64_t d, double* R, double* W) {
+  return lsq_factor_ex(ctx, SA, m, d, R, W, LSQ_PREC_F64);
+}
+
+extern "C" lsq_status lsq_factor_ex(lsq_ctx* ctx, const double* SA, int64_t m, int64_t d, double* R, double* W,
+                                    int32_t gram_precision) {
   if (!ctx || !SA || !R || !W) return LSQ_ERR_ARG;
+  if (gram_precision != LSQ_PREC_F64 && gram_precision != LSQ_PREC_MIXED) return LSQ_ERR_ARG;
   if (d < 1 || d > LSQ_MAX_D || m < d || m > (1ll << 31) - 1) return LSQ_ERR_ARG;
   const int di = (int)d, mi = (int)m;
   const int nblk = (di + 31) / 32, dp = nblk * 32;
@@ -367,8 +451,11 @@ extern "C" lsq_status lsq_factor(lsq_ctx* ctx, const double* SA, int64_t m, int6
   LSQ_CUDA_TRY(cudaMemsetAsync(Rf, 0, mat * 8, s));
   LSQ_CUDA_TRY(cudaMemsetAsync(Wf, 0, mat * 8, s));
 
-  gram_kernel<<<dim3((unsigned)tiles.size(), (unsigned)splits), 256, 0, s>>>(SA, mi, di, dp, rows_per_split, d_tiles,
-                                                                             part);
+  const dim3 ggrid((unsigned)tiles.size(), (unsigned)splits);
+  if (gram_precision == LSQ_PREC_MIXED)
+    gram_kernel<true><<<ggrid, 256, 0, s>>>(SA, mi, di, dp, rows_per_split, d_tiles, part);
+  else
+    gram_kernel<false><<<ggrid, 256, 0, s>>>(SA, mi, di, dp, rows_per_split, d_tiles, part);
   LSQ_LAUNCH_CHECK();
   gram_reduce_kernel<<<std::min(4 * ctx->sm_count, (int)((mat + 255) / 256)), 256, 0, s>>>(part, splits, di, dp, G);
   LSQ_LAUNCH_CHECK();
@@ -461,8 +548,7 @@ __global__ void __launch_bounds__(256) gram_batched_kernel(const GramJob* __rest
 #pragma unroll
       for (int j = 0; j < 4; ++j) res[i][j] = acc[i][j];
   } else {
-    // double-FP32: x = xh + xl (FP32 head and the FP32 rounding of the rest), products by
-    // FMA-exact TwoProduct plus the cross terms, sums by TwoSum (Dekker 1971; Knuth)
+    // double-FP32 (df_gram_step)
     __shared__ float2 Xa[TK][TB];
     __shared__ float2 Xb[TK][TB];
     float ah[4][4] = {}, al[4][4] = {};
@@ -470,34 +556,11 @@ __global__ void __launch_bounds__(256) gram_batched_kernel(const GramJob* __rest
       for (int e = threadIdx.x; e < TK * TB; e += 256) {
         const int k = e / TB, c = e % TB;
         const int r = r0 + k;
-        const double va = (r < jb.m && a0 + c < d) ? jb.SA[(int64_t)r * d + a0 + c] : 0.0;
-        const double vb = (r < jb.m && b0 + c < d) ? jb.SA[(int64_t)r * d + b0 + c] : 0.0;
-        const float ha = (float)va, hb = (float)vb;
-        Xa[k][c] = make_float2(ha, (float)(va - (double)ha));
-        Xb[k][c] = make_float2(hb, (float)(vb - (double)hb));
+        Xa[k][c] = df_split((r < jb.m && a0 + c < d) ? jb.SA[(int64_t)r * d + a0 + c] : 0.0);
+        Xb[k][c] = df_split((r < jb.m && b0 + c < d) ? jb.SA[(int64_t)r * d + b0 + c] : 0.0);
       }
       __syncthreads();
-#pragma unroll 4
-      for (int k = 0; k < TK; ++k) {
-        float2 x[4], y[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = Xa[k][ty + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) y[j] = Xb[k][tx + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float p = __fmul_rn(x[i].x, y[j].x);
-            const float pe = __fmaf_rn(x[i].x, y[j].x, -p);
-            const float cross = __fmaf_rn(x[i].x, y[j].y, __fmaf_rn(x[i].y, y[j].x, pe));
-            const float s = __fadd_rn(ah[i][j], p);
-            const float bb = __fsub_rn(s, ah[i][j]);
-            const float err = __fadd_rn(__fsub_rn(ah[i][j], __fsub_rn(s, bb)), __fsub_rn(p, bb));
-            ah[i][j] = s;
-            al[i][j] = __fadd_rn(al[i][j], __fadd_rn(err, cross));
-          }
-      }
+      df_gram_step(Xa, Xb, ty, tx, ah, al);
       __syncthreads();
     }
 #pragma unroll

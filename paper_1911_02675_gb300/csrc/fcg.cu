@@ -359,6 +359,8 @@ lsq_status lsq_fcg_solve(lsq_ctx* ctx, const lsq_matrix* A, const double* b, con
     info->est_err = est;
     info->ms_total = ms_total;
     info->ms_sketch = ms_sketch;
+    info->a32_copy = 0;
+    info->reserved = 0;
   }
   return (lsq_status)status;
 }

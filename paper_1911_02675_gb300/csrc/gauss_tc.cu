@@ -151,30 +151,13 @@ __device__ __forceinline__ RoundKeys round_keys(uint64_t seed) {
   return k;
 }
 
-__device__ __forceinline__ uint4 philox_keyed(uint4 c, const RoundKeys& k) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k.a[r], lo1, hi0 ^ c.w ^ k.b[r], lo0);
-  }
-  return c;
-}
-
-// z(2q, i) (cosine) and z(2q + 1, i) (sine) in FP32 from the same Philox words as the FP64
-// definition; the uniforms keep the top 24 of their 53 bits (BF16 keeps 8)
-__device__ __forceinline__ void gauss_pair_f32(const RoundKeys& k, uint32_t i, uint32_t q, uint32_t t, float& zc,
-                                               float& zs) {
-  const uint4 w = philox_keyed(make_uint4(i, q, t, TAG_GAUSS), k);
-  const float u1 = __fmaf_rn((float)(w.x >> 8), 0x1p-24f, 0x1p-25f);
-  const float u2 = __fmaf_rn((float)(w.z >> 8), 0x1p-24f, 0x1p-25f);
-  const float rad = sqrtf(-2.0f * __logf(u1));
-  float s, c;
-  __sincosf(6.28318530717958647692f * u2, &s, &c);
-  zc = rad * c;
-  zs = rad * s;
+// one Philox4x32 round (multipliers 0xD2511F53, 0xCD9E8D57) with round key (ka, kb)
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t ka, uint32_t kb) {
+  const uint32_t lo0 = 0xD2511F53u * c.x;
+  const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+  const uint32_t lo1 = 0xCD9E8D57u * c.z;
+  const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+  return make_uint4(hi1 ^ c.y ^ ka, lo1, hi0 ^ c.w ^ kb, lo0);
 }
 
 // byte offset of element (row r, k-group kg of 8) of a K-major operand tile with R rows and
@@ -277,15 +260,35 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int r8 = ln & 7, kc = (ln >> 3) & 1, gsub = ln >> 4;
       const int jp = 8 * (2 * gpair + gsub) + r8;
       const int kg = 2 * kk + kc;
+      // z(2q, i) (cosine) and z(2q + 1, i) (sine) in FP32 from the same Philox words as the
+      // FP64 definition (the uniforms keep the top 24 of their 53 bits; BF16 keeps 8). The 8
+      // Philox streams of the unit advance round by round together, so each thread carries 8
+      // independent dependency chains through the multiply-high latency.
+      uint4 w[8];
+      const uint32_t ia0 = i_base + (uint32_t)(kg * 8), qq = (uint32_t)((j0 >> 1) + jp);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) w[q] = make_uint4(ia0 + (uint32_t)q, qq, t, TAG_GAUSS);
+#pragma unroll
+      for (int r = 0; r < 10; ++r) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w[q] = philox_round(w[q], keys.a[r], keys.b[r]);
+      }
       uint32_t ev[4], od[4];
 #pragma unroll
       for (int q = 0; q < 8; q += 2) {
-        float c_a, s_a, c_b, s_b;
-        const uint32_t ia = i_base + (uint32_t)(kg * 8 + q);
-        gauss_pair_f32(keys, ia, (uint32_t)((j0 >> 1) + jp), t, c_a, s_a);
-        gauss_pair_f32(keys, ia + 1, (uint32_t)((j0 >> 1) + jp), t, c_b, s_b);
-        ev[q >> 1] = pack_bf16(c_a, c_b);
-        od[q >> 1] = pack_bf16(s_a, s_b);
+        float zc[2], zs[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float u1 = __fmaf_rn((float)(w[q + h].x >> 8), 0x1p-24f, 0x1p-25f);
+          const float u2 = __fmaf_rn((float)(w[q + h].z >> 8), 0x1p-24f, 0x1p-25f);
+          const float rad = sqrtf(-2.0f * __logf(u1));
+          float sn, cs;
+          __sincosf(6.28318530717958647692f * u2, &sn, &cs);
+          zc[h] = rad * cs;
+          zs[h] = rad * sn;
+        }
+        ev[q >> 1] = pack_bf16(zc[0], zc[1]);
+        od[q >> 1] = pack_bf16(zs[0], zs[1]);
       }
       *reinterpret_cast<uint4*>(stA + core_offset(TC_M, jp, kg)) = make_uint4(ev[0], ev[1], ev[2], ev[3]);
       *reinterpret_cast<uint4*>(stA + core_offset(TC_M, jp + 64, kg)) = make_uint4(od[0], od[1], od[2], od[3]);

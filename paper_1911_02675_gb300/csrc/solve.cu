@@ -54,6 +54,8 @@ struct SolveArgs {
   unsigned* bar;
   int* err;
   double* out;       // [0] iters, [1] status, [2] passes, [3] est_err, [4] exact passes
+  const float* a32;  // COPY kernels: FP32 copy of A (row stride ld32) that the FP32 passes read
+  int64_t ld32;
 };
 
 // out[i] = sum_k M[i*d + k] vec_s[k] for k in [k_lo(i), k_hi(i)), one warp per output
@@ -72,13 +74,33 @@ struct SolveSmem {
   double* scal;  // 8
 };
 
+// The FP32 copy of an FP64 A that the FP32 passes of a mixed solve stream (half the bytes of
+// A): a warp per row, the narrowing of the passes themselves (narrow_f32), so a pass over the
+// copy computes with exactly the values a pass over A would.
+template <int EPL>
+__global__ void __launch_bounds__(LSQ_THREADS) narrow_copy_kernel(const double* __restrict__ A, int64_t n, int d,
+                                                                  int64_t ld, float* __restrict__ a32, int64_t ld32) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * LSQ_WARPS;
+  for (int64_t i = (int64_t)blockIdx.x * LSQ_WARPS + (threadIdx.x >> 5); i < n; i += nw) {
+    const double* a = A + i * ld;
+    double v[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) v[k] = lane + 32 * k < d ? __ldcs(a + lane + 32 * k) : 0.0;
+    float* o = a32 + i * ld32;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k)
+      if (lane + 32 * k < d) o[lane + 32 * k] = narrow_f32(v[k]);
+  }
+}
+
 // MIXED = false: every pass in FP64 arithmetic.  MIXED = true: PCG's passes over A run in
 // FP32 arithmetic and the recursive residual is replaced by an exact b - H x (FP64 pass) when
 // it has dropped by `replace2` since the last replacement, after `refresh_every` iterations,
 // and whenever it passes the stopping test (so convergence is always declared on an exact
 // residual); IHS / Polyak-IHS compute the gradient in FP32 until it is small relative to
 // <b, x> and in FP64 after that (their update has no recursive residual to correct).
-template <typename TA, int EPL, bool MIXED>
+template <typename TA, int EPL, bool MIXED, bool COPY = false>
 __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel(SolveArgs a) {
   extern __shared__ __align__(16) double smem[];
   const int dp = a.dp, d = a.d;
@@ -164,6 +186,13 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
     else fused_pass<TA, EPL, (EPL <= 4)>(A, a.ld, d, dp, r0, r1, vec, S.wred, S.qred, a.part, P, cta);
   };
 
+  // an FP32 pass: over the FP32 copy of A (COPY), else narrowing the rows of A as they arrive;
+  // both compute with the same FP32 values
+  auto f32_pass = [&](const double* vec) {
+    if constexpr (COPY) fused_pass_f32<float, EPL>(a.a32, a.ld32, d, dp, r0, r1, vec, S.wred, S.qred, a.part, P, cta);
+    else fused_pass_f32<TA, EPL>(A, a.ld, d, dp, r0, r1, vec, S.wred, S.qred, a.part, P, cta);
+  };
+
   int status = LSQ_ERR_MAXIT;
   int it = 0;
   double est = 0.0;
@@ -195,7 +224,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
     int it_last = 0;
     while (status == LSQ_ERR_MAXIT && it < a.maxit) {
       if (MIXED) {
-        fused_pass_f32<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+        f32_pass(S.vec);
       } else {
         fused_pass<TA, EPL, (!MIXED && EPL <= 4)>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
         ++exact_passes;
@@ -271,7 +300,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
         exact_pass(S.vec);
         ++exact_passes;
       } else {
-        fused_pass_f32<TA, EPL>(A, a.ld, d, dp, r0, r1, S.vec, S.wred, S.qred, a.part, P, cta);
+        f32_pass(S.vec);
       }
       ++passes;
       if (grid_barrier(a.bar, P, a.err)) return;
@@ -336,15 +365,26 @@ __global__ void transpose_kernel(const double* __restrict__ W, int d, double* __
 // ------------------------------------------------------------------------------------
 typedef void (*solve_fn)(SolveArgs);
 
-template <typename TA, bool MIXED>
+template <typename TA, bool MIXED, bool COPY = false>
 static void* pick_solve(int epl) {
   switch (epl) {
-    case 1: return (void*)solve_kernel<TA, 1, MIXED>;
-    case 2: return (void*)solve_kernel<TA, 2, MIXED>;
-    case 4: return (void*)solve_kernel<TA, 4, MIXED>;
-    case 8: return (void*)solve_kernel<TA, 8, MIXED>;
-    case 16: return (void*)solve_kernel<TA, 16, MIXED>;
-    default: return (void*)solve_kernel<TA, 32, MIXED>;
+    case 1: return (void*)solve_kernel<TA, 1, MIXED, COPY>;
+    case 2: return (void*)solve_kernel<TA, 2, MIXED, COPY>;
+    case 4: return (void*)solve_kernel<TA, 4, MIXED, COPY>;
+    case 8: return (void*)solve_kernel<TA, 8, MIXED, COPY>;
+    case 16: return (void*)solve_kernel<TA, 16, MIXED, COPY>;
+    default: return (void*)solve_kernel<TA, 32, MIXED, COPY>;
+  }
+}
+
+static void* pick_narrow(int epl) {
+  switch (epl) {
+    case 1: return (void*)narrow_copy_kernel<1>;
+    case 2: return (void*)narrow_copy_kernel<2>;
+    case 4: return (void*)narrow_copy_kernel<4>;
+    case 8: return (void*)narrow_copy_kernel<8>;
+    case 16: return (void*)narrow_copy_kernel<16>;
+    default: return (void*)narrow_copy_kernel<32>;
   }
 }
 
@@ -388,6 +428,7 @@ extern "C" void lsq_solve_opts_default(lsq_solve_opts* o) {
   o->grid_blocks = 0;
   o->x0_zero = 0;
   o->fcg_k = -1;
+  o->a32_copy = 1;
 }
 
 extern "C" lsq_status lsq_hmatvec(lsq_ctx* ctx, const lsq_matrix* A, const double* p, double* v, double* q) {
@@ -463,8 +504,17 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   if (method == LSQ_IHS) beta = 0.0;
 
   const int epl = epl_for(d), dp = 32 * epl;
-  void* kern = A->dtype == LSQ_F64 ? (mixed ? pick_solve<double, true>(epl) : pick_solve<double, false>(epl))
-                                   : (mixed ? pick_solve<float, true>(epl) : pick_solve<float, false>(epl));
+  // MIXED with FP64 A: the FP32 passes stream an FP32 copy of A (half the bytes), made once per
+  // call; without the memory for it every pass narrows A itself (the same values)
+  float* a32 = nullptr;
+  const int64_t ld32 = (d + 31) & ~31;
+  if (mixed && A->dtype == LSQ_F64 && o.a32_copy && maxit >= 3) {
+    if (lsq_ensure_a32(ctx, (size_t)A->n * (size_t)ld32 * 4) == LSQ_OK) a32 = reinterpret_cast<float*>(ctx->a32);
+  }
+  void* kern = A->dtype == LSQ_F64
+                   ? (mixed ? (a32 ? pick_solve<double, true, true>(epl) : pick_solve<double, true>(epl))
+                            : pick_solve<double, false>(epl))
+                   : (mixed ? pick_solve<float, true>(epl) : pick_solve<float, false>(epl));
   const size_t smem = solve_smem_bytes(dp);
   LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -520,6 +570,8 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   a.first_step = 1;
   a.force_exact = 0;
   a.refresh_every = o.refresh_every > 0 ? o.refresh_every : 40;
+  a.a32 = a32;
+  a.ld32 = ld32;
   // replace after a 10^5 drop of the residual norm: the FP32 passes' drift after it (about 1e-6
   // of that level) stays near 1e-11 of the initial residual, and convergence is confirmed on an
   // exact residual in any case
@@ -527,6 +579,16 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   a.exact2 = 1e-8;    // IHS: FP64 gradients once the relative gradient is below 10^-4
   cudaStream_t s = ctx->stream;
   LSQ_CUDA_TRY(cudaEventRecord(ctx->ev0, s));
+  if (a32) {
+    void* nk = pick_narrow(epl);
+    const void* Ad = A->data;
+    int64_t n = A->n, ld = A->ld, l32 = ld32;
+    int di = d;
+    void* nargs[] = {(void*)&Ad, &n, &di, &ld, (void*)&a32, &l32};
+    const int nblk = (int)std::min<int64_t>((A->n + LSQ_WARPS - 1) / LSQ_WARPS, 8 * (int64_t)ctx->sm_count);
+    LSQ_CUDA_TRY(cudaLaunchKernel(nk, dim3(nblk), dim3(LSQ_THREADS), nargs, 0, s));
+    LSQ_LAUNCH_CHECK();
+  }
 
   double ms_sketch = 0.0;
   int iters = 0, passes = 0, exact_passes = 0, status = LSQ_ERR_MAXIT;
@@ -616,6 +678,8 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
     info->est_err = est;
     info->ms_total = ms_total;
     info->ms_sketch = ms_sketch;
+    info->a32_copy = a32 ? 1 : 0;
+    info->reserved = 0;
   }
   return (lsq_status)status;
 }

@@ -51,6 +51,7 @@ def test_host_only_entry_points(lib):
     # null arguments are rejected before any CUDA call
     assert lib.lsq_sketch(None, None, 0, 16, 0, None, None) == 1
     assert lib.lsq_factor(None, None, 16, 4, None, None) == 1
+    assert lib.lsq_factor_ex(None, None, 16, 4, None, None, 1) == 1
     assert lib.lsq_destroy(None) == 0
 
 

@@ -49,3 +49,23 @@ def test_rank_deficient_is_reported(L, ctx):
     # the context stays usable
     R, _ = L.lsq_factor(ctx, to_dev(np.eye(8) + 0.1))
     assert np.isfinite(R.cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("m,d,kappa", [(70, 37, 1e2), (1024, 512, 1e6), (1200, 1024, 1e2), (4096, 300, 1e6)])
+def test_factor_double_fp32_gram(L, ctx, m, d, kappa):
+    """The Gram matrix in double-FP32 (about 45-bit operands, exact products, TwoSum sums) gives
+    the FP64 factor to near FP64 accuracy on column-scaled inputs; the Cholesky stays FP64."""
+    SA = W.make_problem(m, d, kappa, seed=d + 1)["A"]
+    R, Wm = L.lsq_factor(ctx, to_dev(SA), precision="mixed")
+    R, Wm = R.cpu().numpy(), Wm.cpu().numpy()
+    Rref = O.factor(SA)
+    colscale = np.abs(Rref).max(axis=0)
+    assert np.max(np.abs(R - Rref) / colscale) < 1e-9
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    np.testing.assert_allclose(Wm @ R, np.eye(d), atol=1e-9)
+    # an FP32-valued SA (what an FP32 sketch produces) splits exactly: the Gram is the FP64 one
+    # up to the order of the sums
+    S32 = SA.astype(np.float32).astype(np.float64)
+    R32, _ = L.lsq_factor(ctx, to_dev(S32), precision="mixed")
+    R64, _ = L.lsq_factor(ctx, to_dev(S32))
+    assert np.max(np.abs(R32.cpu().numpy() - R64.cpu().numpy()) / colscale) < 1e-10

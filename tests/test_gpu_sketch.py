@@ -100,7 +100,7 @@ def test_rejects_bad_arguments(L, ctx):
         L.lsq_sketch(ctx, A, "sjlt", 4, 0, s=5)   # s > m
 
 
-@pytest.mark.parametrize("n,m", [(256, 256), (512, 128), (300, 200)])
+@pytest.mark.parametrize("n,m", [(256, 256), (512, 128), (300, 200), (1024, 256), (800, 130)])
 def test_gaussian_bf16_tensor_core_layout(L, ctx, n, m):
     """A = I_n makes SA = S: every entry of the tensor-core product must be the BF16 rounding of
     z(j, i) (up to one BF16 step where FP32 and FP64 evaluations straddle a rounding boundary),

@@ -202,3 +202,34 @@ def test_mixed_pcg_with_bf16_gaussian_sketch(L, ctx):
     _, Wm = L.lsq_factor(ctx, L.lsq_sketch(ctx, Ad, "gauss", 1024, 0, precision="bf16"))
     x, info = L.lsq_solve(ctx, Ad, to_dev(b), "pcg", Wm, tol=1e-10, maxit=300, m=1024, precision="mixed")
     assert info["status"] == 0 and O.rel_h_err(A64, x.cpu().numpy(), xs) <= 1e-10, info
+
+
+@pytest.mark.parametrize("method,refresh,d", [("pcg", 0, 128), ("pcg", 0, 37), ("pcg", 0, 600), ("polyak", 0, 64),
+                                              ("ihs", 1, 32)])
+def test_mixed_fp32_copy_is_bit_identical(L, ctx, method, refresh, d):
+    """The FP32 copy of an FP64 A holds the values the FP32 passes narrow to, so the mixed solve
+    over it takes the same steps to the last bit as the one that narrows A in every pass, with a
+    ragged d (not a multiple of 32), a nonzero x0 and refreshed single-step launches."""
+    n, m = 9001, max(4 * d, 256)
+    P = W.make_problem(n, d, 1e5, seed=17)
+    A, b = P["A"], P["b"]
+    Ad, bd = to_dev(A), to_dev(b)
+    x0 = to_dev(np.random.default_rng(2).standard_normal(d))
+    if refresh:
+        kw = dict(refresh=1, sketch_type="gauss", seed=4)  # (SJLT sums with atomics: not bitwise repeatable)
+        Wm = None
+    else:
+        kw = {}
+        _, Wm = L.lsq_factor(ctx, L.lsq_sketch(ctx, Ad, "srht", m, 0, precision="f32"))
+    res = []
+    for copy in (0, 1, 0):
+        x, info = L.lsq_solve(ctx, Ad, bd, method, Wm, x0=x0, tol=1e-10, maxit=400, m=m, precision="mixed",
+                              a32_copy=copy, **kw)
+        assert info["a32_copy"] == copy
+        res.append((x.cpu().numpy(), info))
+    (x_0, i_0), (x_1, i_1), (x_2, i_2) = res
+    assert np.array_equal(x_0, x_2), "the solve does not repeat bit for bit"
+    assert i_0["status"] == i_1["status"] == 0
+    assert (i_0["iters"], i_0["passes"], i_0["exact_passes"]) == (i_1["iters"], i_1["passes"], i_1["exact_passes"])
+    assert np.array_equal(x_0, x_1), np.abs(x_0 - x_1).max()
+    assert i_0["est_err"] == i_1["est_err"]
