@@ -28,13 +28,14 @@ import workloads as WL  # noqa: E402
 
 SOLVE_KERNEL = "solve_kernel"
 
-# DRAM traffic of solve_kernel<double, 16, MIXED> from one ncu capture (n = 2^18, d = 512, SRHT m = 4096,
-# 26 passes; profiles/solve_kernel_mixed_262144x512_srht4096.md): dram__bytes_read.sum +
-# dram__bytes_write.sum of the launch divided by its algorithmic bytes.  Scaled to a launch of the
-# bench by its algorithmic bytes (units processed: passes x rows); reported only while the kernel's
-# sources hash to the captured ones.
-SOLVE_TRAFFIC = {"ratio": 28.013047e9 / 27917287424, "sources_sha256":
-                 "8dc7d98e44c7d98b109f2789b98f639444355ec9034528f1b97439a91ea45f4d"}
+# DRAM traffic of the mixed solve phase (narrow_copy_kernel<16> + solve_kernel<double, 16, MIXED, COPY>)
+# from one ncu capture (n = 2^18, d = 512, SRHT m = 4096, 25 passes of which 2 exact;
+# profiles/solve_kernel_mixed_262144x512_srht4096.md): dram__bytes_read.sum + dram__bytes_write.sum of
+# the two launches divided by their algorithmic bytes.  Scaled to a launch of the bench by its
+# algorithmic bytes (units processed: passes x rows); reported only while the kernels' sources hash to
+# the captured ones.
+SOLVE_TRAFFIC = {"ratio": 16142203008.0 / 16106127360, "sources_sha256":
+                 "08379d1dd8e8cd25cbd667c6c50cfbb318933db247f18d1ae0d385fd7bc569f6"}
 
 
 def solve_sources_sha256() -> str:

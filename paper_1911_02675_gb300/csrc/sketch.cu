@@ -4,6 +4,8 @@
 // randomness on the fly from Philox4x32-10; S is never stored.  Partial sums go to a
 // per-split scratch slab and a fixed-order reduction writes SA, so results repeat run
 // to run (SJLT: up to the order of its shared-memory additions).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 
 #include "apass.cuh"
@@ -297,7 +299,7 @@ __global__ void select_write_kernel(const unsigned long long* __restrict__ keys,
 // rows, which keeps all three access patterns free of bank conflicts.
 constexpr int SRHT_THREADS = 512;
 
-__device__ __forceinline__ int zphys(int row, int dc) { return (row + (row >> 4)) * dc; }
+__host__ __device__ __forceinline__ int zphys(int row, int dc) { return (row + (row >> 4)) * dc; }
 
 template <typename TC, int K>
 __device__ __forceinline__ void butterflies(TC* v) {
@@ -577,6 +579,162 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_fast_kernel(
   }
 }
 
+// The common case once more, with the block staged by the tensor memory accelerator: per
+// 2048-row block, eight 256-row x 8-column boxes of A land in shared memory as raw FP64 (or
+// FP32) elements, completion counted in bytes on an mbarrier, while the previous block's
+// radix passes and sampled second level run; the partial of SA lives in registers (thread t
+// owns sampled rows t, t + 512, ...), so the second level reads only the block.  The first
+// register stage is over row bits 7..10 (a thread holds rows q, q + 128, ..., q + 1920 of a
+// column pair, which keeps the reads from the staged block free of bank conflicts), then
+// radix passes over bits 0..3 and 4..6: the stages of a Walsh-Hadamard transform commute, so
+// this is the same transform with its FP32 additions in another order.  Every wait is
+// bounded.
+constexpr int SRHT_TMA_ROWS = 256;  // rows per box
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool srht_mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  uint32_t spins = 0;
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (++spins > (1u << 26)) {
+      atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+template <typename TA, int MY>
+__global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
+    const __grid_constant__ CUtensorMap tmap, int64_t n, int d, int64_t N1, int64_t blocks_per_group,
+    const uint32_t* __restrict__ signbits, const int64_t* __restrict__ rows, int m, float* __restrict__ part,
+    int* err) {
+  constexpr int DC = 8, LOGN2 = 11, N2 = 1 << LOGN2;
+  constexpr uint32_t STAGE_BYTES = N2 * DC * sizeof(TA);
+  using T2 = typename std::conditional<sizeof(TA) == 8, double2, float2>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the staged block starts on a 1024-byte boundary (tensor copies want 128-byte aligned
+  // destinations); the launch adds 1 KB for the offset
+  unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  const TA* stage = reinterpret_cast<const TA*>(base);                    // [N2][DC] as the boxes land
+  float* Z = reinterpret_cast<float*>(base + STAGE_BYTES);                // padded [N2][DC]
+  uint32_t* k1s = reinterpret_cast<uint32_t*>(Z + (size_t)zphys(N2, DC));  // [m]
+  uint16_t* k2s = reinterpret_cast<uint16_t*>(k1s + m);                   // [m]
+  uint32_t* sgn = reinterpret_cast<uint32_t*>(k2s + ((m + 1) & ~1));      // [N2 / 32] signs of the block
+  __shared__ __align__(8) uint64_t full;
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * DC;
+  const int64_t b_begin = (int64_t)blockIdx.y * blocks_per_group;
+  const int64_t b_end = min(N1, b_begin + blocks_per_group);
+  for (int s = tid; s < m; s += SRHT_THREADS) {
+    const int64_t k = rows[s];
+    k1s[s] = (uint32_t)(k >> LOGN2);
+    k2s[s] = (uint16_t)(k & (N2 - 1));
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // thread 0 starts the eight box copies of block `blk` (rows past n and columns past d read 0)
+  auto issue = [&](int64_t blk) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&full)), "r"(STAGE_BYTES)
+                 : "memory");
+#pragma unroll
+    for (int k = 0; k < N2 / SRHT_TMA_ROWS; ++k) {
+      const int32_t x = c0, y = (int32_t)(blk * N2 + k * SRHT_TMA_ROWS);
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+              smem_addr(stage + (size_t)k * SRHT_TMA_ROWS * DC)),
+          "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(y), "r"(smem_addr(&full))
+          : "memory");
+    }
+  };
+  if (tid == 0 && b_begin < b_end) issue(b_begin);
+
+  float y[MY][DC];
+#pragma unroll
+  for (int i = 0; i < MY; ++i)
+#pragma unroll
+    for (int c = 0; c < DC; ++c) y[i][c] = 0.f;
+  const int qq = tid >> 2, pc = tid & 3;  // rows qq + 128 j, columns 2 pc, 2 pc + 1
+  bool ok = true;
+  int64_t issued = b_begin < b_end ? 1 : 0, waited = 0;
+  for (int64_t i1 = b_begin; i1 < b_end; ++i1) {
+    // the block's sign bits (rows past n carry no data)
+    if (tid < N2 / 32) {
+      const int64_t r = i1 * N2 + 32 * tid;
+      sgn[tid] = r < n ? __ldg(signbits + (r >> 5)) : 0u;
+    }
+    ok = ok && srht_mbar_wait(&full, (uint32_t)((i1 - b_begin) & 1), err);
+    // Z is free (the previous second level is done) and the block has landed everywhere
+    if (__syncthreads_or(!ok)) break;
+    ++waited;
+    {
+      float v0[16], v1[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int r = qq + 128 * j;
+        const T2 x = *reinterpret_cast<const T2*>(stage + r * DC + 2 * pc);
+        const uint32_t neg = ((sgn[r >> 5] >> (r & 31)) & 1u) << 31;
+        v0[j] = __uint_as_float(__float_as_uint(lsq_apass::narrow_f32(x.x)) ^ neg);
+        v1[j] = __uint_as_float(__float_as_uint(lsq_apass::narrow_f32(x.y)) ^ neg);
+      }
+      butterflies<float, 4>(v0);
+      butterflies<float, 4>(v1);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        *reinterpret_cast<float2*>(Z + zphys(qq + 128 * j, DC) + 2 * pc) = make_float2(v0[j], v1[j]);
+    }
+    __syncthreads();  // the staged block is consumed: the next one may land
+    if (tid == 0 && i1 + 1 < b_end) {
+      issue(i1 + 1);
+      ++issued;
+    }
+    radix_pass<float, DC, 4>(Z, N2, 0);
+    __syncthreads();
+    radix_pass<float, DC, 3>(Z, N2, 4);
+    __syncthreads();
+    const uint32_t i1w = (uint32_t)i1;
+#pragma unroll
+    for (int i = 0; i < MY; ++i) {
+      const int s = tid + SRHT_THREADS * i;
+      if (s < m) {
+        const bool neg = (__popc(k1s[s] & i1w) & 1) != 0;
+        const float4* zr = reinterpret_cast<const float4*>(Z + zphys(k2s[s], DC));
+        const float4 za = zr[0], zb = zr[1];
+        y[i][0] += neg ? -za.x : za.x;
+        y[i][1] += neg ? -za.y : za.y;
+        y[i][2] += neg ? -za.z : za.z;
+        y[i][3] += neg ? -za.w : za.w;
+        y[i][4] += neg ? -zb.x : zb.x;
+        y[i][5] += neg ? -zb.y : zb.y;
+        y[i][6] += neg ? -zb.z : zb.z;
+        y[i][7] += neg ? -zb.w : zb.w;
+      }
+    }
+  }
+  if (!ok && tid == 0 && issued > waited) {
+    // a failed wait may leave a copy in flight: give it (bounded) time to land before exit
+    (void)srht_mbar_wait(&full, (uint32_t)((issued - 1) & 1), err);
+  }
+  float* out = part + (int64_t)blockIdx.y * m * d;
+#pragma unroll
+  for (int i = 0; i < MY; ++i) {
+    const int s = tid + SRHT_THREADS * i;
+    if (s < m)
+#pragma unroll
+      for (int c = 0; c < DC; ++c)
+        if (c0 + c < d) out[(int64_t)s * d + c0 + c] = ok ? y[i][c] : 0.f;
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // SJLT: s distinct rows per column of S by Lemire's method on successive Philox words,
 // then a shared-memory scatter of each data row into its s target rows.
@@ -735,15 +893,79 @@ static size_t srht_smem_bytes(int logN2, int m, int dc, size_t es) {
   return (N2 + (N2 >> 4) + 1) * dc * es + (size_t)m * dc * es + (size_t)m * 6 + 64;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    (void)cudaGetLastError();
+  }
+  return fn;
+}
+
+// the TMA-staged kernel of the common case, when A's layout allows tensor copies (16-byte
+// aligned base and row stride) and the sampled rows fit 8 register rows per thread; returns
+// false (nothing launched) otherwise
+template <typename TA>
+static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1, const uint32_t* signbits,
+                            const int64_t* rows, float* part, int groups, int64_t blocks_per_group, int* err,
+                            lsq_status* st) {
+  constexpr int DC = 8, N2 = 2048;
+  const size_t es = sizeof(TA);
+  if (m > 8 * SRHT_THREADS) return false;
+  if (((uintptr_t)A->data % 16) != 0 || ((size_t)A->ld * es) % 16 != 0) return false;
+  const size_t smem = 1024 + (size_t)N2 * DC * es + (size_t)zphys(N2, DC) * 4 + (size_t)m * 4 +
+                      (size_t)((m + 1) & ~1) * 2 + (N2 / 32) * 4;
+  if (smem > 232448 - 1024) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  CUtensorMap tm;
+  const cuuint64_t dims[2] = {(cuuint64_t)A->d, (cuuint64_t)A->n};
+  const cuuint64_t strides[1] = {(cuuint64_t)A->ld * es};
+  const cuuint32_t box[2] = {(cuuint32_t)DC, (cuuint32_t)SRHT_TMA_ROWS};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&tm, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(A->data),
+          dims, strides,
+          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  const int d = (int)A->d;
+  const dim3 grid(lsq_ceil_div(d, DC), groups);
+  auto launch = [&](auto kern) -> lsq_status {
+    LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, SRHT_THREADS, smem, ctx->stream>>>(tm, A->n, d, N1, blocks_per_group, signbits, rows, m, part, err);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+  };
+  const int my = (m + SRHT_THREADS - 1) / SRHT_THREADS;
+  if (my <= 1) *st = launch(srht_tma_kernel<TA, 1>);
+  else if (my <= 2) *st = launch(srht_tma_kernel<TA, 2>);
+  else if (my <= 4) *st = launch(srht_tma_kernel<TA, 4>);
+  else *st = launch(srht_tma_kernel<TA, 8>);
+  return true;
+}
+
 template <typename TC, int DC>
 static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN2, int64_t N1,
                               const uint32_t* signbits, const int64_t* rows, TC* part, int groups,
-                              int64_t blocks_per_group) {
+                              int64_t blocks_per_group, int* err, bool& staged) {
   const int d = (int)A->d;
   const size_t smem = srht_smem_bytes(logN2, m, DC, sizeof(TC));
   dim3 grid(lsq_ceil_div(d, DC), groups);
   if constexpr (sizeof(TC) == 4 && DC == 8) {
     if (logN2 == 11) {
+      lsq_status st = LSQ_OK;
+      float* pf = reinterpret_cast<float*>(part);
+      staged = A->dtype == LSQ_F64
+                   ? srht_tma_launch<double>(ctx, A, m, N1, signbits, rows, pf, groups, blocks_per_group, err, &st)
+                   : srht_tma_launch<float>(ctx, A, m, N1, signbits, rows, pf, groups, blocks_per_group, err, &st);
+      if (staged) return st;
       const size_t es = A->dtype == LSQ_F64 ? 8 : 4;
       const size_t vb = 2 * es;  // bytes of one column pair
       const int vec_ok = (((uintptr_t)A->data % vb) == 0 && ((size_t)A->ld * es) % vb == 0) ? 1 : 0;
@@ -801,7 +1023,7 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
   const int64_t nscan = (N + SCAN_BLOCK - 1) / SCAN_BLOCK;
   size_t need = lsq_align256((size_t)N * 8) + lsq_align256((size_t)((N + 31) / 32) * 4) + lsq_align256(65536 * 4) +
                 lsq_align256(4 * 8) + 2 * lsq_align256((size_t)nscan * 4) + lsq_align256((size_t)m * 8) +
-                lsq_align256((size_t)groups * m * d * sizeof(TC));
+                lsq_align256((size_t)groups * m * d * sizeof(TC)) + lsq_align256(4);
   lsq_status st = lsq_ensure_scratch(ctx, need);
   if (st != LSQ_OK) return st;
   Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};
@@ -813,9 +1035,11 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
   unsigned* cnt_eq = cv.take<unsigned>(nscan);
   int64_t* rows = cv.take<int64_t>(m);
   TC* part = cv.take<TC>((size_t)groups * m * d);
+  int* err = cv.take<int>(1);
 
   unsigned long long init_state[4] = {0ull, (unsigned long long)m, 0ull, 0ull};
   LSQ_CUDA_TRY(cudaMemsetAsync(hist, 0, 65536 * 4, ctx->stream));
+  LSQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
   LSQ_CUDA_TRY(cudaMemcpyAsync(state, init_state, sizeof(init_state), cudaMemcpyHostToDevice, ctx->stream));
   srht_keys_kernel<<<grid_for(N, 256, 8 * ctx->sm_count), 256, 0, ctx->stream>>>(N, seed, t, keys, signbits, hist);
   LSQ_LAUNCH_CHECK();
@@ -834,17 +1058,24 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
   select_write_kernel<<<(unsigned)nscan, SCAN_BLOCK, 0, ctx->stream>>>(keys, N, state, cnt_lt, cnt_eq, rows, m);
   LSQ_LAUNCH_CHECK();
 
+  bool staged = false;
   switch (DC) {
-    case 8: st = srht_launch<TC, 8>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group); break;
-    case 4: st = srht_launch<TC, 4>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group); break;
-    case 2: st = srht_launch<TC, 2>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group); break;
-    default: st = srht_launch<TC, 1>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group); break;
+    case 8: st = srht_launch<TC, 8>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, staged); break;
+    case 4: st = srht_launch<TC, 4>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, staged); break;
+    case 2: st = srht_launch<TC, 2>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, staged); break;
+    default: st = srht_launch<TC, 1>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, staged); break;
   }
   if (st != LSQ_OK) return st;
   const int64_t md = (int64_t)m * d;
   reduce_splits_kernel<TC><<<grid_for(md, 256, 4 * ctx->sm_count), 256, 0, ctx->stream>>>(
       part, (int)groups, md, 1.0 / sqrt((double)m), SA);
   LSQ_LAUNCH_CHECK();
+  if (staged) {
+    // a timed-out wait on a staged block is reported here
+    LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 14, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    LSQ_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (ctx->host_status[14]) return (lsq_status)ctx->host_status[14];
+  }
   return LSQ_OK;
 }
 
@@ -885,7 +1116,7 @@ static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint
   const int64_t rows_per_group = (n + groups - 1) / groups;
   groups = (n + rows_per_group - 1) / rows_per_group;
   size_t need = lsq_align256((size_t)n * s * 4) + lsq_align256((size_t)n * 4) +
-                lsq_align256((size_t)groups * m * d * sizeof(TC));
+                lsq_align256((size_t)groups * m * d * sizeof(TC)) + lsq_align256(4);
   lsq_status st = lsq_ensure_scratch(ctx, need);
   if (st != LSQ_OK) return st;
   Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};

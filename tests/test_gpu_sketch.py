@@ -62,6 +62,24 @@ def test_srht_fp64(L, ctx, n, d, m, seed):
     assert rel_fro(SA32, O.sketch_srht(A, m, seed)) < 5e-6
 
 
+@pytest.mark.parametrize("n,d,m,dtype,ld", [(5000, 13, 700, np.float64, 14), (5000, 13, 700, np.float32, 16),
+                                             (9000, 24, 4096, np.float64, 24), (9000, 24, 4097, np.float64, 24),
+                                             (3000, 20, 300, np.float64, 21), (2048, 8, 64, np.float64, 8)])
+def test_srht_fp32_arithmetic_layouts(L, ctx, n, d, m, dtype, ld):
+    """FP32-arithmetic SRHT over row strides and sizes that take the staged (tensor-copy) kernel
+    -- ragged n and d, FP32 storage, 8 sampled rows per thread -- and ones that do not (more
+    than 4096 sampled rows, a row stride that is not a multiple of 16 bytes)."""
+    A = W.make_problem(n, d, 1e4, seed=n + d)["A"].astype(dtype)
+    big = torch.zeros((n, ld), dtype=torch.float64 if dtype == np.float64 else torch.float32, device="cuda")
+    big[:, :d] = to_dev(A)
+    SA = L.lsq_sketch(ctx, big[:, :d], "srht", m, 5, t=2, precision="f32").cpu().numpy()
+    ref = O.sketch_srht(A.astype(np.float64), m, 5, 2)
+    assert rel_fro(SA, ref) < 5e-6
+    # repeatable bit for bit
+    SA2 = L.lsq_sketch(ctx, big[:, :d], "srht", m, 5, t=2, precision="f32").cpu().numpy()
+    assert np.array_equal(SA, SA2)
+
+
 @pytest.mark.parametrize("n,d,m,s,seed,t", [(100, 4, 10, 3, 1, 0), (5000, 33, 64, 8, 2, 2), (20000, 130, 512, 8, 3, 0),
                                             (3000, 9, 7, 7, 5, 1), (1000, 2, 40, 1, 6, 0)])
 def test_sjlt_positions_bit_exact(L, ctx, n, d, m, s, seed, t):
