@@ -28,14 +28,15 @@ import workloads as WL  # noqa: E402
 
 SOLVE_KERNEL = "solve_kernel"
 
-# DRAM traffic of the mixed solve phase (narrow_copy_kernel<16> + solve_kernel<double, 16, MIXED, COPY>)
-# from one ncu capture (n = 2^18, d = 512, SRHT m = 4096, 25 passes of which 2 exact;
-# profiles/solve_kernel_mixed_262144x512_srht4096.md): dram__bytes_read.sum + dram__bytes_write.sum of
-# the two launches divided by their algorithmic bytes.  Scaled to a launch of the bench by its
-# algorithmic bytes (units processed: passes x rows); reported only while the kernels' sources hash to
-# the captured ones.
-SOLVE_TRAFFIC = {"ratio": 16142203008.0 / 16106127360, "sources_sha256":
-                 "08379d1dd8e8cd25cbd667c6c50cfbb318933db247f18d1ae0d385fd7bc569f6"}
+# DRAM traffic of the mixed solve phase from one ncu capture (n = 2^18, d = 512, SRHT m = 4096, 25 passes
+# of which 2 exact; profiles/solve_kernel_mixed_262144x512_srht4096.md): dram__bytes_read.sum +
+# dram__bytes_write.sum divided by the algorithmic bytes, for solve_kernel<double, 16, MIXED, COPY> alone
+# (the FP32 copy supplied by the sketch) and with the solve's own narrow_copy_kernel<16>.  Scaled to a
+# launch of the bench by its algorithmic bytes (units processed: passes x rows); reported only while the
+# kernels' sources hash to the captured ones.
+SOLVE_TRAFFIC = {"ratio_solve": (14.553369e9 + 0.035296768e9) / 14495514624,
+                 "ratio_with_copy": 16142203008.0 / 16106127360, "sources_sha256":
+                 "76ae7aef4829a57935c1877664b65173d25e0b417dcda9455b9c88bb7c5f7c5d"}
 
 
 def solve_sources_sha256() -> str:
@@ -272,11 +273,15 @@ def run_ours(args):
     ctx = L.Context(dev)
     stream = torch.cuda.current_stream(dev)
 
+    # mixed precision over FP64 A: the sketch also writes the FP32 narrowing of A that the solve's
+    # FP32 passes stream (a caller-owned buffer, like SA, W and x)
+    a32 = L.narrow_buffer(A) if (args.precision == "mixed" and A.dtype == torch.float64) else None
+
     def solve_once(Ad, bd):
-        SA = L.lsq_sketch(ctx, Ad, args.sketch, args.m, 0, precision=args.sketch_precision)
+        SA = L.lsq_sketch(ctx, Ad, args.sketch, args.m, 0, precision=args.sketch_precision, a32=a32)
         _, Wm = L.lsq_factor(ctx, SA, precision=args.precision)
         x, info = L.lsq_solve(ctx, Ad, bd, "pcg", Wm, tol=args.tol, maxit=1000, m=args.m,
-                              precision=args.precision)
+                              precision=args.precision, a32=a32)
         return x, info
 
     for _ in range(args.warmup):
@@ -309,11 +314,13 @@ def run_ours(args):
     exact_passes = statistics.median(i["exact_passes"] for i in infos)
     iters = statistics.median(i["iters"] for i in infos)
     pass_bytes = n * d * A.element_size()
-    a32_copy = bool(infos[-1]["a32_copy"])
+    a32_copy = int(infos[-1]["a32_copy"])
     if a32_copy:
-        # one FP32 copy of A (read 8, write 4 bytes an element), FP32 passes over the copy,
-        # exact residual passes over A
-        solve_bytes = n * d * 12 + (passes - exact_passes) * n * d * 4 + exact_passes * pass_bytes
+        # FP32 passes over the FP32 copy of A, exact residual passes over A, plus (when the solve
+        # made the copy itself) one read of A and one write of the copy
+        solve_bytes = (passes - exact_passes) * n * d * 4 + exact_passes * pass_bytes
+        if a32_copy == 1:
+            solve_bytes += n * d * 12
     else:
         solve_bytes = passes * pass_bytes
     achieved = solve_bytes / (solve_ms * 1e-3) / 1e9
@@ -370,9 +377,9 @@ def run_ours(args):
         cpu = {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
 
     traffic = None
-    if (args.precision == "mixed" and args.a_dtype == "f64" and d == 512
+    if (args.precision == "mixed" and args.a_dtype == "f64" and d == 512 and a32_copy
             and solve_sources_sha256() == SOLVE_TRAFFIC["sources_sha256"]):
-        traffic = SOLVE_TRAFFIC["ratio"] * solve_bytes
+        traffic = SOLVE_TRAFFIC["ratio_solve" if a32_copy == 2 else "ratio_with_copy"] * solve_bytes
 
     if rank == 0:
         clocks = clk.summary()

@@ -115,6 +115,14 @@ typedef struct {
                         the iteration index for refreshed embeddings */
   int32_t s;         /* SJLT nonzeros per column of S, 1..32 (default 8); ignored otherwise */
   int32_t precision; /* lsq_sketch_precision (default LSQ_SKETCH_F64) */
+  float* a32;        /* optional, FP64 A only: device, caller-owned n x ld32 FP32 buffer that
+                        receives the FP32 narrowing of A (mantissa truncation, clamped
+                        exponent), the values the FP32 passes of a mixed solve compute with;
+                        hand it to lsq_solve through lsq_solve_opts.a32 so that the solve need
+                        not make its own copy.  The FP32 SRHT writes it while it streams A;
+                        other sketches add one pass.  NULL (zero-initialised opts) = none. */
+  int64_t ld32;      /* row stride of a32 in elements: >= d and a multiple of 4; a32 16-byte
+                        aligned (else LSQ_ERR_ARG) */
 } lsq_sketch_opts;
 
 /* ---------------------------------------------------------------------------------
@@ -190,6 +198,10 @@ typedef struct {
   int32_t x0_zero;     /* 1: x0 is zero, so the initial residual b - H x0 = b needs no pass over A */
   int32_t fcg_k;       /* LSQ_FCG: directions kept for orthogonalisation; < 0 (default) keeps
                           all of them (GCC), 1 gives IPCG, k gives FCG(k) */
+  const float* a32;    /* optional: the FP32 narrowing of A (lsq_sketch_opts.a32), row stride
+                          ld32; MIXED solves of FP64 A stream it instead of making a copy.  The
+                          caller guarantees it holds the narrowing of this A.  NULL = none. */
+  int64_t ld32;
   int32_t a32_copy;    /* MIXED PCG / IHS with FP64 A and maxit >= 3: 1 (default) makes an FP32
                           copy of A once per call (n x ceil32(d) x 4 bytes of device memory,
                           kept by the context for later calls) that the FP32 passes read
@@ -208,7 +220,8 @@ typedef struct {
   double est_err;       /* final stopping quantity sqrt((1+sqrt(rho))^2 r^T H_S^-1 r / <b,x>) */
   double ms_total;      /* device time of the whole call (ms), CUDA events */
   double ms_sketch;     /* refreshed only: time in sketch + factor (ms) */
-  int32_t a32_copy;     /* 1 when the FP32 passes read an FP32 copy of A (opts->a32_copy) */
+  int32_t a32_copy;     /* FP32 passes over an FP32 copy of A: 1 made by this call
+                           (opts->a32_copy), 2 the caller's (opts->a32); 0 none */
   int32_t reserved;
 } lsq_solve_info;
 

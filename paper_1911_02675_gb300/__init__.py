@@ -53,7 +53,8 @@ class LsqMatrix(ctypes.Structure):
 
 
 class LsqSketchOpts(ctypes.Structure):
-    _fields_ = [("t", ctypes.c_uint32), ("s", ctypes.c_int32), ("precision", ctypes.c_int32)]
+    _fields_ = [("t", ctypes.c_uint32), ("s", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("a32", ctypes.c_void_p), ("ld32", ctypes.c_int64)]
 
 
 class LsqSolveOpts(ctypes.Structure):
@@ -61,7 +62,8 @@ class LsqSolveOpts(ctypes.Structure):
                 ("refresh", ctypes.c_int32), ("sketch_type", ctypes.c_int32), ("m", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("s", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("refresh_every", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("x0_zero", ctypes.c_int32),
-                ("fcg_k", ctypes.c_int32), ("a32_copy", ctypes.c_int32)]
+                ("fcg_k", ctypes.c_int32), ("a32", ctypes.c_void_p), ("ld32", ctypes.c_int64),
+                ("a32_copy", ctypes.c_int32)]
 
 
 class LsqProblem(ctypes.Structure):
@@ -211,12 +213,28 @@ def lsq_destroy(ctx: Context) -> None:
     ctx.close()
 
 
+def _check_a32(A: torch.Tensor, a32: torch.Tensor):
+    if (a32.dtype != torch.float32 or not a32.is_cuda or a32.dim() != 2 or a32.shape[0] != A.shape[0]
+            or a32.shape[1] < A.shape[1] or a32.stride(1) != 1 or a32.stride(0) % 4):
+        raise ValueError("a32 must be a CUDA float32 n x (>= d) matrix with a row stride that is a multiple of 4")
+
+
+def narrow_buffer(A: torch.Tensor) -> torch.Tensor:
+    """An uninitialised buffer of the shape lsq_sketch(..., a32=) fills (n x ceil32(d) FP32)."""
+    return torch.empty((A.shape[0], (A.shape[1] + 31) // 32 * 32), dtype=torch.float32, device=A.device)
+
+
 def lsq_sketch(ctx: Context, A: torch.Tensor, kind: str, m: int, seed: int, t: int = 0, s: int = 8,
-               precision: str = "f64", out: torch.Tensor | None = None) -> torch.Tensor:
+               precision: str = "f64", out: torch.Tensor | None = None, a32: torch.Tensor | None = None) -> torch.Tensor:
+    """SA (m x d FP64).  With `a32` (FP64 A), also writes the FP32 narrowing of A into it for a later
+    mixed lsq_solve(..., a32=a32)."""
     ctx.sync_stream()
     M = as_matrix(A)
     SA = out if out is not None else torch.empty((m, A.shape[1]), dtype=torch.float64, device=A.device)
-    opts = LsqSketchOpts(t, s, SKETCH_PRECISION[precision])
+    opts = LsqSketchOpts(t, s, SKETCH_PRECISION[precision], None, 0)
+    if a32 is not None:
+        _check_a32(A, a32)
+        opts.a32, opts.ld32 = a32.data_ptr(), a32.stride(0)
     st = _L.lsq_sketch(ctx.handle, ctypes.byref(M), SKETCH[kind], m, seed, ctypes.byref(opts), _ptr(SA))
     if st:
         raise LsqError(st, "lsq_sketch")
@@ -264,7 +282,11 @@ def lsq_solve(ctx: Context, A: torch.Tensor, b: torch.Tensor, method: str, W: to
         raise ValueError("W must be a contiguous d x d float64 tensor")
     if x0 is None:
         opts.setdefault("x0_zero", 1)
+    a32 = opts.pop("a32", None)
     o = solve_opts(**opts)
+    if a32 is not None:
+        _check_a32(A, a32)
+        o.a32, o.ld32 = a32.data_ptr(), a32.stride(0)
     info = LsqSolveInfo()
     st = _L.lsq_solve(ctx.handle, ctypes.byref(M), _ptr(b), METHOD[method], _ptr(W), _ptr(x), float(tol), int(maxit),
                       ctypes.byref(o), ctypes.byref(info))

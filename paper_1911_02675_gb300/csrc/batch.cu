@@ -1118,6 +1118,8 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     so.t = (uint32_t)p;
     so.s = (int)std::min<int64_t>(o.s > 0 ? o.s : 8, m);  // an SJLT column has at most m nonzeros
     so.precision = o.sketch_precision;
+    so.a32 = nullptr;
+    so.ld32 = 0;
     double* SA = reinterpret_cast<double*>(base + sa_off[p]);
     st = lsq_sketch(ctx, &probs[p].A, o.sketch_type, m, o.seed, &so, SA);
     if (st != LSQ_OK) return st;

@@ -55,6 +55,8 @@ void lsq_count_launch();
 lsq_status lsq_ensure_scratch(lsq_ctx* ctx, size_t bytes);
 lsq_status lsq_ensure_state(lsq_ctx* ctx, size_t bytes);
 lsq_status lsq_ensure_a32(lsq_ctx* ctx, size_t bytes);
+// a32[i * ld32 + c] = FP32 narrowing of A[i][c] (FP64 A), on the context's stream (solve.cu)
+lsq_status lsq_narrow_copy(lsq_ctx* ctx, const lsq_matrix* A, float* a32, int64_t ld32);
 
 // Factorisations of many sketches (batched solves): W_p = R_p^{-1} and W_p^T; status_out[p]
 // (host) = LSQ_OK or LSQ_ERR_RANK; the Gram matrices in double-FP32 when df_gram.

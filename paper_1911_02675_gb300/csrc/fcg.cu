@@ -293,6 +293,8 @@ lsq_status lsq_fcg_solve(lsq_ctx* ctx, const lsq_matrix* A, const double* b, con
   lsq_sketch_opts so;
   so.s = o.s > 0 ? o.s : 8;
   so.precision = mixed ? LSQ_SKETCH_F32 : LSQ_SKETCH_F64;
+  so.a32 = nullptr;
+  so.ld32 = 0;
   int status = LSQ_ERR_MAXIT, t = 0;
   double est = 0.0, ms_sketch = 0.0;
   cudaEvent_t e_a, e_b;

@@ -178,37 +178,76 @@ __global__ void radix_hist_kernel(const unsigned long long* __restrict__ keys, i
   }
 }
 
-// one CTA of 1024 threads: finds the bucket holding rank `need`, clears the histogram
-__global__ void radix_pick_kernel(unsigned* __restrict__ hist, unsigned long long* __restrict__ state) {
-  __shared__ unsigned long long part[1024];
-  __shared__ int found;
-  const int tid = threadIdx.x;
+// one CTA of 1024 threads: finds the bucket holding rank `need`, clears the histogram.
+// Thread t sums buckets [64 t, 64 t + 64) (16-byte loads), the CTA scans the 1024 partial
+// counts (warp shuffles, then the 32 warp totals), and warp 0 scans the 64 buckets of the
+// thread whose range holds rank `need`.
+__global__ void __launch_bounds__(1024) radix_pick_kernel(unsigned* __restrict__ hist,
+                                                          unsigned long long* __restrict__ state) {
+  __shared__ unsigned long long wsum[32];
+  __shared__ int owner;
+  __shared__ unsigned long long owner_before;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint4* hp = reinterpret_cast<const uint4*>(hist) + tid * 16;
   unsigned long long local = 0;
-  for (int b = tid * 64; b < tid * 64 + 64; ++b) local += hist[b];
-  part[tid] = local;
-  if (tid == 0) found = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const uint4 q = hp[k];
+    local += (unsigned long long)q.x + q.y + q.z + q.w;
+  }
+  // inclusive scan of the per-thread counts
+  unsigned long long inc = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[w] = inc;
+  if (tid == 0) owner = -1;
   __syncthreads();
-  if (tid == 0) {
-    unsigned long long need = state[1], below = state[2], cum = 0;
-    for (int g = 0; g < 1024 && !found; ++g) {
-      if (cum + part[g] >= need) {
-        for (int b = g * 64; b < g * 64 + 64; ++b) {
-          if (cum + hist[b] >= need) {
-            state[0] = (state[0] << 16) | (unsigned long long)b;
-            state[1] = need - cum;
-            state[2] = below + cum;
-            found = 1;
-            break;
-          }
-          cum += hist[b];
-        }
-      } else {
-        cum += part[g];
-      }
+  if (w == 0) {
+    unsigned long long x = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    wsum[lane] = x;  // inclusive over warps
+  }
+  __syncthreads();
+  const unsigned long long before = (w > 0 ? wsum[w - 1] : 0ull) + inc - local;
+  const unsigned long long need = state[1], below = state[2];
+  if (before < need && need <= before + local) {
+    owner = tid;
+    owner_before = before;
+  }
+  __syncthreads();
+  if (w == 0 && owner >= 0) {
+    // warp 0 walks the owner's 64 buckets: two per lane, one warp scan, first crossing by ballot
+    const int t = owner;
+    const unsigned h0 = hist[64 * t + 2 * lane], h1 = hist[64 * t + 2 * lane + 1];
+    unsigned long long x = (unsigned long long)h0 + h1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const unsigned long long ex = owner_before + x - h0 - h1;  // before bucket 2 lane
+    const bool hit0 = ex + h0 >= need, hit1 = ex + h0 + h1 >= need;
+    const unsigned m0 = __ballot_sync(0xffffffffu, hit0), m1 = __ballot_sync(0xffffffffu, hit1);
+    const int l0 = m0 ? __ffs(m0) - 1 : 32, l1 = m1 ? __ffs(m1) - 1 : 32;
+    // the first bucket whose running count reaches `need`
+    const int bkt = l0 <= l1 ? 2 * l0 : 2 * l1 + 1;
+    if (lane == (bkt >> 1)) {
+      const unsigned long long cum = (bkt & 1) ? ex + h0 : ex;
+      state[0] = (state[0] << 16) | (unsigned long long)(64 * t + bkt);
+      state[1] = need - cum;
+      state[2] = below + cum;
     }
   }
   __syncthreads();
-  for (int b = tid; b < 65536; b += 1024) hist[b] = 0u;
+  uint4* hw = reinterpret_cast<uint4*>(hist);
+  for (int k = tid; k < 65536 / 4; k += 1024) hw[k] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 constexpr int SCAN_BLOCK = 1024;
@@ -614,7 +653,7 @@ template <typename TA, int MY>
 __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
     const __grid_constant__ CUtensorMap tmap, int64_t n, int d, int64_t N1, int64_t blocks_per_group,
     const uint32_t* __restrict__ signbits, const int64_t* __restrict__ rows, int m, float* __restrict__ part,
-    int* err) {
+    int* err, float* __restrict__ a32, int64_t ld32) {
   constexpr int DC = 8, LOGN2 = 11, N2 = 1 << LOGN2;
   constexpr uint32_t STAGE_BYTES = N2 * DC * sizeof(TA);
   using T2 = typename std::conditional<sizeof(TA) == 8, double2, float2>::type;
@@ -682,9 +721,20 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
       for (int j = 0; j < 16; ++j) {
         const int r = qq + 128 * j;
         const T2 x = *reinterpret_cast<const T2*>(stage + r * DC + 2 * pc);
+        const float f0 = lsq_apass::narrow_f32(x.x), f1 = lsq_apass::narrow_f32(x.y);
+        if (a32 != nullptr) {
+          // the FP32 copy of A on the way (the narrowing of the solve's FP32 passes)
+          const int64_t rg = i1 * N2 + r;
+          const int cg = c0 + 2 * pc;
+          if (rg < n) {
+            float* o = a32 + rg * ld32 + cg;
+            if (cg + 1 < d) __stcs(reinterpret_cast<float2*>(o), make_float2(f0, f1));
+            else if (cg < d) __stcs(o, f0);
+          }
+        }
         const uint32_t neg = ((sgn[r >> 5] >> (r & 31)) & 1u) << 31;
-        v0[j] = __uint_as_float(__float_as_uint(lsq_apass::narrow_f32(x.x)) ^ neg);
-        v1[j] = __uint_as_float(__float_as_uint(lsq_apass::narrow_f32(x.y)) ^ neg);
+        v0[j] = __uint_as_float(__float_as_uint(f0) ^ neg);
+        v1[j] = __uint_as_float(__float_as_uint(f1) ^ neg);
       }
       butterflies<float, 4>(v0);
       butterflies<float, 4>(v1);
@@ -915,7 +965,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 template <typename TA>
 static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1, const uint32_t* signbits,
                             const int64_t* rows, float* part, int groups, int64_t blocks_per_group, int* err,
-                            lsq_status* st) {
+                            float* a32, int64_t ld32, lsq_status* st) {
   constexpr int DC = 8, N2 = 2048;
   const size_t es = sizeof(TA);
   if (m > 8 * SRHT_THREADS) return false;
@@ -939,7 +989,8 @@ static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1
   const dim3 grid(lsq_ceil_div(d, DC), groups);
   auto launch = [&](auto kern) -> lsq_status {
     LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, SRHT_THREADS, smem, ctx->stream>>>(tm, A->n, d, N1, blocks_per_group, signbits, rows, m, part, err);
+    kern<<<grid, SRHT_THREADS, smem, ctx->stream>>>(tm, A->n, d, N1, blocks_per_group, signbits, rows, m, part, err,
+                                                     a32, ld32);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
   };
@@ -954,7 +1005,7 @@ static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1
 template <typename TC, int DC>
 static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN2, int64_t N1,
                               const uint32_t* signbits, const int64_t* rows, TC* part, int groups,
-                              int64_t blocks_per_group, int* err, bool& staged) {
+                              int64_t blocks_per_group, int* err, float* a32, int64_t ld32, bool& staged) {
   const int d = (int)A->d;
   const size_t smem = srht_smem_bytes(logN2, m, DC, sizeof(TC));
   dim3 grid(lsq_ceil_div(d, DC), groups);
@@ -963,8 +1014,10 @@ static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN
       lsq_status st = LSQ_OK;
       float* pf = reinterpret_cast<float*>(part);
       staged = A->dtype == LSQ_F64
-                   ? srht_tma_launch<double>(ctx, A, m, N1, signbits, rows, pf, groups, blocks_per_group, err, &st)
-                   : srht_tma_launch<float>(ctx, A, m, N1, signbits, rows, pf, groups, blocks_per_group, err, &st);
+                   ? srht_tma_launch<double>(ctx, A, m, N1, signbits, rows, pf, groups, blocks_per_group, err, a32,
+                                             ld32, &st)
+                   : srht_tma_launch<float>(ctx, A, m, N1, signbits, rows, pf, groups, blocks_per_group, err, nullptr,
+                                            0, &st);
       if (staged) return st;
       const size_t es = A->dtype == LSQ_F64 ? 8 : 4;
       const size_t vb = 2 * es;  // bytes of one column pair
@@ -995,7 +1048,8 @@ static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN
 }
 
 template <typename TC>
-static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA) {
+static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
+                           float* a32, int64_t ld32, bool& a32_done) {
   const int d = (int)A->d;
   int64_t N = 1;
   int logN = 0;
@@ -1060,16 +1114,21 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
 
   bool staged = false;
   switch (DC) {
-    case 8: st = srht_launch<TC, 8>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, staged); break;
-    case 4: st = srht_launch<TC, 4>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, staged); break;
-    case 2: st = srht_launch<TC, 2>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, staged); break;
-    default: st = srht_launch<TC, 1>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, staged); break;
+    case 8: st = srht_launch<TC, 8>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, a32,
+                                  ld32, staged); break;
+    case 4: st = srht_launch<TC, 4>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, a32,
+                                  ld32, staged); break;
+    case 2: st = srht_launch<TC, 2>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, a32,
+                                  ld32, staged); break;
+    default: st = srht_launch<TC, 1>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, a32,
+                                  ld32, staged); break;
   }
   if (st != LSQ_OK) return st;
   const int64_t md = (int64_t)m * d;
   reduce_splits_kernel<TC><<<grid_for(md, 256, 4 * ctx->sm_count), 256, 0, ctx->stream>>>(
       part, (int)groups, md, 1.0 / sqrt((double)m), SA);
   LSQ_LAUNCH_CHECK();
+  a32_done = staged && a32 != nullptr && A->dtype == LSQ_F64;
   if (staged) {
     // a timed-out wait on a staged block is reported here
     LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 14, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1155,16 +1214,27 @@ extern "C" lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type
   if (prec != LSQ_SKETCH_F64 && prec != LSQ_SKETCH_F32 && prec != LSQ_SKETCH_BF16) return LSQ_ERR_ARG;
   if (prec == LSQ_SKETCH_BF16 && type != LSQ_SKETCH_GAUSS) return LSQ_ERR_ARG;
   const bool f64 = prec == LSQ_SKETCH_F64;
+  float* a32 = (opts && A->dtype == LSQ_F64) ? opts->a32 : nullptr;
+  const int64_t ld32 = a32 ? opts->ld32 : 0;
+  if (a32 && (ld32 < A->d || ld32 % 4 != 0 || ((uintptr_t)a32 % 16) != 0)) return LSQ_ERR_ARG;
+  bool a32_done = false;
   switch (type) {
     case LSQ_SKETCH_GAUSS:
-      if (prec == LSQ_SKETCH_BF16) return lsq_gauss_tc_run(ctx, A, (int)m, seed, t, SA);
-      return f64 ? gauss_run<double>(ctx, A, (int)m, seed, t, SA) : gauss_run<float>(ctx, A, (int)m, seed, t, SA);
+      if (prec == LSQ_SKETCH_BF16) st = lsq_gauss_tc_run(ctx, A, (int)m, seed, t, SA);
+      else st = f64 ? gauss_run<double>(ctx, A, (int)m, seed, t, SA) : gauss_run<float>(ctx, A, (int)m, seed, t, SA);
+      break;
     case LSQ_SKETCH_SRHT:
-      return f64 ? srht_run<double>(ctx, A, (int)m, seed, t, SA) : srht_run<float>(ctx, A, (int)m, seed, t, SA);
+      st = f64 ? srht_run<double>(ctx, A, (int)m, seed, t, SA, a32, ld32, a32_done)
+               : srht_run<float>(ctx, A, (int)m, seed, t, SA, a32, ld32, a32_done);
+      break;
     case LSQ_SKETCH_SJLT:
       if (s < 1 || s > 32 || s > m) return LSQ_ERR_ARG;
-      return f64 ? sjlt_run<double>(ctx, A, (int)m, s, seed, t, SA) : sjlt_run<float>(ctx, A, (int)m, s, seed, t, SA);
+      st = f64 ? sjlt_run<double>(ctx, A, (int)m, s, seed, t, SA) : sjlt_run<float>(ctx, A, (int)m, s, seed, t, SA);
+      break;
     default:
       return LSQ_ERR_ARG;
   }
+  // the FP32 copy, where the sketch did not write it on the way
+  if (st == LSQ_OK && a32 && !a32_done) st = lsq_narrow_copy(ctx, A, a32, ld32);
+  return st;
 }

@@ -428,7 +428,22 @@ extern "C" void lsq_solve_opts_default(lsq_solve_opts* o) {
   o->grid_blocks = 0;
   o->x0_zero = 0;
   o->fcg_k = -1;
+  o->a32 = nullptr;
+  o->ld32 = 0;
   o->a32_copy = 1;
+}
+
+lsq_status lsq_narrow_copy(lsq_ctx* ctx, const lsq_matrix* A, float* a32, int64_t ld32) {
+  const int d = (int)A->d, epl = epl_for(d);
+  void* nk = pick_narrow(epl);
+  const void* Ad = A->data;
+  int64_t n = A->n, ld = A->ld, l32 = ld32;
+  int di = d;
+  void* nargs[] = {(void*)&Ad, &n, &di, &ld, (void*)&a32, &l32};
+  const int nblk = (int)std::min<int64_t>((A->n + LSQ_WARPS - 1) / LSQ_WARPS, 8 * (int64_t)ctx->sm_count);
+  LSQ_CUDA_TRY(cudaLaunchKernel(nk, dim3(nblk), dim3(LSQ_THREADS), nargs, 0, ctx->stream));
+  LSQ_LAUNCH_CHECK();
+  return LSQ_OK;
 }
 
 extern "C" lsq_status lsq_hmatvec(lsq_ctx* ctx, const lsq_matrix* A, const double* p, double* v, double* q) {
@@ -507,8 +522,13 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   // MIXED with FP64 A: the FP32 passes stream an FP32 copy of A (half the bytes), made once per
   // call; without the memory for it every pass narrows A itself (the same values)
   float* a32 = nullptr;
-  const int64_t ld32 = (d + 31) & ~31;
-  if (mixed && A->dtype == LSQ_F64 && o.a32_copy && maxit >= 3) {
+  int64_t ld32 = (d + 31) & ~31;
+  const bool user_a32 = o.a32 != nullptr && mixed && A->dtype == LSQ_F64;
+  if (user_a32) {
+    if (o.ld32 < d || o.ld32 % 4 != 0 || ((uintptr_t)o.a32 % 16) != 0) return LSQ_ERR_ARG;
+    a32 = const_cast<float*>(o.a32);
+    ld32 = o.ld32;
+  } else if (mixed && A->dtype == LSQ_F64 && o.a32_copy && maxit >= 3) {
     if (lsq_ensure_a32(ctx, (size_t)A->n * (size_t)ld32 * 4) == LSQ_OK) a32 = reinterpret_cast<float*>(ctx->a32);
   }
   void* kern = A->dtype == LSQ_F64
@@ -579,15 +599,9 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   a.exact2 = 1e-8;    // IHS: FP64 gradients once the relative gradient is below 10^-4
   cudaStream_t s = ctx->stream;
   LSQ_CUDA_TRY(cudaEventRecord(ctx->ev0, s));
-  if (a32) {
-    void* nk = pick_narrow(epl);
-    const void* Ad = A->data;
-    int64_t n = A->n, ld = A->ld, l32 = ld32;
-    int di = d;
-    void* nargs[] = {(void*)&Ad, &n, &di, &ld, (void*)&a32, &l32};
-    const int nblk = (int)std::min<int64_t>((A->n + LSQ_WARPS - 1) / LSQ_WARPS, 8 * (int64_t)ctx->sm_count);
-    LSQ_CUDA_TRY(cudaLaunchKernel(nk, dim3(nblk), dim3(LSQ_THREADS), nargs, 0, s));
-    LSQ_LAUNCH_CHECK();
+  if (a32 && !user_a32) {
+    st = lsq_narrow_copy(ctx, A, a32, ld32);
+    if (st != LSQ_OK) return st;
   }
 
   double ms_sketch = 0.0;
@@ -623,6 +637,8 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
     lsq_sketch_opts so;
     so.s = o.s > 0 ? o.s : 8;
     so.precision = LSQ_SKETCH_F64;
+    so.a32 = nullptr;
+    so.ld32 = 0;
     for (int t = 0; t <= maxit; ++t) {
       if (t == maxit) {
         status = LSQ_ERR_MAXIT;
@@ -678,7 +694,7 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
     info->est_err = est;
     info->ms_total = ms_total;
     info->ms_sketch = ms_sketch;
-    info->a32_copy = a32 ? 1 : 0;
+    info->a32_copy = a32 ? (user_a32 ? 2 : 1) : 0;
     info->reserved = 0;
   }
   return (lsq_status)status;

@@ -143,3 +143,39 @@ def test_gaussian_bf16_accuracy(L, ctx, n, d, m, dtype):
     SA = L.lsq_sketch(ctx, to_dev(A), "gauss", m, 3, precision="bf16").cpu().numpy()
     ref = O.sketch_gauss(A.astype(np.float64), m, 3)
     assert rel_fro(SA, ref) < 1e-2  # BF16 operands: about 2^-9 per product, random signs
+
+
+def narrow_truncate(A):
+    """FP64 -> FP32 by mantissa truncation with the exponent clamped to FP32's range (the
+    narrowing of the mixed solve's FP32 passes), written out on the bits."""
+    u = np.ascontiguousarray(A, dtype=np.float64).view(np.uint64)
+    hi, lo = (u >> np.uint64(32)).astype(np.uint64), (u & np.uint64(0xFFFFFFFF)).astype(np.uint64)
+    e = (hi >> np.uint64(20)) & np.uint64(0x7FF)
+    ec = np.clip(e, 896, 1151).astype(np.uint64) - np.uint64(896)
+    mant = (((hi & np.uint64(0xFFFFF)) << np.uint64(3)) | (lo >> np.uint64(29))) & np.uint64(0x7FFFFF)
+    sign = hi & np.uint64(0x80000000)
+    return (sign | (ec << np.uint64(23)) | mant).astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("kind,precision,n,d", [("srht", "f32", 5000, 13), ("srht", "f32", 9000, 64),
+                                                ("srht", "f64", 3000, 20), ("gauss", "f32", 1000, 40),
+                                                ("sjlt", "f32", 2000, 33)])
+def test_sketch_writes_fp32_copy(L, ctx, kind, precision, n, d):
+    """lsq_sketch(..., a32=) leaves the FP32 narrowing of A (the values of a mixed solve's FP32
+    passes): written by the staged SRHT on the way, by a separate pass otherwise."""
+    A = W.make_problem(n, d, 1e6, seed=d)["A"]
+    Ad = to_dev(A)
+    a32 = torch.full((n, (d + 31) // 32 * 32), np.nan, dtype=torch.float32, device="cuda")
+    SA = L.lsq_sketch(ctx, Ad, kind, 256, 3, precision=precision, a32=a32).cpu().numpy()
+    got = a32.cpu().numpy()[:, :d]
+    want = narrow_truncate(A)
+    assert np.array_equal(got, want)
+    # truncation: |a32| <= |A| within one FP32 unit in the last place
+    assert np.all(np.abs(want.astype(np.float64)) <= np.abs(A))
+    assert np.all(np.abs(A - want) <= 2.0 ** -23 * np.abs(A))
+    # the sketch itself is unchanged by the extra output (SJLT: up to the order of its atomic sums)
+    SA0 = L.lsq_sketch(ctx, Ad, kind, 256, 3, precision=precision).cpu().numpy()
+    if kind == "sjlt":
+        assert rel_fro(SA, SA0) < 1e-6
+    else:
+        assert np.array_equal(SA, SA0)

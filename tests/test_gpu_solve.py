@@ -233,3 +233,19 @@ def test_mixed_fp32_copy_is_bit_identical(L, ctx, method, refresh, d):
     assert (i_0["iters"], i_0["passes"], i_0["exact_passes"]) == (i_1["iters"], i_1["passes"], i_1["exact_passes"])
     assert np.array_equal(x_0, x_1), np.abs(x_0 - x_1).max()
     assert i_0["est_err"] == i_1["est_err"]
+
+
+def test_mixed_solve_with_the_sketch_fp32_copy(L, ctx):
+    """The FP32 copy the sketch writes (lsq_sketch(a32=)) replaces the solve's own copy: the same
+    iterates to the last bit, and the solve reports it used the caller's copy."""
+    n, d, m = 30000, 96, 512
+    P = W.make_problem(n, d, 1e5, seed=21)
+    Ad, bd = to_dev(P["A"]), to_dev(P["b"])
+    a32 = L.narrow_buffer(Ad)
+    SA = L.lsq_sketch(ctx, Ad, "srht", m, 0, precision="f32", a32=a32)
+    _, Wm = L.lsq_factor(ctx, SA, precision="mixed")
+    x1, i1 = L.lsq_solve(ctx, Ad, bd, "pcg", Wm, tol=1e-10, maxit=300, m=m, precision="mixed", a32=a32)
+    x0, i0 = L.lsq_solve(ctx, Ad, bd, "pcg", Wm, tol=1e-10, maxit=300, m=m, precision="mixed")
+    assert i1["a32_copy"] == 2 and i0["a32_copy"] == 1
+    assert i0["status"] == i1["status"] == 0 and i0["passes"] == i1["passes"]
+    assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
