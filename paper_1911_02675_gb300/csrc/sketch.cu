@@ -622,12 +622,11 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_fast_kernel(
 // 2048-row block, eight 256-row x 8-column boxes of A land in shared memory as raw FP64 (or
 // FP32) elements, completion counted in bytes on an mbarrier, while the previous block's
 // radix passes and sampled second level run; the partial of SA lives in registers (thread t
-// owns sampled rows t, t + 512, ...), so the second level reads only the block.  The first
-// register stage is over row bits 7..10 (a thread holds rows q, q + 128, ..., q + 1920 of a
-// column pair, which keeps the reads from the staged block free of bank conflicts), then
-// radix passes over bits 0..3 and 4..6: the stages of a Walsh-Hadamard transform commute, so
-// this is the same transform with its FP32 additions in another order.  Every wait is
-// bounded.
+// owns sampled rows t, t + 512, ...), so the second level reads only the block.  The register
+// stage is over row bits 8..10 (a thread holds rows q, q + 256, ..., q + 1792 of a column
+// quad), then radix passes over bits 0..3 and 4..7: the stages of a Walsh-Hadamard transform
+// commute, so this is the same transform with its FP32 additions in another order.  The sign
+// words of the next block are loaded one block ahead.  Every wait is bounded.
 constexpr int SRHT_TMA_ROWS = 256;  // rows per box
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -702,45 +701,74 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
   for (int i = 0; i < MY; ++i)
 #pragma unroll
     for (int c = 0; c < DC; ++c) y[i][c] = 0.f;
-  const int qq = tid >> 2, pc = tid & 3;  // rows qq + 128 j, columns 2 pc, 2 pc + 1
+  // load phase: thread t holds rows qq + 256 j (j < 8) of the column quad 4 p4 .. 4 p4 + 3
+  // (qq = t / 2, p4 = t % 2), so a quarter-warp owns 256 contiguous bytes of each staged row
+  // group; FP64 rows are read as two 16-byte halves, lanes 4..7 of a quarter taking the upper
+  // half first, which puts the quarter's 8 reads on 8 distinct 16-byte bank groups
+  const int qq = tid >> 1, p4 = tid & 1, hf = (tid >> 2) & 1;
   bool ok = true;
   int64_t issued = b_begin < b_end ? 1 : 0, waited = 0;
+  // the sign words of the next block are loaded a block ahead (rows past n carry no data)
+  uint32_t sgn_next = 0;
+  if (tid < N2 / 32 && b_begin < b_end) {
+    const int64_t r = b_begin * N2 + 32 * tid;
+    sgn_next = r < n ? __ldg(signbits + (r >> 5)) : 0u;
+  }
   for (int64_t i1 = b_begin; i1 < b_end; ++i1) {
-    // the block's sign bits (rows past n carry no data)
     if (tid < N2 / 32) {
-      const int64_t r = i1 * N2 + 32 * tid;
-      sgn[tid] = r < n ? __ldg(signbits + (r >> 5)) : 0u;
+      sgn[tid] = sgn_next;
+      const int64_t r = (i1 + 1) * N2 + 32 * tid;
+      sgn_next = (i1 + 1 < b_end && r < n) ? __ldg(signbits + (r >> 5)) : 0u;
     }
     ok = ok && srht_mbar_wait(&full, (uint32_t)((i1 - b_begin) & 1), err);
     // Z is free (the previous second level is done) and the block has landed everywhere
     if (__syncthreads_or(!ok)) break;
     ++waited;
     {
-      float v0[16], v1[16];
+      float v[4][8];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int r = qq + 128 * j;
-        const T2 x = *reinterpret_cast<const T2*>(stage + r * DC + 2 * pc);
-        const float f0 = lsq_apass::narrow_f32(x.x), f1 = lsq_apass::narrow_f32(x.y);
+      for (int j = 0; j < 8; ++j) {
+        const int r = qq + 256 * j;
+        float f[4];
+        if constexpr (sizeof(TA) == 8) {
+          const double2 x0 = *reinterpret_cast<const double2*>(stage + r * DC + 4 * p4 + 2 * hf);
+          const double2 x1 = *reinterpret_cast<const double2*>(stage + r * DC + 4 * p4 + 2 * (hf ^ 1));
+          const double2 xa = hf ? x1 : x0, xb = hf ? x0 : x1;
+          f[0] = lsq_apass::narrow_f32(xa.x);
+          f[1] = lsq_apass::narrow_f32(xa.y);
+          f[2] = lsq_apass::narrow_f32(xb.x);
+          f[3] = lsq_apass::narrow_f32(xb.y);
+        } else {
+          const float4 x = *reinterpret_cast<const float4*>(stage + r * DC + 4 * p4);
+          f[0] = x.x;
+          f[1] = x.y;
+          f[2] = x.z;
+          f[3] = x.w;
+        }
         if (a32 != nullptr) {
           // the FP32 copy of A on the way (the narrowing of the solve's FP32 passes)
           const int64_t rg = i1 * N2 + r;
-          const int cg = c0 + 2 * pc;
+          const int cg = c0 + 4 * p4;
           if (rg < n) {
             float* o = a32 + rg * ld32 + cg;
-            if (cg + 1 < d) __stcs(reinterpret_cast<float2*>(o), make_float2(f0, f1));
-            else if (cg < d) __stcs(o, f0);
+            if (cg + 3 < d) {
+              __stcs(reinterpret_cast<float4*>(o), make_float4(f[0], f[1], f[2], f[3]));
+            } else {
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if (cg + c < d) __stcs(o + c, f[c]);
+            }
           }
         }
         const uint32_t neg = ((sgn[r >> 5] >> (r & 31)) & 1u) << 31;
-        v0[j] = __uint_as_float(__float_as_uint(f0) ^ neg);
-        v1[j] = __uint_as_float(__float_as_uint(f1) ^ neg);
-      }
-      butterflies<float, 4>(v0);
-      butterflies<float, 4>(v1);
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        *reinterpret_cast<float2*>(Z + zphys(qq + 128 * j, DC) + 2 * pc) = make_float2(v0[j], v1[j]);
+        for (int c = 0; c < 4; ++c) v[c][j] = __uint_as_float(__float_as_uint(f[c]) ^ neg);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) butterflies<float, 3>(v[c]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        *reinterpret_cast<float4*>(Z + zphys(qq + 256 * j, DC) + 4 * p4) = make_float4(v[0][j], v[1][j], v[2][j], v[3][j]);
     }
     __syncthreads();  // the staged block is consumed: the next one may land
     if (tid == 0 && i1 + 1 < b_end) {
@@ -749,16 +777,20 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
     }
     radix_pass<float, DC, 4>(Z, N2, 0);
     __syncthreads();
-    radix_pass<float, DC, 3>(Z, N2, 4);
+    radix_pass<float, DC, 4>(Z, N2, 4);
     __syncthreads();
     const uint32_t i1w = (uint32_t)i1;
+    // lanes 4..7 of each quarter-warp read the second half of their row first: rows fall on
+    // even or odd 16-byte bank groups by half, so the two orders spread a quarter's reads
+    const int hsw = (tid >> 2) & 1;
 #pragma unroll
     for (int i = 0; i < MY; ++i) {
       const int s = tid + SRHT_THREADS * i;
       if (s < m) {
         const bool neg = (__popc(k1s[s] & i1w) & 1) != 0;
         const float4* zr = reinterpret_cast<const float4*>(Z + zphys(k2s[s], DC));
-        const float4 za = zr[0], zb = zr[1];
+        const float4 z0 = zr[hsw], z1 = zr[hsw ^ 1];
+        const float4 za = hsw ? z1 : z0, zb = hsw ? z0 : z1;
         y[i][0] += neg ? -za.x : za.x;
         y[i][1] += neg ? -za.y : za.y;
         y[i][2] += neg ? -za.z : za.z;
