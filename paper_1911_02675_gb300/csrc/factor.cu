@@ -180,73 +180,91 @@ __device__ void tile_task(TileSmem& sm, double* out, const double* Xm, bool tran
   *o = (acc ? *o : 0.0) + alpha * sum;
 }
 
-// Cholesky of one 32 x 32 diagonal block and the inverse of its factor, by the whole CTA:
-// lane l owns column l; the dot products of each step are split over 4 warps (one per SM
-// sub-partition, so 4 FP64 pipes work on them) and added in warp order by warp 0.  FP64
-// instructions are costly on this part (a warp instruction holds a sub-partition's FP64 unit
-// for ~70 cycles), so each pivot takes one reciprocal square root and the rest are products:
-// R[j][j] = piv * rsqrt(piv), R[j][l] = t_l * rsqrt(piv); the inverse reuses 1 / R[i][i].
+// Upper-triangle task index e -> (a, b), 0 <= a <= b, e = b (b + 1) / 2 + a.
+__device__ __forceinline__ void tri_decode(int e, int& a, int& b) {
+  int bb = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while (bb * (bb + 1) / 2 > e) --bb;
+  while ((bb + 1) * (bb + 2) / 2 <= e) ++bb;
+  b = bb;
+  a = e - bb * (bb + 1) / 2;
+}
+
+// Cholesky of one 32 x 32 diagonal block and the inverse of its factor, by the whole CTA.
+// FP64 instructions are costly on this part (a warp instruction holds a sub-partition's FP64
+// unit for ~70 cycles whatever its active lanes), so both steps are right-looking with the
+// live entries of each step packed densely onto threads, one barrier per step:
+//   Cholesky, step j: R[j][l] = G[j][l] / sqrt(G[j][j]) and G[i][l] -= G[j][i] G[j][l] / G[j][j]
+//     for j < i <= l; the thread that updates G[j+1][j+1] also takes its reciprocal square
+//     root, so the next pivot is ready at the barrier;
+//   inverse, step i (from the bottom): W[i][l] = (delta_il - S[i][l]) / R[i][i] for l >= i and
+//     S[k][l] += R[k][i] W[i][l] for k < i <= l (S in the block's buffer).
 // Sets *err to LSQ_ERR_RANK on a non-positive or non-finite pivot.
 __device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, int* err) {
-  __shared__ double Gs[32][33];
+  __shared__ double Gs[32][33];  // the block, updated in place; then the inverse's sums S
   __shared__ double Rs[32][33];
   __shared__ double Ws[32][33];
-  __shared__ double part[4][32];
-  __shared__ double rinv[32];
+  __shared__ double rinv[32], pinv[32];
   __shared__ int bad;
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int tid = threadIdx.x, nt = blockDim.x;
   // stage the block (one round trip for the whole CTA)
-  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+  for (int e = tid; e < 1024; e += nt) {
     Gs[e >> 5][e & 31] = Gkk[(int64_t)(e >> 5) * ld + (e & 31)];
     Rs[e >> 5][e & 31] = 0.0;
     Ws[e >> 5][e & 31] = 0.0;
   }
-  if (threadIdx.x == 0) bad = 0;
+  if (tid == 0) bad = 0;
   __syncthreads();
-  // left-looking by columns: t_l = G[j][l] - sum_{i < j} R[i][j] R[i][l] for l >= j
+  if (tid == 0) {
+    const double g = Gs[0][0];
+    if (!(g > 0.0) || !isfinite(g)) bad = 1;
+    const double r = rsqrt(g);
+    rinv[0] = r;
+    pinv[0] = r * r;
+  }
+  __syncthreads();
   for (int j = 0; j < 32; ++j) {
-    if (w < 4) {
-      double t = 0.0;
-      for (int i = w; i < j; i += 4) t = fma(Rs[i][j], Rs[i][l], t);
-      part[w][l] = t;
-    }
-    __syncthreads();
-    if (w == 0) {
-      const double t = Gs[j][l] - ((part[0][l] + part[1][l]) + (part[2][l] + part[3][l]));
-      const double piv = __shfl_sync(0xffffffffu, t, j);
-      if (!(piv > 0.0) || !isfinite(piv)) {
-        if (l == 0) bad = 1;
-      } else {
-        const double ri = rsqrt(piv);
-        if (l == j) {
-          Rs[j][j] = piv * ri;
-          rinv[j] = ri;
-        } else if (l > j) {
-          Rs[j][l] = t * ri;
+    const int S = 31 - j, T = S * (S + 1) / 2;
+    const double ri = rinv[j], pv = pinv[j];
+    for (int e = tid; e < T + 32 - j; e += nt) {
+      if (e < T) {
+        int a, b;
+        tri_decode(e, a, b);
+        const int i = j + 1 + a, l = j + 1 + b;
+        const double g = fma(-(Gs[j][i] * pv), Gs[j][l], Gs[i][l]);
+        Gs[i][l] = g;
+        if (e == 0) {  // (i, l) = (j + 1, j + 1): the next pivot
+          if (!(g > 0.0) || !isfinite(g)) bad = 1;
+          const double r = rsqrt(g);
+          rinv[j + 1] = r;
+          pinv[j + 1] = r * r;
         }
+      } else {
+        const int l = j + (e - T);
+        Rs[j][l] = Gs[j][l] * ri;
       }
     }
     __syncthreads();
   }
-  // the inverse row by row from the bottom: W[i][l] = (delta_il - sum_{i < k <= l} R[i][k] W[k][l]) / R[i][i]
   if (!bad) {
+    for (int e = tid; e < 1024; e += nt) Gs[e >> 5][e & 31] = 0.0;
+    __syncthreads();
     for (int i = 31; i >= 0; --i) {
-      if (w < 4) {
-        double t = 0.0;
-        for (int k = i + 1 + w; k <= l; k += 4) t = fma(Rs[i][k], Ws[k][l], t);
-        part[w][l] = t;
+      const int w = 32 - i;
+      const double ri = rinv[i];
+      for (int e = tid; e < (i + 1) * w; e += nt) {
+        const int k = e / w, l = i + e % w;
+        const double wil = ((i == l ? 1.0 : 0.0) - Gs[i][l]) * ri;
+        if (k == i) Ws[i][l] = wil;
+        else Gs[k][l] = fma(Rs[k][i], wil, Gs[k][l]);
       }
-      __syncthreads();
-      if (w == 0 && l >= i)
-        Ws[i][l] = ((i == l ? 1.0 : 0.0) - ((part[0][l] + part[1][l]) + (part[2][l] + part[3][l]))) * rinv[i];
       __syncthreads();
     }
   }
-  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+  for (int e = tid; e < 1024; e += nt) {
     Rkk[(int64_t)(e >> 5) * ld + (e & 31)] = Rs[e >> 5][e & 31];
     Wkk[(int64_t)(e >> 5) * ld + (e & 31)] = Ws[e >> 5][e & 31];
   }
-  if (threadIdx.x == 0 && bad) atomicCAS(err, 0, (int)LSQ_ERR_RANK);
+  if (tid == 0 && bad) atomicCAS(err, 0, (int)LSQ_ERR_RANK);
   __syncthreads();
 }
 
