@@ -63,13 +63,21 @@ __device__ __forceinline__ void box_muller<float>(uint4 w, float& zc, float& zs)
   zs = rad * s;
 }
 
-// out[j*d + c] = scale * sum_g part[g][j][c]   (fixed order in g)
+// out[j*d + c] = scale * sum_g part[g][j][c]   (fixed order in g).  FP32 partials are summed as
+// (head, tail) FP32 pairs (TwoSum: exact up to the final rounding of the pair) on the FP32 pipe,
+// which does ~70x the FP64 pipe's adds on this part; FP64 partials in FP64.
 template <typename TP>
 __global__ void reduce_splits_kernel(const TP* __restrict__ part, int splits, int64_t md, double scale,
                                      double* __restrict__ out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < md; e += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int g = 0; g < splits; ++g) s += (double)part[(int64_t)g * md + e];
+    if constexpr (sizeof(TP) == 4) {
+      float h = 0.f, t = 0.f;
+      for (int g = 0; g < splits; ++g) lsq_apass::df_add(h, t, part[(int64_t)g * md + e], 0.f);
+      s = (double)h + (double)t;
+    } else {
+      for (int g = 0; g < splits; ++g) s += (double)part[(int64_t)g * md + e];
+    }
     out[e] = scale * s;
   }
 }
