@@ -1111,23 +1111,39 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   std::vector<double*> w_ptr(nprob), wt_ptr(nprob);
   std::vector<int> m_of(nprob), d_of(nprob);
   cudaEventRecord(e1, s);
+  // SJLT in FP32: every problem's sketch in one launch
+  const bool one_launch = o.sketch_type == LSQ_SKETCH_SJLT && o.sketch_precision == LSQ_SKETCH_F32;
+  if (one_launch) {
+    std::vector<lsq_matrix> mats(nprob);
+    std::vector<int> ms(nprob);
+    std::vector<double*> sas(nprob);
+    for (int p = 0; p < nprob; ++p) {
+      const int d = (int)probs[p].A.d;
+      mats[p] = probs[p].A;
+      ms[p] = (int)std::max<int64_t>(d, (int64_t)ceil(o.m_factor * (double)d));
+      sas[p] = reinterpret_cast<double*>(base + sa_off[p]);
+    }
+    st = lsq_sjlt_batched(ctx, nprob, mats.data(), ms.data(), o.s > 0 ? o.s : 8, o.seed, sas.data());
+    if (st != LSQ_OK) return st;
+  }
   for (int p = 0; p < nprob; ++p) {
     const int d = (int)probs[p].A.d;
     const int64_t m = std::max<int64_t>(d, (int64_t)ceil(o.m_factor * (double)d));
+    double* SA = reinterpret_cast<double*>(base + sa_off[p]);
+    sa_ptr[p] = SA;
+    w_ptr[p] = reinterpret_cast<double*>(base + off[p].W);
+    wt_ptr[p] = reinterpret_cast<double*>(base + off[p].WT);
+    m_of[p] = (int)m;
+    d_of[p] = d;
+    if (one_launch) continue;
     lsq_sketch_opts so;
     so.t = (uint32_t)p;
     so.s = (int)std::min<int64_t>(o.s > 0 ? o.s : 8, m);  // an SJLT column has at most m nonzeros
     so.precision = o.sketch_precision;
     so.a32 = nullptr;
     so.ld32 = 0;
-    double* SA = reinterpret_cast<double*>(base + sa_off[p]);
     st = lsq_sketch(ctx, &probs[p].A, o.sketch_type, m, o.seed, &so, SA);
     if (st != LSQ_OK) return st;
-    sa_ptr[p] = SA;
-    w_ptr[p] = reinterpret_cast<double*>(base + off[p].W);
-    wt_ptr[p] = reinterpret_cast<double*>(base + off[p].WT);
-    m_of[p] = (int)m;
-    d_of[p] = d;
   }
   cudaEventRecord(e2, s);
   st = lsq_factor_batched(ctx, nprob, sa_ptr.data(), m_of.data(), d_of.data(), w_ptr.data(), wt_ptr.data(), mixed,

@@ -8,6 +8,9 @@
 #include <cudaTypedefs.h>
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "apass.cuh"
 #include "common.cuh"
 
@@ -829,29 +832,37 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
 // SJLT: s distinct rows per column of S by Lemire's method on successive Philox words,
 // then a shared-memory scatter of each data row into its s target rows.
 // ------------------------------------------------------------------------------------
-__global__ void sjlt_hash_kernel(int64_t n, int m, int s, uint64_t seed, uint32_t t, int32_t* __restrict__ h,
-                                 uint32_t* __restrict__ signs) {
+// The s target rows of data row i in SJLT instance t: Lemire's bounded integers in [0, m) from the
+// successive words of Philox(i, draw, t, TAG_SJLT), duplicates skipped (at most 4096 draws).
+template <int SMAX>
+__device__ __forceinline__ void sjlt_targets(uint64_t seed, int64_t i, uint32_t t, int m, int s,
+                                             int32_t (&picked)[SMAX]) {
   const uint32_t range = (uint32_t)m;
   const uint32_t threshold = (uint32_t)(0u - range) % range;
+  int got = 0;
+  for (uint32_t draw = 0; got < s && draw < 4096u; ++draw) {
+    const uint4 w = philox_at(seed, (uint32_t)i, draw, t, TAG_SJLT);
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (got >= s) break;
+      const unsigned long long prod = (unsigned long long)words[k] * range;
+      const uint32_t low = (uint32_t)prod;
+      if (low < range && low < threshold) continue;
+      const int32_t v = (int32_t)(prod >> 32);
+      bool dup = false;
+      for (int q = 0; q < got; ++q) dup |= (picked[q] == v);
+      if (!dup) picked[got++] = v;
+    }
+  }
+  for (int k = got; k < SMAX; ++k) picked[k] = 0;  // unreachable for s <= m; keeps every index in range
+}
+
+__global__ void sjlt_hash_kernel(int64_t n, int m, int s, uint64_t seed, uint32_t t, int32_t* __restrict__ h,
+                                 uint32_t* __restrict__ signs) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t picked[32];
-    int got = 0;
-    for (uint32_t draw = 0; got < s && draw < 4096u; ++draw) {
-      const uint4 w = philox_at(seed, (uint32_t)i, draw, t, TAG_SJLT);
-      const uint32_t words[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (got >= s) break;
-        const unsigned long long prod = (unsigned long long)words[k] * range;
-        const uint32_t low = (uint32_t)prod;
-        if (low < range && low < threshold) continue;
-        const int32_t v = (int32_t)(prod >> 32);
-        bool dup = false;
-        for (int q = 0; q < got; ++q) dup |= (picked[q] == v);
-        if (!dup) picked[got++] = v;
-      }
-    }
-    for (int k = got; k < s; ++k) picked[k] = 0;  // unreachable for s <= m; keeps every index in range
+    sjlt_targets<32>(seed, i, t, m, s, picked);
     for (int k = 0; k < s; ++k) h[i * s + k] = picked[k];
     signs[i] = philox_at(seed, (uint32_t)i, 0u, t, TAG_SJLT_SIGN).x;
   }
@@ -932,6 +943,87 @@ __global__ void __launch_bounds__(SJLT_THREADS, 1) sjlt_scatter_kernel(const voi
   for (int e = threadIdx.x; e < m * DC; e += blockDim.x) {
     const int row = e / DC, cc = e % DC;
     if (c0 + cc < d) out[(int64_t)row * d + c0 + cc] = Y[e];
+  }
+}
+
+// Many SJLT sketches in one launch (FP32 arithmetic, 8-column tiles): work item (problem,
+// column tile, row group) -> one CTA, which draws each row's targets and sign word itself
+// (no hash pass: a problem with d columns redraws them d / 8 times, ~25 integer instructions
+// an element), loads the row's 8 elements as two 16-byte vectors where A allows, and scatters
+// them with shared-memory additions as sjlt_scatter_kernel does.
+struct SjltJob {
+  const void* A;
+  int64_t n, ld, rpg;  // rows, row stride, rows per group
+  float* part;         // [groups][m][d]
+  int dtype, d, m, s, vec;
+  uint32_t t;
+};
+
+template <int SMAX>
+__global__ void __launch_bounds__(SJLT_THREADS, 1) sjlt_batched_kernel(const SjltJob* __restrict__ jobs,
+                                                                      const int4* __restrict__ items,
+                                                                      uint64_t seed) {
+  constexpr int DC = 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Y = reinterpret_cast<float*>(smem_raw);  // [m][DC]
+  const int4 it = items[blockIdx.x];
+  const SjltJob jb = jobs[it.x];
+  const int c0 = it.y * DC, m = jb.m, s = jb.s, d = jb.d;
+  const int64_t i_begin = (int64_t)it.z * jb.rpg;
+  const int64_t i_end = min(jb.n, i_begin + jb.rpg);
+  for (int e = threadIdx.x; e < m * DC; e += blockDim.x) Y[e] = 0.f;
+  __syncthreads();
+  const int rot = (threadIdx.x & 31) & (DC - 1);
+  const bool vec = jb.vec != 0 && c0 + DC <= d;
+  for (int64_t i = i_begin + threadIdx.x; i < i_end; i += SJLT_THREADS) {
+    float a[DC];
+    if (vec && jb.dtype == LSQ_F32) {
+      const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(jb.A) + i * jb.ld + c0);
+      const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
+      a[0] = x0.x; a[1] = x0.y; a[2] = x0.z; a[3] = x0.w;
+      a[4] = x1.x; a[5] = x1.y; a[6] = x1.z; a[7] = x1.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < DC; ++c) a[c] = c0 + c < d ? load_as<float>(jb.A, i * jb.ld + c0 + c, jb.dtype) : 0.f;
+    }
+    int32_t tg[SMAX];
+    sjlt_targets<SMAX>(seed, i, jb.t, m, s, tg);
+    const uint32_t sw = philox_at(seed, (uint32_t)i, 0u, jb.t, TAG_SJLT_SIGN).x;
+    rotate_by<float, DC>(a, rot);
+#pragma unroll
+    for (int k = 0; k < SMAX; ++k) {
+      if (k >= s) break;
+      float* yr = Y + (size_t)tg[k] * DC;
+      const bool neg = (sw >> k) & 1u;
+#pragma unroll
+      for (int c = 0; c < DC; ++c) atomicAdd(yr + ((c + rot) & (DC - 1)), neg ? -a[c] : a[c]);
+    }
+  }
+  __syncthreads();
+  float* out = jb.part + (int64_t)it.z * m * d;
+  for (int e = threadIdx.x; e < m * DC; e += blockDim.x) {
+    const int row = e / DC, cc = e % DC;
+    if (c0 + cc < d) out[(int64_t)row * d + c0 + cc] = Y[e];
+  }
+}
+
+// SA_p = scale_p * sum over the groups of problem p's partials (double-FP32 sums), one launch;
+// element e of the concatenation belongs to the problem whose prefix range holds it
+__global__ void sjlt_batched_reduce_kernel(const SjltJob* __restrict__ jobs, const int64_t* __restrict__ prefix,
+                                           const int* __restrict__ groups, double* const* __restrict__ SA, int nprob,
+                                           int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    const SjltJob& jb = jobs[lo];
+    const int64_t md = (int64_t)jb.m * jb.d, k = e - prefix[lo];
+    float h = 0.f, t = 0.f;
+    for (int g = 0; g < groups[lo]; ++g) lsq_apass::df_add(h, t, jb.part[(int64_t)g * md + k], 0.f);
+    SA[lo][k] = ((double)h + (double)t) / sqrt((double)jb.s);
   }
 }
 
@@ -1277,4 +1369,93 @@ extern "C" lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type
   // the FP32 copy, where the sketch did not write it on the way
   if (st == LSQ_OK && a32 && !a32_done) st = lsq_narrow_copy(ctx, A, a32, ld32);
   return st;
+}
+
+// Sketches of many problems in one launch (SJLT, FP32 arithmetic): problem p draws instance
+// t = p of `seed` into SA[p] (m[p] x d FP64), exactly the embedding lsq_sketch would draw.
+lsq_status lsq_sjlt_batched(lsq_ctx* ctx, int nprob, const lsq_matrix* A, const int* m, int s, uint64_t seed,
+                            double* const* SA) {
+  if (nprob <= 0) return LSQ_OK;
+  constexpr int DC = 8;
+  std::vector<SjltJob> jobs(nprob);
+  std::vector<int4> items;
+  std::vector<int64_t> prefix(nprob);
+  std::vector<int> groups(nprob);
+  int64_t total = 0;
+  size_t part_elems = 0;
+  size_t smem_max = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const lsq_matrix& a = A[p];
+    const int d = (int)a.d, mp = m[p];
+    const int sp = std::min(s, mp);
+    if ((size_t)mp * DC * 4 > 200 * 1024 || sp < 1 || sp > 32) return LSQ_ERR_ARG;
+    smem_max = std::max(smem_max, (size_t)mp * DC * 4);
+    // about 16k rows per work item, at most 64 groups
+    const int64_t g = std::max<int64_t>(1, std::min<int64_t>(64, (a.n + 16383) / 16384));
+    const int64_t rpg = (a.n + g - 1) / g;
+    const int gp = (int)((a.n + rpg - 1) / rpg);
+    const size_t es = a.dtype == LSQ_F64 ? 8 : 4;
+    SjltJob& jb = jobs[p];
+    jb.A = a.data;
+    jb.n = a.n;
+    jb.ld = a.ld;
+    jb.rpg = rpg;
+    jb.part = nullptr;
+    jb.dtype = a.dtype;
+    jb.d = d;
+    jb.m = mp;
+    jb.s = sp;
+    jb.vec = (((uintptr_t)a.data % 16) == 0 && ((size_t)a.ld * es) % 16 == 0) ? 1 : 0;
+    jb.t = (uint32_t)p;
+    groups[p] = gp;
+    prefix[p] = total;
+    total += (int64_t)mp * d;
+    part_elems += (size_t)gp * mp * d;
+    for (int ct = 0; ct < (d + DC - 1) / DC; ++ct)
+      for (int gg = 0; gg < gp; ++gg) items.push_back(make_int4(p, ct, gg, 0));
+  }
+  // the costliest items first (rows of the group x sampled rows)
+  std::stable_sort(items.begin(), items.end(), [&](const int4& x, const int4& y) {
+    const double cx = (double)std::min<int64_t>(jobs[x.x].rpg, jobs[x.x].n) * jobs[x.x].m;
+    const double cy = (double)std::min<int64_t>(jobs[y.x].rpg, jobs[y.x].n) * jobs[y.x].m;
+    return cx > cy;
+  });
+  const size_t need = lsq_align256(part_elems * 4) + lsq_align256(nprob * sizeof(SjltJob)) +
+                      lsq_align256(items.size() * sizeof(int4)) + lsq_align256(nprob * 8) +
+                      lsq_align256(nprob * 4) + lsq_align256(nprob * sizeof(double*));
+  lsq_status st = lsq_ensure_scratch(ctx, need);
+  if (st != LSQ_OK) return st;
+  Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};
+  float* part = cv.take<float>(part_elems);
+  SjltJob* d_jobs = cv.take<SjltJob>(nprob);
+  int4* d_items = cv.take<int4>(items.size());
+  int64_t* d_prefix = cv.take<int64_t>(nprob);
+  int* d_groups = cv.take<int>(nprob);
+  double** d_sa = cv.take<double*>(nprob);
+  size_t off = 0;
+  for (int p = 0; p < nprob; ++p) {
+    jobs[p].part = part + off;
+    off += (size_t)groups[p] * jobs[p].m * jobs[p].d;
+  }
+  cudaStream_t str = ctx->stream;
+  LSQ_CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs.data(), nprob * sizeof(SjltJob), cudaMemcpyHostToDevice, str));
+  LSQ_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, str));
+  LSQ_CUDA_TRY(cudaMemcpyAsync(d_prefix, prefix.data(), nprob * 8, cudaMemcpyHostToDevice, str));
+  LSQ_CUDA_TRY(cudaMemcpyAsync(d_groups, groups.data(), nprob * 4, cudaMemcpyHostToDevice, str));
+  LSQ_CUDA_TRY(cudaMemcpyAsync(d_sa, SA, nprob * sizeof(double*), cudaMemcpyHostToDevice, str));
+  const int smax = s <= 8 ? 8 : 32;
+  if (smax == 8) {
+    auto kern = sjlt_batched_kernel<8>;
+    LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    kern<<<(unsigned)items.size(), SJLT_THREADS, smem_max, str>>>(d_jobs, d_items, seed);
+  } else {
+    auto kern = sjlt_batched_kernel<32>;
+    LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    kern<<<(unsigned)items.size(), SJLT_THREADS, smem_max, str>>>(d_jobs, d_items, seed);
+  }
+  LSQ_LAUNCH_CHECK();
+  sjlt_batched_reduce_kernel<<<grid_for(total, 256, 8 * ctx->sm_count), 256, 0, str>>>(d_jobs, d_prefix, d_groups,
+                                                                                          d_sa, nprob, total);
+  LSQ_LAUNCH_CHECK();
+  return LSQ_OK;
 }
