@@ -661,7 +661,8 @@ lsq_status lsq_factor_batched(lsq_ctx* ctx, int nprob, const double* const* SA, 
   int per_sm = 0;
   LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_inv_batched_kernel, 256, 0));
   if (per_sm < 1) return LSQ_ERR_CUDA;
-  const int gmax = std::min(per_sm, 2) * ctx->sm_count;
+  const int cta_per_sm = std::min(per_sm, 4);
+  const int gmax = cta_per_sm * ctx->sm_count;
   size_t need = 4 * mats + lsq_align256(sizeof(GramJob) * nprob) + lsq_align256(sizeof(CholJob) * nprob) +
                 lsq_align256(sizeof(int4) * units.size()) + lsq_align256(sizeof(int4) * std::max<size_t>(1, nodes.size())) +
                 lsq_align256(sizeof(int) * levels.size()) + lsq_align256(sizeof(int) * gmax) +
@@ -714,27 +715,53 @@ lsq_status lsq_factor_batched(lsq_ctx* ctx, int nprob, const double* const* SA, 
   else
     gram_batched_kernel<false><<<(unsigned)units.size(), 256, 0, s>>>(d_gj, d_units);
   LSQ_LAUNCH_CHECK();
-  // waves of problems whose groups fit the cooperative grid
+  // CTA groups sized so that every problem takes about the same time T: its FP64 work (the
+  // Cholesky and the inverse, 2 d^3 / 3 FMAs) at the rate of g CTAs, but no less than its chain
+  // of diagonal blocks; T is the longest chain or the whole work spread over the grid, whichever
+  // is larger.  The largest problems first, in waves that fill the cooperative grid.
   std::vector<int> order(nprob);
   for (int p = 0; p < nprob; ++p) order[p] = p;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return d[x] > d[y]; });
+  const double cta_rate = 1.75 * 2.0e9 / cta_per_sm;  // FP64 FMA per second of a CTA
+  auto work = [&](int p) { const double dd = ((d[p] + 31) / 32) * 32.0; return 2.0 / 3.0 * dd * dd * dd; };
+  double total_work = 0.0, longest_chain = 0.0;
+  for (int p = 0; p < nprob; ++p) {
+    total_work += work(p);
+    longest_chain = std::max(longest_chain, ((d[p] + 31) / 32) * 60e-6);
+  }
+  std::vector<int> gsize(nprob);
+  auto size_groups = [&](double T) {
+    long long sum = 0;
+    for (int p = 0; p < nprob; ++p) {
+      const int nblk = (d[p] + 31) / 32;
+      const int cap = std::min(gmax, std::max(1, 4 * nblk * nblk));
+      gsize[p] = std::max(1, std::min(cap, (int)std::ceil(work(p) / (T * cta_rate))));
+      sum += gsize[p];
+    }
+    return sum;
+  };
+  if (nprob <= gmax) {
+    // one wave: the shortest T whose groups fill the grid (bisection on T)
+    double lo = longest_chain, hi = std::max(lo, total_work / cta_rate);
+    for (int it = 0; it < 60; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (size_groups(mid) <= gmax) hi = mid;
+      else lo = mid;
+    }
+    size_groups(hi);
+  } else {
+    size_groups(std::max(longest_chain, total_work / (gmax * cta_rate)));
+  }
   size_t next = 0;
   while (next < order.size()) {
     const size_t w0 = next;
-    size_t w1 = std::min(order.size(), w0 + (size_t)gmax);
-    double wsum = 0.0;
-    for (size_t i = w0; i < w1; ++i) {
-      const double nb = (d[order[i]] + 31) / 32;
-      wsum += nb * nb * nb + 4.0;
-    }
+    size_t w1 = w0;
+    int used = 0;
+    while (w1 < order.size() && used + gsize[order[w1]] <= gmax) used += gsize[order[w1++]];
     std::vector<int> ctajob;
-    int spare = gmax - (int)(w1 - w0);
     for (size_t i = w0; i < w1; ++i) {
       const int p = order[i];
-      const int nblk = (d[p] + 31) / 32;
-      const double wgt = (double)nblk * nblk * nblk + 4.0;
-      int g = 1 + (int)std::floor((double)spare * wgt / wsum);
-      g = std::min(g, std::max(1, 4 * nblk * nblk));
+      const int g = gsize[p];
       cj[p].cta0 = (int)ctajob.size();
       cj[p].ncta = g;
       for (int q = 0; q < g; ++q) ctajob.push_back(p);
