@@ -35,6 +35,7 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_KS = 64;  // rows of A per stage (4 MMAs of K = 16)
 constexpr uint32_t TC_SPIN = 1u << 26;
+constexpr int TC_GEN = 512;  // generating threads
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -117,6 +118,62 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// shared::cluster address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+// bounded wait with cluster-scope acquire (the arrivals include other CTAs' releases)
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity, int* err) {
+  uint32_t spins = 0;
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (++spins > TC_SPIN) {
+      atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void st_cluster_v2(uint32_t addr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared::cluster.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
@@ -196,18 +253,31 @@ __global__ void __launch_bounds__(256) pack_kernel(const TA* __restrict__ A, int
   }
 }
 
-template <int NT, int STAGES, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1)
+// Warp roles: warps 0..15 generate S (one (row pair, k-group) unit per thread and stage), warp
+// 16 (one elected lane) starts the bulk copies of A's blobs and issues the MMAs.  Stage s is
+// handed over through three mbarriers: `full` (the blob landed, bytes counted), `sfull` (every
+// generating warp of every CTA of the cluster wrote its part of S: 16 x CL arrivals) and
+// `empty` (the MMAs that read the stage completed, one commit per CTA of the cluster).  No
+// CTA-wide barrier runs inside the loop.  CL = 2: the two CTAs of a cluster own adjacent
+// column tiles of the same rows of SA, so they need the same S; each generates 4 of the 8
+// K-columns of every core-matrix row and stores them into both CTAs' stages.
+template <int NT, int STAGES, int CL>
+__global__ void __launch_bounds__(TC_GEN + 32, 1)
     gauss_tc_kernel(const uint8_t* __restrict__ pk, int64_t nkb, int nct, int d, int m, uint64_t seed, uint32_t t,
                     int64_t row0, int64_t kb_per_split, int accumulate, float* __restrict__ part, int* err) {
   constexpr int A_BYTES = TC_M * TC_KS * 2;
   constexpr int B_BYTES = NT * TC_KS * 2;
   constexpr uint32_t IDESC = idesc_bf16(TC_M, 256);
   constexpr int UNITS = (TC_M / 2) * (TC_KS / 8);  // 512 (pair of rows, k-group) per stage
+  constexpr int PER = 8 / CL;                      // K-columns of a unit this CTA generates
+  constexpr int GW = TC_GEN / 32;                  // generating warps
+  static_assert(CL == 1 || CL == 2, "a single CTA or a CTA pair");
+  static_assert(UNITS == TC_GEN, "one unit per generating thread and stage");
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
   __shared__ __align__(8) uint64_t full[STAGES];
+  __shared__ __align__(8) uint64_t sfull[STAGES];
   __shared__ __align__(8) uint64_t empty[STAGES];
   __shared__ uint32_t tmem_base_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -215,67 +285,63 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int64_t kb_begin = (int64_t)blockIdx.z * kb_per_split;
   const int64_t kb_end = min(nkb, kb_begin + kb_per_split);
   const int64_t nsteps = kb_end > kb_begin ? kb_end - kb_begin : 0;
-  const RoundKeys keys = round_keys(seed);
+  const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
 
   if (warp == 0) tmem_alloc(&tmem_base_s, NT);
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&sfull[s], GW * CL);
+      mbar_init(&empty[s], CL);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
-  __syncthreads();
+  // every CTA of the cluster has initialised its barriers before any remote access
+  if (CL > 1) cluster_sync_all();
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
   bool ok = true;
-  int64_t copies = 0;  // bulk copies started (thread 0)
+  int64_t copies = 0;  // bulk copies started (MMA lane)
 
-  for (int64_t step = 0; step < nsteps; ++step) {
-    const int s = (int)(step % STAGES);
-    if (step >= STAGES) {
-      // the MMAs that read this stage STAGES steps ago have completed
-      ok = ok && mbar_wait_bounded(&empty[s], (uint32_t)(((step / STAGES) - 1) & 1), err);
-    }
-    if (__syncthreads_or(!ok)) {
-      ok = false;
-      break;
-    }
-    const int64_t kb = kb_begin + step;
-    uint8_t* stA = sA + s * A_BYTES;
-    uint8_t* stB = sB + s * B_BYTES;
-    if (tid == 0) {
-      mbar_expect_tx(&full[s], (uint32_t)B_BYTES);
-      bulk_g2s(stB, pk + ((size_t)kb * nct + ct) * (size_t)B_BYTES, (uint32_t)B_BYTES, &full[s]);
-      ++copies;
-    }
-    // S tile: unit u -> pair jp (tile rows jp and jp + 64), k-group kg; a warp's 32 stores
-    // fill 512 contiguous bytes
-    const uint32_t i_base = (uint32_t)(row0 + kb * TC_KS);
-#pragma unroll 1
-    for (int u = tid; u < UNITS; u += THREADS) {
-      const int ln = u & 31, blk = u >> 5;
-      const int kk = blk & 3, gpair = blk >> 2;
-      const int r8 = ln & 7, kc = (ln >> 3) & 1, gsub = ln >> 4;
-      const int jp = 8 * (2 * gpair + gsub) + r8;
-      const int kg = 2 * kk + kc;
+  if (warp < GW) {
+    // ---- generators
+    const RoundKeys keys = round_keys(seed);
+    const int u = tid;
+    const int ln = u & 31, blk = u >> 5;
+    const int kk = blk & 3, gpair = blk >> 2;
+    const int r8 = ln & 7, kc = (ln >> 3) & 1, gsub = ln >> 4;
+    const int jp = 8 * (2 * gpair + gsub) + r8;
+    const int kg = 2 * kk + kc;
+    const uint32_t qq = (uint32_t)((j0 >> 1) + jp);
+    const uint32_t off_e = core_offset(TC_M, jp, kg) + rank * (PER * 2);
+    const uint32_t off_o = core_offset(TC_M, jp + 64, kg) + rank * (PER * 2);
+    for (int64_t step = 0; step < nsteps; ++step) {
+      const int s = (int)(step % STAGES);
+      // the MMAs (of every CTA of the cluster) that read this stage STAGES steps ago are done
+      // (the warp decides together, so that it stays converged)
+      if (step >= STAGES &&
+          !__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((step / STAGES) - 1) & 1), err))) {
+        ok = false;
+        break;
+      }
+      uint8_t* stA = sA + s * A_BYTES;
       // z(2q, i) (cosine) and z(2q + 1, i) (sine) in FP32 from the same Philox words as the
-      // FP64 definition (the uniforms keep the top 24 of their 53 bits; BF16 keeps 8). The 8
-      // Philox streams of the unit advance round by round together, so each thread carries 8
-      // independent dependency chains through the multiply-high latency.
-      uint4 w[8];
-      const uint32_t ia0 = i_base + (uint32_t)(kg * 8), qq = (uint32_t)((j0 >> 1) + jp);
+      // FP64 definition (the uniforms keep the top 24 of their 53 bits; BF16 keeps 8); the
+      // PER Philox streams of the unit advance round by round together
+      const uint32_t ia0 = (uint32_t)(row0 + (kb_begin + step) * TC_KS) + (uint32_t)(kg * 8) + rank * PER;
+      uint4 w[PER];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) w[q] = make_uint4(ia0 + (uint32_t)q, qq, t, TAG_GAUSS);
+      for (int q = 0; q < PER; ++q) w[q] = make_uint4(ia0 + (uint32_t)q, qq, t, TAG_GAUSS);
 #pragma unroll
       for (int r = 0; r < 10; ++r) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) w[q] = philox_round(w[q], keys.a[r], keys.b[r]);
+        for (int q = 0; q < PER; ++q) w[q] = philox_round(w[q], keys.a[r], keys.b[r]);
       }
-      uint32_t ev[4], od[4];
+      uint32_t ev[PER / 2], od[PER / 2];
 #pragma unroll
-      for (int q = 0; q < 8; q += 2) {
+      for (int q = 0; q < PER; q += 2) {
         float zc[2], zs[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -290,88 +356,134 @@ __global__ void __launch_bounds__(THREADS, 1)
         ev[q >> 1] = pack_bf16(zc[0], zc[1]);
         od[q >> 1] = pack_bf16(zs[0], zs[1]);
       }
-      *reinterpret_cast<uint4*>(stA + core_offset(TC_M, jp, kg)) = make_uint4(ev[0], ev[1], ev[2], ev[3]);
-      *reinterpret_cast<uint4*>(stA + core_offset(TC_M, jp + 64, kg)) = make_uint4(od[0], od[1], od[2], od[3]);
-    }
-    // generic-proxy writes -> visible to the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      ok = mbar_wait_bounded(&full[s], (uint32_t)((step / STAGES) & 1), err);
-      if (ok) {
-        tc_fence_after();
+      if constexpr (CL == 1) {
+        *reinterpret_cast<uint4*>(stA + off_e) = make_uint4(ev[0], ev[1], ev[2], ev[3]);
+        *reinterpret_cast<uint4*>(stA + off_o) = make_uint4(od[0], od[1], od[2], od[3]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      } else {
+        const uint32_t le = smem_u32(stA + off_e), lo = smem_u32(stA + off_o);
 #pragma unroll
-        for (int kk = 0; kk < TC_KS / 16; ++kk) {
-          const uint64_t ad = smem_desc(smem_u32(stA + kk * TC_M * 32), 128, 256);
-#pragma unroll
-          for (int h = 0; h < NT / 256; ++h) {
-            const uint64_t bd = smem_desc(smem_u32(stB + kk * NT * 32 + h * (256 / 8) * 256), 128, 256);
-            mma_bf16(tmem + h * 256, ad, bd, IDESC, (step > 0 || kk > 0) ? 1u : 0u);
-          }
+        for (int c = 0; c < CL; ++c) {
+          const uint32_t peer = (rank + (uint32_t)c) % CL;
+          st_cluster_v2(peer_addr(le, peer), ev[0], ev[1]);
+          st_cluster_v2(peer_addr(lo, peer), od[0], od[1]);
         }
-        mma_commit(&empty[s]);
+        asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive_local(&sfull[s]);
+        if constexpr (CL > 1) {
+#pragma unroll
+          for (int c = 1; c < CL; ++c) mbar_arrive_remote(peer_addr(smem_u32(&sfull[s]), (rank + (uint32_t)c) % CL));
+        }
       }
     }
+  } else {
+    // ---- copies and MMAs: the whole warp waits, lane 0 issues
+    for (int64_t step = 0; step < nsteps; ++step) {
+      const int s = (int)(step % STAGES);
+      if (step >= STAGES &&
+          !__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((step / STAGES) - 1) & 1), err))) {
+        ok = false;
+        break;
+      }
+      uint8_t* stA = sA + s * A_BYTES;
+      uint8_t* stB = sB + s * B_BYTES;
+      if (lane == 0) {
+        mbar_expect_tx(&full[s], (uint32_t)B_BYTES);
+        bulk_g2s(stB, pk + ((size_t)(kb_begin + step) * nct + ct) * (size_t)B_BYTES, (uint32_t)B_BYTES, &full[s]);
+      }
+      ++copies;
+      const uint32_t par = (uint32_t)((step / STAGES) & 1);
+      const bool got = (CL > 1 ? mbar_wait_cluster_bounded(&sfull[s], par, err) : mbar_wait_bounded(&sfull[s], par, err)) &&
+                       mbar_wait_bounded(&full[s], par, err);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
+      if (lane == 0) {
+        tc_fence_after();
+#pragma unroll
+        for (int k2 = 0; k2 < TC_KS / 16; ++k2) {
+          const uint64_t ad = smem_desc(smem_u32(stA + k2 * TC_M * 32), 128, 256);
+#pragma unroll
+          for (int h = 0; h < NT / 256; ++h) {
+            const uint64_t bd = smem_desc(smem_u32(stB + k2 * NT * 32 + h * (256 / 8) * 256), 128, 256);
+            mma_bf16(tmem + h * 256, ad, bd, IDESC, (step > 0 || k2 > 0) ? 1u : 0u);
+          }
+        }
+        if constexpr (CL > 1) mma_commit_mc(&empty[s], (uint16_t)((1u << CL) - 1u));
+        else mma_commit(&empty[s]);
+      }
+      __syncwarp();
+    }
   }
-  // all MMAs done: the last commit tracks every earlier one
+  // all MMAs done: the final phase of every stage counts the last commits of every CTA
   ok = !__syncthreads_or(!ok);
   if (ok && nsteps > 0) {
-    const int64_t last = nsteps - 1;
-    ok = mbar_wait_bounded(&empty[last % STAGES], (uint32_t)((last / STAGES) & 1), err);
+    const int64_t first = nsteps > STAGES ? nsteps - STAGES : 0;
+    for (int64_t st = first; st < nsteps && ok; ++st)
+      ok = mbar_wait_bounded(&empty[st % STAGES], (uint32_t)((st / STAGES) & 1), err);
   }
   ok = !__syncthreads_or(!ok);
-  if (!ok && tid == 0) {
+  if (!ok && warp == GW) {
     // a failed run may leave bulk copies in flight: wait (bounded) for each stage's last one
     for (int64_t c = (copies > STAGES ? copies - STAGES : 0); c < copies; ++c)
       (void)mbar_wait_bounded(&full[c % STAGES], (uint32_t)((c / STAGES) & 1), err);
   }
+  __syncwarp();
   tc_fence_after();
-  if (ok && nsteps > 0) {
-    // warp w reads TMEM lanes 32 (w % 4) .. + 31; the warps sharing a lane group split the columns
-    constexpr int GROUPS = THREADS / 128;
-    const int lg = warp & 3, cg = warp >> 2;
-    const int L = 32 * lg + lane;
-    const int j = j0 + (L < 64 ? 2 * L : 2 * (L - 64) + 1);
-    float* out = part + (int64_t)blockIdx.z * m * d;
-    for (int cb = 16 * cg; cb < NT; cb += 16 * GROUPS) {
-      uint32_t r[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)cb, r);
-      const int col0 = ct * NT + cb;
-      if (j < m && col0 < d) {
-        float* o = out + (int64_t)j * d + col0;
-        if ((d & 3) == 0 && col0 + 16 <= d) {
+  if (warp < GW) {
+    if (ok && nsteps > 0) {
+      // warp w reads TMEM lanes 32 (w % 4) .. + 31; the warps sharing a lane group split the columns
+      constexpr int GROUPS = GW / 4;
+      const int lg = warp & 3, cg = warp >> 2;
+      const int L = 32 * lg + lane;
+      const int j = j0 + (L < 64 ? 2 * L : 2 * (L - 64) + 1);
+      float* out = part + (int64_t)blockIdx.z * m * d;
+      for (int cb = 16 * cg; cb < NT; cb += 16 * GROUPS) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)cb, r);
+        const int col0 = ct * NT + cb;
+        if (j < m && col0 < d) {
+          float* o = out + (int64_t)j * d + col0;
+          if ((d & 3) == 0 && col0 + 16 <= d) {
 #pragma unroll
-          for (int q = 0; q < 16; q += 4) {
-            float4 v = make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]), __uint_as_float(r[q + 2]),
-                                   __uint_as_float(r[q + 3]));
-            if (accumulate) {
-              const float4 p = *reinterpret_cast<const float4*>(o + q);
-              v.x += p.x;
-              v.y += p.y;
-              v.z += p.z;
-              v.w += p.w;
+            for (int q = 0; q < 16; q += 4) {
+              float4 v = make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]), __uint_as_float(r[q + 2]),
+                                     __uint_as_float(r[q + 3]));
+              if (accumulate) {
+                const float4 p = *reinterpret_cast<const float4*>(o + q);
+                v.x += p.x;
+                v.y += p.y;
+                v.z += p.z;
+                v.w += p.w;
+              }
+              *reinterpret_cast<float4*>(o + q) = v;
             }
-            *reinterpret_cast<float4*>(o + q) = v;
-          }
-        } else {
+          } else {
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            if (col0 + q < d) o[q] = (accumulate ? o[q] : 0.f) + __uint_as_float(r[q]);
+            for (int q = 0; q < 16; ++q)
+              if (col0 + q < d) o[q] = (accumulate ? o[q] : 0.f) + __uint_as_float(r[q]);
+          }
         }
       }
-    }
-  } else if (!accumulate) {
-    // nothing accumulated (no rows, or a failed run): the partial tile is zero
-    float* out = part + (int64_t)blockIdx.z * m * d;
-    for (int e = tid; e < TC_M * NT; e += THREADS) {
-      const int row = e / NT, col = ct * NT + e % NT;
-      const int jj = j0 + (row < 64 ? 2 * row : 2 * (row - 64) + 1);
-      if (jj < m && col < d) out[(int64_t)jj * d + col] = 0.f;
+    } else if (!accumulate) {
+      // nothing accumulated (no rows, or a failed run): the partial tile is zero
+      float* out = part + (int64_t)blockIdx.z * m * d;
+      for (int e = tid; e < TC_M * NT; e += TC_GEN) {
+        const int row = e / NT, col = ct * NT + e % NT;
+        const int jj = j0 + (row < 64 ? 2 * row : 2 * (row - 64) + 1);
+        if (jj < m && col < d) out[(int64_t)jj * d + col] = 0.f;
+      }
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, NT);
+  // no CTA leaves while another CTA of its cluster may still write into its shared memory
+  if (CL > 1) cluster_sync_all();
 }
 
 // out[e] = scale * sum_g part[g][e], fixed order in g
@@ -384,13 +496,31 @@ __global__ void reduce_tc_kernel(const float* __restrict__ part, int splits, int
   }
 }
 
-template <int NT, int STAGES, int THREADS>
+template <int NT, int STAGES, int CL>
 lsq_status launch_tc(lsq_ctx* ctx, dim3 grid, const uint8_t* pk, int64_t nkb, int nct, int d, int m, uint64_t seed,
                      uint32_t t, int64_t row0, int64_t kb_per_split, int accumulate, float* part, int* err) {
   const size_t smem = (size_t)STAGES * (TC_M * TC_KS * 2 + NT * TC_KS * 2);
-  auto k = gauss_tc_kernel<NT, STAGES, THREADS>;
+  auto k = gauss_tc_kernel<NT, STAGES, CL>;
   LSQ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k<<<grid, THREADS, smem, ctx->stream>>>(pk, nkb, nct, d, m, seed, t, row0, kb_per_split, accumulate, part, err);
+  if (CL == 1) {
+    k<<<grid, TC_GEN + 32, smem, ctx->stream>>>(pk, nkb, nct, d, m, seed, t, row0, kb_per_split, accumulate, part,
+                                                err);
+  } else {
+    // clusters of CL CTAs along the column tiles (grid.y is a multiple of CL)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(TC_GEN + 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = CL;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    LSQ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, accumulate, part, err));
+  }
   LSQ_LAUNCH_CHECK();
   return LSQ_OK;
 }
@@ -451,8 +581,13 @@ lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t s
                                                          row0, nkb, nt, nct, pk);
     LSQ_LAUNCH_CHECK();
     const int acc = kb0 > 0 ? 1 : 0;
-    st = nt == 512 ? launch_tc<512, 2, 512>(ctx, grid, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, acc, part, err)
-                   : launch_tc<256, 4, 512>(ctx, grid, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, acc, part, err);
+    // a CTA pair shares S when d needs two 512-column tiles (nt = 256 only for d <= 256)
+    if (nt == 512 && nct % 2 == 0)
+      st = launch_tc<512, 2, 2>(ctx, grid, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, acc, part, err);
+    else if (nt == 512)
+      st = launch_tc<512, 2, 1>(ctx, grid, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, acc, part, err);
+    else
+      st = launch_tc<256, 4, 1>(ctx, grid, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, acc, part, err);
     if (st != LSQ_OK) return st;
   }
   const int64_t md = (int64_t)m * d;
