@@ -147,10 +147,6 @@ __device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
-}
-
 // bounded wait with cluster-scope acquire (the arrivals include other CTAs' releases)
 __device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity, int* err) {
   uint32_t spins = 0;
@@ -170,8 +166,12 @@ __device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_
   }
 }
 
-__device__ __forceinline__ void st_cluster_v2(uint32_t addr, uint32_t a, uint32_t b) {
-  asm volatile("st.shared::cluster.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+// bulk copy of `bytes` from this CTA's shared memory to a shared::cluster address (another
+// CTA of the cluster), completion counted on the mbarrier at `bar` (shared::cluster)
+__device__ __forceinline__ void bulk_s2peer(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "r"(smem_u32(src)), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -253,14 +253,15 @@ __global__ void __launch_bounds__(256) pack_kernel(const TA* __restrict__ A, int
   }
 }
 
-// Warp roles: warps 0..15 generate S (one (row pair, k-group) unit per thread and stage), warp
-// 16 (one elected lane) starts the bulk copies of A's blobs and issues the MMAs.  Stage s is
-// handed over through three mbarriers: `full` (the blob landed, bytes counted), `sfull` (every
-// generating warp of every CTA of the cluster wrote its part of S: 16 x CL arrivals) and
-// `empty` (the MMAs that read the stage completed, one commit per CTA of the cluster).  No
-// CTA-wide barrier runs inside the loop.  CL = 2: the two CTAs of a cluster own adjacent
-// column tiles of the same rows of SA, so they need the same S; each generates 4 of the 8
-// K-columns of every core-matrix row and stores them into both CTAs' stages.
+// Warp roles: warps 0..15 generate S, warp 16 starts the bulk copies of A's blobs and issues
+// the MMAs (one elected lane; the whole warp waits).  Stage s is handed over through mbarriers:
+// `full` (the blob landed, bytes counted), `gen` (every generating warp of this CTA wrote its
+// part of S and fenced it for the async proxy), `sfull` (CL = 2: the other CTA's half of S
+// landed, bytes counted) and `empty` (the MMAs that read the stage completed, one commit per
+// CTA of the cluster).  No CTA-wide barrier runs inside the loop.  CL = 2: the two CTAs of a
+// cluster own adjacent column tiles of the same rows of SA, so they need the same S; CTA r
+// generates the K-steps 2r and 2r + 1 of each stage (one contiguous 8 KB half) and sends it
+// to the other CTA with one shared-to-shared bulk copy, so S is generated once per row tile.
 template <int NT, int STAGES, int CL>
 __global__ void __launch_bounds__(TC_GEN + 32, 1)
     gauss_tc_kernel(const uint8_t* __restrict__ pk, int64_t nkb, int nct, int d, int m, uint64_t seed, uint32_t t,
@@ -272,11 +273,13 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
   constexpr int PER = 8 / CL;                      // K-columns of a unit this CTA generates
   constexpr int GW = TC_GEN / 32;                  // generating warps
   static_assert(CL == 1 || CL == 2, "a single CTA or a CTA pair");
-  static_assert(UNITS == TC_GEN, "one unit per generating thread and stage");
+  static_assert(UNITS == TC_GEN, "one unit (or two half units) per generating thread and stage");
+  constexpr uint32_t HALF_A = A_BYTES / 2;        // one CTA's part of a stage of S (CL = 2)
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
   __shared__ __align__(8) uint64_t full[STAGES];
+  __shared__ __align__(8) uint64_t gen[STAGES];
   __shared__ __align__(8) uint64_t sfull[STAGES];
   __shared__ __align__(8) uint64_t empty[STAGES];
   __shared__ uint32_t tmem_base_s;
@@ -291,7 +294,8 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&sfull[s], GW * CL);
+      mbar_init(&gen[s], GW);
+      mbar_init(&sfull[s], 1);
       mbar_init(&empty[s], CL);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -303,20 +307,25 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
   bool ok = true;
-  int64_t copies = 0;  // bulk copies started (MMA lane)
+  int64_t copies = 0;  // bulk copies of blobs started (MMA warp)
+  int64_t armed = 0;   // CL = 2: stages armed for the other CTA's half of S (MMA warp)
 
   if (warp < GW) {
     // ---- generators
     const RoundKeys keys = round_keys(seed);
-    const int u = tid;
+    // CL = 1: thread -> unit (row pair jp, k-group kg), a warp's stores fill 512 contiguous
+    // bytes.  CL = 2: thread -> half unit (k-values 4 hq .. 4 hq + 3) of the 256 units of this
+    // CTA's K-steps 2 rank, 2 rank + 1; a warp's 8-byte stores fill 256 contiguous bytes.
+    const int u = CL == 1 ? tid : tid >> 1, hq = CL == 1 ? 0 : tid & 1;
     const int ln = u & 31, blk = u >> 5;
-    const int kk = blk & 3, gpair = blk >> 2;
+    const int kk = CL == 1 ? (blk & 3) : 2 * (int)rank + (blk & 1);
+    const int gpair = CL == 1 ? blk >> 2 : blk >> 1;
     const int r8 = ln & 7, kc = (ln >> 3) & 1, gsub = ln >> 4;
     const int jp = 8 * (2 * gpair + gsub) + r8;
     const int kg = 2 * kk + kc;
     const uint32_t qq = (uint32_t)((j0 >> 1) + jp);
-    const uint32_t off_e = core_offset(TC_M, jp, kg) + rank * (PER * 2);
-    const uint32_t off_o = core_offset(TC_M, jp + 64, kg) + rank * (PER * 2);
+    const uint32_t off_e = core_offset(TC_M, jp, kg) + hq * (PER * 2);
+    const uint32_t off_o = core_offset(TC_M, jp + 64, kg) + hq * (PER * 2);
     for (int64_t step = 0; step < nsteps; ++step) {
       const int s = (int)(step % STAGES);
       // the MMAs (of every CTA of the cluster) that read this stage STAGES steps ago are done
@@ -330,7 +339,7 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
       // z(2q, i) (cosine) and z(2q + 1, i) (sine) in FP32 from the same Philox words as the
       // FP64 definition (the uniforms keep the top 24 of their 53 bits; BF16 keeps 8); the
       // PER Philox streams of the unit advance round by round together
-      const uint32_t ia0 = (uint32_t)(row0 + (kb_begin + step) * TC_KS) + (uint32_t)(kg * 8) + rank * PER;
+      const uint32_t ia0 = (uint32_t)(row0 + (kb_begin + step) * TC_KS) + (uint32_t)(kg * 8) + hq * PER;
       uint4 w[PER];
 #pragma unroll
       for (int q = 0; q < PER; ++q) w[q] = make_uint4(ia0 + (uint32_t)q, qq, t, TAG_GAUSS);
@@ -359,25 +368,14 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
       if constexpr (CL == 1) {
         *reinterpret_cast<uint4*>(stA + off_e) = make_uint4(ev[0], ev[1], ev[2], ev[3]);
         *reinterpret_cast<uint4*>(stA + off_o) = make_uint4(od[0], od[1], od[2], od[3]);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       } else {
-        const uint32_t le = smem_u32(stA + off_e), lo = smem_u32(stA + off_o);
-#pragma unroll
-        for (int c = 0; c < CL; ++c) {
-          const uint32_t peer = (rank + (uint32_t)c) % CL;
-          st_cluster_v2(peer_addr(le, peer), ev[0], ev[1]);
-          st_cluster_v2(peer_addr(lo, peer), od[0], od[1]);
-        }
-        asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+        *reinterpret_cast<uint2*>(stA + off_e) = make_uint2(ev[0], ev[1]);
+        *reinterpret_cast<uint2*>(stA + off_o) = make_uint2(od[0], od[1]);
       }
+      // generic-proxy writes -> visible to the async proxy (tensor core, bulk copy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive_local(&sfull[s]);
-        if constexpr (CL > 1) {
-#pragma unroll
-          for (int c = 1; c < CL; ++c) mbar_arrive_remote(peer_addr(smem_u32(&sfull[s]), (rank + (uint32_t)c) % CL));
-        }
-      }
+      if (lane == 0) mbar_arrive_local(&gen[s]);
     }
   } else {
     // ---- copies and MMAs: the whole warp waits, lane 0 issues
@@ -396,8 +394,21 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
       }
       ++copies;
       const uint32_t par = (uint32_t)((step / STAGES) & 1);
-      const bool got = (CL > 1 ? mbar_wait_cluster_bounded(&sfull[s], par, err) : mbar_wait_bounded(&sfull[s], par, err)) &&
-                       mbar_wait_bounded(&full[s], par, err);
+      bool got = mbar_wait_bounded(&gen[s], par, err);
+      if constexpr (CL > 1) {
+        if (lane == 0) {
+          // this CTA's half of S to the other CTA (its stage s is free: `empty` counted its
+          // commit too), and this CTA expects the other half
+          const uint32_t peer = rank ^ 1u;
+          if (got) bulk_s2peer(peer_addr(smem_u32(stA + rank * HALF_A), peer), stA + rank * HALF_A, HALF_A,
+                               peer_addr(smem_u32(&sfull[s]), peer));
+          mbar_expect_tx(&sfull[s], HALF_A);
+        }
+        ++armed;
+        __syncwarp();
+        got = got && mbar_wait_cluster_bounded(&sfull[s], par, err);
+      }
+      got = got && mbar_wait_bounded(&full[s], par, err);
       if (!__all_sync(0xffffffffu, got)) {
         ok = false;
         break;
@@ -428,9 +439,12 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
   }
   ok = !__syncthreads_or(!ok);
   if (!ok && warp == GW) {
-    // a failed run may leave bulk copies in flight: wait (bounded) for each stage's last one
+    // a failed run may leave bulk copies in flight (blobs, and the other CTA's halves of S
+    // into this CTA): wait (bounded) for each stage's last one
     for (int64_t c = (copies > STAGES ? copies - STAGES : 0); c < copies; ++c)
       (void)mbar_wait_bounded(&full[c % STAGES], (uint32_t)((c / STAGES) & 1), err);
+    for (int64_t c = (armed > STAGES ? armed - STAGES : 0); c < armed; ++c)
+      (void)mbar_wait_bounded(&sfull[c % STAGES], (uint32_t)((c / STAGES) & 1), err);
   }
   __syncwarp();
   tc_fence_after();
