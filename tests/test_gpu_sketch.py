@@ -64,7 +64,8 @@ def test_srht_fp64(L, ctx, n, d, m, seed):
 
 @pytest.mark.parametrize("n,d,m,dtype,ld", [(5000, 13, 700, np.float64, 14), (5000, 13, 700, np.float32, 16),
                                              (9000, 24, 4096, np.float64, 24), (9000, 24, 4097, np.float64, 24),
-                                             (3000, 20, 300, np.float64, 21), (2048, 8, 64, np.float64, 8)])
+                                             (3000, 20, 300, np.float64, 21), (2048, 8, 64, np.float64, 8),
+                                             (2048, 3, 64, np.float64, 4), (3000, 5, 100, np.float32, 8)])
 def test_srht_fp32_arithmetic_layouts(L, ctx, n, d, m, dtype, ld):
     """FP32-arithmetic SRHT over row strides and sizes that take the staged (tensor-copy) kernel
     -- ragged n and d, FP32 storage, 8 sampled rows per thread -- and ones that do not (more
