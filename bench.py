@@ -36,7 +36,7 @@ SOLVE_KERNEL = "solve_kernel"
 # kernels' sources hash to the captured ones.
 SOLVE_TRAFFIC = {"ratio_solve": (14.553369e9 + 0.035296768e9) / 14495514624,
                  "ratio_with_copy": 16142203008.0 / 16106127360, "sources_sha256":
-                 "76ae7aef4829a57935c1877664b65173d25e0b417dcda9455b9c88bb7c5f7c5d"}
+                 "1a8d144bf30235183f0fe8d3075270a436e785d88c1e3c5d34dbf5a5f054046b"}
 
 
 def solve_sources_sha256() -> str:
