@@ -137,6 +137,19 @@ struct TileSmem {
   double Y[2][32][8];
 };
 
+// the diagonal-block routines' arrays
+struct DiagSmem {
+  double a[32][33], b[32][33], c[32][33];
+  double rinv[32], pinv[32];
+  int bad;
+};
+
+// one shared workspace: a CTA runs one of these routines at a time
+union FactorSmem {
+  TileSmem tile;
+  DiagSmem diag;
+};
+
 // 8-byte asynchronous copies global -> shared (the thread does not wait for the data)
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
@@ -189,28 +202,25 @@ __device__ __forceinline__ void tri_decode(int e, int& a, int& b) {
   a = e - bb * (bb + 1) / 2;
 }
 
-// Cholesky of one 32 x 32 diagonal block and the inverse of its factor, by the whole CTA.
-// FP64 instructions are costly on this part (a warp instruction holds a sub-partition's FP64
-// unit for ~70 cycles whatever its active lanes), so both steps are right-looking with the
-// live entries of each step packed densely onto threads, one barrier per step:
-//   Cholesky, step j: R[j][l] = G[j][l] / sqrt(G[j][j]) and G[i][l] -= G[j][i] G[j][l] / G[j][j]
-//     for j < i <= l; the thread that updates G[j+1][j+1] also takes its reciprocal square
-//     root, so the next pivot is ready at the barrier;
-//   inverse, step i (from the bottom): W[i][l] = (delta_il - S[i][l]) / R[i][i] for l >= i and
-//     S[k][l] += R[k][i] W[i][l] for k < i <= l (S in the block's buffer).
+// Cholesky of one 32 x 32 diagonal block by the whole CTA: R into Rkk, and 1 / R[i][i] into the
+// block's own diagonal in G (the block is not read again).  FP64 instructions are costly on
+// this part (a warp instruction holds a sub-partition's FP64 unit for ~70 cycles whatever its
+// active lanes), so the factorisation is right-looking with the live entries of each step
+// packed densely onto threads, one barrier per step:
+//   step j: R[j][l] = G[j][l] / sqrt(G[j][j]) and G[i][l] -= G[j][i] G[j][l] / G[j][j] for
+//   j < i <= l; the thread that updates G[j+1][j+1] also takes its reciprocal square root, so
+//   the next pivot is ready at the barrier.
 // Sets *err to LSQ_ERR_RANK on a non-positive or non-finite pivot.
-__device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, int* err) {
-  __shared__ double Gs[32][33];  // the block, updated in place; then the inverse's sums S
-  __shared__ double Rs[32][33];
-  __shared__ double Ws[32][33];
-  __shared__ double rinv[32], pinv[32];
-  __shared__ int bad;
+__device__ void diag_chol(DiagSmem& sm, double* Gkk, double* Rkk, int ld, int* err) {
+  double (*Gs)[33] = sm.a;
+  double (*Rs)[33] = sm.b;
+  double* rinv = sm.rinv;
+  double* pinv = sm.pinv;
+  int& bad = sm.bad;
   const int tid = threadIdx.x, nt = blockDim.x;
-  // stage the block (one round trip for the whole CTA)
   for (int e = tid; e < 1024; e += nt) {
     Gs[e >> 5][e & 31] = Gkk[(int64_t)(e >> 5) * ld + (e & 31)];
     Rs[e >> 5][e & 31] = 0.0;
-    Ws[e >> 5][e & 31] = 0.0;
   }
   if (tid == 0) bad = 0;
   __syncthreads();
@@ -245,26 +255,62 @@ __device__ void diag_block(const double* Gkk, double* Rkk, double* Wkk, int ld, 
     }
     __syncthreads();
   }
-  if (!bad) {
-    for (int e = tid; e < 1024; e += nt) Gs[e >> 5][e & 31] = 0.0;
-    __syncthreads();
-    for (int i = 31; i >= 0; --i) {
-      const int w = 32 - i;
-      const double ri = rinv[i];
-      for (int e = tid; e < (i + 1) * w; e += nt) {
-        const int k = e / w, l = i + e % w;
-        const double wil = ((i == l ? 1.0 : 0.0) - Gs[i][l]) * ri;
-        if (k == i) Ws[i][l] = wil;
-        else Gs[k][l] = fma(Rs[k][i], wil, Gs[k][l]);
-      }
-      __syncthreads();
-    }
-  }
-  for (int e = tid; e < 1024; e += nt) {
-    Rkk[(int64_t)(e >> 5) * ld + (e & 31)] = Rs[e >> 5][e & 31];
-    Wkk[(int64_t)(e >> 5) * ld + (e & 31)] = Ws[e >> 5][e & 31];
-  }
+  for (int e = tid; e < 1024; e += nt) Rkk[(int64_t)(e >> 5) * ld + (e & 31)] = Rs[e >> 5][e & 31];
+  if (tid < 32) Gkk[(int64_t)tid * ld + tid] = rinv[tid];
   if (tid == 0 && bad) atomicCAS(err, 0, (int)LSQ_ERR_RANK);
+  __syncthreads();
+}
+
+// W = R^{-1} of one 32 x 32 upper triangular block (Rkk; 1 / R[i][i] on the block's diagonal in
+// G), right-looking from the bottom row, one barrier per step:
+//   W[i][l] = (delta_il - S[i][l]) / R[i][i] for l >= i, then S[k][l] += R[k][i] W[i][l], k < i <= l.
+__device__ void diag_inv(DiagSmem& sm, const double* Gkk, const double* Rkk, double* Wkk, int ld) {
+  double (*Rs)[33] = sm.a;
+  double (*Ss)[33] = sm.b;
+  double (*Ws)[33] = sm.c;
+  double* rinv = sm.rinv;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < 1024; e += nt) {
+    Rs[e >> 5][e & 31] = Rkk[(int64_t)(e >> 5) * ld + (e & 31)];
+    Ss[e >> 5][e & 31] = 0.0;
+    Ws[e >> 5][e & 31] = 0.0;
+  }
+  if (tid < 32) rinv[tid] = Gkk[(int64_t)tid * ld + tid];
+  __syncthreads();
+  for (int i = 31; i >= 0; --i) {
+    const int w = 32 - i;
+    const double ri = rinv[i];
+    for (int e = tid; e < (i + 1) * w; e += nt) {
+      const int k = e / w, l = i + e % w;
+      const double wil = ((i == l ? 1.0 : 0.0) - Ss[i][l]) * ri;
+      if (k == i) Ws[i][l] = wil;
+      else Ss[k][l] = fma(Rs[k][i], wil, Ss[k][l]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < 1024; e += nt) Wkk[(int64_t)(e >> 5) * ld + (e & 31)] = Ws[e >> 5][e & 31];
+  __syncthreads();
+}
+
+// 32 x 8 panel task: out = R^{-T} Gt (R = Rkk upper, 1 / R[i][i] on the diagonal of Gkk) by
+// forward substitution: warp c solves column c, lane i keeps row i's running value, and each
+// step's new unknown is broadcast by a shuffle (no CTA barrier inside the solve).
+__device__ void trsm_task(TileSmem& sm, double* out, const double* Rkk, const double* Gt, const double* Gkk, int ld) {
+  const int tid = threadIdx.x, lane = tid & 31, c = tid >> 5;
+  for (int e = tid; e < 1024; e += blockDim.x) sm.X[0][e >> 5][e & 31] = Rkk[(int64_t)(e >> 5) * ld + (e & 31)];
+  __syncthreads();
+  if (c < 8) {
+    double acc = Gt[(int64_t)lane * ld + c];
+    const double di = Gkk[(int64_t)lane * ld + lane];
+    double x = 0.0;
+#pragma unroll 4
+    for (int p = 0; p < 32; ++p) {
+      const double xp = __shfl_sync(0xffffffffu, acc * di, p);
+      if (lane == p) x = xp;
+      if (lane > p) acc = fma(-sm.X[0][p][lane], xp, acc);
+    }
+    out[(int64_t)lane * ld + c] = x;
+  }
   __syncthreads();
 }
 
@@ -274,21 +320,23 @@ __device__ void chol_inv_body(double* __restrict__ G, double* __restrict__ Rf, d
                               double* __restrict__ Tb, int nblk, const int4* __restrict__ nodes,
                               const int* __restrict__ level_start, int nlevels, unsigned* bar, unsigned nb,
                               unsigned rank, int* err) {
-  __shared__ TileSmem sm;
+  __shared__ FactorSmem fsm;
+  TileSmem& sm = fsm.tile;
   const int dp = nblk * 32;
   // Look-ahead: CTA 0 applies the trailing update to the next diagonal block first and
   // factors it at once, while the other CTAs update the rest of the trailing matrix; each
   // panel then needs two grid barriers.
-  if (rank == 0) diag_block(G, Rf, Wf, dp, err);
+  if (rank == 0) diag_chol(fsm.diag, G, Rf, dp, err);
   if (grid_barrier(bar, nb, err)) return;
   for (int k = 0; k < nblk; ++k) {
     const int64_t kk = (int64_t)k * 32;
     const int rest = nblk - 1 - k;
-    // panel: R[k][j] = W[k][k]^T G[k][j]
+    // panel: R[k][j] = R[k][k]^{-T} G[k][j] (forward substitution; the inverses of the
+    // diagonal blocks are taken after the factorisation, off this chain)
     for (int task = rank; task < rest * 4; task += nb) {
       const int j = k + 1 + task / 4, q = task % 4;
       const int64_t col = (int64_t)j * 32 + q * 8;
-      tile_task(sm, Rf + kk * dp + col, Wf + kk * dp + kk, true, G + kk * dp + col, 32, dp, 1.0, false);
+      trsm_task(sm, Rf + kk * dp + col, Rf + kk * dp + kk, G + kk * dp + col, G + kk * dp + kk, dp);
     }
     if (grid_barrier(bar, nb, err)) return;
     if (rest == 0) break;
@@ -326,7 +374,7 @@ __device__ void chol_inv_body(double* __restrict__ G, double* __restrict__ Rf, d
         __threadfence();
       }
       __syncthreads();
-      if (*(volatile int*)err == 0) diag_block(G + k1 * dp + k1, Rf + k1 * dp + k1, Wf + k1 * dp + k1, dp, err);
+      if (*(volatile int*)err == 0) diag_chol(fsm.diag, G + k1 * dp + k1, Rf + k1 * dp + k1, dp, err);
     }
     const int others = nb > 1 ? (int)nb - 1 : 1;
     const int first = nb > 1 ? (int)rank - 1 : 0;
@@ -344,6 +392,12 @@ __device__ void chol_inv_body(double* __restrict__ G, double* __restrict__ Rf, d
     }
     if (grid_barrier(bar, nb, err)) return;
   }
+  // the inverses of the diagonal blocks, all at once
+  for (int k = (int)rank; k < nblk; k += (int)nb) {
+    const int64_t kk = (int64_t)k * 32;
+    diag_inv(fsm.diag, G + kk * dp + kk, Rf + kk * dp + kk, Wf + kk * dp + kk, dp);
+  }
+  if (grid_barrier(bar, nb, err)) return;
   // W = R^{-1}: merge sibling blocks bottom-up
   for (int lev = 0; lev < nlevels; ++lev) {
     const int n0 = level_start[lev], n1 = level_start[lev + 1];
@@ -378,7 +432,7 @@ __device__ void chol_inv_body(double* __restrict__ G, double* __restrict__ Rf, d
   }
 }
 
-__global__ void __launch_bounds__(256) chol_inv_kernel(double* __restrict__ G, double* __restrict__ Rf,
+__global__ void __launch_bounds__(256, 2) chol_inv_kernel(double* __restrict__ G, double* __restrict__ Rf,
                                                        double* __restrict__ Wf, double* __restrict__ Tb, int nblk,
                                                        const int4* __restrict__ nodes, const int* __restrict__ level_start,
                                                        int nlevels, unsigned* bar, int* err) {
