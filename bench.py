@@ -31,12 +31,13 @@ SOLVE_KERNEL = "solve_kernel"
 # DRAM traffic of the mixed solve phase from one ncu capture (n = 2^18, d = 512, SRHT m = 4096, 25 passes
 # of which 2 exact; profiles/solve_kernel_mixed_262144x512_srht4096.md): dram__bytes_read.sum +
 # dram__bytes_write.sum divided by the algorithmic bytes, for solve_kernel<double, 16, MIXED, COPY> alone
-# (the FP32 copy supplied by the sketch) and with the solve's own narrow_copy_kernel<16>.  Scaled to a
+# (the FP32 copy supplied by the sketch) and with the solve's own narrow_copy_kernel<16> (1.554 GB, from
+# a full capture of that kernel, unchanged since).  Scaled to a
 # launch of the bench by its algorithmic bytes (units processed: passes x rows); reported only while the
 # kernels' sources hash to the captured ones.
-SOLVE_TRAFFIC = {"ratio_solve": (14.553369e9 + 0.035296768e9) / 14495514624,
-                 "ratio_with_copy": 16142203008.0 / 16106127360, "sources_sha256":
-                 "1a8d144bf30235183f0fe8d3075270a436e785d88c1e3c5d34dbf5a5f054046b"}
+SOLVE_TRAFFIC = {"ratio_solve": (14553383680 + 34299136) / 14495514624,
+                 "ratio_with_copy": (1553537240 + 14553383680 + 34299136) / 16106127360, "sources_sha256":
+                 "6d4ffa57355c67fce4b7e1bdd34151cf0fd8ea56c8d2d38f56204ef8be266794"}
 
 
 def solve_sources_sha256() -> str:

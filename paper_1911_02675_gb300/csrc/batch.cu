@@ -716,8 +716,10 @@ __device__ void direction_block(const BatchArgs& a, const BProb& pr, int blk, in
       fin[j] = isfinite(rz);
       conv[j] = fin[j] && (rz == 0.0 || rz <= pr.tol2 * bx);
       // a drop-triggered replacement within 10^2 (in norm) of the tolerance is left to the one
-      // that confirms convergence a few iterations later
-      const bool near = rz <= 1e4 * pr.tol2 * bx;
+      // that confirms convergence a few iterations later -- unless the drop since the last
+      // exact residual passes FP32's resolution (10^7 in norm), where the recursive residual
+      // is rounding noise
+      const bool near = rz <= 1e4 * pr.tol2 * bx && rz >= 1e-14 * pr.rz_rep[j];
       if (a.mixed && !after_exact && fin[j] &&
           (conv[j] || (!near && rz <= a.replace2 * pr.rz_rep[j]) || it + 1 - pr.it_last[j] >= a.refresh_every))
         need = true;
@@ -762,7 +764,9 @@ __device__ void direction_block(const BatchArgs& a, const BProb& pr, int blk, in
       continue;
     }
     ++left;
-    const double beta = rzn[j] / pr.rz[cur * kp + j];
+    // after an exact residual more than twice (in norm) the recursive one of the previous
+    // iteration, the old direction is not trusted: restart from the preconditioned residual
+    const double beta = (after_exact && rzn[j] > 4.0 * pr.rz[cur * kp + j]) ? 0.0 : rzn[j] / pr.rz[cur * kp + j];
     if (c < pr.d) {
       const double p = pr.Z[j * dp + c] + beta * pr.P[j * dp + c];
       pr.P[j * dp + c] = p;

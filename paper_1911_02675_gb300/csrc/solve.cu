@@ -256,8 +256,11 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
       bx = total(red_bx);
       bool conv = rho_new == 0.0 || rho_new <= a.tol2 * bx;
       // a drop-triggered replacement within 10^2 (in norm) of the tolerance is left to the one
-      // that confirms convergence a few iterations later
-      const bool near = rho_new <= 1e4 * a.tol2 * bx;
+      // that confirms convergence a few iterations later -- unless the drop since the last
+      // exact residual passes FP32's resolution (10^7 in norm), where the recursive residual
+      // is rounding noise
+      const bool near = rho_new <= 1e4 * a.tol2 * bx && rho_new >= 1e-14 * rho_last;
+      bool replaced = false;
       if (MIXED && (conv || (!near && rho_new <= a.replace2 * rho_last) || it + 1 - it_last >= a.refresh_every)) {
         // replace the recursive residual by b - H x evaluated in FP64
         for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec2[c] = c < d ? a.x[c] : 0.0;
@@ -276,8 +279,11 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
         conv = rho_new == 0.0 || rho_new <= a.tol2 * bx;
         rho_last = rho_new;
         it_last = it + 1;
+        replaced = true;
       }
-      const double beta = rho_new / rho;
+      // after an exact residual more than twice (in norm) the recursive one of the previous
+      // iteration, the old direction is not trusted: restart from the preconditioned residual
+      const double beta = (replaced && rho_new > 4.0 * rho) ? 0.0 : rho_new / rho;
       for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec[c] = c < d ? a.rh[c] + beta * S.vec[c] : 0.0;
       __syncthreads();
       rho = rho_new;
