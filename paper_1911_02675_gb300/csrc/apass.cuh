@@ -320,6 +320,103 @@ __device__ void fused_pass_df(const TA* __restrict__ A, int64_t ld, int d, int d
   __syncthreads();
 }
 
+// The same pass for FP64 rows, staged through shared memory: each warp has one row slot
+// (slots: LSQ_WARPS x dp doubles, which may lie in wred past its first dp entries) and, as
+// soon as the current row is split into registers, has the next row copied into the slot
+// with cp.async while it computes, so a row is in flight without holding registers (the
+// split row and the double-FP32 accumulators already fill them).  Each lane copies and reads
+// only its own elements (columns lane + 32 k): its own cp.async.wait_group orders the data,
+// and a __syncwarp (which orders the memory operations of the lanes it joins) separates the
+// loads of the current row from the copy of the next one into the same slot.  Same
+// arithmetic, in the same order, as fused_pass_df.
+__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_none() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int EPL>
+__device__ void fused_pass_df_staged(const double* __restrict__ A, int64_t ld, int d, int dp, int64_t r0, int64_t r1,
+                                     const double* vec_s, double* wred, double* qred, double* part, int P, int cta,
+                                     double* slots) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* xs = reinterpret_cast<float2*>(wred);  // (head, tail) of x, dp entries
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+    const double xv = vec_s[c];
+    const float xh = (float)xv;
+    xs[c] = make_float2(xh, (float)(xv - (double)xh));
+  }
+  double* slot = slots + (int64_t)warp * dp + lane;
+  float vh[EPL], vl[EPL];
+  bool ok[EPL];
+#pragma unroll
+  for (int k = 0; k < EPL; ++k) {
+    ok[k] = lane + 32 * k < d;
+    vh[k] = 0.0f;
+    vl[k] = 0.0f;
+    // columns at or past d are never copied: zero in the slot for the whole pass
+    if (!ok[k]) slot[32 * k] = 0.0;
+  }
+  __syncthreads();  // xs complete; no warp still reads wred from before the pass
+  int64_t i = r0 + warp;
+  if (i < r1) {
+    const double* a = A + i * ld + lane;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k)
+      if (ok[k]) cp_async_8(slot + 32 * k, a + 32 * k);
+  }
+  cp_async_commit_group();
+  for (; i < r1; i += LSQ_WARPS) {
+    cp_async_wait_none();  // row i has landed
+    float ah[EPL], al[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) split_df(slot[32 * k], ah[k], al[k]);
+    __syncwarp();
+    const int64_t inext = i + LSQ_WARPS;
+    if (inext < r1) {
+      const double* a = A + inext * ld + lane;
+#pragma unroll
+      for (int k = 0; k < EPL; ++k)
+        if (ok[k]) cp_async_8(slot + 32 * k, a + 32 * k);
+    }
+    cp_async_commit_group();
+    float wh = 0.0f, wl = 0.0f;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) {
+      const float2 xv = xs[lane + 32 * k];
+      df_fma(ah[k], al[k], xv.x, xv.y, wh, wl);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, wh, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, wl, o);
+      df_add(wh, wl, oh, ol);
+    }
+    float nh, nl;
+    two_sum(wh, wl, nh, nl);
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) df_fma(ah[k], al[k], nh, nl, vh[k], vl[k]);
+  }
+  cp_async_wait_none();
+  __syncthreads();  // every warp is done with xs and its slot before wred is overwritten
+#pragma unroll
+  for (int k = 0; k < EPL; ++k) {
+    const int c = lane + 32 * k;
+    if (c < dp) wred[warp * dp + c] = (double)vh[k] + (double)vl[k];
+  }
+  if (lane == 0) qred[warp] = 0.0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+    double sum = 0.0;
+#pragma unroll
+    for (int w2 = 0; w2 < LSQ_WARPS; ++w2) sum += wred[w2 * dp + c];
+    part[(int64_t)c * P + cta] = sum;
+  }
+  if (threadIdx.x == 0) part[(int64_t)dp * P + cta] = 0.0;
+  __syncthreads();
+}
+
 // sum_{j < P} src[j] by one warp, fixed order
 __device__ __forceinline__ double warp_sum_strip(const double* src, int P) {
   const int lane = threadIdx.x & 31;

@@ -170,4 +170,38 @@ __device__ __forceinline__ int grid_barrier(unsigned* bar, unsigned nblocks, int
   return *(volatile int*)err;
 }
 
+// Grid-wide barrier over an arrival count that only grows within a launch (zeroed before
+// it): every CTA passes the same sequence of barriers, so the k-th one of each CTA waits for
+// the count to reach k * nblocks (`target` is the CTA's running k * nblocks).  Nothing is
+// reset, so the last arrival costs one add and each waiter one acquire load per poll.  The
+// wait is bounded like grid_barrier's.
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int grid_sync_count(unsigned long long* cnt, unsigned long long& target, unsigned nblocks,
+                                               int* err) {
+  __syncthreads();
+  target += nblocks;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
+    const uint64_t t0 = global_ns();
+    unsigned spins = 0;
+    while (ld_acquire_u64(cnt) < target) {
+      if (*(volatile int*)err != 0) break;  // another CTA already gave up
+      if (++spins > LSQ_SPIN_LIMIT || global_ns() - t0 > LSQ_WAIT_NS) {
+        atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)err;
+}
+
 static inline int lsq_ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

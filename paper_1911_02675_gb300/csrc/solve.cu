@@ -108,9 +108,12 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
   S.vec = smem;
   S.vec2 = S.vec + dp;
   S.wred = S.vec2 + dp;
-  S.qred = S.wred + LSQ_WARPS * dp;
+  double* stage = S.wred + LSQ_WARPS * dp;  // dp: r or z staging for the triangular products
+  S.qred = stage + dp;
   S.scal = S.qred + LSQ_WARPS;
-  double* stage = S.scal + 8;  // dp: r or z staging for the triangular products
+  // the staged exact pass (MIXED, FP64 A): x in wred[0, dp), one row slot per warp in
+  // wred[dp, 8 dp) + stage
+  double* slots = S.wred + dp;
 
   const int P = gridDim.x, cta = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -118,6 +121,10 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
   const int64_t r0 = (int64_t)cta * a.rows_per_cta;
   const int64_t r1 = min(a.n, r0 + a.rows_per_cta);
   const TA* A = reinterpret_cast<const TA*>(a.A);
+  // grid barriers: a count that only grows (bar[2..3], zeroed before the launch)
+  unsigned long long bar_target = 0;
+  unsigned long long* bar_count = reinterpret_cast<unsigned long long*>(a.bar + 2);
+  auto gsync = [&]() -> int { return grid_sync_count(bar_count, bar_target, P, a.err); };
   double* red_rho = a.red;
   double* red_bx = a.red + P;
   int passes = 0, exact_passes = 0;
@@ -132,7 +139,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
       const double zi = warp_row_dot(a.WT + (int64_t)i * d, stage, 0, i + 1);
       if (lane == 0) a.z[i] = zi;
     }
-    if (grid_barrier(a.bar, P, a.err)) return 1;
+    if (gsync()) return 1;
     for (int c = threadIdx.x; c < dp; c += blockDim.x) stage[c] = c < d ? a.z[c] : 0.0;
     __syncthreads();
     double part_rho = 0.0;
@@ -150,7 +157,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
       for (int w = 0; w < LSQ_WARPS; ++w) s += S.qred[w];
       red_rho[cta] = s;
     }
-    return grid_barrier(a.bar, P, a.err);
+    return gsync();
   };
 
   // every CTA: the same fixed-order sums of the per-CTA scalars
@@ -163,6 +170,18 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
     const double s = S.scal[7];
     __syncthreads();
     return s;
+  };
+
+  // the same sums for two strips at once (warps 0 and 1)
+  auto total2 = [&](const double* red0, const double* red1, double& s0, double& s1) {
+    if (warp < 2) {
+      const double s = warp_sum_strip(warp == 0 ? red0 : red1, P);
+      if (lane == 0) S.scal[6 + warp] = s;
+    }
+    __syncthreads();
+    s0 = S.scal[6];
+    s1 = S.scal[7];
+    __syncthreads();
   };
 
   // partial of <b, x> over the columns this CTA owns, x read from `xsrc`
@@ -182,7 +201,10 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
 
   // a pass whose v is accurate to (nearly) FP64: native FP64, or double-FP32 in MIXED mode
   auto exact_pass = [&](const double* vec) {
-    if (MIXED) fused_pass_df<TA, EPL>(A, a.ld, d, dp, r0, r1, vec, S.wred, S.qred, a.part, P, cta);
+    if constexpr (MIXED && sizeof(TA) == 8)
+      fused_pass_df_staged<EPL>(reinterpret_cast<const double*>(A), a.ld, d, dp, r0, r1, vec, S.wred, S.qred, a.part,
+                                P, cta, slots);
+    else if (MIXED) fused_pass_df<TA, EPL>(A, a.ld, d, dp, r0, r1, vec, S.wred, S.qred, a.part, P, cta);
     else fused_pass<TA, EPL, (EPL <= 4)>(A, a.ld, d, dp, r0, r1, vec, S.wred, S.qred, a.part, P, cta);
   };
 
@@ -205,17 +227,17 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
       exact_pass(S.vec);
       ++passes;
       ++exact_passes;
-      if (grid_barrier(a.bar, P, a.err)) return;
+      if (gsync()) return;
     }
     for (int c = gw; c < d; c += nw) {
       const double v = a.x0_zero ? 0.0 : warp_sum_strip(a.part + (int64_t)c * P, P);
       if (lane == 0) a.r[c] = a.b[c] - v;
     }
     bx_partial(a.x);
-    if (grid_barrier(a.bar, P, a.err)) return;
+    if (gsync()) return;
     if (precond(a.r, a.rh)) return;
-    double rho = total(red_rho);
-    double bx = total(red_bx);
+    double rho, bx;
+    total2(red_rho, red_bx, rho, bx);
     for (int c = threadIdx.x; c < dp; c += blockDim.x) S.vec[c] = c < d ? a.rh[c] : 0.0;
     __syncthreads();
     est = (bx > 0.0) ? sqrt(a.lam1 * rho / bx) : 0.0;
@@ -230,11 +252,27 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
         ++exact_passes;
       }
       ++passes;
-      if (grid_barrier(a.bar, P, a.err)) return;
-      if (warp == 0) {
-        const double qq = warp_sum_strip(a.part + (int64_t)dp * P, P);
-        if (lane == 0) S.scal[0] = qq;
+      if (gsync()) return;
+      // q (warp 0) and the first column of every warp are summed in one round of loads, with
+      // the same per-strip order as warp_sum_strip; b, x and r of that column come with them
+      double sq = 0.0, sv = 0.0, b0 = 0.0, x0 = 0.0, rr0 = 0.0;
+      {
+        const double* pq = a.part + (int64_t)dp * P;
+        const double* pv = a.part + (int64_t)gw * P;
+        const bool hasv = gw < d;
+        if (hasv && lane == 0) {
+          b0 = a.b[gw];
+          x0 = a.x[gw];
+          rr0 = a.r[gw];
+        }
+        for (int j = lane; j < P; j += 32) {
+          if (warp == 0) sq += pq[j];
+          if (hasv) sv += pv[j];
+        }
+        sq = warp_sum(sq);
+        sv = warp_sum(sv);
       }
+      if (warp == 0 && lane == 0) S.scal[0] = sq;
       __syncthreads();
       const double q = S.scal[0];
       if (!(q > 0.0) || !isfinite(q) || !isfinite(rho)) {
@@ -242,18 +280,34 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
         break;
       }
       const double alpha = rho / q;
-      for (int c = gw; c < d; c += nw) {
+      // x += alpha p, r -= alpha H p, and this CTA's partial of <b, x> (bx_partial's order)
+      double bxp = 0.0;
+      if (gw < d && lane == 0) {
+        const double xn = x0 + alpha * S.vec[gw];
+        a.x[gw] = xn;
+        a.r[gw] = rr0 - alpha * sv;
+        bxp += b0 * xn;
+      }
+      for (int c = gw + nw; c < d; c += nw) {  // more columns than warps in the grid
         const double v = warp_sum_strip(a.part + (int64_t)c * P, P);
         if (lane == 0) {
-          a.x[c] += alpha * S.vec[c];
+          const double xn = a.x[c] + alpha * S.vec[c];
+          a.x[c] = xn;
           a.r[c] -= alpha * v;
+          bxp += a.b[c] * xn;
         }
       }
-      bx_partial(a.x);
-      if (grid_barrier(a.bar, P, a.err)) return;
+      if (lane == 0) S.qred[warp] = bxp;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < LSQ_WARPS; ++w) t += S.qred[w];
+        red_bx[cta] = t;
+      }
+      if (gsync()) return;
       if (precond(a.r, a.rh)) return;
-      double rho_new = total(red_rho);
-      bx = total(red_bx);
+      double rho_new;
+      total2(red_rho, red_bx, rho_new, bx);
       bool conv = rho_new == 0.0 || rho_new <= a.tol2 * bx;
       // a drop-triggered replacement within 10^2 (in norm) of the tolerance is left to the one
       // that confirms convergence a few iterations later -- unless the drop since the last
@@ -268,12 +322,12 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
         exact_pass(S.vec2);
         ++passes;
         ++exact_passes;
-        if (grid_barrier(a.bar, P, a.err)) return;
+        if (gsync()) return;
         for (int c = gw; c < d; c += nw) {
           const double v = warp_sum_strip(a.part + (int64_t)c * P, P);
           if (lane == 0) a.r[c] = a.b[c] - v;
         }
-        if (grid_barrier(a.bar, P, a.err)) return;
+        if (gsync()) return;
         if (precond(a.r, a.rh)) return;
         rho_new = total(red_rho);
         conv = rho_new == 0.0 || rho_new <= a.tol2 * bx;
@@ -309,13 +363,13 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
         f32_pass(S.vec);
       }
       ++passes;
-      if (grid_barrier(a.bar, P, a.err)) return;
+      if (gsync()) return;
       for (int c = gw; c < d; c += nw) {
         const double v = warp_sum_strip(a.part + (int64_t)c * P, P);
         if (lane == 0) a.g[c] = v - a.b[c];
       }
       bx_partial(S.vec);
-      if (grid_barrier(a.bar, P, a.err)) return;
+      if (gsync()) return;
       if (precond(a.g, a.rh)) return;
       const double gam = total(red_rho);
       const double bx = total(red_bx);
@@ -403,7 +457,8 @@ static lsq_status check_matrix(const lsq_matrix* A) {
   return LSQ_OK;
 }
 
-static size_t solve_smem_bytes(int dp) { return (size_t)(dp * 2 + LSQ_WARPS * dp + LSQ_WARPS + 8 + dp) * 8; }
+// vec, vec2, wred, stage, qred, scal
+static size_t solve_smem_bytes(int dp) { return (size_t)(dp * 2 + LSQ_WARPS * dp + dp + LSQ_WARPS + 8) * 8; }
 
 static double theta_ratio(int type, double m, double d, double N) {
   // mu = theta1 / theta2 for refreshed embeddings
