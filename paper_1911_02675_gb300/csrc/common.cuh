@@ -174,7 +174,9 @@ __device__ __forceinline__ int grid_barrier(unsigned* bar, unsigned nblocks, int
 // it): every CTA passes the same sequence of barriers, so the k-th one of each CTA waits for
 // the count to reach k * nblocks (`target` is the CTA's running k * nblocks).  Nothing is
 // reset, so the last arrival costs one add and each waiter one acquire load per poll.  The
-// wait is bounded like grid_barrier's.
+// CTA barrier orders its threads' writes before thread 0's release-add, the release is
+// cumulative, and the acquire load that sees the count orders the reads after the closing
+// CTA barrier, so no separate fence is needed.  The wait is bounded like grid_barrier's.
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -186,7 +188,6 @@ __device__ __forceinline__ int grid_sync_count(unsigned long long* cnt, unsigned
   __syncthreads();
   target += nblocks;
   if (threadIdx.x == 0) {
-    __threadfence();
     asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
     const uint64_t t0 = global_ns();
     unsigned spins = 0;
@@ -198,7 +199,6 @@ __device__ __forceinline__ int grid_sync_count(unsigned long long* cnt, unsigned
       }
       __nanosleep(32);
     }
-    __threadfence();
   }
   __syncthreads();
   return *(volatile int*)err;

@@ -117,7 +117,10 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
 
   const int P = gridDim.x, cta = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gw = cta * LSQ_WARPS + warp, nw = P * LSQ_WARPS;
+  const int nw = P * LSQ_WARPS;
+  // the grid's warps take the columns of the vectors and the rows of W in turn, CTA-major
+  // (column i on CTA i mod P), so their FP64 work and loads run on every SM
+  const int cw = cta + P * warp;
   const int64_t r0 = (int64_t)cta * a.rows_per_cta;
   const int64_t r1 = min(a.n, r0 + a.rows_per_cta);
   const TA* A = reinterpret_cast<const TA*>(a.A);
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
   auto precond = [&](const double* src, double* dst) -> int {
     for (int c = threadIdx.x; c < dp; c += blockDim.x) stage[c] = c < d ? src[c] : 0.0;
     __syncthreads();
-    for (int i = gw; i < d; i += nw) {
+    for (int i = cw; i < d; i += nw) {
       const double zi = warp_row_dot(a.WT + (int64_t)i * d, stage, 0, i + 1);
       if (lane == 0) a.z[i] = zi;
     }
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
     for (int c = threadIdx.x; c < dp; c += blockDim.x) stage[c] = c < d ? a.z[c] : 0.0;
     __syncthreads();
     double part_rho = 0.0;
-    for (int j = gw; j < d; j += nw) {
+    for (int j = cw; j < d; j += nw) {
       const double v = warp_row_dot(a.W + (int64_t)j * d, stage, j, d);
       if (lane == 0) {
         dst[j] = v;
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
   // partial of <b, x> over the columns this CTA owns, x read from `xsrc`
   auto bx_partial = [&](const double* xsrc) {
     double s = 0.0;
-    for (int c = gw; c < d; c += nw)
+    for (int c = cw; c < d; c += nw)
       if (lane == 0) s += a.b[c] * xsrc[c];
     if (lane == 0) S.qred[warp] = s;
     __syncthreads();
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
       ++exact_passes;
       if (gsync()) return;
     }
-    for (int c = gw; c < d; c += nw) {
+    for (int c = cw; c < d; c += nw) {
       const double v = a.x0_zero ? 0.0 : warp_sum_strip(a.part + (int64_t)c * P, P);
       if (lane == 0) a.r[c] = a.b[c] - v;
     }
@@ -258,12 +261,12 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
       double sq = 0.0, sv = 0.0, b0 = 0.0, x0 = 0.0, rr0 = 0.0;
       {
         const double* pq = a.part + (int64_t)dp * P;
-        const double* pv = a.part + (int64_t)gw * P;
-        const bool hasv = gw < d;
+        const double* pv = a.part + (int64_t)cw * P;
+        const bool hasv = cw < d;
         if (hasv && lane == 0) {
-          b0 = a.b[gw];
-          x0 = a.x[gw];
-          rr0 = a.r[gw];
+          b0 = a.b[cw];
+          x0 = a.x[cw];
+          rr0 = a.r[cw];
         }
         for (int j = lane; j < P; j += 32) {
           if (warp == 0) sq += pq[j];
@@ -282,13 +285,13 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
       const double alpha = rho / q;
       // x += alpha p, r -= alpha H p, and this CTA's partial of <b, x> (bx_partial's order)
       double bxp = 0.0;
-      if (gw < d && lane == 0) {
-        const double xn = x0 + alpha * S.vec[gw];
-        a.x[gw] = xn;
-        a.r[gw] = rr0 - alpha * sv;
+      if (cw < d && lane == 0) {
+        const double xn = x0 + alpha * S.vec[cw];
+        a.x[cw] = xn;
+        a.r[cw] = rr0 - alpha * sv;
         bxp += b0 * xn;
       }
-      for (int c = gw + nw; c < d; c += nw) {  // more columns than warps in the grid
+      for (int c = cw + nw; c < d; c += nw) {  // more columns than warps in the grid
         const double v = warp_sum_strip(a.part + (int64_t)c * P, P);
         if (lane == 0) {
           const double xn = a.x[c] + alpha * S.vec[c];
@@ -323,7 +326,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
         ++passes;
         ++exact_passes;
         if (gsync()) return;
-        for (int c = gw; c < d; c += nw) {
+        for (int c = cw; c < d; c += nw) {
           const double v = warp_sum_strip(a.part + (int64_t)c * P, P);
           if (lane == 0) a.r[c] = a.b[c] - v;
         }
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
       }
       ++passes;
       if (gsync()) return;
-      for (int c = gw; c < d; c += nw) {
+      for (int c = cw; c < d; c += nw) {
         const double v = warp_sum_strip(a.part + (int64_t)c * P, P);
         if (lane == 0) a.g[c] = v - a.b[c];
       }
