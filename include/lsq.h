@@ -98,6 +98,20 @@ LSQ_API lsq_status lsq_destroy(lsq_ctx* ctx);
 /* Replaces the stream of the context (the previous stream is not synchronised). */
 LSQ_API lsq_status lsq_set_stream(lsq_ctx* ctx, void* cuda_stream);
 
+/* Deferred checks.  on = 1: lsq_sketch and lsq_factor / lsq_factor_ex stop waiting for their
+ * own work.  The statuses they would have waited for (a timed-out wait inside a sketch
+ * kernel, LSQ_ERR_RANK from the Cholesky) are kept on the device, the first error of each
+ * kind, and reported with the usual codes by the next call on the context that waits for its
+ * stream: lsq_solve (a deferred error is returned in preference to the solve's own status,
+ * whose results are then meaningless) or lsq_sync.  Host code queued meanwhile (the next
+ * call's set-up) overlaps the device work.  on = 0 (the default) restores waiting; statuses
+ * already deferred stay pending until the next waiting call.  LSQ_ERR_ARG for a NULL ctx. */
+LSQ_API lsq_status lsq_set_deferred_checks(lsq_ctx* ctx, int32_t on);
+
+/* Waits for the context's stream and reports (then clears) the first deferred error, else
+ * LSQ_OK.  LSQ_ERR_ARG for a NULL ctx. */
+LSQ_API lsq_status lsq_sync(lsq_ctx* ctx);
+
 /* Arithmetic of lsq_sketch.
  *   LSQ_SKETCH_F64: FP64 (the +-1 weights of SRHT/SJLT are exact; agrees with an FP64
  *                   evaluation of S A to rounding).
@@ -159,7 +173,8 @@ LSQ_API lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
  *   W  : device, d x d FP64 output: W = R^{-1} (upper triangular), which lsq_solve
  *        uses to apply H_S^{-1} r = W (W^T r) as two parallel triangular products.
  * Status LSQ_ERR_RANK (after a synchronisation) if a pivot is not positive. This call
- * waits for its own work so that it can report the rank check.
+ * waits for its own work so that it can report the rank check, unless deferred checks are
+ * on (lsq_set_deferred_checks), when the rank failure is reported by the next waiting call.
  * --------------------------------------------------------------------------------- */
 LSQ_API lsq_status lsq_factor(lsq_ctx* ctx, const double* SA, int64_t m, int64_t d, double* R, double* W);
 

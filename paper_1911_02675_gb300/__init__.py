@@ -35,7 +35,7 @@ SKETCH_PRECISION = {"f64": 0, "f32": 1, "bf16": 2}
 DTYPE = {torch.float64: 0, torch.float32: 1}
 
 # every symbol the header declares
-EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_sketch", "lsq_factor", "lsq_factor_ex", "lsq_solve",
+EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_set_deferred_checks", "lsq_sync", "lsq_sketch", "lsq_factor", "lsq_factor_ex", "lsq_solve",
            "lsq_solve_opts_default", "lsq_hmatvec", "lsq_status_str", "lsq_version", "lsq_launch_count",
            "lsq_hmatvec_noalloc", "lsq_grad_a", "lsq_advise_sketch_size", "lsq_batch_opts_default",
            "lsq_solve_batched")
@@ -111,6 +111,8 @@ def _load():
     L.lsq_create.argtypes = [ctypes.POINTER(P), P]
     L.lsq_destroy.argtypes = [P]
     L.lsq_set_stream.argtypes = [P, P]
+    L.lsq_set_deferred_checks.argtypes = [P, i32]
+    L.lsq_sync.argtypes = [P]
     L.lsq_sketch.argtypes = [P, ctypes.POINTER(LsqMatrix), i32, i64, u64, ctypes.POINTER(LsqSketchOpts), P]
     L.lsq_factor.argtypes = [P, P, i64, i64, P, P]
     L.lsq_factor_ex.argtypes = [P, P, i64, i64, P, P, i32]
@@ -192,6 +194,13 @@ class Context:
 
     def sync_stream(self):
         _L.lsq_set_stream(self.handle, _stream_handle(self.device))
+
+    def set_deferred_checks(self, on: bool = True):
+        """Sketch and factor calls stop waiting for their own work; their errors (a timed-out
+        wait, LSQ_ERR_RANK) are raised by the next lsq_solve or lsq_sync on this context."""
+        st = _L.lsq_set_deferred_checks(self.handle, 1 if on else 0)
+        if st:
+            raise LsqError(st, "lsq_set_deferred_checks")
 
     def close(self):
         if getattr(self, "handle", None):
@@ -293,6 +302,14 @@ def lsq_solve(ctx: Context, A: torch.Tensor, b: torch.Tensor, method: str, W: to
     if st and not (st == LSQ_ERR_MAXIT and not raise_on_maxit):
         raise LsqError(st, "lsq_solve")
     return x, info.as_dict()
+
+
+def lsq_sync(ctx: Context) -> None:
+    """Waits for the context's stream; raises LsqError for a deferred sketch or factor error."""
+    ctx.sync_stream()
+    st = _L.lsq_sync(ctx.handle)
+    if st:
+        raise LsqError(st, "lsq_sync")
 
 
 def lsq_hmatvec(ctx: Context, A: torch.Tensor, p: torch.Tensor):

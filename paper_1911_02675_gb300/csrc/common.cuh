@@ -27,7 +27,10 @@ struct lsq_ctx {
   size_t state_bytes;      // refreshed solve can call the sketch and the factor between steps)
   void* a32;               // FP32 copy of an FP64 A that a mixed-precision solve streams
   size_t a32_bytes;
-  int* host_status;        // pinned host word for status read-back
+  int* host_status;        // pinned host words for status read-back (32 ints; 16, 17: deferred)
+  int* dev_pending;        // device words: first deferred sketch / factor error (0 = none)
+  int32_t defer_checks;    // lsq_set_deferred_checks
+  int32_t pending;         // deferred statuses may be set on the device
   cudaStream_t capture;    // non-blocking stream on which CUDA graphs are captured (lazily)
   cudaEvent_t ev0, ev1;
 };
@@ -40,6 +43,13 @@ struct lsq_ctx {
       return LSQ_ERR_CUDA;                         \
     }                                              \
   } while (0)
+
+// Deferred checks: keep the first nonzero *err of kind `slot` (0 sketch, 1 factor) on the
+// device without waiting; lsq_pending_enqueue queues their read-back before a stream sync,
+// lsq_pending_take reports (and clears) them after it.
+lsq_status lsq_defer_status(lsq_ctx* c, const int* err, int slot);
+lsq_status lsq_pending_enqueue(lsq_ctx* c);
+lsq_status lsq_pending_take(lsq_ctx* c);
 
 // Number of kernels this library has launched in the process (lsq_launch_count).
 void lsq_count_launch();

@@ -19,13 +19,16 @@ extern "C" lsq_status lsq_create(lsq_ctx** out, void* stream) {
   c->device = dev;
   c->sm_count = prop.multiProcessorCount;
   c->stream = (cudaStream_t)stream;
-  if (cudaMallocHost((void**)&c->host_status, 64) != cudaSuccess ||
-      cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+  if (cudaMallocHost((void**)&c->host_status, 128) != cudaSuccess || cudaMalloc((void**)&c->dev_pending, 8) != cudaSuccess ||
+      cudaMemset(c->dev_pending, 0, 8) != cudaSuccess || cudaEventCreate(&c->ev0) != cudaSuccess ||
+      cudaEventCreate(&c->ev1) != cudaSuccess) {
     (void)cudaGetLastError();
     if (c->host_status) cudaFreeHost(c->host_status);
+    if (c->dev_pending) cudaFree(c->dev_pending);
     free(c);
     return LSQ_ERR_CUDA;
   }
+  memset(c->host_status, 0, 128);
   *out = c;
   return LSQ_OK;
 }
@@ -38,6 +41,7 @@ extern "C" lsq_status lsq_destroy(lsq_ctx* c) {
   if (c->a32) cudaFree(c->a32);
   if (c->capture) cudaStreamDestroy(c->capture);
   cudaFreeHost(c->host_status);
+  cudaFree(c->dev_pending);
   cudaEventDestroy(c->ev0);
   cudaEventDestroy(c->ev1);
   (void)cudaGetLastError();
@@ -49,6 +53,51 @@ extern "C" lsq_status lsq_set_stream(lsq_ctx* c, void* stream) {
   if (!c) return LSQ_ERR_ARG;
   c->stream = (cudaStream_t)stream;
   return LSQ_OK;
+}
+
+extern "C" lsq_status lsq_set_deferred_checks(lsq_ctx* c, int32_t on) {
+  if (!c) return LSQ_ERR_ARG;
+  c->defer_checks = on ? 1 : 0;
+  return LSQ_OK;
+}
+
+namespace {
+__global__ void keep_first_status_kernel(const int* err, int* slot) {
+  if (*slot == 0) *slot = *err;
+}
+}  // namespace
+
+lsq_status lsq_defer_status(lsq_ctx* c, const int* err, int slot) {
+  keep_first_status_kernel<<<1, 1, 0, c->stream>>>(err, c->dev_pending + slot);
+  LSQ_LAUNCH_CHECK();
+  c->pending = 1;
+  return LSQ_OK;
+}
+
+lsq_status lsq_pending_enqueue(lsq_ctx* c) {
+  if (c->pending)
+    LSQ_CUDA_TRY(cudaMemcpyAsync(c->host_status + 16, c->dev_pending, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                 c->stream));
+  return LSQ_OK;
+}
+
+lsq_status lsq_pending_take(lsq_ctx* c) {
+  if (!c->pending) return LSQ_OK;
+  c->pending = 0;
+  const int e = c->host_status[16] ? c->host_status[16] : c->host_status[17];
+  if (e) {
+    c->host_status[16] = c->host_status[17] = 0;
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->dev_pending, 0, 2 * sizeof(int), c->stream));
+  }
+  return (lsq_status)e;
+}
+
+extern "C" lsq_status lsq_sync(lsq_ctx* c) {
+  if (!c) return LSQ_ERR_ARG;
+  lsq_status st = lsq_pending_enqueue(c);
+  if (st != LSQ_OK) return st;
+  LSQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return lsq_pending_take(c);
 }
 
 static lsq_status grow(lsq_ctx* c, void** buf, size_t* have, size_t bytes) {

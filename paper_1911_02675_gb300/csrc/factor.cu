@@ -546,6 +546,7 @@ extern "C" lsq_status lsq_factor_ex(lsq_ctx* ctx, const double* SA, int64_t m, i
   lsq_count_launch();
   copy_out_kernel<<<std::min(4 * ctx->sm_count, (int)((d * d + 255) / 256)), 256, 0, s>>>(Rf, Wf, di, dp, R, W);
   LSQ_LAUNCH_CHECK();
+  if (ctx->defer_checks) return lsq_defer_status(ctx, err, 1);  // the rank check, reported later
   LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   LSQ_CUDA_TRY(cudaStreamSynchronize(s));
   const int code = *ctx->host_status;

@@ -608,7 +608,8 @@ lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t s
   const int rgrid = (int)std::min<int64_t>((md + 255) / 256, 4 * (int64_t)ctx->sm_count);
   reduce_tc_kernel<<<rgrid, 256, 0, ctx->stream>>>(part, splits, md, 1.0 / sqrt((double)m), SA);
   LSQ_LAUNCH_CHECK();
-  // a timed-out wait inside the tensor-core kernel is reported here
+  // a timed-out wait inside the tensor-core kernel is reported here (or deferred)
+  if (ctx->defer_checks) return lsq_defer_status(ctx, err, 0);
   LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 13, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   LSQ_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return ctx->host_status[13] ? (lsq_status)ctx->host_status[13] : LSQ_OK;

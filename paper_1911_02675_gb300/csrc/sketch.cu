@@ -1262,7 +1262,8 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
   LSQ_LAUNCH_CHECK();
   a32_done = staged && a32 != nullptr && A->dtype == LSQ_F64;
   if (staged) {
-    // a timed-out wait on a staged block is reported here
+    // a timed-out wait on a staged block is reported here (or deferred)
+    if (ctx->defer_checks) return lsq_defer_status(ctx, err, 0);
     LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 14, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     LSQ_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     if (ctx->host_status[14]) return (lsq_status)ctx->host_status[14];

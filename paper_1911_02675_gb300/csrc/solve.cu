@@ -563,7 +563,16 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   }
   if (!(rho < 1.0)) return LSQ_ERR_ARG;
   const double lam1 = (1.0 + sqrt(rho)) * (1.0 + sqrt(rho));
-  if (method == LSQ_FCG) return lsq_fcg_solve(ctx, A, b, refresh ? nullptr : W, x, tol, maxit, o, lam1, info);
+  if (method == LSQ_FCG) {
+    const lsq_status fst = lsq_fcg_solve(ctx, A, b, refresh ? nullptr : W, x, tol, maxit, o, lam1, info);
+    if (ctx->pending) {  // a deferred sketch or factor error outranks the solve's status
+      if (lsq_pending_enqueue(ctx) != LSQ_OK) return LSQ_ERR_CUDA;
+      LSQ_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      const lsq_status deferred = lsq_pending_take(ctx);
+      if (deferred != LSQ_OK) return deferred;
+    }
+    return fst;
+  }
   double mu = o.mu, beta = o.beta;
   if (method == LSQ_PCG) {
     mu = 0.0;
@@ -683,6 +692,7 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
     LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status, a.out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
     LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 12, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     LSQ_CUDA_TRY(cudaEventRecord(ctx->ev1, s));
+    if (lsq_pending_enqueue(ctx) != LSQ_OK) return LSQ_ERR_CUDA;
     LSQ_CUDA_TRY(cudaStreamSynchronize(s));
     const double* o4 = reinterpret_cast<const double*>(ctx->host_status);
     const int errc = ctx->host_status[12];
@@ -743,6 +753,7 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
       break;
     }
     cudaEventRecord(ctx->ev1, s);
+    if (lsq_pending_enqueue(ctx) != LSQ_OK) return LSQ_ERR_CUDA;
     cudaStreamSynchronize(s);
     cudaEventDestroy(e_a);
     cudaEventDestroy(e_b);
@@ -761,5 +772,8 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
     info->a32_copy = a32 ? (user_a32 ? 2 : 1) : 0;
     info->reserved = 0;
   }
+  // a deferred sketch or factor error (lsq_set_deferred_checks) outranks the solve's status
+  const lsq_status deferred = lsq_pending_take(ctx);
+  if (deferred != LSQ_OK) return deferred;
   return (lsq_status)status;
 }

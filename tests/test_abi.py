@@ -53,6 +53,8 @@ def test_host_only_entry_points(lib):
     assert lib.lsq_factor(None, None, 16, 4, None, None) == 1
     assert lib.lsq_factor_ex(None, None, 16, 4, None, None, 1) == 1
     assert lib.lsq_destroy(None) == 0
+    assert lib.lsq_set_deferred_checks(None, 1) == 1
+    assert lib.lsq_sync(None) == 1
 
 
 def test_python_binding_exports_match_header():

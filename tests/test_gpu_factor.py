@@ -51,6 +51,35 @@ def test_rank_deficient_is_reported(L, ctx):
     assert np.isfinite(R.cpu().numpy()).all()
 
 
+def test_rank_deficient_is_reported_when_deferred(L):
+    """With deferred checks the factor returns at once; the rank failure is raised by the next
+    waiting call (lsq_sync, or lsq_solve in preference to its own status), then cleared."""
+    c = L.Context(0)
+    try:
+        c.set_deferred_checks(True)
+        SA = np.random.default_rng(0).standard_normal((50, 8))
+        SA[:, 3] = 0.0
+        L.lsq_factor(c, to_dev(SA))  # no error yet
+        with pytest.raises(L.LsqError) as e:
+            L.lsq_sync(c)
+        assert e.value.status == L.LSQ_ERR_RANK
+        L.lsq_sync(c)  # cleared
+        # reported by the solve that follows
+        P = W.make_problem(400, 8, 1e2, seed=5)
+        A, b = to_dev(P["A"]), to_dev(P["b"])
+        _, Wbad = L.lsq_factor(c, to_dev(SA))
+        with pytest.raises(L.LsqError) as e:
+            L.lsq_solve(c, A, b, "pcg", Wbad, tol=1e-10, maxit=50, m=50)
+        assert e.value.status == L.LSQ_ERR_RANK
+        # a good factor and solve go through
+        _, Wok = L.lsq_factor(c, L.lsq_sketch(c, A, "srht", 64, 0))
+        x, info = L.lsq_solve(c, A, b, "pcg", Wok, tol=1e-10, maxit=200, m=64)
+        assert info["status"] == 0
+        L.lsq_sync(c)
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("m,d,kappa", [(70, 37, 1e2), (1024, 512, 1e6), (1200, 1024, 1e2), (4096, 300, 1e6)])
 def test_factor_double_fp32_gram(L, ctx, m, d, kappa):
     """The Gram matrix in double-FP32 (about 45-bit operands, exact products, TwoSum sums) gives

@@ -249,3 +249,28 @@ def test_mixed_solve_with_the_sketch_fp32_copy(L, ctx):
     assert i1["a32_copy"] == 2 and i0["a32_copy"] == 1
     assert i0["status"] == i1["status"] == 0 and i0["passes"] == i1["passes"]
     assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
+
+
+@pytest.mark.parametrize("sketch", ["srht", "gauss"])
+def test_deferred_checks_pipeline_is_identical(L, sketch):
+    """With deferred checks (no waits inside the sketch and the factor) the pipeline computes
+    the same sketch, factor and iterates to the last bit; lsq_sync then reports no error."""
+    n, d, m = 20000, 64, 512
+    P = W.make_problem(n, d, 1e4, seed=23)
+    out = []
+    for defer in (False, True):
+        c = L.Context(0)
+        try:
+            c.set_deferred_checks(defer)
+            Ad, bd = to_dev(P["A"]), to_dev(P["b"])
+            prec = "bf16" if sketch == "gauss" else "f32"
+            SA = L.lsq_sketch(c, Ad, sketch, m, 0, precision=prec)
+            _, Wm = L.lsq_factor(c, SA, precision="mixed")
+            x, info = L.lsq_solve(c, Ad, bd, "pcg", Wm, tol=1e-10, maxit=300, m=m, precision="mixed")
+            L.lsq_sync(c)
+            assert info["status"] == 0
+            out.append((SA.cpu().numpy(), Wm.cpu().numpy(), x.cpu().numpy()))
+        finally:
+            c.close()
+    for u, v in zip(out[0], out[1]):
+        assert np.array_equal(u, v)
