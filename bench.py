@@ -280,8 +280,12 @@ def run_ours(args):
     # FP32 passes stream (a caller-owned buffer, like SA, W and x)
     a32 = L.narrow_buffer(A) if (args.precision == "mixed" and A.dtype == torch.float64) else None
 
-    def solve_once(Ad, bd):
-        SA = L.lsq_sketch(ctx, Ad, args.sketch, args.m, 0, precision=args.sketch_precision, a32=a32)
+    def solve_once(Ad, bd, A_from=None):
+        # A_from: pinned host rows that lsq_upload_sketch copies into Ad while sketching them
+        if A_from is None:
+            SA = L.lsq_sketch(ctx, Ad, args.sketch, args.m, 0, precision=args.sketch_precision, a32=a32)
+        else:
+            SA = L.lsq_upload_sketch(ctx, A_from, Ad, args.sketch, args.m, 0, precision=args.sketch_precision, a32=a32)
         _, Wm = L.lsq_factor(ctx, SA, precision=args.precision)
         x, info = L.lsq_solve(ctx, Ad, bd, "pcg", Wm, tol=args.tol, maxit=1000, m=args.m,
                               precision=args.precision, a32=a32)
@@ -363,9 +367,8 @@ def run_ours(args):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize(dev)
             e0.record(stream)
-            A_dev2.copy_(A_pin, non_blocking=True)
             b_dev2.copy_(b_pin, non_blocking=True)
-            xx, _ = solve_once(A_dev2, b_dev2)
+            xx, _ = solve_once(A_dev2, b_dev2, A_from=A_pin)
             x_pin.copy_(xx, non_blocking=True)
             e1.record(stream)
             torch.cuda.synchronize(dev)

@@ -164,6 +164,23 @@ typedef struct {
 LSQ_API lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, int64_t m, uint64_t seed,
                       const lsq_sketch_opts* opts, double* SA);
 
+/* lsq_upload_sketch: lsq_sketch of a matrix that is still in host memory, with the
+ * host-to-device copy overlapped by the transform.
+ *   host_A  : host, n x d elements of A->dtype, row stride host_ld >= d elements; page-locked
+ *             memory lets the copies run asynchronously (pageable memory is copied in turn).
+ *   A       : device destination (data, n, d, ld, dtype as lsq_sketch); it receives the host
+ *             matrix and is then the A of the sketch.
+ *   other arguments, results and status as lsq_sketch (deferred checks apply).
+ * SRHT with the staged transform (n > 2048 rows, 32-byte column tiles, 16-byte aligned rows,
+ * FP32 arithmetic): the rows are copied per row-block group on an internal stream, which first
+ * waits for the work already queued on the context stream, and each group's transform starts
+ * on the context stream as soon as its rows have landed (the SRHT sums per-group partials, so
+ * the result is that of lsq_sketch).  Any other case copies the whole matrix on the context
+ * stream, then sketches.  The context stream waits for every copy, so later calls see all of
+ * A.  LSQ_ERR_ARG for a NULL ctx, host_A or A, or host_ld < d. */
+LSQ_API lsq_status lsq_upload_sketch(lsq_ctx* ctx, const void* host_A, int64_t host_ld, const lsq_matrix* A,
+                                     int32_t type, int64_t m, uint64_t seed, const lsq_sketch_opts* opts, double* SA);
+
 /* ---------------------------------------------------------------------------------
  * lsq_factor: the preconditioner factor of H_S = (SA)^T (SA) (Section 1, PCG
  * paragraph; Section 6, which allows either a QR of SA or a Cholesky factor of H_S).

@@ -35,7 +35,7 @@ SKETCH_PRECISION = {"f64": 0, "f32": 1, "bf16": 2}
 DTYPE = {torch.float64: 0, torch.float32: 1}
 
 # every symbol the header declares
-EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_set_deferred_checks", "lsq_sync", "lsq_sketch", "lsq_factor", "lsq_factor_ex", "lsq_solve",
+EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_set_deferred_checks", "lsq_sync", "lsq_sketch", "lsq_upload_sketch", "lsq_factor", "lsq_factor_ex", "lsq_solve",
            "lsq_solve_opts_default", "lsq_hmatvec", "lsq_status_str", "lsq_version", "lsq_launch_count",
            "lsq_hmatvec_noalloc", "lsq_grad_a", "lsq_advise_sketch_size", "lsq_batch_opts_default",
            "lsq_solve_batched")
@@ -114,6 +114,7 @@ def _load():
     L.lsq_set_deferred_checks.argtypes = [P, i32]
     L.lsq_sync.argtypes = [P]
     L.lsq_sketch.argtypes = [P, ctypes.POINTER(LsqMatrix), i32, i64, u64, ctypes.POINTER(LsqSketchOpts), P]
+    L.lsq_upload_sketch.argtypes = [P, P, i64, ctypes.POINTER(LsqMatrix), i32, i64, u64, ctypes.POINTER(LsqSketchOpts), P]
     L.lsq_factor.argtypes = [P, P, i64, i64, P, P]
     L.lsq_factor_ex.argtypes = [P, P, i64, i64, P, P, i32]
     L.lsq_solve.argtypes = [P, ctypes.POINTER(LsqMatrix), P, i32, P, P, dbl, i32, ctypes.POINTER(LsqSolveOpts),
@@ -247,6 +248,28 @@ def lsq_sketch(ctx: Context, A: torch.Tensor, kind: str, m: int, seed: int, t: i
     st = _L.lsq_sketch(ctx.handle, ctypes.byref(M), SKETCH[kind], m, seed, ctypes.byref(opts), _ptr(SA))
     if st:
         raise LsqError(st, "lsq_sketch")
+    return SA
+
+
+def lsq_upload_sketch(ctx: Context, A_host: torch.Tensor, A: torch.Tensor, kind: str, m: int, seed: int, t: int = 0,
+                      s: int = 8, precision: str = "f64", out: torch.Tensor | None = None,
+                      a32: torch.Tensor | None = None) -> torch.Tensor:
+    """Copies the host matrix A_host (CPU, row-major, pinned for overlap) into the device matrix A
+    (same shape and dtype) and returns SA as lsq_sketch(ctx, A, ...) would, the SRHT transform
+    running on each row range as it lands."""
+    ctx.sync_stream()
+    if A_host.device.type != "cpu" or A_host.dtype != A.dtype or A_host.shape != A.shape or A_host.stride(1) != 1:
+        raise ValueError("A_host must be a CPU matrix of A's shape and dtype with unit column stride")
+    M = as_matrix(A)
+    SA = out if out is not None else torch.empty((m, A.shape[1]), dtype=torch.float64, device=A.device)
+    opts = LsqSketchOpts(t, s, SKETCH_PRECISION[precision], None, 0)
+    if a32 is not None:
+        _check_a32(A, a32)
+        opts.a32, opts.ld32 = a32.data_ptr(), a32.stride(0)
+    st = _L.lsq_upload_sketch(ctx.handle, A_host.data_ptr(), A_host.stride(0), ctypes.byref(M), SKETCH[kind], m, seed,
+                              ctypes.byref(opts), _ptr(SA))
+    if st:
+        raise LsqError(st, "lsq_upload_sketch")
     return SA
 
 

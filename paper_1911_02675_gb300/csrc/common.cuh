@@ -32,6 +32,8 @@ struct lsq_ctx {
   int32_t defer_checks;    // lsq_set_deferred_checks
   int32_t pending;         // deferred statuses may be set on the device
   cudaStream_t capture;    // non-blocking stream on which CUDA graphs are captured (lazily)
+  cudaStream_t copy;       // non-blocking stream of lsq_upload_sketch's row copies (lazily)
+  cudaEvent_t ev_copy;     // hand-over between the copy stream and the context stream
   cudaEvent_t ev0, ev1;
 };
 

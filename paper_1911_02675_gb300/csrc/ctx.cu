@@ -40,6 +40,11 @@ extern "C" lsq_status lsq_destroy(lsq_ctx* c) {
   if (c->state) cudaFree(c->state);
   if (c->a32) cudaFree(c->a32);
   if (c->capture) cudaStreamDestroy(c->capture);
+  if (c->copy) {
+    cudaStreamSynchronize(c->copy);
+    cudaStreamDestroy(c->copy);
+  }
+  if (c->ev_copy) cudaEventDestroy(c->ev_copy);
   cudaFreeHost(c->host_status);
   cudaFree(c->dev_pending);
   cudaEventDestroy(c->ev0);

@@ -663,8 +663,9 @@ template <typename TA, int MY>
 __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
     const __grid_constant__ CUtensorMap tmap, int64_t n, int d, int64_t N1, int64_t blocks_per_group,
     const uint32_t* __restrict__ signbits, const int64_t* __restrict__ rows, int m, float* __restrict__ part,
-    int* err, float* __restrict__ a32, int64_t ld32) {
+    int* err, float* __restrict__ a32, int64_t ld32, int gy0) {
   constexpr int DC = 8, LOGN2 = 11, N2 = 1 << LOGN2;
+  const int64_t gy = (int64_t)blockIdx.y + gy0;  // row-block group (a launch may cover a range of them)
   constexpr uint32_t STAGE_BYTES = N2 * DC * sizeof(TA);
   using T2 = typename std::conditional<sizeof(TA) == 8, double2, float2>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -679,7 +680,7 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
   __shared__ __align__(8) uint64_t full;
   const int tid = threadIdx.x;
   const int c0 = blockIdx.x * DC;
-  const int64_t b_begin = (int64_t)blockIdx.y * blocks_per_group;
+  const int64_t b_begin = gy * blocks_per_group;
   const int64_t b_end = min(N1, b_begin + blocks_per_group);
   for (int s = tid; s < m; s += SRHT_THREADS) {
     const int64_t k = rows[s];
@@ -817,7 +818,7 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
     // a failed wait may leave a copy in flight: give it (bounded) time to land before exit
     (void)srht_mbar_wait(&full, (uint32_t)((issued - 1) & 1), err);
   }
-  float* out = part + (int64_t)blockIdx.y * m * d;
+  float* out = part + gy * m * d;
 #pragma unroll
   for (int i = 0; i < MY; ++i) {
     const int s = tid + SRHT_THREADS * i;
@@ -1091,22 +1092,32 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// the TMA-staged kernel of the common case, when A's layout allows tensor copies (16-byte
-// aligned base and row stride) and the sampled rows fit 8 register rows per thread; returns
-// false (nothing launched) otherwise
+// whether the TMA-staged kernel of the common case applies: A's layout allows tensor copies
+// (16-byte aligned base and row stride), the sampled rows fit 8 register rows per thread and
+// the staged block fits shared memory
 template <typename TA>
-static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1, const uint32_t* signbits,
-                            const int64_t* rows, float* part, int groups, int64_t blocks_per_group, int* err,
-                            float* a32, int64_t ld32, lsq_status* st) {
+static bool srht_tma_usable(const lsq_matrix* A, int m) {
   constexpr int DC = 8, N2 = 2048;
   const size_t es = sizeof(TA);
   if (m > 8 * SRHT_THREADS) return false;
   if (((uintptr_t)A->data % 16) != 0 || ((size_t)A->ld * es) % 16 != 0) return false;
   const size_t smem = 1024 + (size_t)N2 * DC * es + (size_t)zphys(N2, DC) * 4 + (size_t)m * 4 +
                       (size_t)((m + 1) & ~1) * 2 + (N2 / 32) * 4;
-  if (smem > 232448 - 1024) return false;
+  return smem <= 232448 - 1024 && tensor_map_encoder() != nullptr;
+}
+
+// the TMA-staged kernel of the common case over row-block groups [gy0, gy0 + groups), when
+// srht_tma_usable; returns false (nothing launched) otherwise
+template <typename TA>
+static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1, const uint32_t* signbits,
+                            const int64_t* rows, float* part, int groups, int64_t blocks_per_group, int* err,
+                            float* a32, int64_t ld32, lsq_status* st, int gy0 = 0) {
+  constexpr int DC = 8, N2 = 2048;
+  const size_t es = sizeof(TA);
+  if (!srht_tma_usable<TA>(A, m)) return false;
+  const size_t smem = 1024 + (size_t)N2 * DC * es + (size_t)zphys(N2, DC) * 4 + (size_t)m * 4 +
+                      (size_t)((m + 1) & ~1) * 2 + (N2 / 32) * 4;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return false;
   CUtensorMap tm;
   const cuuint64_t dims[2] = {(cuuint64_t)A->d, (cuuint64_t)A->n};
   const cuuint64_t strides[1] = {(cuuint64_t)A->ld * es};
@@ -1122,7 +1133,7 @@ static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1
   auto launch = [&](auto kern) -> lsq_status {
     LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, SRHT_THREADS, smem, ctx->stream>>>(tm, A->n, d, N1, blocks_per_group, signbits, rows, m, part, err,
-                                                     a32, ld32);
+                                                     a32, ld32, gy0);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
   };
@@ -1179,9 +1190,36 @@ static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN
   return LSQ_OK;
 }
 
+// lsq_upload_sketch: the host rows that become A (row stride host_ld elements)
+struct SketchUpload {
+  const void* host;
+  int64_t host_ld;
+};
+
+// rows [r0, r1) of the host matrix into A's buffer, queued on `s`
+static lsq_status upload_rows(const SketchUpload* up, const lsq_matrix* A, int64_t r0, int64_t r1, cudaStream_t s) {
+  if (r1 <= r0) return LSQ_OK;
+  const size_t es = A->dtype == LSQ_F64 ? 8 : 4;
+  char* dst = static_cast<char*>(const_cast<void*>(A->data)) + (size_t)r0 * A->ld * es;
+  const char* src = static_cast<const char*>(up->host) + (size_t)r0 * up->host_ld * es;
+  if (A->ld == A->d && up->host_ld == A->d)
+    LSQ_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)(r1 - r0) * A->d * es, cudaMemcpyHostToDevice, s));
+  else
+    LSQ_CUDA_TRY(cudaMemcpy2DAsync(dst, A->ld * es, src, up->host_ld * es, A->d * es, r1 - r0, cudaMemcpyHostToDevice,
+                                   s));
+  return LSQ_OK;
+}
+
+// the context's copy stream and event (created on first use)
+static lsq_status ensure_copy_stream(lsq_ctx* ctx) {
+  if (!ctx->copy) LSQ_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+  if (!ctx->ev_copy) LSQ_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_copy, cudaEventDisableTiming));
+  return LSQ_OK;
+}
+
 template <typename TC>
 static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
-                           float* a32, int64_t ld32, bool& a32_done) {
+                           float* a32, int64_t ld32, bool& a32_done, const SketchUpload* up = nullptr) {
   const int d = (int)A->d;
   int64_t N = 1;
   int logN = 0;
@@ -1245,7 +1283,43 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
   LSQ_LAUNCH_CHECK();
 
   bool staged = false;
-  switch (DC) {
+  bool launched = false;
+  if (up) {
+    const bool f64a = A->dtype == LSQ_F64;
+    const bool chunked = sizeof(TC) == 4 && DC == 8 && logN2 == 11 &&
+                         (f64a ? srht_tma_usable<double>(A, m) : srht_tma_usable<float>(A, m));
+    if (!chunked) {
+      st = upload_rows(up, A, 0, A->n, ctx->stream);  // the whole matrix first, in stream order
+      if (st != LSQ_OK) return st;
+    } else {
+      // group g's rows go up on the copy stream (after the work already queued on the context
+      // stream, which may still read A's buffer); its transform waits for them alone
+      st = ensure_copy_stream(ctx);
+      if (st != LSQ_OK) return st;
+      LSQ_CUDA_TRY(cudaEventRecord(ctx->ev_copy, ctx->stream));
+      LSQ_CUDA_TRY(cudaStreamWaitEvent(ctx->copy, ctx->ev_copy, 0));
+      const int64_t rows_per_group = blocks_per_group * 2048;
+      float* pf = reinterpret_cast<float*>(part);
+      for (int64_t g = 0; g < groups; ++g) {
+        const int64_t r0 = g * rows_per_group, r1 = std::min<int64_t>(A->n, r0 + rows_per_group);
+        if (r1 > r0) {
+          st = upload_rows(up, A, r0, r1, ctx->copy);
+          if (st != LSQ_OK) return st;
+          LSQ_CUDA_TRY(cudaEventRecord(ctx->ev_copy, ctx->copy));
+          LSQ_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_copy, 0));
+        }
+        lsq_status lst = LSQ_OK;
+        const bool ok = f64a ? srht_tma_launch<double>(ctx, A, m, N1, signbits, rows, pf, 1, blocks_per_group, err, a32,
+                                                       ld32, &lst, (int)g)
+                             : srht_tma_launch<float>(ctx, A, m, N1, signbits, rows, pf, 1, blocks_per_group, err,
+                                                      nullptr, 0, &lst, (int)g);
+        if (!ok) return LSQ_ERR_CUDA;  // srht_tma_usable said it would launch
+        if (lst != LSQ_OK) return lst;
+      }
+      staged = launched = true;
+    }
+  }
+  if (!launched) switch (DC) {
     case 8: st = srht_launch<TC, 8>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, a32,
                                   ld32, staged); break;
     case 4: st = srht_launch<TC, 4>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, a32,
@@ -1335,8 +1409,8 @@ static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint
 
 lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA);
 
-extern "C" lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, int64_t m, uint64_t seed,
-                                 const lsq_sketch_opts* opts, double* SA) {
+static lsq_status sketch_impl(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, int64_t m, uint64_t seed,
+                              const lsq_sketch_opts* opts, double* SA, const SketchUpload* up) {
   if (!ctx || !SA) return LSQ_ERR_ARG;
   lsq_status st = validate_matrix(A);
   if (st != LSQ_OK) return st;
@@ -1351,14 +1425,20 @@ extern "C" lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type
   const int64_t ld32 = a32 ? opts->ld32 : 0;
   if (a32 && (ld32 < A->d || ld32 % 4 != 0 || ((uintptr_t)a32 % 16) != 0)) return LSQ_ERR_ARG;
   bool a32_done = false;
+  if (type != LSQ_SKETCH_GAUSS && type != LSQ_SKETCH_SRHT && type != LSQ_SKETCH_SJLT) return LSQ_ERR_ARG;
+  if (type == LSQ_SKETCH_SJLT && (s < 1 || s > 32 || s > m)) return LSQ_ERR_ARG;
+  if (up && type != LSQ_SKETCH_SRHT) {  // only the SRHT consumes the rows as they land
+    st = upload_rows(up, A, 0, A->n, ctx->stream);
+    if (st != LSQ_OK) return st;
+  }
   switch (type) {
     case LSQ_SKETCH_GAUSS:
       if (prec == LSQ_SKETCH_BF16) st = lsq_gauss_tc_run(ctx, A, (int)m, seed, t, SA);
       else st = f64 ? gauss_run<double>(ctx, A, (int)m, seed, t, SA) : gauss_run<float>(ctx, A, (int)m, seed, t, SA);
       break;
     case LSQ_SKETCH_SRHT:
-      st = f64 ? srht_run<double>(ctx, A, (int)m, seed, t, SA, a32, ld32, a32_done)
-               : srht_run<float>(ctx, A, (int)m, seed, t, SA, a32, ld32, a32_done);
+      st = f64 ? srht_run<double>(ctx, A, (int)m, seed, t, SA, a32, ld32, a32_done, up)
+               : srht_run<float>(ctx, A, (int)m, seed, t, SA, a32, ld32, a32_done, up);
       break;
     case LSQ_SKETCH_SJLT:
       if (s < 1 || s > 32 || s > m) return LSQ_ERR_ARG;
@@ -1370,6 +1450,19 @@ extern "C" lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type
   // the FP32 copy, where the sketch did not write it on the way
   if (st == LSQ_OK && a32 && !a32_done) st = lsq_narrow_copy(ctx, A, a32, ld32);
   return st;
+}
+
+extern "C" lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, int64_t m, uint64_t seed,
+                                 const lsq_sketch_opts* opts, double* SA) {
+  return sketch_impl(ctx, A, type, m, seed, opts, SA, nullptr);
+}
+
+extern "C" lsq_status lsq_upload_sketch(lsq_ctx* ctx, const void* host_A, int64_t host_ld, const lsq_matrix* A,
+                                        int32_t type, int64_t m, uint64_t seed, const lsq_sketch_opts* opts,
+                                        double* SA) {
+  if (!ctx || !host_A || !A || host_ld < A->d) return LSQ_ERR_ARG;
+  const SketchUpload up{host_A, host_ld};
+  return sketch_impl(ctx, A, type, m, seed, opts, SA, &up);
 }
 
 // Sketches of many problems in one launch (SJLT, FP32 arithmetic): problem p draws instance

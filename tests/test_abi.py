@@ -55,6 +55,7 @@ def test_host_only_entry_points(lib):
     assert lib.lsq_destroy(None) == 0
     assert lib.lsq_set_deferred_checks(None, 1) == 1
     assert lib.lsq_sync(None) == 1
+    assert lib.lsq_upload_sketch(None, None, 4, None, 0, 16, 0, None, None) == 1
 
 
 def test_python_binding_exports_match_header():

@@ -180,3 +180,30 @@ def test_sketch_writes_fp32_copy(L, ctx, kind, precision, n, d):
         assert rel_fro(SA, SA0) < 1e-6
     else:
         assert np.array_equal(SA, SA0)
+
+
+@pytest.mark.parametrize("n,d,m,dtype,kind,pinned", [
+    (2**17 + 777, 64, 512, np.float64, "srht", True),     # many row-block groups, ragged tail
+    (300000, 512, 4096, np.float64, "srht", True),         # the headline's shape class
+    (70000, 40, 256, np.float32, "srht", True),            # FP32 A, d not a multiple of 8
+    (1500, 24, 64, np.float64, "srht", False),             # under one 2048-row block: whole copy
+    (5000, 33, 128, np.float64, "gauss", True),            # other sketches: whole copy, then sketch
+])
+def test_upload_sketch_matches_sketch_of_device_copy(L, ctx, n, d, m, dtype, kind, pinned):
+    """lsq_upload_sketch copies A while the SRHT transforms the row groups that have landed: A on
+    the device, SA and the FP32 copy equal those of lsq_sketch on A already resident."""
+    rng = np.random.default_rng(n + d)
+    A = rng.standard_normal((n, d)).astype(dtype) * np.logspace(0, 3, d).astype(dtype)
+    A_host = torch.from_numpy(A)
+    if pinned:
+        A_host = A_host.pin_memory()
+    Ad = torch.empty(A_host.shape, dtype=A_host.dtype, device="cuda")
+    prec = "f32" if kind == "srht" else "f64"
+    a32 = L.narrow_buffer(Ad) if dtype == np.float64 else None
+    SA_up = L.lsq_upload_sketch(ctx, A_host, Ad, kind, m, 5, precision=prec, a32=a32)
+    a32_up = a32.clone() if a32 is not None else None
+    assert torch.equal(Ad.cpu(), torch.from_numpy(A))
+    SA_ref = L.lsq_sketch(ctx, Ad, kind, m, 5, precision=prec, a32=a32)
+    assert torch.equal(SA_up, SA_ref)
+    if a32 is not None:  # the pad columns past d are never written nor read
+        assert torch.equal(a32_up[:, :d], a32[:, :d])
