@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing plain FP64 PCG beside the build")
+    ap.add_argument("--m-sweep", default="", help="comma-separated sketch sizes: time the solve at each "
+                    "(time against m, beside Section 6's advised m*) instead of the bench line")
     ap.add_argument("--batch", type=int, default=0,
                     help="time the batched solve of this many uneven problems instead (k right-hand sides each)")
     ap.add_argument("--batch-seed", type=int, default=1)
@@ -290,6 +292,37 @@ def run_ours(args):
         x, info = L.lsq_solve(ctx, Ad, bd, "pcg", Wm, tol=args.tol, maxit=1000, m=args.m,
                               precision=args.precision, a32=a32)
         return x, info
+
+    if args.m_sweep:
+        # time to tolerance against the sketch size (the paper's trade-off of Section 6: a larger m
+        # costs more sketch and factor but fewer passes), beside the advised m*
+        sweep = []
+        for m in (int(v) for v in args.m_sweep.split(",")):
+            args.m = m
+            for _ in range(max(1, args.warmup)):
+                solve_once(A, b)
+            ms, inf = [], None
+            for _ in range(max(1, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                e0.record(stream)
+                _, inf = solve_once(A, b)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms.append(e0.elapsed_time(e1))
+            total = statistics.median(ms)
+            sweep.append({"m": m, "ms": total, "solve_ms": inf["ms_total"], "sketch_factor_ms": total - inf["ms_total"],
+                          "iters": inf["iters"], "passes": inf["passes"], "est_err": inf["est_err"],
+                          "status": inf["status"]})
+        try:
+            adv = L.lsq_advise_sketch_size(n, d, args.tol, args.sketch)
+        except L.LsqError:
+            adv = None
+        if rank == 0:
+            print(json.dumps({"metric": "time-to-1e-10 H-norm error per solve against sketch size", "unit": "ms",
+                              "higher_is_better": False, "sweep": sweep, "advised": adv,
+                              "config": workload_config(args, f"replicas{world}")}), flush=True)
+        return
 
     for _ in range(args.warmup):
         x, info = solve_once(A, b)

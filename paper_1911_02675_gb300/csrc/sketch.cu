@@ -662,10 +662,16 @@ __device__ __forceinline__ bool srht_mbar_wait(uint64_t* bar, uint32_t parity, i
 template <typename TA, int MY>
 __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
     const __grid_constant__ CUtensorMap tmap, int64_t n, int d, int64_t N1, int64_t blocks_per_group,
-    const uint32_t* __restrict__ signbits, const int64_t* __restrict__ rows, int m, float* __restrict__ part,
-    int* err, float* __restrict__ a32, int64_t ld32, int gy0) {
+    const uint32_t* __restrict__ signbits, const int64_t* __restrict__ rows_all, int m_all,
+    float* __restrict__ part, int* err, float* __restrict__ a32_all, int64_t ld32, int gy0) {
   constexpr int DC = 8, LOGN2 = 11, N2 = 1 << LOGN2;
   const int64_t gy = (int64_t)blockIdx.y + gy0;  // row-block group (a launch may cover a range of them)
+  // sampled rows [s0, s0 + m) of the m_all: up to 8 per thread, more in further grid.z slices
+  // (each slice transforms the block again); the first slice writes the FP32 copy
+  const int s0 = (int)blockIdx.z * 8 * SRHT_THREADS;
+  const int m = min(m_all - s0, 8 * SRHT_THREADS);
+  const int64_t* __restrict__ rows = rows_all + s0;
+  float* __restrict__ a32 = blockIdx.z == 0 ? a32_all : nullptr;
   constexpr uint32_t STAGE_BYTES = N2 * DC * sizeof(TA);
   using T2 = typename std::conditional<sizeof(TA) == 8, double2, float2>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -818,7 +824,7 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
     // a failed wait may leave a copy in flight: give it (bounded) time to land before exit
     (void)srht_mbar_wait(&full, (uint32_t)((issued - 1) & 1), err);
   }
-  float* out = part + gy * m * d;
+  float* out = part + (gy * m_all + s0) * d;
 #pragma unroll
   for (int i = 0; i < MY; ++i) {
     const int s = tid + SRHT_THREADS * i;
@@ -1099,10 +1105,10 @@ template <typename TA>
 static bool srht_tma_usable(const lsq_matrix* A, int m) {
   constexpr int DC = 8, N2 = 2048;
   const size_t es = sizeof(TA);
-  if (m > 8 * SRHT_THREADS) return false;
   if (((uintptr_t)A->data % 16) != 0 || ((size_t)A->ld * es) % 16 != 0) return false;
-  const size_t smem = 1024 + (size_t)N2 * DC * es + (size_t)zphys(N2, DC) * 4 + (size_t)m * 4 +
-                      (size_t)((m + 1) & ~1) * 2 + (N2 / 32) * 4;
+  const int ms = std::min(m, 8 * SRHT_THREADS);  // sampled rows per grid.z slice
+  const size_t smem = 1024 + (size_t)N2 * DC * es + (size_t)zphys(N2, DC) * 4 + (size_t)ms * 4 +
+                      (size_t)((ms + 1) & ~1) * 2 + (N2 / 32) * 4;
   return smem <= 232448 - 1024 && tensor_map_encoder() != nullptr;
 }
 
@@ -1115,8 +1121,10 @@ static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1
   constexpr int DC = 8, N2 = 2048;
   const size_t es = sizeof(TA);
   if (!srht_tma_usable<TA>(A, m)) return false;
-  const size_t smem = 1024 + (size_t)N2 * DC * es + (size_t)zphys(N2, DC) * 4 + (size_t)m * 4 +
-                      (size_t)((m + 1) & ~1) * 2 + (N2 / 32) * 4;
+  const int ms = std::min(m, 8 * SRHT_THREADS);
+  const int slices = lsq_ceil_div(m, 8 * SRHT_THREADS);
+  const size_t smem = 1024 + (size_t)N2 * DC * es + (size_t)zphys(N2, DC) * 4 + (size_t)ms * 4 +
+                      (size_t)((ms + 1) & ~1) * 2 + (N2 / 32) * 4;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   CUtensorMap tm;
   const cuuint64_t dims[2] = {(cuuint64_t)A->d, (cuuint64_t)A->n};
@@ -1129,7 +1137,7 @@ static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
   const int d = (int)A->d;
-  const dim3 grid(lsq_ceil_div(d, DC), groups);
+  const dim3 grid(lsq_ceil_div(d, DC), groups, slices);
   auto launch = [&](auto kern) -> lsq_status {
     LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, SRHT_THREADS, smem, ctx->stream>>>(tm, A->n, d, N1, blocks_per_group, signbits, rows, m, part, err,
@@ -1137,7 +1145,7 @@ static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
   };
-  const int my = (m + SRHT_THREADS - 1) / SRHT_THREADS;
+  const int my = (ms + SRHT_THREADS - 1) / SRHT_THREADS;
   if (my <= 1) *st = launch(srht_tma_kernel<TA, 1>);
   else if (my <= 2) *st = launch(srht_tma_kernel<TA, 2>);
   else if (my <= 4) *st = launch(srht_tma_kernel<TA, 4>);
@@ -1231,9 +1239,16 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
   int DC = (int)(32 / sizeof(TC));
   int logN2 = std::min(logN, 11);
   auto fits = [&](int dc, int l2) { return srht_smem_bytes(l2, m, dc, sizeof(TC)) <= budget; };
-  while (DC > 1 && !fits(DC, logN2)) DC >>= 1;
-  while (logN2 > 0 && !fits(DC, logN2)) --logN2;
-  if (!fits(DC, logN2) || logN2 > 16) return LSQ_ERR_ARG;
+  // the staged kernel keeps its sampled partials in registers (slices of 4096 rows), so the
+  // shared-memory budget below, for the kernels that accumulate SA in shared memory, does not
+  // apply to it
+  const bool tma = sizeof(TC) == 4 && logN2 == 11 &&
+                   (A->dtype == LSQ_F64 ? srht_tma_usable<double>(A, m) : srht_tma_usable<float>(A, m));
+  if (!tma) {
+    while (DC > 1 && !fits(DC, logN2)) DC >>= 1;
+    while (logN2 > 0 && !fits(DC, logN2)) --logN2;
+    if (!fits(DC, logN2) || logN2 > 16) return LSQ_ERR_ARG;
+  }
   const int64_t N1 = N >> logN2;
   const int tiles = lsq_ceil_div(d, DC);
   // about eight waves of one CTA per SM, so the last partial wave costs little

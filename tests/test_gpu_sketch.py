@@ -65,11 +65,12 @@ def test_srht_fp64(L, ctx, n, d, m, seed):
 @pytest.mark.parametrize("n,d,m,dtype,ld", [(5000, 13, 700, np.float64, 14), (5000, 13, 700, np.float32, 16),
                                              (9000, 24, 4096, np.float64, 24), (9000, 24, 4097, np.float64, 24),
                                              (3000, 20, 300, np.float64, 21), (2048, 8, 64, np.float64, 8),
-                                             (2048, 3, 64, np.float64, 4), (3000, 5, 100, np.float32, 8)])
+                                             (2048, 3, 64, np.float64, 4), (3000, 5, 100, np.float32, 8),
+                                             (20000, 40, 9000, np.float64, 40), (12000, 16, 8192, np.float32, 16)])
 def test_srht_fp32_arithmetic_layouts(L, ctx, n, d, m, dtype, ld):
     """FP32-arithmetic SRHT over row strides and sizes that take the staged (tensor-copy) kernel
-    -- ragged n and d, FP32 storage, 8 sampled rows per thread -- and ones that do not (more
-    than 4096 sampled rows, a row stride that is not a multiple of 16 bytes)."""
+    -- ragged n and d, FP32 storage, 8 sampled rows per thread, more than 4096 sampled rows in
+    slices of 4096 -- and ones that do not (a row stride that is not a multiple of 16 bytes)."""
     A = W.make_problem(n, d, 1e4, seed=n + d)["A"].astype(dtype)
     big = torch.zeros((n, ld), dtype=torch.float64 if dtype == np.float64 else torch.float32, device="cuda")
     big[:, :d] = to_dev(A)
@@ -186,6 +187,7 @@ def test_sketch_writes_fp32_copy(L, ctx, kind, precision, n, d):
     (2**17 + 777, 64, 512, np.float64, "srht", True),     # many row-block groups, ragged tail
     (300000, 512, 4096, np.float64, "srht", True),         # the headline's shape class
     (70000, 40, 256, np.float32, "srht", True),            # FP32 A, d not a multiple of 8
+    (50000, 48, 6000, np.float64, "srht", True),           # two slices of sampled rows
     (1500, 24, 64, np.float64, "srht", False),             # under one 2048-row block: whole copy
     (5000, 33, 128, np.float64, "gauss", True),            # other sketches: whole copy, then sketch
 ])
