@@ -15,6 +15,7 @@ import argparse
 import json
 import os
 import statistics
+import tempfile
 import subprocess
 import sys
 import time
@@ -96,8 +97,10 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/lsq_clocks_{os.getpid()}.csv"
+        # the raw samples go to LSQ_CLOCKS_DIR (default: the system temporary directory); the
+        # bench line carries their summary
+        out_dir = os.environ.get("LSQ_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"lsq_clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
