@@ -38,7 +38,7 @@ SOLVE_KERNEL = "solve_kernel"
 # kernels' sources hash to the captured ones.
 SOLVE_TRAFFIC = {"ratio_solve": (14554827000 + 35496960) / 14495514624,
                  "ratio_with_copy": (1553537240 + 14554827000 + 35496960) / 16106127360, "sources_sha256":
-                 "3144026a6686f1a17aa1ce0111679289cee6200a748589f9e357fa51a6cb2c1d"}
+                 "654f37a9fa44f45b95c5afc2f1f72269ec01fbce18c482a3e16a6ecb5b501c5a"}
 
 
 def solve_sources_sha256() -> str:
@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=os.environ.get("LSQ_BENCH_PRECISION", "mixed"), choices=["f64", "mixed"])
     ap.add_argument("--sketch", default="srht", choices=["srht", "sjlt", "gauss"])
-    ap.add_argument("--sketch-precision", default="f32", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--sketch-precision", default=None, choices=["f64", "f32", "bf16"],
+                    help="sketch arithmetic (default: f32 for the single solve, bf16 for the batched SJLT)")
     ap.add_argument("--a-dtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--outlier-frac", type=float, default=0.0)
     ap.add_argument("--m", "--sketch-rows", dest="m", type=int, default=4096)
@@ -75,7 +76,11 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="time the batched solve of this many uneven problems instead (k right-hand sides each)")
     ap.add_argument("--batch-seed", type=int, default=1)
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.sketch_precision is None:
+        # the batched workload's SJLT over BF16-rounded A; the single solve's SRHT in FP32
+        args.sketch_precision = "bf16" if args.batch > 0 else "f32"
+    return args
 
 
 def peaks():

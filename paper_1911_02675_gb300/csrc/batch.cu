@@ -1115,8 +1115,9 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   std::vector<double*> w_ptr(nprob), wt_ptr(nprob);
   std::vector<int> m_of(nprob), d_of(nprob);
   cudaEventRecord(e1, s);
-  // SJLT in FP32: every problem's sketch in one launch
-  const bool one_launch = o.sketch_type == LSQ_SKETCH_SJLT && o.sketch_precision == LSQ_SKETCH_F32;
+  // SJLT in FP32 (or over BF16-rounded A): every problem's sketch in one launch
+  const bool one_launch = o.sketch_type == LSQ_SKETCH_SJLT &&
+                          (o.sketch_precision == LSQ_SKETCH_F32 || o.sketch_precision == LSQ_SKETCH_BF16);
   if (one_launch) {
     std::vector<lsq_matrix> mats(nprob);
     std::vector<int> ms(nprob);
@@ -1127,7 +1128,8 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
       ms[p] = (int)std::max<int64_t>(d, (int64_t)ceil(o.m_factor * (double)d));
       sas[p] = reinterpret_cast<double*>(base + sa_off[p]);
     }
-    st = lsq_sjlt_batched(ctx, nprob, mats.data(), ms.data(), o.s > 0 ? o.s : 8, o.seed, sas.data());
+    st = lsq_sjlt_batched(ctx, nprob, mats.data(), ms.data(), o.s > 0 ? o.s : 8, o.seed, sas.data(),
+                          o.sketch_precision == LSQ_SKETCH_BF16);
     if (st != LSQ_OK) return st;
   }
   for (int p = 0; p < nprob; ++p) {

@@ -67,9 +67,10 @@ void lsq_count_launch();
 lsq_status lsq_ensure_scratch(lsq_ctx* ctx, size_t bytes);
 lsq_status lsq_ensure_state(lsq_ctx* ctx, size_t bytes);
 lsq_status lsq_ensure_a32(lsq_ctx* ctx, size_t bytes);
-// SJLT sketches of nprob problems in one launch (FP32 arithmetic; instance t = p) (sketch.cu)
+// SJLT sketches of nprob problems in one launch (FP32 arithmetic, over BF16-rounded A when bf16;
+// instance t = p) (sketch.cu)
 lsq_status lsq_sjlt_batched(lsq_ctx* ctx, int nprob, const lsq_matrix* A, const int* m, int s, uint64_t seed,
-                            double* const* SA);
+                            double* const* SA, int bf16);
 // a32[i * ld32 + c] = FP32 narrowing of A[i][c] (FP64 A), on the context's stream (solve.cu)
 lsq_status lsq_narrow_copy(lsq_ctx* ctx, const lsq_matrix* A, float* a32, int64_t ld32);
 

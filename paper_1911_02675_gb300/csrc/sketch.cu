@@ -5,6 +5,7 @@
 // per-split scratch slab and a fixed-order reduction writes SA, so results repeat run
 // to run (SJLT: up to the order of its shared-memory additions).
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <math.h>
 
@@ -897,12 +898,22 @@ __device__ __forceinline__ void rotate_by(TC (&a)[DC], int r) {
   }
 }
 
+// LSQ_SKETCH_BF16 for the SJLT: an element of A rounded to FP32, then to BF16 (nearest, ties to
+// even); the +-1 signs are exact and the sums stay FP32
+__device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
 template <typename TC, int DC, int SMAX>
 __device__ __forceinline__ void sjlt_load_row(const void* A, int dtype, int64_t ld, int c0, int d, int s,
                                               const int32_t* h, const uint32_t* signs, int64_t i, bool ok, TC (&a)[DC],
-                                              int32_t (&tg)[SMAX], uint32_t& sw) {
+                                              int32_t (&tg)[SMAX], uint32_t& sw, bool bf16) {
 #pragma unroll
   for (int c = 0; c < DC; ++c) a[c] = (ok && c0 + c < d) ? load_as<TC>(A, i * ld + c0 + c, dtype) : (TC)0;
+  if constexpr (sizeof(TC) == 4) {
+    if (bf16) {
+#pragma unroll
+      for (int c = 0; c < DC; ++c) a[c] = round_bf16(a[c]);
+    }
+  }
 #pragma unroll
   for (int k = 0; k < SMAX; ++k) tg[k] = (ok && k < s) ? __ldg(h + i * s + k) : -1;
   sw = ok ? __ldg(signs + i) : 0u;
@@ -913,7 +924,8 @@ __global__ void __launch_bounds__(SJLT_THREADS, 1) sjlt_scatter_kernel(const voi
                                                                       int64_t n, int d, int64_t ld, int m, int s,
                                                                       const int32_t* __restrict__ h,
                                                                       const uint32_t* __restrict__ signs,
-                                                                      int64_t rows_per_group, TC* __restrict__ part) {
+                                                                      int64_t rows_per_group, TC* __restrict__ part,
+                                                                      int bf16) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* Y = reinterpret_cast<TC*>(smem_raw);  // [m][DC]
   const int c0 = blockIdx.x * DC;
@@ -926,10 +938,10 @@ __global__ void __launch_bounds__(SJLT_THREADS, 1) sjlt_scatter_kernel(const voi
   int32_t tg[SMAX], tn[SMAX];
   uint32_t sw = 0, swn = 0;
   int64_t i = i_begin + threadIdx.x;
-  sjlt_load_row<TC, DC, SMAX>(A, dtype, ld, c0, d, s, h, signs, i, i < i_end, a, tg, sw);
+  sjlt_load_row<TC, DC, SMAX>(A, dtype, ld, c0, d, s, h, signs, i, i < i_end, a, tg, sw, bf16 != 0);
   for (; i < i_end; i += SJLT_THREADS) {
     const int64_t inext = i + SJLT_THREADS;
-    sjlt_load_row<TC, DC, SMAX>(A, dtype, ld, c0, d, s, h, signs, inext, inext < i_end, an, tn, swn);
+    sjlt_load_row<TC, DC, SMAX>(A, dtype, ld, c0, d, s, h, signs, inext, inext < i_end, an, tn, swn, bf16 != 0);
     rotate_by<TC, DC>(a, rot);
 #pragma unroll
     for (int k = 0; k < SMAX; ++k) {
@@ -962,7 +974,7 @@ struct SjltJob {
   const void* A;
   int64_t n, ld, rpg;  // rows, row stride, rows per group
   float* part;         // [groups][m][d]
-  int dtype, d, m, s, vec;
+  int dtype, d, m, s, vec, bf16;
   uint32_t t;
 };
 
@@ -992,6 +1004,10 @@ __global__ void __launch_bounds__(SJLT_THREADS, 1) sjlt_batched_kernel(const Sjl
     } else {
 #pragma unroll
       for (int c = 0; c < DC; ++c) a[c] = c0 + c < d ? load_as<float>(jb.A, i * jb.ld + c0 + c, jb.dtype) : 0.f;
+    }
+    if (jb.bf16) {
+#pragma unroll
+      for (int c = 0; c < DC; ++c) a[c] = round_bf16(a[c]);
     }
     int32_t tg[SMAX];
     sjlt_targets<SMAX>(seed, i, jb.t, m, s, tg);
@@ -1362,7 +1378,7 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
 
 template <typename TC, int DC>
 static lsq_status sjlt_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, const int32_t* h,
-                              const uint32_t* signs, TC* part, int groups, int64_t rows_per_group) {
+                              const uint32_t* signs, TC* part, int groups, int64_t rows_per_group, bool bf16) {
   const int d = (int)A->d;
   const size_t smem = (size_t)m * DC * sizeof(TC);
   dim3 grid(lsq_ceil_div(d, DC), groups);
@@ -1370,19 +1386,20 @@ static lsq_status sjlt_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, c
     auto kern = sjlt_scatter_kernel<TC, DC, 8>;
     LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, SJLT_THREADS, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, s, h, signs,
-                                                    rows_per_group, part);
+                                                    rows_per_group, part, bf16 ? 1 : 0);
   } else {
     auto kern = sjlt_scatter_kernel<TC, DC, 32>;
     LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, SJLT_THREADS, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, s, h, signs,
-                                                    rows_per_group, part);
+                                                    rows_per_group, part, bf16 ? 1 : 0);
   }
   LSQ_LAUNCH_CHECK();
   return LSQ_OK;
 }
 
 template <typename TC>
-static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint64_t seed, uint32_t t, double* SA) {
+static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint64_t seed, uint32_t t, double* SA,
+                           bool bf16 = false) {
   const int d = (int)A->d;
   const int64_t n = A->n;
   const size_t budget = 200 * 1024;
@@ -1407,10 +1424,10 @@ static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint
   sjlt_hash_kernel<<<grid_for(n, 256, 16 * ctx->sm_count), 256, 0, ctx->stream>>>(n, m, s, seed, t, h, signs);
   LSQ_LAUNCH_CHECK();
   switch (DC) {
-    case 8: st = sjlt_launch<TC, 8>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group); break;
-    case 4: st = sjlt_launch<TC, 4>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group); break;
-    case 2: st = sjlt_launch<TC, 2>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group); break;
-    default: st = sjlt_launch<TC, 1>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group); break;
+    case 8: st = sjlt_launch<TC, 8>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group, bf16); break;
+    case 4: st = sjlt_launch<TC, 4>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group, bf16); break;
+    case 2: st = sjlt_launch<TC, 2>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group, bf16); break;
+    default: st = sjlt_launch<TC, 1>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group, bf16); break;
   }
   if (st != LSQ_OK) return st;
   const int64_t md = (int64_t)m * d;
@@ -1434,7 +1451,7 @@ static lsq_status sketch_impl(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
   const int s = (opts && opts->s > 0) ? opts->s : 8;
   const int prec = opts ? opts->precision : LSQ_SKETCH_F64;
   if (prec != LSQ_SKETCH_F64 && prec != LSQ_SKETCH_F32 && prec != LSQ_SKETCH_BF16) return LSQ_ERR_ARG;
-  if (prec == LSQ_SKETCH_BF16 && type != LSQ_SKETCH_GAUSS) return LSQ_ERR_ARG;
+  if (prec == LSQ_SKETCH_BF16 && type != LSQ_SKETCH_GAUSS && type != LSQ_SKETCH_SJLT) return LSQ_ERR_ARG;
   const bool f64 = prec == LSQ_SKETCH_F64;
   float* a32 = (opts && A->dtype == LSQ_F64) ? opts->a32 : nullptr;
   const int64_t ld32 = a32 ? opts->ld32 : 0;
@@ -1457,7 +1474,8 @@ static lsq_status sketch_impl(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
       break;
     case LSQ_SKETCH_SJLT:
       if (s < 1 || s > 32 || s > m) return LSQ_ERR_ARG;
-      st = f64 ? sjlt_run<double>(ctx, A, (int)m, s, seed, t, SA) : sjlt_run<float>(ctx, A, (int)m, s, seed, t, SA);
+      st = f64 ? sjlt_run<double>(ctx, A, (int)m, s, seed, t, SA)
+               : sjlt_run<float>(ctx, A, (int)m, s, seed, t, SA, prec == LSQ_SKETCH_BF16);
       break;
     default:
       return LSQ_ERR_ARG;
@@ -1483,7 +1501,7 @@ extern "C" lsq_status lsq_upload_sketch(lsq_ctx* ctx, const void* host_A, int64_
 // Sketches of many problems in one launch (SJLT, FP32 arithmetic): problem p draws instance
 // t = p of `seed` into SA[p] (m[p] x d FP64), exactly the embedding lsq_sketch would draw.
 lsq_status lsq_sjlt_batched(lsq_ctx* ctx, int nprob, const lsq_matrix* A, const int* m, int s, uint64_t seed,
-                            double* const* SA) {
+                            double* const* SA, int bf16) {
   if (nprob <= 0) return LSQ_OK;
   constexpr int DC = 8;
   std::vector<SjltJob> jobs(nprob);
@@ -1515,6 +1533,7 @@ lsq_status lsq_sjlt_batched(lsq_ctx* ctx, int nprob, const lsq_matrix* A, const 
     jb.m = mp;
     jb.s = sp;
     jb.vec = (((uintptr_t)a.data % 16) == 0 && ((size_t)a.ld * es) % 16 == 0) ? 1 : 0;
+    jb.bf16 = bf16 ? 1 : 0;
     jb.t = (uint32_t)p;
     groups[p] = gp;
     prefix[p] = total;

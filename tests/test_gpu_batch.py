@@ -38,11 +38,13 @@ def _dev(probs, dtype):
     return [(to_dev(q["A"].astype(dtype)), to_dev(q["B"])) for q in probs]
 
 
-@pytest.mark.parametrize("precision", ["mixed", "f64"])
-def test_batch_reaches_xstar(L, ctx, precision):
+@pytest.mark.parametrize("precision,sketch_precision", [("mixed", "f32"), ("f64", "f32"), ("mixed", "bf16")])
+def test_batch_reaches_xstar(L, ctx, precision, sketch_precision):
+    """Every right-hand side reaches 1e-10 against x*, also with the SJLT over BF16-rounded A
+    (the sketch is only the preconditioner's embedding; PCG wins the accuracy back)."""
     probs = W.make_batch(SHAPES, seed=11, scale_max=1e4, dtype=np.float32)
     X, per, info = L.lsq_solve_batched(ctx, _dev(probs, np.float32), tol=1e-10, maxit=300, precision=precision,
-                                       seed=4)
+                                       sketch_precision=sketch_precision, seed=4)
     assert info["status"] == 0, (info, per)
     for q, Xp, (it, st) in zip(probs, X, per):
         A64 = q["A"].astype(np.float64)

@@ -209,3 +209,24 @@ def test_upload_sketch_matches_sketch_of_device_copy(L, ctx, n, d, m, dtype, kin
     assert torch.equal(SA_up, SA_ref)
     if a32 is not None:  # the pad columns past d are never written nor read
         assert torch.equal(a32_up[:, :d], a32[:, :d])
+
+
+def _round_bf16(A):
+    """FP32 rounding, then BF16 (nearest, ties to even) by the bit pattern, back to FP64."""
+    u = np.ascontiguousarray(A.astype(np.float32)).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("n,d,m,s,dtype", [(5000, 33, 256, 8, np.float32), (3000, 20, 128, 4, np.float64),
+                                           (20000, 64, 512, 8, np.float32)])
+def test_sjlt_bf16_is_the_sketch_of_rounded_a(L, ctx, n, d, m, s, dtype):
+    """LSQ_SKETCH_BF16 for the SJLT: the FP64 sketch of A rounded to BF16 (exact +-1 signs and
+    positions), up to the FP32 sums."""
+    A = W.make_problem(n, d, 1e3, seed=n + s)["A"].astype(dtype)
+    Ab = _round_bf16(A)
+    assert np.max(np.abs(Ab - A)) > 0  # the rounding does something
+    SA = L.lsq_sketch(ctx, to_dev(A), "sjlt", m, 3, s=s, precision="bf16").cpu().numpy()
+    ref = O.sketch_sjlt(Ab, m, s, 3, 0)
+    assert rel_fro(SA, ref) < 1e-6
+    assert rel_fro(SA, O.sketch_sjlt(A.astype(np.float64), m, s, 3, 0)) < 1e-2  # ~ BF16 resolution
