@@ -323,11 +323,16 @@ __device__ void chol_inv_body(double* __restrict__ G, double* __restrict__ Rf, d
   __shared__ FactorSmem fsm;
   TileSmem& sm = fsm.tile;
   const int dp = nblk * 32;
+  // the group's barriers: a count that only grows (bar[2..3], zeroed before the launch)
+  unsigned long long bar_target = 0;
+  auto gsync = [&]() -> int {
+    return grid_sync_count(reinterpret_cast<unsigned long long*>(bar + 2), bar_target, nb, err);
+  };
   // Look-ahead: CTA 0 applies the trailing update to the next diagonal block first and
   // factors it at once, while the other CTAs update the rest of the trailing matrix; each
   // panel then needs two grid barriers.
   if (rank == 0) diag_chol(fsm.diag, G, Rf, dp, err);
-  if (grid_barrier(bar, nb, err)) return;
+  if (gsync()) return;
   for (int k = 0; k < nblk; ++k) {
     const int64_t kk = (int64_t)k * 32;
     const int rest = nblk - 1 - k;
@@ -338,7 +343,7 @@ __device__ void chol_inv_body(double* __restrict__ G, double* __restrict__ Rf, d
       const int64_t col = (int64_t)j * 32 + q * 8;
       trsm_task(sm, Rf + kk * dp + col, Rf + kk * dp + kk, G + kk * dp + col, G + kk * dp + kk, dp);
     }
-    if (grid_barrier(bar, nb, err)) return;
+    if (gsync()) return;
     if (rest == 0) break;
     // trailing update: G[i][j] -= R[k][i]^T R[k][j], k < i <= j; pair 0 is the next
     // diagonal block (k+1, k+1)
@@ -390,14 +395,14 @@ __device__ void chol_inv_body(double* __restrict__ G, double* __restrict__ Rf, d
                   dp, -1.0, true);
       }
     }
-    if (grid_barrier(bar, nb, err)) return;
+    if (gsync()) return;
   }
   // the inverses of the diagonal blocks, all at once
   for (int k = (int)rank; k < nblk; k += (int)nb) {
     const int64_t kk = (int64_t)k * 32;
     diag_inv(fsm.diag, G + kk * dp + kk, Rf + kk * dp + kk, Wf + kk * dp + kk, dp);
   }
-  if (grid_barrier(bar, nb, err)) return;
+  if (gsync()) return;
   // W = R^{-1}: merge sibling blocks bottom-up
   for (int lev = 0; lev < nlevels; ++lev) {
     const int n0 = level_start[lev], n1 = level_start[lev + 1];
@@ -414,7 +419,7 @@ __device__ void chol_inv_body(double* __restrict__ G, double* __restrict__ Rf, d
       }
       base += rows * cols4;
     }
-    if (grid_barrier(bar, nb, err)) return;
+    if (gsync()) return;
     // phase 2: W[a:mid, mid:b] = -W[a:mid, a:mid] T[a:mid, mid:b]
     base = 0;
     for (int nd = n0; nd < n1; ++nd) {
@@ -428,7 +433,7 @@ __device__ void chol_inv_body(double* __restrict__ G, double* __restrict__ Rf, d
       }
       base += rows * cols4;
     }
-    if (grid_barrier(bar, nb, err)) return;
+    if (gsync()) return;
   }
 }
 
