@@ -174,8 +174,8 @@ LSQ_API lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
  *   A       : device destination (data, n, d, ld, dtype as lsq_sketch); it receives the host
  *             matrix and is then the A of the sketch.
  *   other arguments, results and status as lsq_sketch (deferred checks apply).
- * SRHT with the staged transform (n > 2048 rows, 32-byte column tiles, 16-byte aligned rows,
- * FP32 arithmetic): the rows are copied per row-block group on an internal stream, which first
+ * SRHT with the staged transform (n > 1024 rows, so that the zero-padded length holds whole
+ * 2048-row blocks; 16-byte aligned rows; FP32 arithmetic): the rows are copied per row-block group on an internal stream, which first
  * waits for the work already queued on the context stream, and each group's transform starts
  * on the context stream as soon as its rows have landed (the SRHT sums per-group partials, so
  * the result is that of lsq_sketch).  Any other case copies the whole matrix on the context

@@ -188,7 +188,8 @@ def test_sketch_writes_fp32_copy(L, ctx, kind, precision, n, d):
     (300000, 512, 4096, np.float64, "srht", True),         # the headline's shape class
     (70000, 40, 256, np.float32, "srht", True),            # FP32 A, d not a multiple of 8
     (50000, 48, 6000, np.float64, "srht", True),           # two slices of sampled rows
-    (1500, 24, 64, np.float64, "srht", False),             # under one 2048-row block: whole copy
+    (1500, 24, 64, np.float64, "srht", False),             # one zero-padded block, pageable host memory
+    (900, 24, 64, np.float64, "srht", True),               # padded length under 2048: whole copy
     (5000, 33, 128, np.float64, "gauss", True),            # other sketches: whole copy, then sketch
 ])
 def test_upload_sketch_matches_sketch_of_device_copy(L, ctx, n, d, m, dtype, kind, pinned):
