@@ -10,7 +10,7 @@ closed-form parameters of the paper.
 
 Functions and the passages they follow:
   philox4x32_10          Philox4x32-10 (Salmon et al., SC'11), the generator every sketch draws from
-  gauss_matrix, sketch_gauss   Gaussian embedding N(0, 1/m)            Section 2
+  gauss_matrix, sketch_gauss, sketch_gauss_rows   Gaussian embedding N(0, 1/m)   Section 2
   srht_signs, srht_rows, sketch_srht   S = R H E with zero padding      Section 2 (+ footnote)
   sjlt_hash, sketch_sjlt  s nonzeros +-1/sqrt(s) per column of S         Section 2 (last paragraph)
   gram, cholesky_upper, qr_r, tri_inv_upper, precond_solve
@@ -56,6 +56,7 @@ def lib():
             "orc_gauss_z": (dbl, [u64, u32, i64, i64]),
             "orc_gauss_matrix": (None, [i64, i64, u64, u32, P]),
             "orc_sketch_gauss": (None, [P, i64, i64, i64, i64, u64, u32, P]),
+            "orc_sketch_gauss_rows": (None, [P, i64, i64, i64, i64, u64, u32, P, i64, P]),
             "orc_next_pow2": (i64, [i64]),
             "orc_srht_signs": (None, [i64, u64, u32, P]),
             "orc_srht_rows": (None, [i64, i64, u64, u32, P]),
@@ -136,6 +137,17 @@ def sketch_gauss(A, m: int, seed: int, t: int = 0) -> np.ndarray:
     SA = np.empty((m, d))
     lib().orc_sketch_gauss(_ptr(A), n, d, ld, m, seed, t, _ptr(SA))
     return SA
+
+
+def sketch_gauss_rows(A, m: int, seed: int, rows, t: int = 0) -> np.ndarray:
+    """Rows `rows` of the Gaussian SA (m rows in all) without the others."""
+    A, n, d, ld = _mat(A)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    if rows.size and (rows.min() < 0 or rows.max() >= m):
+        raise ValueError("row index outside the sketch")
+    out = np.empty((rows.size, d))
+    lib().orc_sketch_gauss_rows(_ptr(A), n, d, ld, m, seed, t, _ptr(rows), rows.size, _ptr(out))
+    return out
 
 
 def next_pow2(n: int) -> int:

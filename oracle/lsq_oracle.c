@@ -137,6 +137,25 @@ void orc_sketch_gauss(const double* A, int64_t n, int64_t d, int64_t ld, int64_t
   }
 }
 
+/* Rows `rows[0..k-1]` of SA = S A for the m x n Gaussian S above (the same entries
+   z(j,i)/sqrt(m)), without the other rows: a row sample of the sketch, for checks and timing
+   of the sketch at sizes where all m rows would take too long. */
+void orc_sketch_gauss_rows(const double* A, int64_t n, int64_t d, int64_t ld, int64_t m, uint64_t seed,
+                           uint32_t t, const int64_t* rows, int64_t k, double* SA_rows) {
+  double scale = 1.0 / sqrt((double)m);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t r = 0; r < k; ++r) {
+    int64_t j = rows[r];
+    double* out = SA_rows + r * d;
+    for (int64_t c = 0; c < d; ++c) out[c] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      double s = scale * orc_gauss_z(seed, t, j, i);
+      const double* a = A + i * ld;
+      for (int64_t c = 0; c < d; ++c) out[c] += s * a[c];
+    }
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* SRHT, Section 2: S = R H E (row sampling without replacement, Hadamard,   */
 /* random signs), zero padding of n to N = 2^ceil(log2 n) (footnote there).   */

@@ -67,6 +67,16 @@ def test_gaussian_sketch_is_explicit_product():
     assert abs((O.gauss_matrix(64, 400, 11) ** 2).mean() * 64 - 1) < 0.03
 
 
+def test_gaussian_sketch_rows_are_rows_of_the_explicit_product():
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((53, 6))
+    S = O.gauss_matrix(12, 53, seed=5, t=1)
+    rows = np.array([11, 0, 7, 7])
+    np.testing.assert_allclose(O.sketch_gauss_rows(A, 12, seed=5, rows=rows, t=1), (S @ A)[rows], rtol=1e-13,
+                               atol=1e-13)
+    np.testing.assert_array_equal(O.sketch_gauss_rows(A, 12, 5, rows, t=1), O.sketch_gauss(A, 12, 5, t=1)[rows])
+
+
 def test_gaussian_inverse_moments_monte_carlo():
     """E[C_S^-1] = theta1 I and E[C_S^-2] = theta2 I (Section 2, Gaussian moments)."""
     n, d, m, trials = 40, 4, 16, 3000
