@@ -1,13 +1,21 @@
 """Benchmark: time-to-1e-10 (relative H-norm error) of the randomized-preconditioned
 least-squares solve on one GB300, sketch + factor + iterations, A resident in HBM.
 
-Workload (default): A 2^20 x 512 FP64, A = G diag(sigma), sigma log-spaced 1..1e6,
-b = A^T (A x_true + 0.1 eps); SRHT sketch m = 4096 (seed 0); PCG from x0 = 0 to 1e-10.
-A (4 GiB) is larger than L2 (~129 MB), so no flush is needed between steps.
+Default workload (fp32_4194304x1024_gauss4096_pcg): A 2^22 x 1024 stored in FP32,
+A = G diag(sigma) with sigma log-spaced 1..1e5 and 5 % of the rows scaled x100 (high-leverage
+outliers), b = A^T (A x_true + 0.1 eps) formed in FP64 from the FP32 values; Gaussian sketch
+m = 4096 (seed 0) generated on the fly in BF16 on the tensor cores with FP32 accumulation;
+double-FP32 Gram, FP64 Cholesky and triangular products; mixed-precision PCG (FP32 passes over
+A, FP64 residual replacement and update) from x0 = 0 to 1e-10.  A (16 GiB) is larger than L2
+(~129 MB), so no flush is needed between steps.
+
+The line also carries, under "secondary", the FP64 workload fp64_1048576x512_srht4096_pcg
+(A 2^20 x 512 FP64, sigma 1..1e6, FP32 SRHT m = 4096 that writes the FP32 copy of A, mixed PCG).
 
 Prints one JSON line (see the repository's design notes for every key).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision f64|mixed] [--sketch srht|sjlt|gauss] [--m 4096] [--n-log2 20] [--d 512]
+                    [--workload NAME] [--precision f64|mixed] [--sketch srht|sjlt|gauss] [--m 4096]
+                    [--n-log2 22] [--d 1024] [--a-dtype f32|f64] [--no-secondary] ...
 """
 from __future__ import annotations
 
@@ -29,16 +37,32 @@ import workloads as WL  # noqa: E402
 
 SOLVE_KERNEL = "solve_kernel"
 
-# DRAM traffic of the mixed solve phase from one ncu capture (n = 2^18, d = 512, SRHT m = 4096, 25 passes
-# of which 2 exact; profiles/solve_kernel_mixed_262144x512_srht4096.md): dram__bytes_read.sum +
-# dram__bytes_write.sum divided by the algorithmic bytes, for solve_kernel<double, 16, MIXED, COPY> alone
-# (the FP32 copy supplied by the sketch) and with the solve's own narrow_copy_kernel<16> (1.554 GB, from
-# a full capture of that kernel, unchanged since).  Scaled to a
-# launch of the bench by its algorithmic bytes (units processed: passes x rows); reported only while the
-# kernels' sources hash to the captured ones.
-SOLVE_TRAFFIC = {"ratio_solve": (14554827000 + 35496960) / 14495514624,
-                 "ratio_with_copy": (1553537240 + 14554827000 + 35496960) / 16106127360, "sources_sha256":
-                 "654f37a9fa44f45b95c5afc2f1f72269ec01fbce18c482a3e16a6ecb5b501c5a"}
+# The timed workloads, named by what they are.  Explicit shape options override a preset.
+PRESETS = {
+    # FP32-stored A with outliers, BF16 Gaussian sketch on the tensor cores, mixed PCG
+    "fp32_4194304x1024_gauss4096_pcg": dict(n_log2=22, d=1024, sigma_max=1e5, a_dtype="f32", outlier_frac=0.05,
+                                            sketch="gauss", sketch_precision="bf16", m=4096),
+    # FP64 A, FP32 SRHT writing the FP32 copy of A, mixed PCG
+    "fp64_1048576x512_srht4096_pcg": dict(n_log2=20, d=512, sigma_max=1e6, a_dtype="f64", outlier_frac=0.0,
+                                          sketch="srht", sketch_precision="f32", m=4096),
+}
+DEFAULT_WORKLOAD = "fp32_4194304x1024_gauss4096_pcg"
+SECONDARY = {"fp32_4194304x1024_gauss4096_pcg": "fp64_1048576x512_srht4096_pcg"}
+
+# DRAM traffic of solve_kernel over its algorithmic bytes, from one ncu capture per instance
+# (dram__bytes_read.sum + dram__bytes_write.sum of the kernel / the algorithmic bytes of that
+# launch), keyed by (A dtype, d, FP32 copy of A): scaled to a launch of the bench by its
+# algorithmic bytes (units processed: passes x rows), and reported only while the solve
+# sources hash to the captured ones.
+#   ("f64", 512, 2): n = 2^18, SRHT m = 4096, 25 passes of which 2 exact, the FP32 copy supplied by
+#   the sketch; ("f64", 512, 1) adds the solve's own narrow_copy_kernel<16> (1.554 GB).
+SOLVE_TRAFFIC = {
+    "sources_sha256": "654f37a9fa44f45b95c5afc2f1f72269ec01fbce18c482a3e16a6ecb5b501c5a",
+    "ratios": {
+        ("f64", 512, 2): (14554827000 + 35496960) / 14495514624,
+        ("f64", 512, 1): (1553537240 + 14554827000 + 35496960) / 16106127360,
+    },
+}
 
 
 def solve_sources_sha256() -> str:
@@ -51,45 +75,67 @@ def solve_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(PRESETS),
+                    help="preset workload; the shape options below override its fields")
     ap.add_argument("--precision", default=os.environ.get("LSQ_BENCH_PRECISION", "mixed"), choices=["f64", "mixed"])
-    ap.add_argument("--sketch", default="srht", choices=["srht", "sjlt", "gauss"])
+    ap.add_argument("--sketch", default=None, choices=["srht", "sjlt", "gauss"])
     ap.add_argument("--sketch-precision", default=None, choices=["f64", "f32", "bf16"],
-                    help="sketch arithmetic (default: f32 for the single solve, bf16 for the batched SJLT)")
-    ap.add_argument("--a-dtype", default="f64", choices=["f64", "f32"])
-    ap.add_argument("--outlier-frac", type=float, default=0.0)
-    ap.add_argument("--m", "--sketch-rows", dest="m", type=int, default=4096)
-    ap.add_argument("--n-log2", type=int, default=20)
-    ap.add_argument("--d", "--dim", dest="d", type=int, default=512)
-    ap.add_argument("--sigma-max", type=float, default=1e6)
+                    help="sketch arithmetic (default: the preset's; bf16 for the batched SJLT)")
+    ap.add_argument("--a-dtype", default=None, choices=["f64", "f32"])
+    ap.add_argument("--outlier-frac", type=float, default=None)
+    ap.add_argument("--m", "--sketch-rows", dest="m", type=int, default=None)
+    ap.add_argument("--n-log2", type=int, default=None)
+    ap.add_argument("--d", "--dim", dest="d", type=int, default=None)
+    ap.add_argument("--sigma-max", type=float, default=None)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (cpu_baseline and the accuracy check)")
     ap.add_argument("--no-plain", action="store_true", help="skip timing plain FP64 PCG beside the build")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workload")
     ap.add_argument("--m-sweep", default="", help="comma-separated sketch sizes: time the solve at each "
                     "(time against m, beside Section 6's advised m*) instead of the bench line")
     ap.add_argument("--batch", type=int, default=0,
                     help="time the batched solve of this many uneven problems instead (k right-hand sides each)")
     ap.add_argument("--batch-seed", type=int, default=1)
-    args = ap.parse_args()
-    if args.sketch_precision is None:
-        # the batched workload's SJLT over BF16-rounded A; the single solve's SRHT in FP32
-        args.sketch_precision = "bf16" if args.batch > 0 else "f32"
+    args = ap.parse_args(argv)
+    apply_preset(args, args.workload)
+    if args.batch > 0 and args.sketch_precision_given is False:
+        args.sketch_precision = "bf16"  # the batched workload's SJLT over BF16-rounded A
     return args
+
+
+def apply_preset(args, name):
+    """Fills every shape option left unset from the preset `name`."""
+    args.sketch_precision_given = args.sketch_precision is not None
+    for k, v in PRESETS[name].items():
+        if getattr(args, k, None) is None:
+            setattr(args, k, v)
+    return args
+
+
+def preset_args(base, name, steps):
+    """A copy of `base` on the preset workload `name` (for the secondary line)."""
+    a = argparse.Namespace(**vars(base))
+    for k, v in PRESETS[name].items():
+        setattr(a, k, v)
+    a.workload, a.steps = name, steps
+    return a
 
 
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), float(p.get("bf16_tflops_sustained", p["bf16_tflops"])), \
+            "measured"
     except Exception:
-        return 6800.0, 1900.0, "fallback"
+        return 6800.0, 1900.0, 1700.0, "fallback"
 
 
 class ClockSampler:
@@ -172,66 +218,125 @@ def dist_info():
 
 
 def make_inputs(args, seed):
+    """The workload's (A, b) on the host (FP32 or FP64 A; b formed in FP64 from A's values)."""
+    return WL.make_problem(1 << args.n_log2, args.d, args.sigma_max, seed=seed,
+                           dtype=np.float32 if args.a_dtype == "f32" else np.float64,
+                           outlier_frac=args.outlier_frac)
+
+
+def workload_config(args, parallelism):
     n = 1 << args.n_log2
-    if args.a_dtype == "f32":
-        return None  # drawn on the device (run_ours)
-    P = WL.make_problem(n, args.d, args.sigma_max, seed=seed)
-    return P
+    elem = 8 if args.a_dtype == "f64" else 4
+    cfg = {"workload": f"{args.a_dtype[:1]}p{args.a_dtype[1:]}_{n}x{args.d}_{args.sketch}{args.m}_pcg",
+           "n": n, "d": args.d, "sigma_max": args.sigma_max, "outlier_frac": args.outlier_frac,
+           "sketch": args.sketch, "m": args.m, "sketch_precision": args.sketch_precision,
+           "precision": args.precision, "method": "pcg", "tol": args.tol, "A_dtype": args.a_dtype,
+           "l2": f"inputs larger than L2 (A = {n * args.d * elem / 2**30:.1f} GiB), no flush",
+           "parallelism": parallelism}
+    return cfg
 
 
-# ------------------------------------------------------------------------------ oracle arm
-def oracle_solve_sample(args, n_sample, P=None, seed=1):
-    """One solve of the oracle (sketch + factor + PCG) on the first n_sample rows of the
-    workload recipe (or on the given problem P).  Returns phase times (s) and iterations."""
+# ------------------------------------------------------------------------------ oracle legs
+# (the only places the bench runs the oracle: the cpu_baseline leg, its accuracy check, and the
+# reference arm)
+GAUSS_ORACLE_FULL_LIMIT = 2e10  # m n d multiply-adds the oracle's Gaussian sketch runs in whole
+
+
+def _as_f64(A):
+    return A if A.dtype == np.float64 else A.astype(np.float64)
+
+
+def oracle_estimate(args, P, A64=None, sketch_rows=16):
+    """Oracle time (ms) per solve of the workload: sketch + factor + PCG on the host cores.
+
+    * up to 2^20 rows, a Gaussian sketch within GAUSS_ORACLE_FULL_LIMIT multiply-adds, or another
+      sketch: the whole workload (above 2^20 rows: the first 2^20 rows, the O(n) phases scaled);
+    * a larger Gaussian sketch: `sketch_rows` rows of S timed over all n rows and scaled by
+      m / sketch_rows (the oracle's sketch is a plain triple loop); the factor timed on an m x d
+      matrix; the iterations as (T + 1) passes over all of A, T = ceil(log(4/tol^2)/log(m/d)) the
+      iteration count Section 6 predicts, one pass timed as the mean of two."""
     import oracle as O
 
-    if P is None or P["A"].shape[0] != n_sample:
-        P = WL.make_problem(n_sample, args.d, args.sigma_max, seed=seed)
-    A, b = P["A"], P["b"]
-    m = min(args.m, O.next_pow2(n_sample))
+    n, d, m = P["A"].shape[0], args.d, args.m
+    A64 = _as_f64(P["A"]) if A64 is None else A64
+    b = P["b"]
+    if args.sketch == "gauss" and float(m) * n * d > GAUSS_ORACLE_FULL_LIMIT:
+        rows = np.linspace(0, m - 1, sketch_rows).astype(np.int64)
+        t0 = time.perf_counter()
+        O.sketch_gauss_rows(A64, m, 0, rows)
+        t_sketch = (time.perf_counter() - t0) * m / sketch_rows
+        M = np.random.default_rng(0).standard_normal((m, d))
+        t0 = time.perf_counter()
+        O.factor(M)
+        t_factor = time.perf_counter() - t0
+        p = np.random.default_rng(1).standard_normal(d)
+        t0 = time.perf_counter()
+        for _ in range(2):
+            O.hmatvec(A64, p)
+        t_pass = (time.perf_counter() - t0) / 2
+        T = O.pcg_iterations_bound(args.tol ** 2, d / m)
+        est = t_sketch + t_factor + (T + 1) * t_pass
+        sample = (f"oracle (FP64 on the FP64 upcast of A): Gaussian SA on {sketch_rows} of {m} rows of S over all "
+                  f"{n} rows, scaled by {m / sketch_rows:g} ({t_sketch * sketch_rows / m:.2f} s measured); factor of "
+                  f"an {m} x {d} matrix ({t_factor:.2f} s); {T} + 1 passes over A for PCG to {args.tol:g} "
+                  f"(T = Section 6's predicted count at rho = d/m), one pass {t_pass:.3f} s measured")
+        return est * 1e3, sample, O.num_threads()
+    n_sample = min(n, 1 << 20)
+    As, bs = A64[:n_sample], b
+    if n_sample < n:
+        Ps = WL.make_problem(n_sample, d, args.sigma_max, seed=1, outlier_frac=args.outlier_frac,
+                             dtype=P["A"].dtype)
+        As, bs = _as_f64(Ps["A"]), Ps["b"]
+    ms = min(m, O.next_pow2(n_sample))
     t0 = time.perf_counter()
-    SA = O.sketch(A, args.sketch, m, 0)
+    SA = O.sketch(As, args.sketch, ms, 0)
     t1 = time.perf_counter()
     R = O.factor(SA)
     t2 = time.perf_counter()
-    x, it, st, _ = O.pcg(A, b, R, tol=args.tol, maxit=500, rho_hat=args.d / m)
+    _, it, _, _ = O.pcg(As, bs, R, tol=args.tol, maxit=1000, rho_hat=d / ms)
     t3 = time.perf_counter()
-    return {"sketch": t1 - t0, "factor": t2 - t1, "iters_s": t3 - t2, "iters": it, "status": st, "n": n_sample, "m": m}
+    scale = n / n_sample
+    est = (t1 - t0) * scale + (t2 - t1) + (t3 - t2) * scale
+    what = "the whole workload" if scale == 1 else f"the first {n_sample} rows of the same recipe"
+    sample = (f"oracle on {what} (d={d}, {args.sketch} m={ms}, PCG to {args.tol:g}, {it} iterations)"
+              + ("" if scale == 1 else f"; sketch and passes scaled by {scale:g}, factor unscaled")
+              + f"; measured {t3 - t0:.2f} s")
+    return est * 1e3, sample, O.num_threads()
 
 
-def oracle_n_sample(args):
-    """The whole workload up to 2^20 rows (seconds of CPU work); above that the first 2^20 rows."""
-    return min(1 << args.n_log2, 1 << 20)
-
-
-def oracle_estimate(args, n_sample, P=None):
-    """Oracle time per solve at the full workload: measured on the whole workload when it has at
-    most 2^20 rows; otherwise the O(n) phases (sketch, passes over A) of an n_sample-row solve
-    are scaled by n_full / n_sample and the factor, which does not depend on n, is not."""
+def oracle_accuracy(A64, b, x):
+    """Relative H-norm error ||x - x*||_H / ||x*||_H of the GPU's x, by the oracle: x* - x = H^{-1} r
+    with r = b - H x (the oracle's double-double residual), so ||x - x*||_H^2 = r^T H^{-1} r, with
+    H^{-1} r from the oracle's PCG to 1e-3 (an error of 1e-6 relative in r^T H^{-1} r), and
+    ||x*||_H^2 = <b, x*> estimated by <b, x>.  The PCG's preconditioner is numpy's Cholesky factor
+    of the Gram matrix of the first max(64 d, 4096) rows (any preconditioner gives the same H^{-1} r; enough rows that the
+    5 % high-leverage rows of the FP32 workload are well represented)."""
     import oracle as O
 
-    r = oracle_solve_sample(args, n_sample, P)
-    scale = (1 << args.n_log2) / r["n"]
-    est = r["sketch"] * scale + r["factor"] + r["iters_s"] * scale
-    what = "the whole workload" if scale == 1 else f"the first {r['n']} rows of the same recipe"
-    sample = (f"oracle on {what} (d={args.d}, {args.sketch} m={r['m']}, PCG to {args.tol:g}, {r['iters']} "
-              f"iterations)" + ("" if scale == 1 else f"; sketch and passes scaled by {scale:g}, factor unscaled")
-              + f"; measured {r['sketch'] + r['factor'] + r['iters_s']:.2f} s")
-    return est * 1e3, sample, O.num_threads()
+    n, d = A64.shape
+    k = min(n, max(64 * d, 4096))
+    t0 = time.perf_counter()
+    Ak = A64[:k]
+    R = np.linalg.cholesky(Ak.T @ Ak).T  # (library Cholesky: only a preconditioner, not part of the result)
+    r = O.residual_dd(A64, b, x)
+    z, it, st, _ = O.pcg(A64, r, R, tol=1e-3, maxit=500, rho_hat=d / k)
+    err = float(np.sqrt(max(float(r @ z), 0.0) / float(b @ x)))
+    return {"rel_h_err_vs_oracle": err, "oracle_s": time.perf_counter() - t0, "oracle_pcg_iters": it,
+            "oracle": "sqrt(r^T H^-1 r / <b, x>), r = b - H x in double-double, H^-1 r by the oracle's PCG"}
 
 
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    n_sample = oracle_n_sample(args)
-    P = WL.make_problem(n_sample, args.d, args.sigma_max, seed=1)
+    P = make_inputs(args, seed=1)
+    A64 = _as_f64(P["A"])
     times = []
     for _ in range(args.warmup):
-        oracle_estimate(args, n_sample, P)
+        oracle_estimate(args, P, A64, sketch_rows=8)
     sample, cores = "", 0
     for _ in range(args.steps):
-        ms, sample, cores = oracle_estimate(args, n_sample, P)
+        ms, sample, cores = oracle_estimate(args, P, A64, sketch_rows=8)
         times.append(ms)
     value = statistics.median(times)
     line = {
@@ -245,41 +350,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(args, parallelism):
-    n = 1 << args.n_log2
-    return {"workload": f"{'fp64' if args.a_dtype == 'f64' else 'fp32'}_{n}x{args.d}_{args.sketch}{args.m}_pcg",
-            "n": n, "d": args.d, "sigma_max": args.sigma_max, "sketch": args.sketch, "m": args.m,
-            "sketch_precision": args.sketch_precision, "precision": args.precision, "method": "pcg",
-            "tol": args.tol, "A_dtype": args.a_dtype, "l2": "inputs larger than L2 (A = "
-            f"{n * args.d * (8 if args.a_dtype == 'f64' else 4) / 2**30:.1f} GiB), no flush", "parallelism": parallelism}
-
-
 # ------------------------------------------------------------------------------ our arm
-def run_ours(args):
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _time_calls(torch, dev, stream, fn, reps):
+    out = []
+    for _ in range(reps):
+        e0, e1 = _events(torch)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        out.append((e0.elapsed_time(e1), r))
+    return out
+
+
+def measure_workload(args, rank, world, local, secondary=False):
+    """Times the workload `args` on this rank's GPU; returns the fields of its bench line."""
     import torch
 
-    rank, world, local = dist_info()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     import paper_1911_02675_gb300 as L
 
-    hbm, _, peak_kind = peaks()
+    hbm, bf16_burst, bf16_sust, peak_kind = peaks()
     P = make_inputs(args, seed=1 + rank)
-    if P is None:
-        Pd = WL.make_problem_cuda(1 << args.n_log2, args.d, args.sigma_max, seed=1 + rank, dtype=torch.float32,
-                                  outlier_frac=args.outlier_frac, device=dev)
-        A, b = Pd["A"], Pd["b"]
-        A_host, b_host = None, b.cpu()
-        args.no_e2e = True
-    else:
-        A_host = torch.from_numpy(P["A"])
-        b_host = torch.from_numpy(P["b"])
-        A = A_host.to(dev)
-        b = b_host.to(dev)
+    A_host = torch.from_numpy(P["A"])
+    b_host = torch.from_numpy(P["b"])
+    A = A_host.to(dev)
+    b = b_host.to(dev)
     n, d = A.shape
     ctx = L.Context(dev)
     # the sketch and the factor do not wait for their own work; their errors surface at the solve
@@ -309,16 +410,9 @@ def run_ours(args):
             args.m = m
             for _ in range(max(1, args.warmup)):
                 solve_once(A, b)
-            ms, inf = [], None
-            for _ in range(max(1, args.steps)):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize(dev)
-                e0.record(stream)
-                _, inf = solve_once(A, b)
-                e1.record(stream)
-                torch.cuda.synchronize(dev)
-                ms.append(e0.elapsed_time(e1))
-            total = statistics.median(ms)
+            res = _time_calls(torch, dev, stream, lambda: solve_once(A, b)[1], max(1, args.steps))
+            total = statistics.median(t for t, _ in res)
+            inf = res[-1][1]
             sweep.append({"m": m, "ms": total, "solve_ms": inf["ms_total"], "sketch_factor_ms": total - inf["ms_total"],
                           "iters": inf["iters"], "passes": inf["passes"], "est_err": inf["est_err"],
                           "status": inf["status"]})
@@ -326,18 +420,17 @@ def run_ours(args):
             adv = L.lsq_advise_sketch_size(n, d, args.tol, args.sketch)
         except L.LsqError:
             adv = None
-        if rank == 0:
-            print(json.dumps({"metric": "time-to-1e-10 H-norm error per solve against sketch size", "unit": "ms",
-                              "higher_is_better": False, "sweep": sweep, "advised": adv,
-                              "config": workload_config(args, f"replicas{world}")}), flush=True)
-        return
+        ctx.close()
+        return {"metric": "time-to-1e-10 H-norm error per solve against sketch size", "unit": "ms",
+                "higher_is_better": False, "sweep": sweep, "advised": adv,
+                "config": workload_config(args, f"replicas{world}")}
 
     for _ in range(args.warmup):
         x, info = solve_once(A, b)
     torch.cuda.synchronize(dev)
 
     # device-timed steps (inputs resident), kernel-level split of the solve phase
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [_events(torch) for _ in range(args.steps)]
     infos = []
     launches0 = L.lsq_launch_count()
     if world > 1:
@@ -354,9 +447,8 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b_) for a, b_ in ev]
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_solve = total_ms / (args.steps * world)
+    x_last = x.cpu().numpy()
 
-    # accuracy of the last solve against the oracle-free residual check is in the tests;
-    # here report the solver's own estimate
     solve_ms = statistics.median(i["ms_total"] for i in infos)
     passes = statistics.median(i["passes"] for i in infos)
     exact_passes = statistics.median(i["exact_passes"] for i in infos)
@@ -372,28 +464,68 @@ def run_ours(args):
     else:
         solve_bytes = passes * pass_bytes
     achieved = solve_bytes / (solve_ms * 1e-3) / 1e9
+    traffic = None
+    key = (args.a_dtype, d, a32_copy)
+    if (args.precision == "mixed" and key in SOLVE_TRAFFIC["ratios"]
+            and solve_sources_sha256() == SOLVE_TRAFFIC["sources_sha256"]):
+        traffic = SOLVE_TRAFFIC["ratios"][key] * solve_bytes
 
-    # plain FP64 PCG on the same inputs (FP64 sketch, FP64 passes), the metric's comparison
+    # the sketch phase alone (the tensor-core kernel for the BF16 Gaussian sketch), after the timed steps
+    sk = _time_calls(torch, dev, stream, lambda: L.lsq_sketch(ctx, A, args.sketch, args.m, 0,
+                                                              precision=args.sketch_precision, a32=a32), 3)
+    L.lsq_sync(ctx)
+    sketch_ms = statistics.median(t for t, _ in sk)
+    roofline_sketch = None
+    if args.sketch == "gauss" and args.sketch_precision == "bf16":
+        flops = 2.0 * args.m * n * d
+        roofline_sketch = {"bound": "tensor", "kernel": "gauss_tc_kernel (with pack_kernel and the split sum)",
+                           "achieved": flops / (sketch_ms * 1e-3) / 1e12, "peak": bf16_sust, "unit": "TFLOP/s",
+                           "frac": flops / (sketch_ms * 1e-3) / 1e12 / bf16_sust,
+                           "peak_kind": f"{peak_kind} (sustained bf16)", "algorithmic_flops": flops,
+                           "sketch_ms": sketch_ms}
+    elif args.sketch == "srht":
+        sbytes = n * d * A.element_size() + (n * d * 4 if a32 is not None else 0)
+        roofline_sketch = {"bound": "hbm", "kernel": "srht_tma_kernel (with the row selection and the split sum)",
+                           "achieved": sbytes / (sketch_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": sbytes / (sketch_ms * 1e-3) / 1e9 / hbm, "peak_kind": f"{peak_kind} (burst copy)",
+                           "algorithmic_bytes": sbytes, "sketch_ms": sketch_ms}
+
+    # plain FP64 PCG on the same GPU: the same sketch type in FP64 arithmetic, FP64 factor and FP64
+    # passes over FP64 data (the FP64 upcast of an FP32 A)
     plain = None
     if not args.no_plain and (args.precision != "f64" or args.sketch_precision != "f64"):
-        def plain_once():
-            SA = L.lsq_sketch(ctx, A, args.sketch, args.m, 0, precision="f64")
-            _, Wm = L.lsq_factor(ctx, SA)
-            return L.lsq_solve(ctx, A, b, "pcg", Wm, tol=args.tol, maxit=1000, m=args.m, precision="f64")
+        A64d = A if A.dtype == torch.float64 else A.to(torch.float64)
 
-        plain_once()
-        p_ms, p_info = [], None
-        for _ in range(max(1, args.steps)):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize(dev)
-            e0.record(stream)
-            _, p_info = plain_once()
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            p_ms.append(e0.elapsed_time(e1))
-        pm = statistics.median(p_ms)
-        plain = {"ms": pm, "iters": p_info["iters"], "est_err": p_info["est_err"], "status": p_info["status"],
-                 "speedup": pm / statistics.median(step_ms)}
+        def plain_sketch(kind):
+            return L.lsq_sketch(ctx, A64d, kind, args.m, 0, precision="f64")
+
+        def plain_rest(SA):
+            _, Wm = L.lsq_factor(ctx, SA)
+            return L.lsq_solve(ctx, A64d, b, "pcg", Wm, tol=args.tol, maxit=1000, m=args.m, precision="f64")
+
+        slow_sketch = args.sketch == "gauss" and float(args.m) * n * d > 1e12
+        entries = {}
+        for kind in [args.sketch] + (["srht"] if args.sketch != "srht" else []):
+            # the FP64 SIMT Gaussian sketch of a large A takes about a minute: timed once
+            reps = 1 if (slow_sketch and kind == "gauss") else 3
+            if reps > 1:
+                plain_rest(plain_sketch(kind))  # warm-up (context scratch for the FP64 shapes)
+            s_ms = statistics.median(t for t, _ in _time_calls(torch, dev, stream, lambda: plain_sketch(kind), reps))
+            SA64 = plain_sketch(kind)
+            L.lsq_sync(ctx)
+            plain_rest(SA64)
+            rest = _time_calls(torch, dev, stream, lambda: plain_rest(SA64), 3)
+            r_ms = statistics.median(t for t, _ in rest)
+            inf = rest[-1][1][1]
+            entries[kind] = {"ms": s_ms + r_ms, "sketch_ms": s_ms, "factor_solve_ms": r_ms, "iters": inf["iters"],
+                             "est_err": inf["est_err"], "status": inf["status"], "sketch": f"{kind} f64",
+                             "sketch_reps": reps, "speedup": (s_ms + r_ms) / statistics.median(step_ms)}
+        plain = dict(entries[args.sketch])
+        if args.sketch != "srht":
+            plain["srht_f64"] = entries["srht"]
+        if A64d is not A:
+            del A64d
+        torch.cuda.empty_cache()
 
     # end to end: pinned host A and b -> device, solve, x -> host, every step
     e2e = None
@@ -403,53 +535,73 @@ def run_ours(args):
         x_pin = torch.empty(d, dtype=torch.float64).pin_memory()
         A_dev2 = torch.empty_like(A)
         b_dev2 = torch.empty_like(b)
-        e_ms = []
-        for k in range(max(1, min(args.steps, 3))):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize(dev)
-            e0.record(stream)
+
+        def e2e_once():
             b_dev2.copy_(b_pin, non_blocking=True)
             xx, _ = solve_once(A_dev2, b_dev2, A_from=A_pin)
             x_pin.copy_(xx, non_blocking=True)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            e_ms.append(e0.elapsed_time(e1))
-        del A_dev2
-        e2e = {"value": statistics.median(e_ms), "unit": "ms", "h2d_bytes_per_step": n * d * 8 + d * 8,
-               "d2h_bytes_per_step": d * 8}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and args.a_dtype == "f64":
-        ms, sample, cores = oracle_estimate(args, oracle_n_sample(args), P)
+        e2e_once()  # warm-up
+        e_ms = [t for t, _ in _time_calls(torch, dev, stream, e2e_once, max(1, min(args.steps, 3)))]
+        del A_dev2, A_pin
+        e2e = {"value": statistics.median(e_ms), "unit": "ms",
+               "h2d_bytes_per_step": n * d * A.element_size() + d * 8, "d2h_bytes_per_step": d * 8,
+               "path": "lsq_upload_sketch (host A copied into HBM inside the call), factor, solve, x to host"}
+
+    cpu, accuracy = None, None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        A64 = _as_f64(P["A"])
+        ms, sample, cores = oracle_estimate(args, P, A64)
         cpu = {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
+        accuracy = oracle_accuracy(A64, P["b"], x_last)
+        accuracy["tol"] = args.tol
+        accuracy["met"] = bool(accuracy["rel_h_err_vs_oracle"] <= args.tol)
+        del A64
 
-    traffic = None
-    if (args.precision == "mixed" and args.a_dtype == "f64" and d == 512 and a32_copy
-            and solve_sources_sha256() == SOLVE_TRAFFIC["sources_sha256"]):
-        traffic = SOLVE_TRAFFIC["ratio_solve" if a32_copy == 2 else "ratio_with_copy"] * solve_bytes
-
-    if rank == 0:
-        clocks = clk.summary()
-        line = {
-            "metric": "time-to-1e-10 H-norm error per solve", "value": ms_per_solve, "unit": "ms",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "f64" else "f32+f64",
-            "data": "synthetic (seeded; A = G diag(sigma), replicas on distinct seeds)",
-            "config": workload_config(args, f"replicas{world}"),
-            "phases": {"solve_ms": solve_ms, "iters": iters, "passes": passes, "exact_passes": exact_passes,
-                       "a32_copy": a32_copy,
-                       "sketch_factor_ms": statistics.median(step_ms) - solve_ms,
-                       "status": infos[-1]["status"], "est_err": infos[-1]["est_err"]},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": SOLVE_KERNEL, "peak_kind": f"{peak_kind} (burst copy)",
-                         "algorithmic_bytes_per_launch": solve_bytes},
-            "plain_fp64_pcg": plain,
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-        }
-        print(json.dumps(line), flush=True)
+    out = {
+        "metric": "time-to-1e-10 H-norm error per solve", "value": ms_per_solve, "unit": "ms",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "f64" else ("bf16+f32+f64" if args.sketch_precision == "bf16" else "f32+f64"),
+        "data": "synthetic (seeded; A = G diag(sigma), replicas on distinct seeds)",
+        "config": workload_config(args, f"replicas{world}"),
+        "phases": {"solve_ms": solve_ms, "iters": iters, "passes": passes, "exact_passes": exact_passes,
+                   "a32_copy": a32_copy, "sketch_factor_ms": statistics.median(step_ms) - solve_ms,
+                   "sketch_ms": sketch_ms, "status": infos[-1]["status"], "est_err": infos[-1]["est_err"]},
+        "accuracy": accuracy,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "kernel": SOLVE_KERNEL, "peak_kind": f"{peak_kind} (burst copy)",
+                     "algorithmic_bytes_per_launch": solve_bytes},
+        "roofline_sketch": roofline_sketch,
+        "plain_fp64_pcg": plain,
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": launches,
+    }
     ctx.close()
+    del A
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    line = measure_workload(args, rank, world, local)
+    if not args.m_sweep and not args.no_secondary and args.workload in SECONDARY and world == 1 and \
+            all(getattr(args, k) == v for k, v in PRESETS[args.workload].items()):
+        sec = preset_args(args, SECONDARY[args.workload], steps=min(args.steps, 10))
+        s = measure_workload(sec, rank, world, local, secondary=True)
+        line["secondary"] = {s["config"]["workload"]: {k: s[k] for k in (
+            "value", "unit", "steps", "phases", "accuracy", "roofline", "roofline_sketch", "plain_fp64_pcg",
+            "cpu_baseline", "e2e", "clocks", "gpu_launches", "config")}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -514,7 +666,7 @@ def run_batch(args):
     dev = torch.device("cuda", local)
     import paper_1911_02675_gb300 as L
 
-    hbm, _, peak_kind = peaks()
+    hbm, _, _, peak_kind = peaks()
     shapes = WL.batch_shapes(args.batch, seed=args.batch_seed + rank)
     probs = WL.make_batch_cuda(shapes, seed=args.batch_seed + rank, device=dev)
     a_bytes = [n * d * 4 for n, d, _ in shapes]
@@ -534,7 +686,7 @@ def run_batch(args):
     infos, step_ms, pers = [], [], []
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0, e1 = _events(torch)
             e0.record(stream)
             X, per, info = solve_once()
             e1.record(stream)

@@ -178,9 +178,12 @@ LSQ_API lsq_status lsq_sketch(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
  * 2048-row blocks; 16-byte aligned rows; FP32 arithmetic): the rows are copied per row-block group on an internal stream, which first
  * waits for the work already queued on the context stream, and each group's transform starts
  * on the context stream as soon as its rows have landed (the SRHT sums per-group partials, so
- * the result is that of lsq_sketch).  Any other case copies the whole matrix on the context
- * stream, then sketches.  The context stream waits for every copy, so later calls see all of
- * A.  LSQ_ERR_ARG for a NULL ctx, host_A or A, or host_ld < d. */
+ * the result is that of lsq_sketch).  The tensor-core Gaussian sketch (LSQ_SKETCH_BF16) works
+ * the same way on its row chunks (up to 1 GiB of BF16 A each): chunk k + 1 is copied while
+ * chunk k is packed and multiplied.  Any other case copies the whole matrix on the context
+ * stream, then sketches.  The context stream waits for every copy, also when the call returns
+ * an error, so later calls see all of A.  LSQ_ERR_ARG for a NULL ctx, host_A or A, or
+ * host_ld < d. */
 LSQ_API lsq_status lsq_upload_sketch(lsq_ctx* ctx, const void* host_A, int64_t host_ld, const lsq_matrix* A,
                                      int32_t type, int64_t m, uint64_t seed, const lsq_sketch_opts* opts, double* SA);
 
@@ -407,6 +410,20 @@ LSQ_API void lsq_batch_opts_default(lsq_batch_opts* opts);
  * LSQ_ERR_TIMEOUT, LSQ_ERR_ARG or LSQ_ERR_CUDA. Synchronises before returning. */
 LSQ_API lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem* probs, double tol, int32_t maxit,
                                      const lsq_batch_opts* opts, lsq_batch_info* info);
+
+/* ---------------------------------------------------------------------------------
+ * lsq_selftest_wait: a check of the library's failure detection, with no counterpart in the
+ * paper.  Every cooperative kernel synchronises its CTAs with bounded grid barriers: a CTA
+ * that waits longer than the limit gives up, records LSQ_ERR_TIMEOUT and returns, so a kernel
+ * never spins forever and the context stays usable.  This call runs one cooperative launch
+ * (one CTA per SM) of such a barrier -- kind 0: the arrival-count barrier of the solve
+ * kernels, kind 1: the generation barrier of the factor kernels -- that waits for `missing`
+ * arrivals more than the grid has (0 <= missing <= 1024).  missing = 0 returns LSQ_OK;
+ * missing > 0 can never complete and returns LSQ_ERR_TIMEOUT once each waiter has given up
+ * after wait_ns nanoseconds of %globaltimer (<= 0: the library's own 4 s limit; at most 4 s).
+ * Waits for its own work.  LSQ_ERR_ARG for a NULL ctx or a bad kind, missing or wait_ns.
+ * --------------------------------------------------------------------------------- */
+LSQ_API lsq_status lsq_selftest_wait(lsq_ctx* ctx, int32_t kind, int32_t missing, int64_t wait_ns);
 
 /* Human-readable name of a status code (static storage). */
 LSQ_API const char* lsq_status_str(int32_t status);

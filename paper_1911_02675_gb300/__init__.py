@@ -38,7 +38,7 @@ DTYPE = {torch.float64: 0, torch.float32: 1}
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_set_deferred_checks", "lsq_sync", "lsq_sketch", "lsq_upload_sketch", "lsq_factor", "lsq_factor_ex", "lsq_solve",
            "lsq_solve_opts_default", "lsq_hmatvec", "lsq_status_str", "lsq_version", "lsq_launch_count",
            "lsq_hmatvec_noalloc", "lsq_grad_a", "lsq_advise_sketch_size", "lsq_batch_opts_default",
-           "lsq_solve_batched")
+           "lsq_solve_batched", "lsq_selftest_wait")
 
 
 class LsqError(RuntimeError):
@@ -133,6 +133,8 @@ def _load():
     L.lsq_solve_batched.argtypes = [P, i32, ctypes.POINTER(LsqProblem), dbl, i32, ctypes.POINTER(LsqBatchOpts),
                                     ctypes.POINTER(LsqBatchInfo)]
     L.lsq_solve_batched.restype = ctypes.c_int
+    L.lsq_selftest_wait.argtypes = [P, i32, i32, i64]
+    L.lsq_selftest_wait.restype = ctypes.c_int
     L.lsq_status_str.argtypes = [i32]
     L.lsq_status_str.restype = ctypes.c_char_p
     L.lsq_version.restype = ctypes.c_char_p
@@ -443,6 +445,13 @@ def lsq_solve_batched(ctx: Context, problems, tol: float = 1e-10, maxit: int = 1
         raise LsqError(st, "lsq_solve_batched")
     per = [(arr[p].iters, arr[p].status) for p in range(n)]
     return Xs, per, info.as_dict()
+
+
+def lsq_selftest_wait(ctx: Context, kind: int = 0, missing: int = 1, wait_ns: int = 0) -> int:
+    """Runs one bounded grid barrier that waits for `missing` arrivals more than its grid has and
+    returns the status code it ends with (LSQ_ERR_TIMEOUT when missing > 0)."""
+    ctx.sync_stream()
+    return int(_L.lsq_selftest_wait(ctx.handle, int(kind), int(missing), int(wait_ns)))
 
 
 def lsq_advise_sketch_size(n: int, d: int, eps: float, kind: str = "srht") -> dict:

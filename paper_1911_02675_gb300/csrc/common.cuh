@@ -53,6 +53,9 @@ lsq_status lsq_defer_status(lsq_ctx* c, const int* err, int slot);
 lsq_status lsq_pending_enqueue(lsq_ctx* c);
 lsq_status lsq_pending_take(lsq_ctx* c);
 
+// Called by a sketch before it reads rows [r0, r1) of A (lsq_upload_sketch queues their copy).
+typedef lsq_status (*lsq_rows_hook)(void* user, int64_t r0, int64_t r1);
+
 // Number of kernels this library has launched in the process (lsq_launch_count).
 void lsq_count_launch();
 
@@ -155,7 +158,8 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-__device__ __forceinline__ int grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+__device__ __forceinline__ int grid_barrier_bounded(unsigned* bar, unsigned nblocks, int* err, unsigned spin_limit,
+                                                    uint64_t wait_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned gen = ld_acquire_u32(bar + 1);
@@ -170,7 +174,7 @@ __device__ __forceinline__ int grid_barrier(unsigned* bar, unsigned nblocks, int
       unsigned spins = 0;
       while (ld_acquire_u32(bar + 1) == gen) {
         if (*(volatile int*)err != 0) break;  // another CTA already gave up
-        if (++spins > LSQ_SPIN_LIMIT || global_ns() - t0 > LSQ_WAIT_NS) {
+        if (++spins > spin_limit || global_ns() - t0 > wait_ns) {
           atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
           break;
         }
@@ -181,6 +185,10 @@ __device__ __forceinline__ int grid_barrier(unsigned* bar, unsigned nblocks, int
   }
   __syncthreads();
   return *(volatile int*)err;
+}
+
+__device__ __forceinline__ int grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+  return grid_barrier_bounded(bar, nblocks, err, LSQ_SPIN_LIMIT, LSQ_WAIT_NS);
 }
 
 // Grid-wide barrier over an arrival count that only grows within a launch (zeroed before
@@ -196,8 +204,9 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
   return v;
 }
 
-__device__ __forceinline__ int grid_sync_count(unsigned long long* cnt, unsigned long long& target, unsigned nblocks,
-                                               int* err) {
+__device__ __forceinline__ int grid_sync_count_bounded(unsigned long long* cnt, unsigned long long& target,
+                                                       unsigned nblocks, int* err, unsigned spin_limit,
+                                                       uint64_t wait_ns) {
   __syncthreads();
   target += nblocks;
   if (threadIdx.x == 0) {
@@ -206,7 +215,7 @@ __device__ __forceinline__ int grid_sync_count(unsigned long long* cnt, unsigned
     unsigned spins = 0;
     while (ld_acquire_u64(cnt) < target) {
       if (*(volatile int*)err != 0) break;  // another CTA already gave up
-      if (++spins > LSQ_SPIN_LIMIT || global_ns() - t0 > LSQ_WAIT_NS) {
+      if (++spins > spin_limit || global_ns() - t0 > wait_ns) {
         atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
         break;
       }
@@ -215,6 +224,11 @@ __device__ __forceinline__ int grid_sync_count(unsigned long long* cnt, unsigned
   }
   __syncthreads();
   return *(volatile int*)err;
+}
+
+__device__ __forceinline__ int grid_sync_count(unsigned long long* cnt, unsigned long long& target, unsigned nblocks,
+                                               int* err) {
+  return grid_sync_count_bounded(cnt, target, nblocks, err, LSQ_SPIN_LIMIT, LSQ_WAIT_NS);
 }
 
 static inline int lsq_ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

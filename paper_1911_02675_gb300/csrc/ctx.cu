@@ -144,6 +144,45 @@ extern "C" const char* lsq_status_str(int32_t s) {
   }
 }
 
+// ---------------------------------------------------------------------------------
+// lsq_selftest_wait: one cooperative launch of the grid barriers every cooperative kernel of
+// the library uses, waiting for `missing` arrivals more than the grid has.  With missing > 0
+// no CTA can pass, so each waiter gives up at the limit and the launch ends with
+// LSQ_ERR_TIMEOUT, the path every bounded wait takes.
+// ---------------------------------------------------------------------------------
+namespace {
+__global__ void selftest_wait_kernel(int kind, unsigned missing, uint64_t wait_ns, void* bar, int* err) {
+  const unsigned nblocks = gridDim.x + missing;
+  if (kind == 0) {
+    unsigned long long target = 0;
+    grid_sync_count_bounded(static_cast<unsigned long long*>(bar), target, nblocks, err, LSQ_SPIN_LIMIT, wait_ns);
+  } else {
+    grid_barrier_bounded(static_cast<unsigned*>(bar), nblocks, err, LSQ_SPIN_LIMIT, wait_ns);
+  }
+}
+}  // namespace
+
+extern "C" lsq_status lsq_selftest_wait(lsq_ctx* c, int32_t kind, int32_t missing, int64_t wait_ns) {
+  if (!c || (kind != 0 && kind != 1) || missing < 0 || missing > 1024) return LSQ_ERR_ARG;
+  const uint64_t limit = wait_ns > 0 ? (uint64_t)wait_ns : LSQ_WAIT_NS;
+  if (limit > LSQ_WAIT_NS) return LSQ_ERR_ARG;
+  lsq_status st = lsq_ensure_scratch(c, 256);
+  if (st != LSQ_OK) return st;
+  int* err = reinterpret_cast<int*>(c->scratch);
+  void* bar = reinterpret_cast<char*>(c->scratch) + 64;
+  LSQ_CUDA_TRY(cudaMemsetAsync(c->scratch, 0, 128, c->stream));
+  int k = kind;
+  unsigned miss = (unsigned)missing;
+  uint64_t ns = limit;
+  void* args[] = {&k, &miss, &ns, &bar, &err};
+  LSQ_CUDA_TRY(cudaLaunchCooperativeKernel((void*)selftest_wait_kernel, dim3(c->sm_count), dim3(128), args, 0,
+                                           c->stream));
+  lsq_count_launch();
+  LSQ_CUDA_TRY(cudaMemcpyAsync(c->host_status + 15, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  LSQ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return (lsq_status)c->host_status[15];
+}
+
 static std::atomic<unsigned long long> g_launches{0};
 
 void lsq_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }

@@ -558,8 +558,12 @@ int pick_splits(int tiles, int sms, int64_t kb_total, int64_t cap) {
 
 }  // namespace
 
-// BF16 tensor-core Gaussian sketch into SA (FP64, m x d); called by lsq_sketch
-lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA) {
+// BF16 tensor-core Gaussian sketch into SA (FP64, m x d); called by lsq_sketch.  `rows_ready`
+// (may be null) is called with each chunk's row range [r0, r1) before the chunk is read, in row
+// order, so that a caller can queue the upload of those rows and make the context stream wait
+// for them (lsq_upload_sketch): the copy of chunk k + 1 then overlaps the work on chunk k.
+lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
+                            lsq_rows_hook rows_ready, void* hook_user) {
   const int d = (int)A->d;
   const int nt = d > 256 ? 512 : 256;
   const int nct = (d + nt - 1) / nt;
@@ -585,6 +589,10 @@ lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t s
   for (int64_t kb0 = 0; kb0 < kb_total; kb0 += kb_chunk) {
     const int64_t nkb = std::min(kb_chunk, kb_total - kb0);
     const int64_t row0 = kb0 * TC_KS;
+    if (rows_ready) {
+      st = rows_ready(hook_user, row0, std::min<int64_t>(A->n, row0 + nkb * TC_KS));
+      if (st != LSQ_OK) return st;
+    }
     const int64_t units = nkb * 8 * (int64_t)nt * nct;
     const int pgrid = (int)std::min<int64_t>((units + 255) / 256, 16 * (int64_t)ctx->sm_count);
     if (A->dtype == LSQ_F64)

@@ -1439,7 +1439,41 @@ static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint
 
 }  // namespace
 
-lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA);
+lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
+                            lsq_rows_hook rows_ready, void* hook_user);
+
+// lsq_upload_sketch of the tensor-core Gaussian sketch: each chunk's rows go up on the copy stream
+// (which first waits for the work already queued on the context stream, since it may still read
+// A's buffer), and the context stream waits for them before the chunk is packed
+struct ChunkUpload {
+  lsq_ctx* ctx;
+  const SketchUpload* up;
+  const lsq_matrix* A;
+  bool started;
+};
+
+static lsq_status chunk_upload(void* user, int64_t r0, int64_t r1) {
+  ChunkUpload* cu = static_cast<ChunkUpload*>(user);
+  lsq_ctx* ctx = cu->ctx;
+  if (!cu->started) {
+    lsq_status st = ensure_copy_stream(ctx);
+    if (st != LSQ_OK) return st;
+    LSQ_CUDA_TRY(cudaEventRecord(ctx->ev_copy, ctx->stream));
+    LSQ_CUDA_TRY(cudaStreamWaitEvent(ctx->copy, ctx->ev_copy, 0));
+    cu->started = true;
+  }
+  lsq_status st = upload_rows(cu->up, cu->A, r0, r1, ctx->copy);
+  if (st != LSQ_OK) return st;
+  LSQ_CUDA_TRY(cudaEventRecord(ctx->ev_copy, ctx->copy));
+  LSQ_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_copy, 0));
+  return LSQ_OK;
+}
+
+// the context stream waits for every copy queued on the copy stream, whatever path returned
+static void join_copies(lsq_ctx* ctx) {
+  if (!ctx->copy || !ctx->ev_copy) return;
+  if (cudaEventRecord(ctx->ev_copy, ctx->copy) == cudaSuccess) cudaStreamWaitEvent(ctx->stream, ctx->ev_copy, 0);
+}
 
 static lsq_status sketch_impl(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, int64_t m, uint64_t seed,
                               const lsq_sketch_opts* opts, double* SA, const SketchUpload* up) {
@@ -1459,13 +1493,18 @@ static lsq_status sketch_impl(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
   bool a32_done = false;
   if (type != LSQ_SKETCH_GAUSS && type != LSQ_SKETCH_SRHT && type != LSQ_SKETCH_SJLT) return LSQ_ERR_ARG;
   if (type == LSQ_SKETCH_SJLT && (s < 1 || s > 32 || s > m)) return LSQ_ERR_ARG;
-  if (up && type != LSQ_SKETCH_SRHT) {  // only the SRHT consumes the rows as they land
+  // the SRHT and the tensor-core Gaussian sketch consume the rows as they land; the other
+  // sketches take the whole matrix first, in stream order
+  const bool chunked_gauss = type == LSQ_SKETCH_GAUSS && prec == LSQ_SKETCH_BF16;
+  if (up && type != LSQ_SKETCH_SRHT && !chunked_gauss) {
     st = upload_rows(up, A, 0, A->n, ctx->stream);
     if (st != LSQ_OK) return st;
   }
+  ChunkUpload cu{ctx, up, A, false};
   switch (type) {
     case LSQ_SKETCH_GAUSS:
-      if (prec == LSQ_SKETCH_BF16) st = lsq_gauss_tc_run(ctx, A, (int)m, seed, t, SA);
+      if (prec == LSQ_SKETCH_BF16)
+        st = lsq_gauss_tc_run(ctx, A, (int)m, seed, t, SA, up ? chunk_upload : nullptr, up ? &cu : nullptr);
       else st = f64 ? gauss_run<double>(ctx, A, (int)m, seed, t, SA) : gauss_run<float>(ctx, A, (int)m, seed, t, SA);
       break;
     case LSQ_SKETCH_SRHT:
@@ -1480,6 +1519,8 @@ static lsq_status sketch_impl(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
     default:
       return LSQ_ERR_ARG;
   }
+  // later work on the context stream sees all of A, also after an early error return
+  if (up) join_copies(ctx);
   // the FP32 copy, where the sketch did not write it on the way
   if (st == LSQ_OK && a32 && !a32_done) st = lsq_narrow_copy(ctx, A, a32, ld32);
   return st;

@@ -191,17 +191,22 @@ def test_sketch_writes_fp32_copy(L, ctx, kind, precision, n, d):
     (1500, 24, 64, np.float64, "srht", False),             # one zero-padded block, pageable host memory
     (900, 24, 64, np.float64, "srht", True),               # padded length under 2048: whole copy
     (5000, 33, 128, np.float64, "gauss", True),            # other sketches: whole copy, then sketch
+    (600001, 1024, 4096, np.float32, "gauss-bf16", True),  # tensor-core Gaussian: 2 chunks, ragged tail
+    (2**21 + 333, 40, 256, np.float32, "gauss-bf16", True),  # narrow d: 2 chunks of 2^21 rows
+    (3000, 24, 64, np.float64, "gauss-bf16", False),       # one chunk, pageable host memory
 ])
 def test_upload_sketch_matches_sketch_of_device_copy(L, ctx, n, d, m, dtype, kind, pinned):
-    """lsq_upload_sketch copies A while the SRHT transforms the row groups that have landed: A on
-    the device, SA and the FP32 copy equal those of lsq_sketch on A already resident."""
+    """lsq_upload_sketch copies A while the SRHT transforms the row groups that have landed (the
+    tensor-core Gaussian sketch: the chunks that have landed): A on the device, SA and the FP32
+    copy equal those of lsq_sketch on A already resident."""
     rng = np.random.default_rng(n + d)
     A = rng.standard_normal((n, d)).astype(dtype) * np.logspace(0, 3, d).astype(dtype)
     A_host = torch.from_numpy(A)
     if pinned:
         A_host = A_host.pin_memory()
     Ad = torch.empty(A_host.shape, dtype=A_host.dtype, device="cuda")
-    prec = "f32" if kind == "srht" else "f64"
+    prec = {"srht": "f32", "gauss-bf16": "bf16"}.get(kind, "f64")
+    kind = kind.split("-")[0]
     a32 = L.narrow_buffer(Ad) if dtype == np.float64 else None
     SA_up = L.lsq_upload_sketch(ctx, A_host, Ad, kind, m, 5, precision=prec, a32=a32)
     a32_up = a32.clone() if a32 is not None else None
