@@ -140,6 +140,15 @@ typedef struct {
                         other sketches add one pass.  NULL (zero-initialised opts) = none. */
   int64_t ld32;      /* row stride of a32 in elements: >= d and a multiple of 4; a32 16-byte
                         aligned (else LSQ_ERR_ARG) */
+  int64_t row0;      /* A holds rows [row0, row0 + n) of a larger matrix of n_total rows (a row
+                        slab, as on one of several GPUs): SA is then that slab's share
+                        S[:, row0 : row0 + n] A of the whole matrix's sketch, with the same S
+                        (Philox counters take the global row index; the SRHT's signs, sampled
+                        rows and zero padding are the whole matrix's), so that the shares of
+                        the slabs sum to the sketch of the whole matrix (Section 2's S A is a sum
+                        over the rows of A).  SRHT: row0 a multiple of 2048.  Default 0. */
+  int64_t n_total;   /* rows of the whole matrix; <= 0 (default): n.  row0 + n <= n_total < 2^31
+                        (else LSQ_ERR_ARG). */
 } lsq_sketch_opts;
 
 /* ---------------------------------------------------------------------------------
@@ -410,6 +419,32 @@ LSQ_API void lsq_batch_opts_default(lsq_batch_opts* opts);
  * LSQ_ERR_TIMEOUT, LSQ_ERR_ARG or LSQ_ERR_CUDA. Synchronises before returning. */
 LSQ_API lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem* probs, double tol, int32_t maxit,
                                      const lsq_batch_opts* opts, lsq_batch_info* info);
+
+/* ---------------------------------------------------------------------------------
+ * lsq_pcg_tail: the part of one PCG iteration (Section 1, eq. (PCG)) that follows the pass over
+ * A, as a call of its own, for solves whose rows of A are split across GPUs.  H p is a sum over
+ * the rows of A, so with A in row slabs A_k (one per GPU, lsq_sketch's row0 / n_total give the
+ * matching sketch shares) each GPU computes v_k = A_k^T (A_k p) and q_k = ||A_k p||^2 with
+ * lsq_hmatvec, the d + 1 numbers are summed across the GPUs (one all-reduce per iteration), and
+ * every GPU calls lsq_pcg_tail on the same sums, so all of them keep the same iterate.
+ *   d      : 1..1024.
+ *   W      : device, d x d FP64, W = R^{-1} from lsq_factor of the (summed) sketch.
+ *   b      : device, d FP64.
+ *   vq     : device, d + 1 FP64: phase 0: H x0 in vq[0..d) (zeros for x0 = 0; vq[d] unused);
+ *            phase 1: H p in vq[0..d) and p^T H p in vq[d], p the state's current direction.
+ *   phase  : 0 starts (r = b - H x0, z = W W^T r, p = z), 1 takes one step
+ *            (alpha = r^T z / p^T H p, x += alpha p, r -= alpha H p, z = W W^T r,
+ *            beta = r^T z / previous r^T z, p = z + beta p).
+ *   tol, rho : the stopping rule of lsq_solve, (1 + sqrt(rho))^2 r^T z <= tol^2 <b, x>.
+ *   state  : device, 4 d + 8 FP64, caller-owned: x (holding x0 before phase 0), r, z, p, then
+ *            r^T z, <b, x>, alpha, beta, flag (0 running, 1 converged, 2 failed), status, iterations.
+ *            Once the flag is nonzero, phase 1 leaves the state unchanged.
+ *   flag_out : NULL, or host int that receives the flag (the call then waits for its work).
+ * Status LSQ_ERR_BREAKDOWN (with flag_out) when p^T H p <= 0 or a value is not finite;
+ * LSQ_ERR_ARG for bad sizes, phase, tol or rho outside (0, 1).  FP64 throughout.
+ * --------------------------------------------------------------------------------- */
+LSQ_API lsq_status lsq_pcg_tail(lsq_ctx* ctx, int64_t d, const double* W, const double* b, const double* vq,
+                                int32_t phase, double tol, double rho, double* state, int32_t* flag_out);
 
 /* ---------------------------------------------------------------------------------
  * lsq_selftest_wait: a check of the library's failure detection, with no counterpart in the

@@ -38,7 +38,7 @@ DTYPE = {torch.float64: 0, torch.float32: 1}
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_set_deferred_checks", "lsq_sync", "lsq_sketch", "lsq_upload_sketch", "lsq_factor", "lsq_factor_ex", "lsq_solve",
            "lsq_solve_opts_default", "lsq_hmatvec", "lsq_status_str", "lsq_version", "lsq_launch_count",
            "lsq_hmatvec_noalloc", "lsq_grad_a", "lsq_advise_sketch_size", "lsq_batch_opts_default",
-           "lsq_solve_batched", "lsq_selftest_wait")
+           "lsq_solve_batched", "lsq_selftest_wait", "lsq_pcg_tail")
 
 
 class LsqError(RuntimeError):
@@ -54,7 +54,7 @@ class LsqMatrix(ctypes.Structure):
 
 class LsqSketchOpts(ctypes.Structure):
     _fields_ = [("t", ctypes.c_uint32), ("s", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("a32", ctypes.c_void_p), ("ld32", ctypes.c_int64)]
+                ("a32", ctypes.c_void_p), ("ld32", ctypes.c_int64), ("row0", ctypes.c_int64), ("n_total", ctypes.c_int64)]
 
 
 class LsqSolveOpts(ctypes.Structure):
@@ -133,6 +133,8 @@ def _load():
     L.lsq_solve_batched.argtypes = [P, i32, ctypes.POINTER(LsqProblem), dbl, i32, ctypes.POINTER(LsqBatchOpts),
                                     ctypes.POINTER(LsqBatchInfo)]
     L.lsq_solve_batched.restype = ctypes.c_int
+    L.lsq_pcg_tail.argtypes = [P, i64, P, P, P, i32, dbl, dbl, P, ctypes.POINTER(i32)]
+    L.lsq_pcg_tail.restype = ctypes.c_int
     L.lsq_selftest_wait.argtypes = [P, i32, i32, i64]
     L.lsq_selftest_wait.restype = ctypes.c_int
     L.lsq_status_str.argtypes = [i32]
@@ -237,13 +239,15 @@ def narrow_buffer(A: torch.Tensor) -> torch.Tensor:
 
 
 def lsq_sketch(ctx: Context, A: torch.Tensor, kind: str, m: int, seed: int, t: int = 0, s: int = 8,
-               precision: str = "f64", out: torch.Tensor | None = None, a32: torch.Tensor | None = None) -> torch.Tensor:
+               precision: str = "f64", out: torch.Tensor | None = None, a32: torch.Tensor | None = None,
+               row0: int = 0, n_total: int = 0) -> torch.Tensor:
     """SA (m x d FP64).  With `a32` (FP64 A), also writes the FP32 narrowing of A into it for a later
-    mixed lsq_solve(..., a32=a32)."""
+    mixed lsq_solve(..., a32=a32).  With row0 / n_total, A is the row slab [row0, row0 + n) of a
+    matrix of n_total rows and SA its share of that matrix's sketch."""
     ctx.sync_stream()
     M = as_matrix(A)
     SA = out if out is not None else torch.empty((m, A.shape[1]), dtype=torch.float64, device=A.device)
-    opts = LsqSketchOpts(t, s, SKETCH_PRECISION[precision], None, 0)
+    opts = LsqSketchOpts(t, s, SKETCH_PRECISION[precision], None, 0, int(row0), int(n_total))
     if a32 is not None:
         _check_a32(A, a32)
         opts.a32, opts.ld32 = a32.data_ptr(), a32.stride(0)
@@ -264,7 +268,7 @@ def lsq_upload_sketch(ctx: Context, A_host: torch.Tensor, A: torch.Tensor, kind:
         raise ValueError("A_host must be a CPU matrix of A's shape and dtype with unit column stride")
     M = as_matrix(A)
     SA = out if out is not None else torch.empty((m, A.shape[1]), dtype=torch.float64, device=A.device)
-    opts = LsqSketchOpts(t, s, SKETCH_PRECISION[precision], None, 0)
+    opts = LsqSketchOpts(t, s, SKETCH_PRECISION[precision], None, 0, 0, 0)
     if a32 is not None:
         _check_a32(A, a32)
         opts.a32, opts.ld32 = a32.data_ptr(), a32.stride(0)
@@ -445,6 +449,22 @@ def lsq_solve_batched(ctx: Context, problems, tol: float = 1e-10, maxit: int = 1
         raise LsqError(st, "lsq_solve_batched")
     per = [(arr[p].iters, arr[p].status) for p in range(n)]
     return Xs, per, info.as_dict()
+
+
+def lsq_pcg_tail(ctx: Context, W: torch.Tensor, b: torch.Tensor, vq: torch.Tensor, phase: int, tol: float, rho: float,
+                 state: torch.Tensor, wait: bool = True) -> int:
+    """One PCG tail on the summed pass result vq (d + 1 FP64); returns the state's flag (0 running,
+    1 converged) when `wait`, else -1.  Raises LsqError on breakdown."""
+    ctx.sync_stream()
+    d = b.numel()
+    if vq.numel() != d + 1 or state.numel() != 4 * d + 8 or W.shape != (d, d):
+        raise ValueError("vq must hold d + 1 and state 4 d + 8 FP64 entries, W d x d")
+    flag = ctypes.c_int32(-1)
+    st = _L.lsq_pcg_tail(ctx.handle, d, _ptr(W), _ptr(b), _ptr(vq), int(phase), float(tol), float(rho), _ptr(state),
+                         ctypes.byref(flag) if wait else None)
+    if st:
+        raise LsqError(st, "lsq_pcg_tail")
+    return int(flag.value)
 
 
 def lsq_selftest_wait(ctx: Context, kind: int = 0, missing: int = 1, wait_ns: int = 0) -> int:

@@ -1142,7 +1142,7 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     m_of[p] = (int)m;
     d_of[p] = d;
     if (one_launch) continue;
-    lsq_sketch_opts so;
+    lsq_sketch_opts so = {};
     so.t = (uint32_t)p;
     so.s = (int)std::min<int64_t>(o.s > 0 ? o.s : 8, m);  // an SJLT column has at most m nonzeros
     so.precision = o.sketch_precision;

@@ -290,7 +290,7 @@ lsq_status lsq_fcg_solve(lsq_ctx* ctx, const lsq_matrix* A, const double* b, con
     transpose_into<<<dim3((d + 31) / 32, (d + 31) / 32), dim3(32, 8), 0, s>>>(W_fixed, d, WT);
     LSQ_LAUNCH_CHECK();
   }
-  lsq_sketch_opts so;
+  lsq_sketch_opts so = {};
   so.s = o.s > 0 ? o.s : 8;
   so.precision = mixed ? LSQ_SKETCH_F32 : LSQ_SKETCH_F64;
   so.a32 = nullptr;

@@ -563,7 +563,7 @@ int pick_splits(int tiles, int sms, int64_t kb_total, int64_t cap) {
 // order, so that a caller can queue the upload of those rows and make the context stream wait
 // for them (lsq_upload_sketch): the copy of chunk k + 1 then overlaps the work on chunk k.
 lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
-                            lsq_rows_hook rows_ready, void* hook_user) {
+                            lsq_rows_hook rows_ready, void* hook_user, int64_t grow0) {
   const int d = (int)A->d;
   const int nt = d > 256 ? 512 : 256;
   const int nct = (d + nt - 1) / nt;
@@ -588,7 +588,7 @@ lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t s
   const dim3 grid(tiles_m, nct, splits);
   for (int64_t kb0 = 0; kb0 < kb_total; kb0 += kb_chunk) {
     const int64_t nkb = std::min(kb_chunk, kb_total - kb0);
-    const int64_t row0 = kb0 * TC_KS;
+    const int64_t row0 = kb0 * TC_KS;  // of A; grow0 + row0 in the whole matrix (the generator's index)
     if (rows_ready) {
       st = rows_ready(hook_user, row0, std::min<int64_t>(A->n, row0 + nkb * TC_KS));
       if (st != LSQ_OK) return st;
@@ -605,11 +605,11 @@ lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t s
     const int acc = kb0 > 0 ? 1 : 0;
     // a CTA pair shares S when d needs two 512-column tiles (nt = 256 only for d <= 256)
     if (nt == 512 && nct % 2 == 0)
-      st = launch_tc<512, 2, 2>(ctx, grid, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, acc, part, err);
+      st = launch_tc<512, 2, 2>(ctx, grid, pk, nkb, nct, d, m, seed, t, grow0 + row0, kb_per_split, acc, part, err);
     else if (nt == 512)
-      st = launch_tc<512, 2, 1>(ctx, grid, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, acc, part, err);
+      st = launch_tc<512, 2, 1>(ctx, grid, pk, nkb, nct, d, m, seed, t, grow0 + row0, kb_per_split, acc, part, err);
     else
-      st = launch_tc<256, 4, 1>(ctx, grid, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, acc, part, err);
+      st = launch_tc<256, 4, 1>(ctx, grid, pk, nkb, nct, d, m, seed, t, grow0 + row0, kb_per_split, acc, part, err);
     if (st != LSQ_OK) return st;
   }
   const int64_t md = (int64_t)m * d;

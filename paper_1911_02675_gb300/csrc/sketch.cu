@@ -97,7 +97,8 @@ constexpr int GM = 64, GD = 64, GK = 16;
 template <typename T>
 __global__ void __launch_bounds__(256) gauss_sketch_kernel(const void* __restrict__ A, int dtype, int64_t n, int d,
                                                           int64_t ld, int m, uint64_t seed, uint32_t t,
-                                                          int64_t rows_per_split, T* __restrict__ part) {
+                                                          int64_t rows_per_split, T* __restrict__ part,
+                                                          int64_t grow0) {
   __shared__ T Ss[GK][GM];
   __shared__ T As[GK][GD];
   const int j0 = blockIdx.x * GM, c0 = blockIdx.y * GD;
@@ -115,7 +116,8 @@ __global__ void __launch_bounds__(256) gauss_sketch_kernel(const void* __restric
       const int jp = e / GK, k = e % GK;
       const int64_t i = i0 + k;
       T zc = (T)0, zs = (T)0;
-      if (i < i_end) box_muller<T>(philox_at(seed, (uint32_t)i, (uint32_t)((j0 >> 1) + jp), t, TAG_GAUSS), zc, zs);
+      if (i < i_end)
+        box_muller<T>(philox_at(seed, (uint32_t)(i + grow0), (uint32_t)((j0 >> 1) + jp), t, TAG_GAUSS), zc, zs);
       Ss[k][2 * jp] = zc;
       Ss[k][2 * jp + 1] = zs;
     }
@@ -430,7 +432,7 @@ template <typename TC, int DC>
 __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_transform_kernel(
     const void* __restrict__ A, int dtype, int64_t n, int d, int64_t ld, int logN2, int64_t N1,
     int64_t blocks_per_group, const uint32_t* __restrict__ signbits, const int64_t* __restrict__ rows, int m,
-    TC* __restrict__ part) {
+    TC* __restrict__ part, uint32_t blk0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N2 = 1 << logN2;
   TC* Z = reinterpret_cast<TC*>(smem_raw);                   // padded [N2][DC]
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_transform_kernel(
       }
     }
     __syncthreads();
-    const uint32_t i1w = (uint32_t)i1;
+    const uint32_t i1w = (uint32_t)i1 + blk0;  // the block's index in the whole (zero-padded) matrix
     // one sampled row per thread: its k1/k2 and sign once, then the DC columns as 16-byte
     // vectors (a 32-byte row of the block and of the accumulator)
     for (int s = threadIdx.x; s < m; s += blockDim.x) {
@@ -558,7 +560,8 @@ __device__ __forceinline__ void srht_fast_load(TA (&r0)[16], TA (&r1)[16], uint3
 template <typename TA>
 __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_fast_kernel(
     const TA* __restrict__ A, int64_t n, int d, int64_t ld, int64_t N1, int64_t blocks_per_group, int vec_ok,
-    const uint32_t* __restrict__ signbits, const int64_t* __restrict__ rows, int m, float* __restrict__ part) {
+    const uint32_t* __restrict__ signbits, const int64_t* __restrict__ rows, int m, float* __restrict__ part,
+    uint32_t blk0) {
   constexpr int DC = 8, LOGN2 = 11, N2 = 1 << LOGN2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Z = reinterpret_cast<float*>(smem_raw);                        // padded [N2][DC]
@@ -605,7 +608,7 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_fast_kernel(
     __syncthreads();
     radix_pass<float, DC, 3>(Z, N2, 8);
     __syncthreads();
-    const uint32_t i1w = (uint32_t)i1;
+    const uint32_t i1w = (uint32_t)i1 + blk0;  // the block's index in the whole (zero-padded) matrix
     for (int s = threadIdx.x; s < m; s += blockDim.x) {
       const bool neg = (__popc(k1s[s] & i1w) & 1) != 0;
       const float4* zr = reinterpret_cast<const float4*>(Z + zphys(k2s[s], DC));
@@ -664,7 +667,7 @@ template <typename TA, int MY>
 __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
     const __grid_constant__ CUtensorMap tmap, int64_t n, int d, int64_t N1, int64_t blocks_per_group,
     const uint32_t* __restrict__ signbits, const int64_t* __restrict__ rows_all, int m_all,
-    float* __restrict__ part, int* err, float* __restrict__ a32_all, int64_t ld32, int gy0) {
+    float* __restrict__ part, int* err, float* __restrict__ a32_all, int64_t ld32, int gy0, uint32_t blk0) {
   constexpr int DC = 8, LOGN2 = 11, N2 = 1 << LOGN2;
   const int64_t gy = (int64_t)blockIdx.y + gy0;  // row-block group (a launch may cover a range of them)
   // sampled rows [s0, s0 + m) of the m_all: up to 8 per thread, more in further grid.z slices
@@ -798,7 +801,7 @@ __global__ void __launch_bounds__(SRHT_THREADS, 1) srht_tma_kernel(
     __syncthreads();
     radix_pass<float, DC, 4>(Z, N2, 4);
     __syncthreads();
-    const uint32_t i1w = (uint32_t)i1;
+    const uint32_t i1w = (uint32_t)i1 + blk0;  // the block's index in the whole (zero-padded) matrix
     // lanes 4..7 of each quarter-warp read the second half of their row first: rows fall on
     // even or odd 16-byte bank groups by half, so the two orders spread a quarter's reads
     const int hsw = (tid >> 2) & 1;
@@ -867,12 +870,12 @@ __device__ __forceinline__ void sjlt_targets(uint64_t seed, int64_t i, uint32_t 
 }
 
 __global__ void sjlt_hash_kernel(int64_t n, int m, int s, uint64_t seed, uint32_t t, int32_t* __restrict__ h,
-                                 uint32_t* __restrict__ signs) {
+                                 uint32_t* __restrict__ signs, int64_t grow0) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t picked[32];
-    sjlt_targets<32>(seed, i, t, m, s, picked);
+    sjlt_targets<32>(seed, i + grow0, t, m, s, picked);  // column i + grow0 of S
     for (int k = 0; k < s; ++k) h[i * s + k] = picked[k];
-    signs[i] = philox_at(seed, (uint32_t)i, 0u, t, TAG_SJLT_SIGN).x;
+    signs[i] = philox_at(seed, (uint32_t)(i + grow0), 0u, t, TAG_SJLT_SIGN).x;
   }
 }
 
@@ -1070,7 +1073,8 @@ static lsq_status validate_matrix(const lsq_matrix* A) {
 }
 
 template <typename TC>
-static lsq_status gauss_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA) {
+static lsq_status gauss_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
+                            int64_t grow0) {
   const int d = (int)A->d;
   const int gx = lsq_ceil_div(m, GM), gy = lsq_ceil_div(d, GD);
   const int64_t ksteps = (A->n + GK - 1) / GK;
@@ -1084,7 +1088,7 @@ static lsq_status gauss_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t s
   TC* part = reinterpret_cast<TC*>(ctx->scratch);
   dim3 grid(gx, gy, (unsigned)splits);
   gauss_sketch_kernel<TC><<<grid, 256, 0, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, m, seed, t,
-                                                          rows_per_split, part);
+                                                          rows_per_split, part, grow0);
   LSQ_LAUNCH_CHECK();
   const int64_t md = (int64_t)m * d;
   reduce_splits_kernel<TC><<<grid_for(md, 256, 4 * ctx->sm_count), 256, 0, ctx->stream>>>(
@@ -1133,7 +1137,7 @@ static bool srht_tma_usable(const lsq_matrix* A, int m) {
 template <typename TA>
 static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1, const uint32_t* signbits,
                             const int64_t* rows, float* part, int groups, int64_t blocks_per_group, int* err,
-                            float* a32, int64_t ld32, lsq_status* st, int gy0 = 0) {
+                            float* a32, int64_t ld32, lsq_status* st, int gy0, uint32_t blk0) {
   constexpr int DC = 8, N2 = 2048;
   const size_t es = sizeof(TA);
   if (!srht_tma_usable<TA>(A, m)) return false;
@@ -1157,7 +1161,7 @@ static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1
   auto launch = [&](auto kern) -> lsq_status {
     LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, SRHT_THREADS, smem, ctx->stream>>>(tm, A->n, d, N1, blocks_per_group, signbits, rows, m, part, err,
-                                                     a32, ld32, gy0);
+                                                     a32, ld32, gy0, blk0);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
   };
@@ -1172,7 +1176,8 @@ static bool srht_tma_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int64_t N1
 template <typename TC, int DC>
 static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN2, int64_t N1,
                               const uint32_t* signbits, const int64_t* rows, TC* part, int groups,
-                              int64_t blocks_per_group, int* err, float* a32, int64_t ld32, bool& staged) {
+                              int64_t blocks_per_group, int* err, float* a32, int64_t ld32, bool& staged,
+                              uint32_t blk0) {
   const int d = (int)A->d;
   const size_t smem = srht_smem_bytes(logN2, m, DC, sizeof(TC));
   dim3 grid(lsq_ceil_div(d, DC), groups);
@@ -1182,9 +1187,9 @@ static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN
       float* pf = reinterpret_cast<float*>(part);
       staged = A->dtype == LSQ_F64
                    ? srht_tma_launch<double>(ctx, A, m, N1, signbits, rows, pf, groups, blocks_per_group, err, a32,
-                                             ld32, &st)
+                                             ld32, &st, 0, blk0)
                    : srht_tma_launch<float>(ctx, A, m, N1, signbits, rows, pf, groups, blocks_per_group, err, nullptr,
-                                            0, &st);
+                                            0, &st, 0, blk0);
       if (staged) return st;
       const size_t es = A->dtype == LSQ_F64 ? 8 : 4;
       const size_t vb = 2 * es;  // bytes of one column pair
@@ -1194,13 +1199,13 @@ static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN
         LSQ_CUDA_TRY(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kf<<<grid, SRHT_THREADS, smem, ctx->stream>>>(reinterpret_cast<const double*>(A->data), A->n, d, A->ld, N1,
                                                       blocks_per_group, vec_ok, signbits, rows, m,
-                                                      reinterpret_cast<float*>(part));
+                                                      reinterpret_cast<float*>(part), blk0);
       } else {
         auto kf = srht_fast_kernel<float>;
         LSQ_CUDA_TRY(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kf<<<grid, SRHT_THREADS, smem, ctx->stream>>>(reinterpret_cast<const float*>(A->data), A->n, d, A->ld, N1,
                                                       blocks_per_group, vec_ok, signbits, rows, m,
-                                                      reinterpret_cast<float*>(part));
+                                                      reinterpret_cast<float*>(part), blk0);
       }
       LSQ_LAUNCH_CHECK();
       return LSQ_OK;
@@ -1209,7 +1214,7 @@ static lsq_status srht_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int logN
   auto kern = srht_transform_kernel<TC, DC>;
   LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<grid, SRHT_THREADS, smem, ctx->stream>>>(A->data, A->dtype, A->n, d, A->ld, logN2, N1, blocks_per_group,
-                                                   signbits, rows, m, part);
+                                                   signbits, rows, m, part, blk0);
   LSQ_LAUNCH_CHECK();
   return LSQ_OK;
 }
@@ -1243,11 +1248,15 @@ static lsq_status ensure_copy_stream(lsq_ctx* ctx) {
 
 template <typename TC>
 static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
-                           float* a32, int64_t ld32, bool& a32_done, const SketchUpload* up = nullptr) {
+                           float* a32, int64_t ld32, bool& a32_done, const SketchUpload* up, int64_t row0,
+                           int64_t n_total) {
   const int d = (int)A->d;
+  // the Hadamard transform spans the zero-padded rows of the whole matrix (n_total rows, of
+  // which A holds [row0, row0 + n) as whole blocks of 2048 rows); signs and the sampled rows
+  // are those of the whole matrix, and only the blocks that hold rows of A are transformed
   int64_t N = 1;
   int logN = 0;
-  while (N < A->n) { N <<= 1; ++logN; }
+  while (N < n_total) { N <<= 1; ++logN; }
   if (m > N) return LSQ_ERR_ARG;
   // shared memory: padded block + sampled accumulators + sample positions within the
   // 227 KB a CTA may opt into; 32-byte rows (DC * sizeof(TC) = 32) unless m forces narrower
@@ -1265,7 +1274,10 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
     while (logN2 > 0 && !fits(DC, logN2)) --logN2;
     if (!fits(DC, logN2) || logN2 > 16) return LSQ_ERR_ARG;
   }
-  const int64_t N1 = N >> logN2;
+  if (row0 % ((int64_t)1 << logN2) != 0) return LSQ_ERR_ARG;
+  // blocks past the last row of A are all zero and add nothing
+  const int64_t N1 = (A->n + ((int64_t)1 << logN2) - 1) >> logN2;
+  const uint32_t blk0 = (uint32_t)(row0 >> logN2);
   const int tiles = lsq_ceil_div(d, DC);
   // about eight waves of one CTA per SM, so the last partial wave costs little
   int64_t groups = std::max<int64_t>(1, (8 * (int64_t)ctx->sm_count + tiles - 1) / tiles);
@@ -1313,6 +1325,8 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
   select_write_kernel<<<(unsigned)nscan, SCAN_BLOCK, 0, ctx->stream>>>(keys, N, state, cnt_lt, cnt_eq, rows, m);
   LSQ_LAUNCH_CHECK();
 
+  // A's rows start at row0 of the whole matrix (a multiple of 32), and so do their sign bits
+  const uint32_t* sb = signbits + (row0 >> 5);
   bool staged = false;
   bool launched = false;
   if (up) {
@@ -1340,10 +1354,10 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
           LSQ_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_copy, 0));
         }
         lsq_status lst = LSQ_OK;
-        const bool ok = f64a ? srht_tma_launch<double>(ctx, A, m, N1, signbits, rows, pf, 1, blocks_per_group, err, a32,
-                                                       ld32, &lst, (int)g)
-                             : srht_tma_launch<float>(ctx, A, m, N1, signbits, rows, pf, 1, blocks_per_group, err,
-                                                      nullptr, 0, &lst, (int)g);
+        const bool ok = f64a ? srht_tma_launch<double>(ctx, A, m, N1, sb, rows, pf, 1, blocks_per_group, err, a32,
+                                                       ld32, &lst, (int)g, blk0)
+                             : srht_tma_launch<float>(ctx, A, m, N1, sb, rows, pf, 1, blocks_per_group, err,
+                                                      nullptr, 0, &lst, (int)g, blk0);
         if (!ok) return LSQ_ERR_CUDA;  // srht_tma_usable said it would launch
         if (lst != LSQ_OK) return lst;
       }
@@ -1351,14 +1365,14 @@ static lsq_status srht_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t se
     }
   }
   if (!launched) switch (DC) {
-    case 8: st = srht_launch<TC, 8>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, a32,
-                                  ld32, staged); break;
-    case 4: st = srht_launch<TC, 4>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, a32,
-                                  ld32, staged); break;
-    case 2: st = srht_launch<TC, 2>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, a32,
-                                  ld32, staged); break;
-    default: st = srht_launch<TC, 1>(ctx, A, m, logN2, N1, signbits, rows, part, (int)groups, blocks_per_group, err, a32,
-                                  ld32, staged); break;
+    case 8: st = srht_launch<TC, 8>(ctx, A, m, logN2, N1, sb, rows, part, (int)groups, blocks_per_group, err, a32,
+                                  ld32, staged, blk0); break;
+    case 4: st = srht_launch<TC, 4>(ctx, A, m, logN2, N1, sb, rows, part, (int)groups, blocks_per_group, err, a32,
+                                  ld32, staged, blk0); break;
+    case 2: st = srht_launch<TC, 2>(ctx, A, m, logN2, N1, sb, rows, part, (int)groups, blocks_per_group, err, a32,
+                                  ld32, staged, blk0); break;
+    default: st = srht_launch<TC, 1>(ctx, A, m, logN2, N1, sb, rows, part, (int)groups, blocks_per_group, err, a32,
+                                  ld32, staged, blk0); break;
   }
   if (st != LSQ_OK) return st;
   const int64_t md = (int64_t)m * d;
@@ -1399,7 +1413,7 @@ static lsq_status sjlt_launch(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, c
 
 template <typename TC>
 static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint64_t seed, uint32_t t, double* SA,
-                           bool bf16 = false) {
+                           bool bf16, int64_t grow0) {
   const int d = (int)A->d;
   const int64_t n = A->n;
   const size_t budget = 200 * 1024;
@@ -1421,7 +1435,7 @@ static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint
   int32_t* h = cv.take<int32_t>((size_t)n * s);
   uint32_t* signs = cv.take<uint32_t>(n);
   TC* part = cv.take<TC>((size_t)groups * m * d);
-  sjlt_hash_kernel<<<grid_for(n, 256, 16 * ctx->sm_count), 256, 0, ctx->stream>>>(n, m, s, seed, t, h, signs);
+  sjlt_hash_kernel<<<grid_for(n, 256, 16 * ctx->sm_count), 256, 0, ctx->stream>>>(n, m, s, seed, t, h, signs, grow0);
   LSQ_LAUNCH_CHECK();
   switch (DC) {
     case 8: st = sjlt_launch<TC, 8>(ctx, A, m, s, h, signs, part, (int)groups, rows_per_group, bf16); break;
@@ -1440,7 +1454,7 @@ static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint
 }  // namespace
 
 lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
-                            lsq_rows_hook rows_ready, void* hook_user);
+                            lsq_rows_hook rows_ready, void* hook_user, int64_t grow0);
 
 // lsq_upload_sketch of the tensor-core Gaussian sketch: each chunk's rows go up on the copy stream
 // (which first waits for the work already queued on the context stream, since it may still read
@@ -1492,6 +1506,11 @@ static lsq_status sketch_impl(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
   if (a32 && (ld32 < A->d || ld32 % 4 != 0 || ((uintptr_t)a32 % 16) != 0)) return LSQ_ERR_ARG;
   bool a32_done = false;
   if (type != LSQ_SKETCH_GAUSS && type != LSQ_SKETCH_SRHT && type != LSQ_SKETCH_SJLT) return LSQ_ERR_ARG;
+  // A as rows [row0, row0 + n) of a matrix of n_total rows: SA is that slab's share S[:, slab] A
+  const int64_t row0 = opts ? opts->row0 : 0;
+  const int64_t n_total = (opts && opts->n_total > 0) ? opts->n_total : A->n;
+  if (row0 < 0 || row0 + A->n > n_total || n_total >= ((int64_t)1 << 31)) return LSQ_ERR_ARG;
+  if (type == LSQ_SKETCH_SRHT && row0 % 2048 != 0) return LSQ_ERR_ARG;
   if (type == LSQ_SKETCH_SJLT && (s < 1 || s > 32 || s > m)) return LSQ_ERR_ARG;
   // the SRHT and the tensor-core Gaussian sketch consume the rows as they land; the other
   // sketches take the whole matrix first, in stream order
@@ -1504,17 +1523,18 @@ static lsq_status sketch_impl(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
   switch (type) {
     case LSQ_SKETCH_GAUSS:
       if (prec == LSQ_SKETCH_BF16)
-        st = lsq_gauss_tc_run(ctx, A, (int)m, seed, t, SA, up ? chunk_upload : nullptr, up ? &cu : nullptr);
-      else st = f64 ? gauss_run<double>(ctx, A, (int)m, seed, t, SA) : gauss_run<float>(ctx, A, (int)m, seed, t, SA);
+        st = lsq_gauss_tc_run(ctx, A, (int)m, seed, t, SA, up ? chunk_upload : nullptr, up ? &cu : nullptr, row0);
+      else st = f64 ? gauss_run<double>(ctx, A, (int)m, seed, t, SA, row0)
+                    : gauss_run<float>(ctx, A, (int)m, seed, t, SA, row0);
       break;
     case LSQ_SKETCH_SRHT:
-      st = f64 ? srht_run<double>(ctx, A, (int)m, seed, t, SA, a32, ld32, a32_done, up)
-               : srht_run<float>(ctx, A, (int)m, seed, t, SA, a32, ld32, a32_done, up);
+      st = f64 ? srht_run<double>(ctx, A, (int)m, seed, t, SA, a32, ld32, a32_done, up, row0, n_total)
+               : srht_run<float>(ctx, A, (int)m, seed, t, SA, a32, ld32, a32_done, up, row0, n_total);
       break;
     case LSQ_SKETCH_SJLT:
       if (s < 1 || s > 32 || s > m) return LSQ_ERR_ARG;
-      st = f64 ? sjlt_run<double>(ctx, A, (int)m, s, seed, t, SA)
-               : sjlt_run<float>(ctx, A, (int)m, s, seed, t, SA, prec == LSQ_SKETCH_BF16);
+      st = f64 ? sjlt_run<double>(ctx, A, (int)m, s, seed, t, SA, false, row0)
+               : sjlt_run<float>(ctx, A, (int)m, s, seed, t, SA, prec == LSQ_SKETCH_BF16, row0);
       break;
     default:
       return LSQ_ERR_ARG;

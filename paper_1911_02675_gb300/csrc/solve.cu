@@ -708,7 +708,7 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
     cudaEvent_t e_a, e_b;
     LSQ_CUDA_TRY(cudaEventCreate(&e_a));
     LSQ_CUDA_TRY(cudaEventCreate(&e_b));
-    lsq_sketch_opts so;
+    lsq_sketch_opts so = {};
     so.s = o.s > 0 ? o.s : 8;
     so.precision = LSQ_SKETCH_F64;
     so.a32 = nullptr;
