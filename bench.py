@@ -100,6 +100,9 @@ def parse(argv=None):
     ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workload")
     ap.add_argument("--m-sweep", default="", help="comma-separated sketch sizes: time the solve at each "
                     "(time against m, beside Section 6's advised m*) instead of the bench line")
+    ap.add_argument("--sketch-sweep", default="",
+                    help="comma-separated kind:precision[:m] (e.g. sjlt:f32:4096,sjlt:bf16:4096): time lsq_sketch "
+                    "alone for each on the workload instead of the bench line")
     ap.add_argument("--batch", type=int, default=0,
                     help="time the batched solve of this many uneven problems instead (k right-hand sides each)")
     ap.add_argument("--batch-seed", type=int, default=1)
@@ -402,6 +405,28 @@ def measure_workload(args, rank, world, local, secondary=False):
                               precision=args.precision, a32=a32)
         return x, info
 
+    if args.sketch_sweep:
+        # each sketch alone (CUDA events), its bytes of A read per unit time and whether two calls agree bit for bit
+        rows = []
+        for spec in args.sketch_sweep.split(","):
+            parts = spec.split(":")
+            kind, prec = parts[0], parts[1]
+            m = int(parts[2]) if len(parts) > 2 else args.m
+            fn = lambda: L.lsq_sketch(ctx, A, kind, m, 0, precision=prec)  # noqa: E731
+            first = fn()
+            L.lsq_sync(ctx)
+            for _ in range(max(1, args.warmup)):
+                fn()
+            res = _time_calls(torch, dev, stream, fn, max(3, args.steps))
+            L.lsq_sync(ctx)
+            ms = statistics.median(t for t, _ in res)
+            rows.append({"sketch": kind, "precision": prec, "m": m, "ms": ms,
+                         "A_GBps": n * d * A.element_size() / (ms * 1e-3) / 1e9,
+                         "repeats_bitwise": bool(torch.equal(first, res[-1][1]))})
+        ctx.close()
+        return {"metric": "sketch time", "unit": "ms", "higher_is_better": False, "sketches": rows,
+                "config": workload_config(args, f"replicas{world}")}
+
     if args.m_sweep:
         # time to tolerance against the sketch size (the paper's trade-off of Section 6: a larger m
         # costs more sketch and factor but fewer passes), beside the advised m*
@@ -593,7 +618,8 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     line = measure_workload(args, rank, world, local)
-    if not args.m_sweep and not args.no_secondary and args.workload in SECONDARY and world == 1 and \
+    if not args.m_sweep and not args.sketch_sweep and not args.no_secondary and args.workload in SECONDARY and \
+            world == 1 and \
             all(getattr(args, k) == v for k, v in PRESETS[args.workload].items()):
         sec = preset_args(args, SECONDARY[args.workload], steps=min(args.steps, 10))
         s = measure_workload(sec, rank, world, local, secondary=True)

@@ -121,9 +121,12 @@ LSQ_API lsq_status lsq_sync(lsq_ctx* ctx);
  *   LSQ_SKETCH_BF16: Gaussian: S is generated in FP32 from the same Philox words
  *                   (each uniform keeps the top 24 of its 53 bits), S and A are rounded to
  *                   BF16 and multiplied on the tensor cores (tcgen05) with FP32
- *                   accumulation; FP64 output.  SJLT: each element of A is rounded to FP32
- *                   and then to BF16 (nearest, ties to even), the +-1 signs are exact, the
- *                   sums FP32 and the 1/sqrt(s) scale FP64.  Relative error of SA ~ 1e-3.
+ *                   accumulation; FP64 output.  SJLT: also on the tensor cores, with the
+ *                   +-1 entries of S exact in BF16: each element of A is narrowed to FP32
+ *                   (FP64 A: mantissa truncation, as the mixed solve narrows it) and rounded
+ *                   to BF16 (nearest, ties to even), the products are exact, the sums FP32 in
+ *                   a fixed order (the sketch repeats bit for bit) and the 1/sqrt(s) scale
+ *                   FP64.  Relative error of SA ~ 1e-3.
  *                   Not for the SRHT (LSQ_ERR_ARG). */
 typedef enum { LSQ_SKETCH_F64 = 0, LSQ_SKETCH_F32 = 1, LSQ_SKETCH_BF16 = 2 } lsq_sketch_precision;
 

@@ -262,10 +262,18 @@ __global__ void __launch_bounds__(256) pack_kernel(const TA* __restrict__ A, int
 // cluster own adjacent column tiles of the same rows of SA, so they need the same S; CTA r
 // generates the K-steps 2r and 2r + 1 of each stage (one contiguous 8 KB half) and sends it
 // to the other CTA with one shared-to-shared bulk copy, so S is generated once per row tile.
-template <int NT, int STAGES, int CL>
+//
+// SJ = true: the same product with S an SJLT (Section 2, last paragraph) instead: column i of S
+// holds s entries +-1 (exact in BF16; the 1/sqrt(s) scale is applied in FP64 by the reduction)
+// at the rows the hash pass drew (hsj[i * s + k], sign bit k of ssj[i]; i the row of A).  Warp
+// w owns tile rows 8w .. 8w + 7: per stage it zeroes them and writes the entries that land
+// there, so no warp waits on another.  Every product is exact and the FP32 accumulation runs
+// in a fixed order, so the sketch repeats bit for bit.
+template <int NT, int STAGES, int CL, bool SJ>
 __global__ void __launch_bounds__(TC_GEN + 32, 1)
     gauss_tc_kernel(const uint8_t* __restrict__ pk, int64_t nkb, int nct, int d, int m, uint64_t seed, uint32_t t,
-                    int64_t row0, int64_t kb_per_split, int accumulate, float* __restrict__ part, int* err) {
+                    int64_t row0, int64_t kb_per_split, int accumulate, float* __restrict__ part, int* err,
+                    const int32_t* __restrict__ hsj, const uint32_t* __restrict__ ssj, int s_sj, int64_t n_rows) {
   constexpr int A_BYTES = TC_M * TC_KS * 2;
   constexpr int B_BYTES = NT * TC_KS * 2;
   constexpr uint32_t IDESC = idesc_bf16(TC_M, 256);
@@ -282,6 +290,7 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
   __shared__ __align__(8) uint64_t gen[STAGES];
   __shared__ __align__(8) uint64_t sfull[STAGES];
   __shared__ __align__(8) uint64_t empty[STAGES];
+  __shared__ __align__(8) uint64_t zeroed[STAGES];  // SJ: every generating warp zeroed its rows
   __shared__ uint32_t tmem_base_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int j0 = blockIdx.x * TC_M, ct = blockIdx.y;
@@ -297,6 +306,7 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
       mbar_init(&gen[s], GW);
       mbar_init(&sfull[s], 1);
       mbar_init(&empty[s], CL);
+      mbar_init(&zeroed[s], GW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -310,7 +320,69 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
   int64_t copies = 0;  // bulk copies of blobs started (MMA warp)
   int64_t armed = 0;   // CL = 2: stages armed for the other CTA's half of S (MMA warp)
 
-  if (warp < GW) {
+  if (SJ && warp < GW) {
+    // ---- SJLT generators.  Per stage: warp w zeroes tile rows 8w .. 8w + 7 of this CTA's
+    // K-columns, the warps meet on the stage's `zeroed` mbarrier (bounded), then each lane
+    // writes its (K-column, target) pairs, whose target rows and signs it loaded a stage ahead
+    constexpr int KC = TC_KS / CL;                 // K-columns of a stage this CTA writes
+    constexpr int PMAX = KC * 32 / TC_GEN;         // pairs per lane at s = 32 (4 or 2)
+    const int kc0 = CL == 1 ? 0 : KC * (int)rank;  // first of them
+    const int npairs = KC * s_sj;
+    const uint16_t plus = 0x3F80u, minus = 0xBF80u;  // BF16 +1, -1
+    int32_t tgt[PMAX];
+    uint16_t val[PMAX];
+    // pair p of the stage: K-column p / s, target p % s; this thread takes p = tid + TC_GEN q
+    auto fetch = [&](int64_t step) {
+      const int64_t ib = (row0 + (kb_begin + step) * TC_KS) + kc0;  // row of A of K-column kc0
+#pragma unroll
+      for (int q = 0; q < PMAX; ++q) {
+        const int p = tid + TC_GEN * q;
+        tgt[q] = -1;
+        if (step < nsteps && p < npairs) {
+          const int k = p / s_sj, e = p - k * s_sj;
+          const int64_t i = ib + k;
+          if (i < n_rows) {
+            const int off = __ldg(hsj + i * s_sj + e) - j0;
+            if (off >= 0 && off < TC_M) {
+              const int L = (off & 1) ? 64 + (off >> 1) : (off >> 1);  // the tile row of sketch row j0 + off
+              const int kcol = kc0 + k;
+              tgt[q] = (int32_t)(core_offset(TC_M, L, kcol >> 3) + (kcol & 7) * 2);
+              val[q] = ((__ldg(ssj + i) >> e) & 1u) ? minus : plus;
+            }
+          }
+        }
+      }
+    };
+    fetch(0);
+    for (int64_t step = 0; step < nsteps; ++step) {
+      const int s = (int)(step % STAGES);
+      const uint32_t par = (uint32_t)((step / STAGES) & 1);
+      if (step >= STAGES &&
+          !__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((step / STAGES) - 1) & 1), err))) {
+        ok = false;
+        break;
+      }
+      uint8_t* stA = sA + s * A_BYTES;
+      // rows 8w .. 8w + 7 of K-step kk form 256 contiguous bytes at kk * TC_M * 32 + w * 256
+      for (int b = lane; b < (KC / 16) * 16; b += 32) {
+        const int kk = (kc0 >> 4) + (b >> 4);
+        *reinterpret_cast<uint4*>(stA + kk * TC_M * 32 + warp * 256 + (b & 15) * 16) = make_uint4(0u, 0u, 0u, 0u);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive_local(&zeroed[s]);
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&zeroed[s], par, err))) {
+        ok = false;
+        break;
+      }
+#pragma unroll
+      for (int q = 0; q < PMAX; ++q)
+        if (tgt[q] >= 0) *reinterpret_cast<uint16_t*>(stA + tgt[q]) = val[q];
+      fetch(step + 1);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_local(&gen[s]);
+    }
+  } else if (!SJ && warp < GW) {
     // ---- generators
     const RoundKeys keys = round_keys(seed);
     // CL = 1: thread -> unit (row pair jp, k-group kg), a warp's stores fill 512 contiguous
@@ -510,15 +582,23 @@ __global__ void reduce_tc_kernel(const float* __restrict__ part, int splits, int
   }
 }
 
-template <int NT, int STAGES, int CL>
+struct SjltHashes {
+  const int32_t* h;     // n x s target rows (draw order)
+  const uint32_t* sgn;  // n sign words
+  int s;
+  int64_t n;
+};
+
+template <int NT, int STAGES, int CL, bool SJ>
 lsq_status launch_tc(lsq_ctx* ctx, dim3 grid, const uint8_t* pk, int64_t nkb, int nct, int d, int m, uint64_t seed,
-                     uint32_t t, int64_t row0, int64_t kb_per_split, int accumulate, float* part, int* err) {
+                     uint32_t t, int64_t row0, int64_t kb_per_split, int accumulate, float* part, int* err,
+                     const SjltHashes& hs) {
   const size_t smem = (size_t)STAGES * (TC_M * TC_KS * 2 + NT * TC_KS * 2);
-  auto k = gauss_tc_kernel<NT, STAGES, CL>;
+  auto k = gauss_tc_kernel<NT, STAGES, CL, SJ>;
   LSQ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (CL == 1) {
     k<<<grid, TC_GEN + 32, smem, ctx->stream>>>(pk, nkb, nct, d, m, seed, t, row0, kb_per_split, accumulate, part,
-                                                err);
+                                                err, hs.h, hs.sgn, hs.s, hs.n);
   } else {
     // clusters of CL CTAs along the column tiles (grid.y is a multiple of CL)
     cudaLaunchConfig_t cfg = {};
@@ -533,7 +613,8 @@ lsq_status launch_tc(lsq_ctx* ctx, dim3 grid, const uint8_t* pk, int64_t nkb, in
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    LSQ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, accumulate, part, err));
+    LSQ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, pk, nkb, nct, d, m, seed, t, row0, kb_per_split, accumulate, part, err,
+                                    hs.h, hs.sgn, hs.s, hs.n));
   }
   LSQ_LAUNCH_CHECK();
   return LSQ_OK;
@@ -558,12 +639,13 @@ int pick_splits(int tiles, int sms, int64_t kb_total, int64_t cap) {
 
 }  // namespace
 
-// BF16 tensor-core Gaussian sketch into SA (FP64, m x d); called by lsq_sketch.  `rows_ready`
-// (may be null) is called with each chunk's row range [r0, r1) before the chunk is read, in row
-// order, so that a caller can queue the upload of those rows and make the context stream wait
-// for them (lsq_upload_sketch): the copy of chunk k + 1 then overlaps the work on chunk k.
-lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
-                            lsq_rows_hook rows_ready, void* hook_user, int64_t grow0) {
+lsq_status lsq_sjlt_hash_launch(lsq_ctx* ctx, int64_t n, int m, int s, uint64_t seed, uint32_t t, int64_t grow0,
+                                int32_t* h, uint32_t* signs);
+
+// Both sketches share the driver: sjlt_s = 0 the Gaussian, sjlt_s > 0 the SJLT with s nonzeros
+// per column (its target rows drawn first by the hash pass of lsq_sketch's SJLT)
+static lsq_status tc_sketch_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
+                                lsq_rows_hook rows_ready, void* hook_user, int64_t grow0, int sjlt_s) {
   const int d = (int)A->d;
   const int nt = d > 256 ? 512 : 256;
   const int nct = (d + nt - 1) / nt;
@@ -577,13 +659,24 @@ lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t s
   const int64_t cap = std::max<int64_t>(1, ((int64_t)512 << 20) / ((int64_t)m * d * 4));
   const int splits = pick_splits(tiles, ctx->sm_count, kb_chunk, cap);
   const int64_t kb_per_split = (kb_chunk + splits - 1) / splits;
-  const size_t need = lsq_align256((size_t)kb_chunk * nct * blob) + lsq_align256((size_t)splits * m * d * 4) + 256;
+  const bool sj = sjlt_s > 0;
+  const size_t hash_bytes = sj ? lsq_align256((size_t)A->n * sjlt_s * 4) + lsq_align256((size_t)A->n * 4) : 0;
+  const size_t need =
+      lsq_align256((size_t)kb_chunk * nct * blob) + lsq_align256((size_t)splits * m * d * 4) + 256 + hash_bytes;
   lsq_status st = lsq_ensure_scratch(ctx, need);
   if (st != LSQ_OK) return st;
   Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};
   uint8_t* pk = cv.take<uint8_t>((size_t)kb_chunk * nct * blob);
   float* part = cv.take<float>((size_t)splits * m * d);
   int* err = cv.take<int>(1);
+  SjltHashes hs{nullptr, nullptr, 0, A->n};
+  if (sj) {
+    int32_t* h = cv.take<int32_t>((size_t)A->n * sjlt_s);
+    uint32_t* sg = cv.take<uint32_t>((size_t)A->n);
+    st = lsq_sjlt_hash_launch(ctx, A->n, m, sjlt_s, seed, t, grow0, h, sg);
+    if (st != LSQ_OK) return st;
+    hs = SjltHashes{h, sg, sjlt_s, A->n};
+  }
   LSQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
   const dim3 grid(tiles_m, nct, splits);
   for (int64_t kb0 = 0; kb0 < kb_total; kb0 += kb_chunk) {
@@ -603,22 +696,43 @@ lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t s
                                                          row0, nkb, nt, nct, pk);
     LSQ_LAUNCH_CHECK();
     const int acc = kb0 > 0 ? 1 : 0;
+    // the Gaussian generator indexes rows of the whole matrix; the SJLT's hashes are A's own rows
+    const int64_t r0 = sj ? row0 : grow0 + row0;
     // a CTA pair shares S when d needs two 512-column tiles (nt = 256 only for d <= 256)
     if (nt == 512 && nct % 2 == 0)
-      st = launch_tc<512, 2, 2>(ctx, grid, pk, nkb, nct, d, m, seed, t, grow0 + row0, kb_per_split, acc, part, err);
+      st = sj ? launch_tc<512, 2, 2, true>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs)
+              : launch_tc<512, 2, 2, false>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs);
     else if (nt == 512)
-      st = launch_tc<512, 2, 1>(ctx, grid, pk, nkb, nct, d, m, seed, t, grow0 + row0, kb_per_split, acc, part, err);
+      st = sj ? launch_tc<512, 2, 1, true>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs)
+              : launch_tc<512, 2, 1, false>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs);
     else
-      st = launch_tc<256, 4, 1>(ctx, grid, pk, nkb, nct, d, m, seed, t, grow0 + row0, kb_per_split, acc, part, err);
+      st = sj ? launch_tc<256, 4, 1, true>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs)
+              : launch_tc<256, 4, 1, false>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs);
     if (st != LSQ_OK) return st;
   }
   const int64_t md = (int64_t)m * d;
   const int rgrid = (int)std::min<int64_t>((md + 255) / 256, 4 * (int64_t)ctx->sm_count);
-  reduce_tc_kernel<<<rgrid, 256, 0, ctx->stream>>>(part, splits, md, 1.0 / sqrt((double)m), SA);
+  reduce_tc_kernel<<<rgrid, 256, 0, ctx->stream>>>(part, splits, md, 1.0 / sqrt((double)(sj ? sjlt_s : m)), SA);
   LSQ_LAUNCH_CHECK();
   // a timed-out wait inside the tensor-core kernel is reported here (or deferred)
   if (ctx->defer_checks) return lsq_defer_status(ctx, err, 0);
   LSQ_CUDA_TRY(cudaMemcpyAsync(ctx->host_status + 13, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   LSQ_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return ctx->host_status[13] ? (lsq_status)ctx->host_status[13] : LSQ_OK;
+}
+
+// BF16 tensor-core Gaussian sketch into SA (FP64, m x d); called by lsq_sketch.  `rows_ready`
+// (may be null) is called with each chunk's row range [r0, r1) before the chunk is read, in row
+// order, so that a caller can queue the upload of those rows and make the context stream wait
+// for them (lsq_upload_sketch): the copy of chunk k + 1 then overlaps the work on chunk k.
+lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
+                            lsq_rows_hook rows_ready, void* hook_user, int64_t grow0) {
+  return tc_sketch_run(ctx, A, m, seed, t, SA, rows_ready, hook_user, grow0, 0);
+}
+
+// The SJLT with s nonzeros per column of S on the tensor cores (BF16 A, exact +-1 entries,
+// FP32 accumulation in a fixed order, 1/sqrt(s) in FP64); arguments as lsq_gauss_tc_run.
+lsq_status lsq_sjlt_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint64_t seed, uint32_t t, double* SA,
+                           lsq_rows_hook rows_ready, void* hook_user, int64_t grow0) {
+  return tc_sketch_run(ctx, A, m, seed, t, SA, rows_ready, hook_user, grow0, s);
 }

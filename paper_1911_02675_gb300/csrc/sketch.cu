@@ -1455,6 +1455,16 @@ static lsq_status sjlt_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint
 
 lsq_status lsq_gauss_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64_t seed, uint32_t t, double* SA,
                             lsq_rows_hook rows_ready, void* hook_user, int64_t grow0);
+lsq_status lsq_sjlt_tc_run(lsq_ctx* ctx, const lsq_matrix* A, int m, int s, uint64_t seed, uint32_t t, double* SA,
+                           lsq_rows_hook rows_ready, void* hook_user, int64_t grow0);
+
+// the hash pass of the SJLT (target rows in draw order and the sign word of every row of A)
+lsq_status lsq_sjlt_hash_launch(lsq_ctx* ctx, int64_t n, int m, int s, uint64_t seed, uint32_t t, int64_t grow0,
+                                int32_t* h, uint32_t* signs) {
+  sjlt_hash_kernel<<<grid_for(n, 256, 16 * ctx->sm_count), 256, 0, ctx->stream>>>(n, m, s, seed, t, h, signs, grow0);
+  LSQ_LAUNCH_CHECK();
+  return LSQ_OK;
+}
 
 // lsq_upload_sketch of the tensor-core Gaussian sketch: each chunk's rows go up on the copy stream
 // (which first waits for the work already queued on the context stream, since it may still read
@@ -1514,7 +1524,7 @@ static lsq_status sketch_impl(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
   if (type == LSQ_SKETCH_SJLT && (s < 1 || s > 32 || s > m)) return LSQ_ERR_ARG;
   // the SRHT and the tensor-core Gaussian sketch consume the rows as they land; the other
   // sketches take the whole matrix first, in stream order
-  const bool chunked_gauss = type == LSQ_SKETCH_GAUSS && prec == LSQ_SKETCH_BF16;
+  const bool chunked_gauss = (type == LSQ_SKETCH_GAUSS || type == LSQ_SKETCH_SJLT) && prec == LSQ_SKETCH_BF16;
   if (up && type != LSQ_SKETCH_SRHT && !chunked_gauss) {
     st = upload_rows(up, A, 0, A->n, ctx->stream);
     if (st != LSQ_OK) return st;
@@ -1533,8 +1543,11 @@ static lsq_status sketch_impl(lsq_ctx* ctx, const lsq_matrix* A, int32_t type, i
       break;
     case LSQ_SKETCH_SJLT:
       if (s < 1 || s > 32 || s > m) return LSQ_ERR_ARG;
-      st = f64 ? sjlt_run<double>(ctx, A, (int)m, s, seed, t, SA, false, row0)
-               : sjlt_run<float>(ctx, A, (int)m, s, seed, t, SA, prec == LSQ_SKETCH_BF16, row0);
+      if (prec == LSQ_SKETCH_BF16)  // on the tensor cores, in a fixed order
+        st = lsq_sjlt_tc_run(ctx, A, (int)m, s, seed, t, SA, up ? chunk_upload : nullptr, up ? &cu : nullptr, row0);
+      else
+        st = f64 ? sjlt_run<double>(ctx, A, (int)m, s, seed, t, SA, false, row0)
+                 : sjlt_run<float>(ctx, A, (int)m, s, seed, t, SA, false, row0);
       break;
     default:
       return LSQ_ERR_ARG;

@@ -194,6 +194,7 @@ def test_sketch_writes_fp32_copy(L, ctx, kind, precision, n, d):
     (600001, 1024, 4096, np.float32, "gauss-bf16", True),  # tensor-core Gaussian: 2 chunks, ragged tail
     (2**21 + 333, 40, 256, np.float32, "gauss-bf16", True),  # narrow d: 2 chunks of 2^21 rows
     (3000, 24, 64, np.float64, "gauss-bf16", False),       # one chunk, pageable host memory
+    (600001, 600, 1000, np.float32, "sjlt-bf16", True),    # tensor-core SJLT: CTA pairs, 2 chunks
 ])
 def test_upload_sketch_matches_sketch_of_device_copy(L, ctx, n, d, m, dtype, kind, pinned):
     """lsq_upload_sketch copies A while the SRHT transforms the row groups that have landed (the
@@ -205,7 +206,7 @@ def test_upload_sketch_matches_sketch_of_device_copy(L, ctx, n, d, m, dtype, kin
     if pinned:
         A_host = A_host.pin_memory()
     Ad = torch.empty(A_host.shape, dtype=A_host.dtype, device="cuda")
-    prec = {"srht": "f32", "gauss-bf16": "bf16"}.get(kind, "f64")
+    prec = {"srht": "f32", "gauss-bf16": "bf16", "sjlt-bf16": "bf16"}.get(kind, "f64")
     kind = kind.split("-")[0]
     a32 = L.narrow_buffer(Ad) if dtype == np.float64 else None
     SA_up = L.lsq_upload_sketch(ctx, A_host, Ad, kind, m, 5, precision=prec, a32=a32)
@@ -217,22 +218,49 @@ def test_upload_sketch_matches_sketch_of_device_copy(L, ctx, n, d, m, dtype, kin
         assert torch.equal(a32_up[:, :d], a32[:, :d])
 
 
+def _narrow_f32(A):
+    """FP64 -> FP32 by truncating the mantissa (the library's narrowing, for normal values), FP32 as is."""
+    if A.dtype == np.float32:
+        return A
+    u = np.ascontiguousarray(A).view(np.uint64)
+    sign = (u >> 63) << 31
+    e = ((u >> 52) & 0x7FF).astype(np.int64) - 896
+    assert e.min() > 0 and e.max() < 255, "test data in the normal FP32 range"
+    f = sign | (e.astype(np.uint64) << 23) | ((u >> 29) & 0x7FFFFF)
+    return f.astype(np.uint32).view(np.float32)
+
+
 def _round_bf16(A):
-    """FP32 rounding, then BF16 (nearest, ties to even) by the bit pattern, back to FP64."""
-    u = np.ascontiguousarray(A.astype(np.float32)).view(np.uint32).astype(np.uint64)
+    """The library's FP32 narrowing, then BF16 (nearest, ties to even) by the bit pattern, back to FP64."""
+    u = np.ascontiguousarray(_narrow_f32(A)).view(np.uint32).astype(np.uint64)
     u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 @pytest.mark.parametrize("n,d,m,s,dtype", [(5000, 33, 256, 8, np.float32), (3000, 20, 128, 4, np.float64),
-                                           (20000, 64, 512, 8, np.float32)])
+                                           (20000, 64, 512, 8, np.float32), (70001, 600, 1000, 8, np.float64),
+                                           (9000, 300, 96, 32, np.float32), (2000, 16, 8, 8, np.float32)])
 def test_sjlt_bf16_is_the_sketch_of_rounded_a(L, ctx, n, d, m, s, dtype):
-    """LSQ_SKETCH_BF16 for the SJLT: the FP64 sketch of A rounded to BF16 (exact +-1 signs and
-    positions), up to the FP32 sums."""
+    """LSQ_SKETCH_BF16 for the SJLT (on the tensor cores): the FP64 sketch of A narrowed to BF16 (exact
+    +-1 signs and positions), up to the FP32 sums; and it repeats bit for bit."""
     A = W.make_problem(n, d, 1e3, seed=n + s)["A"].astype(dtype)
     Ab = _round_bf16(A)
     assert np.max(np.abs(Ab - A)) > 0  # the rounding does something
-    SA = L.lsq_sketch(ctx, to_dev(A), "sjlt", m, 3, s=s, precision="bf16").cpu().numpy()
+    Ad = to_dev(A)
+    SA = L.lsq_sketch(ctx, Ad, "sjlt", m, 3, s=s, precision="bf16").cpu().numpy()
     ref = O.sketch_sjlt(Ab, m, s, 3, 0)
     assert rel_fro(SA, ref) < 1e-6
+    assert np.array_equal(SA, L.lsq_sketch(ctx, Ad, "sjlt", m, 3, s=s, precision="bf16").cpu().numpy())
     assert rel_fro(SA, O.sketch_sjlt(A.astype(np.float64), m, s, 3, 0)) < 1e-2  # ~ BF16 resolution
+
+
+@pytest.mark.parametrize("n,d,m,s", [(5000, 24, 200, 4), (20001, 600, 1000, 16), (3000, 300, 64, 4),
+                                     (70000, 512, 4096, 4), (999, 7, 8, 4)])
+def test_sjlt_bf16_tensor_core_bit_exact_on_integers(L, ctx, n, d, m, s):
+    """Small integers are exact in BF16 and their FP32 sums are exact, and 1/sqrt(s) is a power
+    of two for s = 4, 16: the tensor-core SJLT equals the oracle's sketch bit for bit, which
+    pins every target row and sign it writes into the tiles of S (window edges at m not a
+    multiple of 128, CTA pairs for d > 512, ragged n)."""
+    A = int_matrix(n, d, seed=n + d)
+    SA = L.lsq_sketch(ctx, to_dev(A), "sjlt", m, 6, s=s, precision="bf16").cpu().numpy()
+    assert np.array_equal(SA, O.sketch_sjlt(A, m, s, 6, 0))
