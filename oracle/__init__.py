@@ -13,7 +13,7 @@ Functions and the passages they follow:
   gauss_matrix, sketch_gauss, sketch_gauss_rows   Gaussian embedding N(0, 1/m)   Section 2
   srht_signs, srht_rows, sketch_srht   S = R H E with zero padding      Section 2 (+ footnote)
   sjlt_hash, sketch_sjlt  s nonzeros +-1/sqrt(s) per column of S         Section 2 (last paragraph)
-  gram, cholesky_upper, qr_r, tri_inv_upper, precond_solve
+  gram, cholesky_upper, qr_r, qr_pivoted, tri_inv_upper, precond_solve
                           factorisations of H_S                         Section 1 (PCG), Section 6
   hmatvec, residual_dd    H p = A^T A p, b - H x                         Section 1 (problem)
   pcg                     PCG with a fixed embedding                     Section 1, eq. (PCG)
@@ -67,6 +67,7 @@ def lib():
             "orc_gram": (None, [P, i64, i64, P]),
             "orc_cholesky_upper": (i32, [P, i64, P]),
             "orc_qr_r": (i32, [P, i64, i64, P]),
+            "orc_qr_pivoted": (i32, [P, i64, i64, dbl, P, P, P]),
             "orc_tri_inv_upper": (None, [P, i64, P]),
             "orc_precond_solve": (None, [P, i64, P, P]),
             "orc_hmatvec": (None, [P, i64, i64, i64, P, P, P]),
@@ -240,6 +241,18 @@ def qr_r(M) -> np.ndarray:
     if st:
         raise np.linalg.LinAlgError(f"zero column {st - 1}")
     return R
+
+
+def qr_pivoted(M, tol: float = 0.0):
+    """Householder QR with column pivoting: (R, perm, rank) with M[:, perm] = Q R, R upper with a
+    positive, non-increasing diagonal; rows of R from `rank` on are zero (Section 1, PCG paragraph)."""
+    M = _f64(M)
+    m, d = M.shape
+    R = np.empty((d, d))
+    perm = np.empty(d, dtype=np.int32)
+    rank = ctypes.c_int64(0)
+    lib().orc_qr_pivoted(_ptr(M), m, d, float(tol), _ptr(R), _ptr(perm), ctypes.byref(rank))
+    return R, perm, rank.value
 
 
 def factor(SA) -> np.ndarray:

@@ -396,6 +396,73 @@ int orc_qr_r(const double* M, int64_t m, int64_t d, double* R) {
   return status;
 }
 
+/* Householder QR with column pivoting (Businger and Golub, 1965) of M (m x d, row-major,
+   m >= d), one of the factorisations of H_S the paper allows (Section 1, PCG paragraph):
+   M[:, perm] = Q R, R upper with positive diagonal.  At step k the column of largest
+   remaining norm (rows k..m-1, recomputed from its entries; ties to the lower index) is
+   moved to position k.  The numerical rank is the number of steps before the largest
+   remaining norm falls to tol times the first pivot's norm; rows of R from the rank on
+   are zero.  perm[k] = the column of M at position k. */
+int orc_qr_pivoted(const double* M, int64_t m, int64_t d, double tol, double* R, int32_t* perm, int64_t* rank) {
+  double* Q = (double*)malloc(sizeof(double) * (size_t)(m * d)); /* column-major work copy */
+  double* v = (double*)malloc(sizeof(double) * (size_t)m);
+  double* nrm = (double*)malloc(sizeof(double) * (size_t)d);
+  for (int64_t r = 0; r < m; ++r)
+    for (int64_t c = 0; c < d; ++c) Q[c * m + r] = M[r * d + c];
+  for (int64_t c = 0; c < d; ++c) perm[c] = (int32_t)c;
+  memset(R, 0, sizeof(double) * (size_t)(d * d));
+  double first = 0.0;
+  int64_t k = 0;
+  for (; k < d; ++k) {
+    /* remaining column norms, then the pivot */
+#pragma omp parallel for schedule(static)
+    for (int64_t c = k; c < d; ++c) {
+      double s2 = 0.0;
+      for (int64_t r = k; r < m; ++r) s2 += Q[c * m + r] * Q[c * m + r];
+      nrm[c] = sqrt(s2);
+    }
+    int64_t p = k;
+    for (int64_t c = k + 1; c < d; ++c)
+      if (nrm[c] > nrm[p]) p = c;
+    if (k == 0) first = nrm[p];
+    if (!(nrm[p] > tol * first) || !(nrm[p] > 0.0)) break;
+    if (p != k) {
+      for (int64_t r = 0; r < m; ++r) {
+        double t = Q[k * m + r];
+        Q[k * m + r] = Q[p * m + r];
+        Q[p * m + r] = t;
+      }
+      int32_t tp = perm[k]; perm[k] = perm[p]; perm[p] = tp;
+      for (int64_t r = 0; r < k; ++r) {
+        double t = R[r * d + k];
+        R[r * d + k] = R[r * d + p];
+        R[r * d + p] = t;
+      }
+    }
+    double* col = Q + k * m;
+    double norm = nrm[p];
+    double alpha = col[k] > 0 ? -norm : norm;
+    for (int64_t r = k; r < m; ++r) v[r] = col[r];
+    v[k] -= alpha;
+    double vnorm2 = 0.0;
+    for (int64_t r = k; r < m; ++r) vnorm2 += v[r] * v[r];
+#pragma omp parallel for schedule(static)
+    for (int64_t c = k; c < d; ++c) {
+      double* x = Q + c * m;
+      double dot = 0.0;
+      for (int64_t r = k; r < m; ++r) dot += v[r] * x[r];
+      double f = 2.0 * dot / vnorm2;
+      for (int64_t r = k; r < m; ++r) x[r] -= f * v[r];
+    }
+    for (int64_t c = k; c < d; ++c) R[k * d + c] = Q[c * m + k];
+    if (R[k * d + k] < 0)
+      for (int64_t c = k; c < d; ++c) R[k * d + c] = -R[k * d + c];
+  }
+  *rank = k;
+  free(Q); free(v); free(nrm);
+  return 0;
+}
+
 /* W = R^{-1} for upper-triangular R, by back substitution on the columns of I */
 void orc_tri_inv_upper(const double* R, int64_t d, double* W) {
   memset(W, 0, sizeof(double) * (size_t)(d * d));

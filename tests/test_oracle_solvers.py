@@ -288,3 +288,40 @@ def test_minimal_root_radius_on_a_grid():
             best = min(best, max(abs(np.linalg.eigvals(M))))
     assert best >= O.refreshed_rate(t1, t2) - 1e-9
     assert best <= O.refreshed_rate(t1, t2) + 1e-2
+
+
+# ---------------------------------------------------------------------------- pivoted QR
+def test_pivoted_qr_matches_lapack():
+    """Column-pivoted Householder QR against LAPACK's (scipy.linalg.qr with pivoting): the same
+    column order where the column norms are well separated, the same R up to row signs."""
+    from scipy.linalg import qr as sp_qr
+
+    rng = np.random.default_rng(5)
+    for m, d in [(60, 7), (300, 24), (257, 64)]:
+        M = rng.standard_normal((m, d)) * np.logspace(0, 4, d)[rng.permutation(d)]
+        R, perm, rank = O.qr_pivoted(M)
+        Rs, Ps = sp_qr(M, pivoting=True, mode="r")
+        Rs = Rs[:d]
+        assert rank == d
+        assert np.array_equal(perm, Ps)
+        Rs = np.sign(np.diag(Rs))[:, None] * Rs
+        np.testing.assert_allclose(R, Rs, rtol=1e-10, atol=1e-12 * np.abs(Rs).max())
+        np.testing.assert_allclose(R.T @ R, M[:, perm].T @ M[:, perm], rtol=1e-12, atol=1e-13 * np.abs(R).max() ** 2)
+        dg = np.diag(R)
+        assert np.all(dg > 0) and np.all(dg[1:] <= dg[:-1] * (1 + 1e-12))
+        assert np.all(np.tril(R, -1) == 0)
+
+
+def test_pivoted_qr_reveals_rank():
+    rng = np.random.default_rng(6)
+    B = rng.standard_normal((200, 5))
+    M = np.column_stack([B, B @ rng.standard_normal((5, 3))])  # rank 5 with 8 columns
+    R, perm, rank = O.qr_pivoted(M, tol=1e-10)
+    assert rank == 5
+    assert np.all(R[5:] == 0)
+    # the leading columns span M: the trailing ones are combinations of them
+    lead = M[:, perm[:5]]
+    coef = np.linalg.lstsq(lead, M[:, perm[5:]], rcond=None)[0]
+    np.testing.assert_allclose(lead @ coef, M[:, perm[5:]], atol=1e-9 * np.abs(M).max())
+    # and a full-rank input with tol = 0 keeps every column
+    assert O.qr_pivoted(B)[2] == 5
