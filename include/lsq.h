@@ -213,6 +213,25 @@ LSQ_API lsq_status lsq_upload_sketch(lsq_ctx* ctx, const void* host_A, int64_t h
  * --------------------------------------------------------------------------------- */
 LSQ_API lsq_status lsq_factor(lsq_ctx* ctx, const double* SA, int64_t m, int64_t d, double* R, double* W);
 
+/* lsq_factor_qr: the preconditioner factor by Householder QR with column pivoting of SA
+ * (Businger-Golub; Section 1, PCG paragraph, names pivoted QR as a way to factor H_S):
+ * SA[:, perm] = Q R, so H_S = P R^T R P^T and H_S^{-1} = W W^T with W = P R^{-1}.  It works on
+ * SA itself, so the factor's error grows with cond(SA) rather than cond(SA)^2 (the Gram route),
+ * and it reveals the numerical rank.
+ *   SA   : device, m x d FP64 (row-major), d <= m <= 65536, d <= 1024.
+ *   tol  : rank threshold in [0, 1): the factorisation stops when the largest remaining column
+ *          norm is at most tol times the first pivot's (0: only exact zeros).
+ *   R    : device, d x d FP64 out: upper triangular, positive non-increasing diagonal, rows from
+ *          the rank on zero.
+ *   W    : device, d x d FP64 out (full rank only): W = P R^{-1}, row perm[i] of W is row i of
+ *          R^{-1}; pass it to lsq_solve with lsq_solve_opts.w_dense = 1.
+ *   perm : device, d int32 out: column perm[k] of SA is the k-th pivot.
+ *   rank_out : host, may be NULL: the numerical rank.
+ * Waits for its work.  LSQ_ERR_RANK if the rank is below d (R and perm are still written),
+ * LSQ_ERR_TIMEOUT if a bounded wait gave up, LSQ_ERR_ARG for bad sizes or tol.  FP64 throughout. */
+LSQ_API lsq_status lsq_factor_qr(lsq_ctx* ctx, const double* SA, int64_t m, int64_t d, double tol, double* R,
+                                 double* W, int32_t* perm, int64_t* rank_out);
+
 /* lsq_factor_ex: lsq_factor with the arithmetic of the Gram matrix chosen.
  *   gram_precision : LSQ_PREC_F64 (= lsq_factor) or LSQ_PREC_MIXED, which forms
  *                    H_S = (SA)^T (SA) in double-FP32 on the FP32 pipe: each entry of SA is
@@ -259,6 +278,10 @@ typedef struct {
                           compute with, so results are bit-identical with 0 (every pass
                           narrows A itself).  Where the memory cannot be had the solve runs as
                           with 0. */
+  int32_t w_dense;     /* fixed-embedding PCG / IHS / Polyak: 1 = W is a general d x d matrix with
+                          H_S^{-1} = W W^T (the pivoted-QR factor of lsq_factor_qr, W = P R^{-1}),
+                          so the two products run over whole rows; 0 (default) = W upper
+                          triangular (lsq_factor), whose zero halves are skipped */
 } lsq_solve_opts;
 
 /* Results of lsq_solve. */

@@ -38,7 +38,7 @@ DTYPE = {torch.float64: 0, torch.float32: 1}
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_set_stream", "lsq_set_deferred_checks", "lsq_sync", "lsq_sketch", "lsq_upload_sketch", "lsq_factor", "lsq_factor_ex", "lsq_solve",
            "lsq_solve_opts_default", "lsq_hmatvec", "lsq_status_str", "lsq_version", "lsq_launch_count",
            "lsq_hmatvec_noalloc", "lsq_grad_a", "lsq_advise_sketch_size", "lsq_batch_opts_default",
-           "lsq_solve_batched", "lsq_selftest_wait", "lsq_pcg_tail")
+           "lsq_solve_batched", "lsq_selftest_wait", "lsq_pcg_tail", "lsq_factor_qr")
 
 
 class LsqError(RuntimeError):
@@ -63,7 +63,7 @@ class LsqSolveOpts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("s", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("refresh_every", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("x0_zero", ctypes.c_int32),
                 ("fcg_k", ctypes.c_int32), ("a32", ctypes.c_void_p), ("ld32", ctypes.c_int64),
-                ("a32_copy", ctypes.c_int32)]
+                ("a32_copy", ctypes.c_int32), ("w_dense", ctypes.c_int32)]
 
 
 class LsqProblem(ctypes.Structure):
@@ -133,6 +133,8 @@ def _load():
     L.lsq_solve_batched.argtypes = [P, i32, ctypes.POINTER(LsqProblem), dbl, i32, ctypes.POINTER(LsqBatchOpts),
                                     ctypes.POINTER(LsqBatchInfo)]
     L.lsq_solve_batched.restype = ctypes.c_int
+    L.lsq_factor_qr.argtypes = [P, P, i64, i64, dbl, P, P, P, ctypes.POINTER(i64)]
+    L.lsq_factor_qr.restype = ctypes.c_int
     L.lsq_pcg_tail.argtypes = [P, i64, P, P, P, i32, dbl, dbl, P, ctypes.POINTER(i32)]
     L.lsq_pcg_tail.restype = ctypes.c_int
     L.lsq_selftest_wait.argtypes = [P, i32, i32, i64]
@@ -292,6 +294,26 @@ def lsq_factor(ctx: Context, SA: torch.Tensor, R: torch.Tensor | None = None, W:
     if st:
         raise LsqError(st, "lsq_factor")
     return R, W
+
+
+def lsq_factor_qr(ctx: Context, SA: torch.Tensor, tol: float = 0.0, raise_on_rank: bool = True):
+    """(R, W, perm, rank) by Householder QR with column pivoting of SA: SA[:, perm] = Q R and
+    W = P R^{-1} (dense: lsq_solve(..., w_dense=1)).  With raise_on_rank=False a rank-deficient SA
+    returns W = None instead of raising."""
+    ctx.sync_stream()
+    if SA.dtype != torch.float64 or not SA.is_contiguous() or not SA.is_cuda:
+        raise ValueError("SA must be a contiguous CUDA float64 matrix")
+    m, d = SA.shape
+    R = torch.empty((d, d), dtype=torch.float64, device=SA.device)
+    W = torch.empty((d, d), dtype=torch.float64, device=SA.device)
+    perm = torch.empty(d, dtype=torch.int32, device=SA.device)
+    rank = ctypes.c_int64(0)
+    st = _L.lsq_factor_qr(ctx.handle, _ptr(SA), m, d, float(tol), _ptr(R), _ptr(W), _ptr(perm), ctypes.byref(rank))
+    if st == LSQ_ERR_RANK and not raise_on_rank:
+        return R, None, perm, rank.value
+    if st:
+        raise LsqError(st, "lsq_factor_qr")
+    return R, W, perm, rank.value
 
 
 def solve_opts(**kw) -> LsqSolveOpts:

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblsq.so")
 SOURCES = ["ctx.cu", "sketch.cu", "gauss_tc.cu", "factor.cu", "solve.cu", "grad.cu", "advise.cu", "noalloc.cu", "fcg.cu",
-           "batch.cu", "dist.cu"]
+           "batch.cu", "dist.cu", "qr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

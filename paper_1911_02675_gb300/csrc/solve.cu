@@ -32,6 +32,7 @@ struct SolveArgs {
   const double* b;
   const double* W;   // d x d upper, stride d
   const double* WT;  // W^T (lower), stride d
+  int w_dense;       // 1: W is a general d x d matrix (H_S^{-1} = W W^T), the products run over whole rows
   double* x;         // user x (in: x0, out)
   double* xprev;     // IHS/Polyak: x_{t-1} carried between single-step launches
   int method;
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
     for (int c = threadIdx.x; c < dp; c += blockDim.x) stage[c] = c < d ? src[c] : 0.0;
     __syncthreads();
     for (int i = cw; i < d; i += nw) {
-      const double zi = warp_row_dot(a.WT + (int64_t)i * d, stage, 0, i + 1);
+      const double zi = warp_row_dot(a.WT + (int64_t)i * d, stage, 0, a.w_dense ? d : i + 1);
       if (lane == 0) a.z[i] = zi;
     }
     if (gsync()) return 1;
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
     __syncthreads();
     double part_rho = 0.0;
     for (int j = cw; j < d; j += nw) {
-      const double v = warp_row_dot(a.W + (int64_t)j * d, stage, j, d);
+      const double v = warp_row_dot(a.W + (int64_t)j * d, stage, a.w_dense ? 0 : j, d);
       if (lane == 0) {
         dst[j] = v;
         part_rho += v * src[j];
@@ -495,6 +496,7 @@ extern "C" void lsq_solve_opts_default(lsq_solve_opts* o) {
   o->a32 = nullptr;
   o->ld32 = 0;
   o->a32_copy = 1;
+  o->w_dense = 0;
 }
 
 lsq_status lsq_narrow_copy(lsq_ctx* ctx, const lsq_matrix* A, float* a32, int64_t ld32) {
@@ -629,6 +631,7 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   if (st != LSQ_OK) return st;
   Carver cv{reinterpret_cast<char*>(ctx->state), 0};
   SolveArgs a;
+  a.w_dense = 0;
   a.part = cv.take<double>((size_t)(dp + 1) * P);
   a.red = cv.take<double>((size_t)4 * P);
   a.r = cv.take<double>(dp);
@@ -683,6 +686,7 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   if (!refresh) {
     a.W = W;
     a.WT = WT;
+    a.w_dense = o.w_dense ? 1 : 0;
     transpose_kernel<<<dim3((d + 31) / 32, (d + 31) / 32), dim3(32, 8), 0, s>>>(W, d, WT);
     LSQ_LAUNCH_CHECK();
     LSQ_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, s));
