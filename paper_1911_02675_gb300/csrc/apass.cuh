@@ -106,6 +106,14 @@ __device__ __forceinline__ float narrow_f32(double x) {
 
 __device__ __forceinline__ float narrow_f32(float x) { return x; }
 
+// column of element k of a lane's row slice: lane + 32 k, or, at EPL >= 16, 128 (k / 4) + 4 lane + k % 4
+// (four adjacent columns per lane, the layout of the bulk-copy pass below, so both compute with
+// the same values in the same order)
+template <int EPL>
+__device__ __forceinline__ int f32_col(int k, int lane) {
+  return EPL >= 16 ? 128 * (k >> 2) + 4 * lane + (k & 3) : lane + 32 * k;
+}
+
 template <typename TA, int EPL>
 __device__ void fused_pass_f32(const TA* __restrict__ A, int64_t ld, int d, int dp, int64_t r0, int64_t r1,
                                const double* vec_s, double* wred, double* qred, double* part, int P, int cta) {
@@ -123,7 +131,7 @@ __device__ void fused_pass_f32(const TA* __restrict__ A, int64_t ld, int d, int 
   bool ok[EPL];
 #pragma unroll
   for (int k = 0; k < EPL; ++k) {
-    const int c = lane + 32 * k;
+    const int c = f32_col<EPL>(k, lane);
     ok[k] = c < d;
     if (PV_REG) pv[PV_REG ? k : 0] = ok[k] ? pf[c] : 0.0f;
     acc[k] = 0.0f;
@@ -133,13 +141,13 @@ __device__ void fused_pass_f32(const TA* __restrict__ A, int64_t ld, int d, int 
   if (PREFETCH && i < r1) {
     const TA* a = A + i * ld;
 #pragma unroll
-    for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
+    for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + f32_col<EPL>(k, lane)) : (TA)0;
   }
   for (; i < r1; i += LSQ_WARPS) {
     if (!PREFETCH) {
       const TA* a = A + i * ld;
 #pragma unroll
-      for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
+      for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + f32_col<EPL>(k, lane)) : (TA)0;
     }
     // narrow the row first (its raw registers die here), then put the next row in flight
     float af[EPL];
@@ -150,12 +158,12 @@ __device__ void fused_pass_f32(const TA* __restrict__ A, int64_t ld, int d, int 
       if (inext < r1) {
         const TA* a = A + inext * ld;
 #pragma unroll
-        for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + lane + 32 * k) : (TA)0;
+        for (int k = 0; k < EPL; ++k) cur[k] = ok[k] ? __ldg(a + f32_col<EPL>(k, lane)) : (TA)0;
       }
     }
     float w = 0.0f;
 #pragma unroll
-    for (int k = 0; k < EPL; ++k) w = fmaf(af[k], PV_REG ? pv[PV_REG ? k : 0] : pf[lane + 32 * k], w);
+    for (int k = 0; k < EPL; ++k) w = fmaf(af[k], PV_REG ? pv[PV_REG ? k : 0] : pf[f32_col<EPL>(k, lane)], w);
     w = warp_sumf(w);
 #pragma unroll
     for (int k = 0; k < EPL; ++k) acc[k] = fmaf(w, af[k], acc[k]);
@@ -164,7 +172,7 @@ __device__ void fused_pass_f32(const TA* __restrict__ A, int64_t ld, int d, int 
   __syncthreads();  // every warp is done with pf before wred is overwritten
 #pragma unroll
   for (int k = 0; k < EPL; ++k) {
-    const int c = lane + 32 * k;
+    const int c = f32_col<EPL>(k, lane);
     if (c < dp) wred[warp * dp + c] = (double)acc[k];
   }
   if (lane == 0) qred[warp] = q;
@@ -183,6 +191,148 @@ __device__ void fused_pass_f32(const TA* __restrict__ A, int64_t ld, int d, int 
   __syncthreads();
 }
 
+
+// ------------------------------------------------------------------------------------
+// The FP32 pass for wide FP32 rows (256 < d <= 1024, d a multiple of 4, 16-byte aligned rows)
+// with the rows staged by bulk copies: each warp keeps RING_NS of its rows in flight in a ring
+// of shared-memory slots, one cp.async.bulk per row started by lane 0 and counted in bytes on
+// the slot's mbarrier, instead of one row prefetched in registers.  The registers that frees
+// hold p, and the deeper queue keeps HBM busy with one 256-thread CTA per SM.  Lane l owns the
+// columns 128 k + 4 l + t (k < 8, t < 4) and reads them as eight 16-byte vectors per row.
+// Every wait is bounded: on a time-out the pass records LSQ_ERR_TIMEOUT, waits (bounded) for
+// its copies still in flight and returns; the caller checks the flag at its next barrier.
+// ------------------------------------------------------------------------------------
+constexpr int RING_NS = 4;
+constexpr uint32_t RING_SPIN = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32a(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ring_init(uint64_t* bars) {
+  // thread 0, before a CTA barrier: one arrival (the expect-tx) per phase
+  for (int e = 0; e < LSQ_WARPS * RING_NS; ++e)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32a(bars + e)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void ring_issue(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32a(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32a(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32a(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t spins = 0; spins < RING_SPIN; ++spins) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32a(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// ring: LSQ_WARPS x RING_NS slots of `slot_floats` floats; bars: LSQ_WARPS x RING_NS mbarriers;
+// phase: this thread's parity bits of its warp's slots (kept across passes by the caller)
+template <int EPL>
+__device__ inline void fused_pass_f32_ring(const float* __restrict__ A, int64_t ld, int d, int dp, int64_t r0,
+                                           int64_t r1, const double* vec_s, double* wred, double* qred, double* part,
+                                           int P, int cta, float* ring, int slot_floats, uint64_t* bars,
+                                           uint32_t& phase, int* err) {
+  static_assert(EPL == 16 || EPL == 32, "rows of 512 or 1024 padded columns");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* pf = reinterpret_cast<float*>(wred);
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) pf[c] = (float)vec_s[c];
+  __syncthreads();
+  float pv[EPL], acc[EPL];
+  bool okc[EPL / 4];
+#pragma unroll
+  for (int k = 0; k < EPL / 4; ++k) {
+    const int c0 = 128 * k + 4 * lane;
+    okc[k] = c0 < d;  // d is a multiple of 4: the four columns are in or out together
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      pv[4 * k + t] = okc[k] ? pf[c0 + t] : 0.0f;
+      acc[4 * k + t] = 0.0f;
+    }
+  }
+  double q = 0.0;
+  float* slots = ring + (size_t)warp * RING_NS * slot_floats;
+  uint64_t* bar = bars + warp * RING_NS;
+  const uint32_t bytes = (uint32_t)d * 4u;
+  const int64_t first = r0 + warp;
+  // rows first + LSQ_WARPS j of this warp; slot j % RING_NS
+  int64_t issued = 0, done = 0;
+  const int64_t nrows = first < r1 ? (r1 - first + LSQ_WARPS - 1) / LSQ_WARPS : 0;
+  for (; issued < nrows && issued < RING_NS; ++issued)
+    if (lane == 0) ring_issue(slots + issued * slot_floats, A + (first + LSQ_WARPS * issued) * ld, bytes, bar + issued);
+  bool good = true;
+  for (; done < nrows; ++done) {
+    const int s = (int)(done % RING_NS);
+    const bool landed = __all_sync(0xffffffffu, ring_wait(bar + s, (phase >> s) & 1u));
+    if (!landed) {
+      good = false;
+      break;
+    }
+    phase ^= 1u << s;
+    const float4* row = reinterpret_cast<const float4*>(slots + s * slot_floats);
+    float af[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL / 4; ++k) {
+      const float4 v = okc[k] ? row[32 * k + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      af[4 * k] = v.x;
+      af[4 * k + 1] = v.y;
+      af[4 * k + 2] = v.z;
+      af[4 * k + 3] = v.w;
+    }
+    __syncwarp();  // every lane has its values: the slot may be refilled
+    if (issued < nrows) {
+      if (lane == 0) ring_issue(slots + s * slot_floats, A + (first + LSQ_WARPS * issued) * ld, bytes, bar + s);
+      ++issued;
+    }
+    float w = 0.0f;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) w = fmaf(af[k], pv[k], w);
+    w = warp_sumf(w);
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) acc[k] = fmaf(w, af[k], acc[k]);
+    q = fma((double)w, (double)w, q);
+  }
+  if (!good) {
+    if (lane == 0) atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
+    // the copies still in flight land before the slots are given up (bounded)
+    for (; done < issued; ++done) {
+      const int s = (int)(done % RING_NS);
+      if (ring_wait(bar + s, (phase >> s) & 1u)) phase ^= 1u << s;
+    }
+  }
+  __syncthreads();  // every warp is done with pf before wred is overwritten
+#pragma unroll
+  for (int k = 0; k < EPL / 4; ++k) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int c = 128 * k + 4 * lane + t;
+      if (c < dp) wred[warp * dp + c] = (double)acc[4 * k + t];
+    }
+  }
+  if (lane == 0) qred[warp] = q;
+  __syncthreads();
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+    double s2 = 0.0;
+#pragma unroll
+    for (int w2 = 0; w2 < LSQ_WARPS; ++w2) s2 += wred[w2 * dp + c];
+    part[(int64_t)c * P + cta] = s2;
+  }
+  if (threadIdx.x == 0) {
+    double s2 = 0.0;
+    for (int w2 = 0; w2 < LSQ_WARPS; ++w2) s2 += qred[w2];
+    part[(int64_t)dp * P + cta] = s2;
+  }
+  __syncthreads();
+}
 
 // ------------------------------------------------------------------------------------
 // Exact pass in double-FP32 arithmetic (the residual replacements of the mixed solve).

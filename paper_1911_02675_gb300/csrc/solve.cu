@@ -57,6 +57,7 @@ struct SolveArgs {
   double* out;       // [0] iters, [1] status, [2] passes, [3] est_err, [4] exact passes
   const float* a32;  // COPY kernels: FP32 copy of A (row stride ld32) that the FP32 passes read
   int64_t ld32;
+  int ring;          // FP32 rows, 256 < d <= 1024: the FP32 passes stage rows by bulk copies
 };
 
 // out[i] = sum_k M[i*d + k] vec_s[k] for k in [k_lo(i), k_hi(i)), one warp per output
@@ -112,6 +113,17 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
   double* stage = S.wred + LSQ_WARPS * dp;  // dp: r or z staging for the triangular products
   S.qred = stage + dp;
   S.scal = S.qred + LSQ_WARPS;
+  // FP32 rows at the widest d (256 < d <= 1024): the bulk-copy ring of the FP32 passes (after the
+  // scalars, on a 128-byte boundary) and its mbarriers
+  constexpr bool RING = MIXED && EPL >= 16 && (COPY || sizeof(TA) == 4);
+  __shared__ __align__(8) uint64_t ring_bars[RING ? LSQ_WARPS * RING_NS : 1];
+  float* ring = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(S.scal + 8) + 127) & ~static_cast<uintptr_t>(127));
+  uint32_t ring_phase = 0;
+  if constexpr (RING) {
+    if (a.ring && threadIdx.x == 0) ring_init(ring_bars);
+    __syncthreads();
+  }
   // the staged exact pass (MIXED, FP64 A): x in wred[0, dp), one row slot per warp in
   // wred[dp, 8 dp) + stage
   double* slots = S.wred + dp;
@@ -215,6 +227,17 @@ __global__ void __launch_bounds__(LSQ_THREADS, (EPL <= 16 ? 2 : 1)) solve_kernel
   // an FP32 pass: over the FP32 copy of A (COPY), else narrowing the rows of A as they arrive;
   // both compute with the same FP32 values
   auto f32_pass = [&](const double* vec) {
+    if constexpr (RING) {
+      if (a.ring) {
+        if constexpr (COPY)
+          fused_pass_f32_ring<EPL>(a.a32, a.ld32, d, dp, r0, r1, vec, S.wred, S.qred, a.part, P, cta, ring, dp,
+                                   ring_bars, ring_phase, a.err);
+        else
+          fused_pass_f32_ring<EPL>(reinterpret_cast<const float*>(A), a.ld, d, dp, r0, r1, vec, S.wred, S.qred,
+                                   a.part, P, cta, ring, dp, ring_bars, ring_phase, a.err);
+        return;
+      }
+    }
     if constexpr (COPY) fused_pass_f32<float, EPL>(a.a32, a.ld32, d, dp, r0, r1, vec, S.wred, S.qred, a.part, P, cta);
     else fused_pass_f32<TA, EPL>(A, a.ld, d, dp, r0, r1, vec, S.wred, S.qred, a.part, P, cta);
   };
@@ -610,7 +633,13 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
                    ? (mixed ? (a32 ? pick_solve<double, true, true>(epl) : pick_solve<double, true>(epl))
                             : pick_solve<double, false>(epl))
                    : (mixed ? pick_solve<float, true>(epl) : pick_solve<float, false>(epl));
-  const size_t smem = solve_smem_bytes(dp);
+  // the FP32 passes of the widest rows stage them by bulk copies (16-byte aligned rows whose
+  // length is a multiple of 16 bytes)
+  const bool f32_rows = mixed && (a32 != nullptr || A->dtype == LSQ_F32);
+  const float* rows32 = a32 ? a32 : reinterpret_cast<const float*>(A->data);
+  const int64_t ld_rows = a32 ? ld32 : A->ld;
+  const bool ring = f32_rows && epl >= 16 && d % 4 == 0 && ((uintptr_t)rows32 % 16) == 0 && (ld_rows * 4) % 16 == 0;
+  const size_t smem = solve_smem_bytes(dp) + (ring ? 128 + (size_t)LSQ_WARPS * lsq_apass::RING_NS * dp * 4 : 0);
   LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LSQ_THREADS, smem));
@@ -668,6 +697,7 @@ extern "C" lsq_status lsq_solve(lsq_ctx* ctx, const lsq_matrix* A, const double*
   a.refresh_every = o.refresh_every > 0 ? o.refresh_every : 40;
   a.a32 = a32;
   a.ld32 = ld32;
+  a.ring = ring ? 1 : 0;
   // replace after a 10^5 drop of the residual norm: the FP32 passes' drift after it (about 1e-6
   // of that level) stays near 1e-11 of the initial residual, and convergence is confirmed on an
   // exact residual in any case
