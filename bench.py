@@ -746,6 +746,7 @@ def run_batch(args):
                        "iters_max": info["iters_max"], "passes": info["passes"], "exact_passes": info["exact_passes"],
                        "statuses": statuses, "rhs": sum(k for _, _, k in shapes),
                        "launch_phases_ms": info["ms_phase"],
+                       "pass_chunk_elems": info["pass_chunk_elems"], "pass_grid": info["pass_grid"],
                        "A_GiB": sum(a_bytes) / 2 ** 30},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": None, "kernel": "batch_kernel", "peak_kind": f"{peak_kind} (burst copy)",

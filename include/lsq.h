@@ -416,6 +416,11 @@ typedef struct {
   int32_t grid_blocks;      /* CTAs of the pass kernel (0: as many as are resident) */
   int32_t profile_phases;   /* 1: run the iterations without the CUDA graph and time each kernel
                                into lsq_batch_info.ms_phase (slower; for tuning) */
+  int32_t autotune;         /* 1 (default): on the first batch of a shape (the n, d and k of every
+                               problem) on a device, time one pass of the first iteration at each
+                               candidate work-unit size (2^19, 2^20, 2^21 elements of A) and pass
+                               grid (all resident CTAs, one per SM) that chunk_rows / grid_blocks
+                               leave open, and keep the fastest for the process */
 } lsq_batch_opts;
 
 typedef struct {
@@ -429,15 +434,20 @@ typedef struct {
   double ms_solve;       /* the persistent PCG launch */
   double ms_phase[8];    /* with opts.profile_phases: time in the pass, update, W^T r, W t and
                             direction kernels of the iterations ([5..7] unused); else zero */
+  int64_t pass_chunk_elems; /* the pass's work unit (elements of A per chunk) the iterations used */
+  int32_t pass_grid;        /* CTAs of the pass kernel the iterations used */
+  int32_t tuned;            /* 1 if this call ran the autotuner (first batch of its shape) */
 } lsq_batch_info;
 
 LSQ_API void lsq_batch_opts_default(lsq_batch_opts* opts);
 
 /* lsq_solve_batched: for every problem p (host array `probs` of nprob entries, device data),
  * draws its sketch (instance t = p), factors it (Cholesky of the Gram matrix, W = R^{-1}),
- * then runs PCG on all right-hand sides of all problems in lockstep iterations, each a CUDA graph
- * of kernels replayed from the host: one pass over A_p per active problem yields A_p^T (A_p P) for
- * all of its search directions at once, then the vector updates and W W^T per right-hand side.
+ * then runs PCG on all right-hand sides of all problems in lockstep iterations: one launch of a
+ * CUDA graph whose conditional WHILE node repeats the iteration's kernels until no problem is
+ * active or maxit iterations have run (decided on the device); per iteration, one pass over A_p
+ * per active problem yields A_p^T (A_p P) for all of its search directions at once, then the
+ * vector updates and W W^T per right-hand side.
  * A right-hand side stops by rule (1+sqrt(rho))^2 r^T H_S^{-1} r <= tol^2 <b, x> (as in
  * lsq_solve); a problem stops when all of its right-hand sides have. Under LSQ_PREC_MIXED the
  * passes run in FP32 with exact (double-FP32) residual replacement as in lsq_solve.

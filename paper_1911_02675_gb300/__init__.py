@@ -75,13 +75,15 @@ class LsqBatchOpts(ctypes.Structure):
     _fields_ = [("sketch_type", ctypes.c_int32), ("s", ctypes.c_int32), ("m_factor", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("sketch_precision", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("rho", ctypes.c_double), ("x0_zero", ctypes.c_int32), ("refresh_every", ctypes.c_int32),
-                ("chunk_rows", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("profile_phases", ctypes.c_int32)]
+                ("chunk_rows", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("profile_phases", ctypes.c_int32),
+                ("autotune", ctypes.c_int32)]
 
 
 class LsqBatchInfo(ctypes.Structure):
     _fields_ = [("iters_max", ctypes.c_int32), ("status", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("exact_passes", ctypes.c_int32), ("ms_total", ctypes.c_double), ("ms_sketch", ctypes.c_double),
-                ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double), ("ms_phase", ctypes.c_double * 8)]
+                ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double), ("ms_phase", ctypes.c_double * 8),
+                ("pass_chunk_elems", ctypes.c_int64), ("pass_grid", ctypes.c_int32), ("tuned", ctypes.c_int32)]
 
     def as_dict(self):
         out = {k: getattr(self, k) for k, _ in self._fields_}

@@ -20,7 +20,9 @@
 // in double-FP32 arithmetic, before its directions are updated.  Partial sums are reduced in a
 // fixed order (deterministic results).
 #include <algorithm>
+#include <map>
 #include <math.h>
+#include <mutex>
 #include <vector>
 
 #include "apass.cuh"
@@ -944,8 +946,10 @@ __global__ void __launch_bounds__(BT) bdir_kernel(BatchArgs a) {
     direction_block(a, pr, bk.y, it, exact_step(pr, it), a.anyx + (it + 1) % 3, a.cnt + (it + 1) % 3);
 }
 
-// end of an iteration: counters of the next one, then the iteration index
-__global__ void btick_kernel(BatchArgs a) {
+// end of an iteration: counters of the next one, then the iteration index; inside the
+// device-driven loop (use_cond) also whether the loop goes on: some problem is still active in
+// the next iteration and the iteration limit is not reached, so the loop always ends
+__global__ void btick_kernel(BatchArgs a, cudaGraphConditionalHandle cond, int use_cond) {
   const int it = *a.iter;
   a.stats[0] += 1;
   if (a.anyx[it % 3]) a.stats[1] += 1;
@@ -954,6 +958,13 @@ __global__ void btick_kernel(BatchArgs a) {
   a.cnt[(nx + 1) % 3] = 0;
   a.anyx[(nx + 1) % 3] = 0;
   *a.iter = nx;
+  if (use_cond) cudaGraphSetConditional(cond, (nx < a.maxit && a.cnt[nx % 3] > 0) ? 1u : 0u);
+}
+
+// before the device-driven loop: whether iteration 0 runs at all
+__global__ void bcond_kernel(BatchArgs a, cudaGraphConditionalHandle cond) {
+  const int it = *a.iter;
+  cudaGraphSetConditional(cond, (it < a.maxit && a.cnt[it % 3] > 0) ? 1u : 0u);
 }
 
 int kp_of(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 12 ? 12 : 16)); }
@@ -961,6 +972,76 @@ int dp_of(int d) {
   int e = 1;
   while (32 * e < d) e <<= 1;
   return 32 * e;
+}
+
+// The work units of the pass: chunks of rows (problem, row0, row1), the offsets of their
+// partial sums, each problem's first chunk and count, and the queue order (decreasing cost:
+// rows x columns, scaled by the directions per element under the FP32 arithmetic).
+struct ChunkPlan {
+  int64_t elems;  // target elements of A per chunk
+  std::vector<int4> chunks;
+  std::vector<int64_t> part_off;
+  std::vector<int> chunk0, nchunk, order;
+  int64_t part_total;
+};
+
+ChunkPlan plan_chunks(const lsq_problem* probs, int nprob, int chunk_rows_opt, int64_t elems, bool mixed) {
+  ChunkPlan pl;
+  pl.elems = elems;
+  pl.part_total = 0;
+  pl.chunk0.resize(nprob);
+  pl.nchunk.resize(nprob);
+  for (int p = 0; p < nprob; ++p) {
+    const int d = (int)probs[p].A.d, dp = dp_of(d), kp = kp_of(probs[p].k);
+    const int rows = chunk_rows_opt > 0 ? ((chunk_rows_opt + 31) / 32) * 32
+                                        : std::max<int>(256, (int)std::min<int64_t>(elems / dp, 1 << 30));
+    pl.chunk0[p] = (int)pl.chunks.size();
+    for (int64_t r0 = 0; r0 < probs[p].A.n; r0 += rows) {
+      pl.chunks.push_back(make_int4(p, (int)r0, (int)std::min<int64_t>(probs[p].A.n, r0 + rows), 0));
+      pl.part_off.push_back(pl.part_total);
+      pl.part_total += (int64_t)kp * dp + kp;
+    }
+    pl.nchunk[p] = (int)pl.chunks.size() - pl.chunk0[p];
+  }
+  const int nch = (int)pl.chunks.size();
+  pl.order.resize(nch);
+  std::vector<double> cost(nch);
+  for (int c = 0; c < nch; ++c) {
+    pl.order[c] = c;
+    const lsq_problem& q = probs[pl.chunks[c].x];
+    const double rows = pl.chunks[c].z - pl.chunks[c].y;
+    cost[c] = rows * (double)dp_of((int)q.A.d) * std::max(1.0, kp_of(q.k) / (mixed ? 6.0 : 1.0));
+  }
+  std::stable_sort(pl.order.begin(), pl.order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  return pl;
+}
+
+// The autotuner's choices, per device and batch shape (FNV-1a over the shapes), for the process
+struct TunedPass {
+  int64_t elems;
+  int grid;
+};
+std::mutex g_tuned_mu;
+std::map<uint64_t, TunedPass> g_tuned;
+
+uint64_t batch_signature(int device, const lsq_problem* probs, int nprob, int dtype, bool mixed) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xFFu;
+      h *= 1099511628211ull;
+    }
+  };
+  mix((uint64_t)device);
+  mix((uint64_t)dtype);
+  mix(mixed ? 1u : 0u);
+  mix((uint64_t)nprob);
+  for (int p = 0; p < nprob; ++p) {
+    mix((uint64_t)probs[p].A.n);
+    mix((uint64_t)probs[p].A.d);
+    mix((uint64_t)probs[p].k);
+  }
+  return h;
 }
 
 }  // namespace
@@ -979,6 +1060,7 @@ extern "C" void lsq_batch_opts_default(lsq_batch_opts* o) {
   o->chunk_rows = 0;
   o->grid_blocks = 0;
   o->profile_phases = 0;
+  o->autotune = 1;
 }
 
 extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem* probs, double tol, int32_t maxit,
@@ -1001,19 +1083,22 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     if (q.k < 1 || q.k > LSQ_MAX_RHS) return LSQ_ERR_ARG;
     const int64_t m = std::max<int64_t>(q.A.d, (int64_t)ceil(o.m_factor * (double)q.A.d));
   }
-  // work unit of the pass: about 2^20 elements of A (4 MB of FP32), at least 256 rows, so narrow
-  // problems do not spread over thousands of partial sums
-  auto chunk_rows_of = [&](int d) {
-    if (o.chunk_rows > 0) return ((o.chunk_rows + 31) / 32) * 32;
-    return std::max(256, (1 << 20) / dp_of(d));
-  };
+  // work unit of the pass: about `elems` elements of A (default 2^20, 4 MB of FP32), at least 256
+  // rows, so narrow problems do not spread over thousands of partial sums; the autotuner tries
+  // several sizes (and pass grids) on the first batch of a shape and keeps the fastest
+  std::vector<int64_t> elems_cand = {(int64_t)1 << 20};
+  if (o.chunk_rows <= 0 && o.autotune) elems_cand = {(int64_t)1 << 20, (int64_t)1 << 19, (int64_t)1 << 21};
+  std::vector<ChunkPlan> plans;
+  for (int64_t e : elems_cand) plans.push_back(plan_chunks(probs, nprob, o.chunk_rows, e, mixed));
+  size_t max_nch = 0;
+  int64_t max_part = 0;
+  for (const ChunkPlan& pl : plans) {
+    max_nch = std::max(max_nch, pl.chunks.size());
+    max_part = std::max(max_part, pl.part_total);
+  }
 
   // ---- layout of the state arena
-  std::vector<int4> chunks;
-  std::vector<int64_t> part_off;
   std::vector<int2> blocks;
-  std::vector<int> chunk0(nprob), nchunk(nprob);
-  int64_t part_total = 0;
   size_t need = 0;
   auto add = [&](size_t bytes) {
     const size_t at = need;
@@ -1044,17 +1129,9 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     f.st = add((size_t)kp * 4);
     f.it_last = add((size_t)kp * 4);
     f.pstate = add(32);
-    chunk0[p] = (int)chunks.size();
-    const int chunk_rows = chunk_rows_of(d);
-    for (int64_t r0 = 0; r0 < probs[p].A.n; r0 += chunk_rows) {
-      chunks.push_back(make_int4(p, (int)r0, (int)std::min<int64_t>(probs[p].A.n, r0 + chunk_rows), 0));
-      part_off.push_back(part_total);
-      part_total += (int64_t)kp * dp + kp;
-    }
-    nchunk[p] = (int)chunks.size() - chunk0[p];
     for (int b = 0; b < nblk; ++b) blocks.push_back(make_int2(p, b));
   }
-  const int nch = (int)chunks.size();
+  const ChunkPlan* plan = &plans[0];
 
   // ---- the pass kernel: dynamic shared memory for the largest problem shape
   void* kpass = dtype == LSQ_F64 ? (mixed ? (void*)bpass_kernel<double, true> : (void*)bpass_kernel<double, false>)
@@ -1069,29 +1146,19 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   int per_sm = 0;
   LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpass, PT, smem));
   if (per_sm < 1) return LSQ_ERR_CUDA;
-  int G = per_sm * ctx->sm_count;
+  const int G_full = per_sm * ctx->sm_count;
+  int G = G_full;
   if (o.grid_blocks > 0) G = std::min(G, o.grid_blocks);
-  G = std::max(1, std::min(G, nch));
-
-  // ---- the queue: chunks by decreasing cost (rows x columns, scaled by the directions per
-  // element under the FP32 arithmetic)
-  std::vector<int> order(nch);
-  std::vector<double> cost(nch);
-  for (int c = 0; c < nch; ++c) {
-    order[c] = c;
-    const lsq_problem& q = probs[chunks[c].x];
-    const double rows = chunks[c].z - chunks[c].y;
-    const double kp = kp_of(q.k);
-    cost[c] = rows * (double)dp_of((int)q.A.d) * std::max(1.0, kp / (mixed ? 6.0 : 1.0));
-  }
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  // the pass grids the autotuner tries: all resident CTAs, one per SM
+  std::vector<int> grid_cand = {G};
+  if (o.grid_blocks <= 0 && o.autotune && per_sm > 1) grid_cand.push_back(ctx->sm_count);
 
   const size_t o_probs = add(sizeof(BProb) * nprob);
-  const size_t o_chunks = add(sizeof(int4) * nch);
-  const size_t o_poff = add(sizeof(int64_t) * nch);
-  const size_t o_order = add(sizeof(int) * nch);
+  const size_t o_chunks = add(sizeof(int4) * max_nch);
+  const size_t o_poff = add(sizeof(int64_t) * max_nch);
+  const size_t o_order = add(sizeof(int) * max_nch);
   const size_t o_blocks = add(sizeof(int2) * blocks.size());
-  const size_t o_part = add((size_t)part_total * 8);
+  const size_t o_part = add((size_t)max_part * 8);
   const size_t o_ctl = add(256);
   std::vector<size_t> sa_off(nprob);
   for (int p = 0; p < nprob; ++p) {
@@ -1192,8 +1259,8 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
       const size_t es = q.A.dtype == LSQ_F64 ? 8 : 4;
       b.vec = (((uintptr_t)q.A.data % 16) == 0 && ((size_t)q.A.ld * es) % 16 == 0) ? 1 : 0;
     }
-    b.chunk0 = chunk0[p];
-    b.nchunk = nchunk[p];
+    b.chunk0 = plan->chunk0[p];
+    b.nchunk = plan->nchunk[p];
     b.B = q.B;
     b.X = q.X;
     b.W = reinterpret_cast<const double*>(base + f.W);
@@ -1220,9 +1287,16 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     b.tol2 = tol * tol / b.lam1;
   }
   LSQ_CUDA_TRY(cudaMemcpy(base + o_probs, hp.data(), sizeof(BProb) * nprob, cudaMemcpyHostToDevice));
-  LSQ_CUDA_TRY(cudaMemcpy(base + o_chunks, chunks.data(), sizeof(int4) * nch, cudaMemcpyHostToDevice));
-  LSQ_CUDA_TRY(cudaMemcpy(base + o_poff, part_off.data(), sizeof(int64_t) * nch, cudaMemcpyHostToDevice));
-  LSQ_CUDA_TRY(cudaMemcpy(base + o_order, order.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
+  // the chunk tables of a plan (the caller makes sure no pass still reads the old ones)
+  auto upload_plan = [&](const ChunkPlan& pl) -> lsq_status {
+    const size_t nc = pl.chunks.size();
+    LSQ_CUDA_TRY(cudaMemcpy(base + o_chunks, pl.chunks.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
+    LSQ_CUDA_TRY(cudaMemcpy(base + o_poff, pl.part_off.data(), sizeof(int64_t) * nc, cudaMemcpyHostToDevice));
+    LSQ_CUDA_TRY(cudaMemcpy(base + o_order, pl.order.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
+    return LSQ_OK;
+  };
+  st = upload_plan(*plan);
+  if (st != LSQ_OK) return st;
   LSQ_CUDA_TRY(cudaMemcpy(base + o_blocks, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice));
   LSQ_CUDA_TRY(cudaMemsetAsync(base + o_ctl, 0, 256, s));
 
@@ -1232,7 +1306,7 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   a.chunks = reinterpret_cast<const int4*>(base + o_chunks);
   a.part_off = reinterpret_cast<const int64_t*>(base + o_poff);
   a.order = reinterpret_cast<const int*>(base + o_order);
-  a.nchunks = nch;
+  a.nchunks = (int)plan->chunks.size();
   a.blocks = reinterpret_cast<const int2*>(base + o_blocks);
   a.nblocks = (int)blocks.size();
   a.part = reinterpret_cast<double*>(base + o_part);
@@ -1272,6 +1346,7 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     if (cudaGetLastError() != cudaSuccess) return LSQ_ERR_CUDA;    \
     if (timed) lsq_count_launch();                                 \
   } while (0)
+  cudaGraphConditionalHandle cond = 0;
   auto iteration = [&](bool timed) -> lsq_status {
     if (timed) cudaEventRecord(pe[0], s);
     lsq_status r = launch_pass(0, timed);
@@ -1288,7 +1363,7 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     if (timed) cudaEventRecord(pe[4], s);
     bdir_kernel<<<gblk, BT, 0, s>>>(a);
     ITER_CHECK();
-    btick_kernel<<<1, 1, 0, s>>>(a);
+    btick_kernel<<<1, 1, 0, s>>>(a, cond, timed ? 0 : 1);
     ITER_CHECK();
     if (timed) cudaEventRecord(pe[5], s);
     return LSQ_OK;
@@ -1320,40 +1395,132 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   binitdir_kernel<<<gblk, BT, 0, s>>>(a);
   LSQ_LAUNCH_CHECK();
 
-  // ---- iterations: one CUDA graph per iteration, replayed; the host looks at the count of
-  // active problems every `check` iterations
+  // ---- autotuner: on the first batch of this shape on this device, one timed pass (after a
+  // warm-up pass) of iteration 0 at each candidate chunk size and pass grid; the fastest is kept
+  // for the process.  A pass only writes its partial sums (the iteration's own pass rewrites
+  // them) and takes chunks from the iteration's queue head, which is reset after each trial.
+  int tuned = 0;
+  if (maxit > 0 && (plans.size() > 1 || grid_cand.size() > 1)) {
+    const uint64_t sig = batch_signature(ctx->device, probs, nprob, dtype, mixed);
+    TunedPass tp{plans[0].elems, grid_cand[0]};
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tuned_mu);
+      auto f = g_tuned.find(sig);
+      if (f != g_tuned.end()) {
+        tp = f->second;
+        have = true;
+      }
+    }
+    if (!have) {
+      cudaEvent_t t0, t1;
+      LSQ_CUDA_TRY(cudaEventCreate(&t0));
+      LSQ_CUDA_TRY(cudaEventCreate(&t1));
+      float best = 1e30f;
+      for (const ChunkPlan& pl : plans) {
+        LSQ_CUDA_TRY(cudaStreamSynchronize(s));  // no pass still reads the tables being replaced
+        st = upload_plan(pl);
+        if (st != LSQ_OK) return st;
+        a.nchunks = (int)pl.chunks.size();
+        for (int g : grid_cand) {
+          G = g;
+          for (int rep = 0; rep < 2; ++rep) {
+            LSQ_CUDA_TRY(cudaMemsetAsync(a.qhead, 0, sizeof(int), s));
+            if (rep == 1) LSQ_CUDA_TRY(cudaEventRecord(t0, s));
+            st = launch_pass(0, true);
+            if (st != LSQ_OK) return st;
+            if (rep == 1) LSQ_CUDA_TRY(cudaEventRecord(t1, s));
+          }
+          LSQ_CUDA_TRY(cudaEventSynchronize(t1));
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, t0, t1);
+          if (ms < best) {
+            best = ms;
+            tp = TunedPass{pl.elems, g};
+          }
+        }
+      }
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      std::lock_guard<std::mutex> lk(g_tuned_mu);
+      g_tuned[sig] = tp;
+      tuned = 1;
+    }
+    // the chosen plan and grid for the iterations
+    for (const ChunkPlan& pl : plans)
+      if (pl.elems == tp.elems) plan = &pl;
+    G = tp.grid;
+    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    st = upload_plan(*plan);
+    if (st != LSQ_OK) return st;
+    a.nchunks = (int)plan->chunks.size();
+    for (int p = 0; p < nprob; ++p) {
+      hp[p].chunk0 = plan->chunk0[p];
+      hp[p].nchunk = plan->nchunk[p];
+    }
+    LSQ_CUDA_TRY(cudaMemcpy(base + o_probs, hp.data(), sizeof(BProb) * nprob, cudaMemcpyHostToDevice));
+    LSQ_CUDA_TRY(cudaMemsetAsync(a.qhead, 0, sizeof(int), s));
+  }
+
+  // ---- iterations: one CUDA graph whose conditional WHILE node runs the iteration body (pass,
+  // update, the two triangular products, directions, tick) until no problem is active or maxit
+  // iterations have run -- the tick kernel decides on the device, so the whole loop is one
+  // launch with no host round trip.  With opts.profile_phases the host drives the iterations
+  // one by one instead, timing each kernel.
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  int it = 0;
   if (!prof && maxit > 0) {
-    // captured on the context's own non-blocking stream (the caller's may be the legacy
-    // default stream, which cannot be captured), replayed on the caller's stream
-    if (!ctx->capture) LSQ_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
+    LSQ_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    auto fail = [&](lsq_status r) {
+      if (graph) cudaGraphDestroy(graph);
+      (void)cudaGetLastError();
+      return r;
+    };
+    if (cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+      return fail(LSQ_ERR_CUDA);
+    // the first node sets the condition of iteration 0
+    cudaGraphNode_t kn;
+    cudaKernelNodeParams kp = {};
+    void* cargs[] = {&a, &cond};
+    kp.func = (void*)bcond_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = cargs;
+    if (cudaGraphAddKernelNode(&kn, graph, nullptr, 0, &kp) != cudaSuccess) return fail(LSQ_ERR_CUDA);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    if (cudaGraphAddNode(&wn, graph, &kn, nullptr, 1, &cp) != cudaSuccess) return fail(LSQ_ERR_CUDA);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // the body is captured on the context's own non-blocking stream (the caller's may be the
+    // legacy default stream, which cannot be captured); the graph runs on the caller's stream
+    if (!ctx->capture && cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(LSQ_ERR_CUDA);
     const cudaStream_t s_user = s;
     s = ctx->capture;
-    LSQ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    st = iteration(false);
-    cudaGraph_t g2 = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(s, &g2);
-    s = s_user;
-    if (st != LSQ_OK || ce != cudaSuccess) {
-      if (g2) cudaGraphDestroy(g2);
-      (void)cudaGetLastError();
-      return st != LSQ_OK ? st : LSQ_ERR_CUDA;
+    if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      s = s_user;
+      return fail(LSQ_ERR_CUDA);
     }
-    graph = g2;
-    LSQ_CUDA_TRY(cudaGraphInstantiate(&gexec, graph, 0));
-  }
-  const int check = 4;
-  int it = 0;
-  int* host_cnt = ctx->host_status + 14;
-  while (it < maxit) {
-    // active problems for iteration it: cnt[it % 3]
-    if (it % check == 0) {
+    st = iteration(false);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &captured);
+    s = s_user;
+    if (st != LSQ_OK || ce != cudaSuccess) return fail(st != LSQ_OK ? st : LSQ_ERR_CUDA);
+    if (cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) return fail(LSQ_ERR_CUDA);
+    LSQ_CUDA_TRY(cudaGraphLaunch(gexec, s));
+  } else if (prof) {
+    int* host_cnt = ctx->host_status + 14;
+    while (it < maxit) {
+      // active problems for iteration it: cnt[it % 3]
       LSQ_CUDA_TRY(cudaMemcpyAsync(host_cnt, a.cnt + it % 3, sizeof(int), cudaMemcpyDeviceToHost, s));
       LSQ_CUDA_TRY(cudaStreamSynchronize(s));
       if (*host_cnt == 0) break;
-    }
-    if (prof) {
       st = iteration(true);
       if (st != LSQ_OK) return st;
       LSQ_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1362,11 +1529,8 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
         cudaEventElapsedTime(&t, pe[q], pe[q + 1]);
         ph[q] += t;
       }
-    } else {
-      LSQ_CUDA_TRY(cudaGraphLaunch(gexec, s));
-      for (int q = 0; q < 6; ++q) lsq_count_launch();
+      ++it;
     }
-    ++it;
   }
   if (gexec) cudaGraphExecDestroy(gexec);
   if (graph) cudaGraphDestroy(graph);
@@ -1385,6 +1549,9 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   LSQ_CUDA_TRY(cudaMemcpy(hdr, ctl, sizeof(hdr), cudaMemcpyDeviceToHost));
   passes += hdr[16];
   exact_passes += mixed ? hdr[17] : hdr[16];
+  // the device-driven loop launched the condition kernel and six kernels per iteration it ran
+  if (!prof && maxit > 0)
+    for (int q = 0; q < 1 + 6 * hdr[16]; ++q) lsq_count_launch();
   const int errc = hdr[20];
   // per-problem results
   int iters_max = 0;
@@ -1415,6 +1582,9 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
     info->ms_factor = ms_factor;
     info->ms_solve = ms_solve;
     for (int q = 0; q < 8; ++q) info->ms_phase[q] = q < 5 ? ph[q] : 0.0;
+    info->pass_chunk_elems = plan->elems;
+    info->pass_grid = G;
+    info->tuned = tuned;
   }
   return overall;
 }

@@ -118,3 +118,29 @@ def test_batch_one_column_problem_is_stable(L, ctx):
         X, per, info = L.lsq_solve_batched(ctx, dev, tol=1e-10, maxit=400, seed=1)
         assert info["status"] == 0, per
         assert per[1][0] <= 10, per
+
+
+def test_batch_autotuner_and_device_loop(L, ctx):
+    """The first call of a batch shape runs the autotuner (one timed pass per candidate work-unit
+    size and grid); the next call of the same shape reuses its choice; either way, and with the
+    autotuner off, every right-hand side reaches the tolerance and the device-driven loop reports
+    the iterations it ran."""
+    shapes = [(5000, 40, 3), (3000, 17, 1), (12000, 64, 6), (2500, 33, 16)]
+    data = W.make_batch(shapes, seed=77)
+    probs = [(to_dev(q["A"]), to_dev(q["B"])) for q in data]
+    xs = [np.stack([O.solve_direct(q["A"].astype(np.float64), q["B"][j]) for j in range(q["B"].shape[0])])
+          for q in data]
+    infos = []
+    for kw in ({}, {}, {"autotune": 0}):
+        X, per, info = L.lsq_solve_batched(ctx, probs, tol=1e-10, maxit=300, **kw)
+        assert info["status"] == 0 and all(st == 0 for _, st in per), (per, info)
+        for (q, Xp, xsp) in zip(data, X, xs):
+            A64 = q["A"].astype(np.float64)
+            for j in range(Xp.shape[0]):
+                assert O.rel_h_err(A64, Xp[j].cpu().numpy(), xsp[j]) <= 1e-10
+        assert info["iters_max"] == max(it for it, _ in per) and info["passes"] >= info["iters_max"]
+        infos.append(info)
+    assert infos[0]["tuned"] == 1 and infos[1]["tuned"] == 0 and infos[2]["tuned"] == 0
+    assert (infos[0]["pass_chunk_elems"], infos[0]["pass_grid"]) == (infos[1]["pass_chunk_elems"], infos[1]["pass_grid"])
+    assert infos[0]["pass_chunk_elems"] in (1 << 19, 1 << 20, 1 << 21)
+    assert infos[2]["pass_chunk_elems"] == 1 << 20
