@@ -54,13 +54,17 @@ SECONDARY = {"fp32_4194304x1024_gauss4096_pcg": "fp64_1048576x512_srht4096_pcg"}
 # launch), keyed by (A dtype, d, FP32 copy of A): scaled to a launch of the bench by its
 # algorithmic bytes (units processed: passes x rows), and reported only while the solve
 # sources hash to the captured ones.
-#   ("f64", 512, 2): n = 2^18, SRHT m = 4096, 25 passes of which 2 exact, the FP32 copy supplied by
-#   the sketch; ("f64", 512, 1) adds the solve's own narrow_copy_kernel<16> (1.554 GB).
+#   ("f32", 1024, 0): A 2^18 x 1024 FP32, Gaussian BF16 m = 4096, 36 passes of which 2 exact
+#   (profiles/solve_kernel_fp32_262144x1024_gauss4096.md);
+#   ("f64", 512, 2): A 2^18 x 512 FP64, SRHT m = 4096, 25 passes of which 2 exact, the FP32 copy
+#   supplied by the sketch (profiles/solve_kernel_mixed_262144x512_srht4096.md); ("f64", 512, 1)
+#   adds the solve's own narrow_copy_kernel<16> (1.554 GB, from a full capture of that kernel).
 SOLVE_TRAFFIC = {
-    "sources_sha256": "654f37a9fa44f45b95c5afc2f1f72269ec01fbce18c482a3e16a6ecb5b501c5a",
+    "sources_sha256": "232fc6a2a9527583b916724cc995f5cd03a73e448fb0ff63976da4503b756e84",
     "ratios": {
-        ("f64", 512, 2): (14554827000 + 35496960) / 14495514624,
-        ("f64", 512, 1): (1553537240 + 14554827000 + 35496960) / 16106127360,
+        ("f32", 1024, 0): (38972452000 + 49136640) / 38654705664,
+        ("f64", 512, 2): (14553740000 + 35124992) / 14495514624,
+        ("f64", 512, 1): (1553537240 + 14553740000 + 35124992) / 16106127360,
     },
 }
 
