@@ -34,6 +34,8 @@ struct lsq_ctx {
   cudaStream_t capture;    // non-blocking stream on which CUDA graphs are captured (lazily)
   cudaStream_t copy;       // non-blocking stream of lsq_upload_sketch's row copies (lazily)
   cudaEvent_t ev_copy;     // hand-over between the copy stream and the context stream
+  cudaStream_t aux;        // non-blocking stream of the tensor-core sketch's packing (lazily)
+  cudaEvent_t ev_aux[5];   // packed chunk ready (2), chunk's MMAs done (2), start (1)
   cudaEvent_t ev0, ev1;
 };
 
@@ -53,8 +55,9 @@ lsq_status lsq_defer_status(lsq_ctx* c, const int* err, int slot);
 lsq_status lsq_pending_enqueue(lsq_ctx* c);
 lsq_status lsq_pending_take(lsq_ctx* c);
 
-// Called by a sketch before it reads rows [r0, r1) of A (lsq_upload_sketch queues their copy).
-typedef lsq_status (*lsq_rows_hook)(void* user, int64_t r0, int64_t r1);
+// Called by a sketch before work on stream `consumer` reads rows [r0, r1) of A
+// (lsq_upload_sketch queues their copy and makes `consumer` wait for it).
+typedef lsq_status (*lsq_rows_hook)(void* user, int64_t r0, int64_t r1, cudaStream_t consumer);
 
 // Number of kernels this library has launched in the process (lsq_launch_count).
 void lsq_count_launch();

@@ -45,6 +45,12 @@ extern "C" lsq_status lsq_destroy(lsq_ctx* c) {
     cudaStreamDestroy(c->copy);
   }
   if (c->ev_copy) cudaEventDestroy(c->ev_copy);
+  if (c->aux) {
+    cudaStreamSynchronize(c->aux);
+    cudaStreamDestroy(c->aux);
+  }
+  for (cudaEvent_t e : c->ev_aux)
+    if (e) cudaEventDestroy(e);
   cudaFreeHost(c->host_status);
   cudaFree(c->dev_pending);
   cudaEventDestroy(c->ev0);

@@ -661,12 +661,19 @@ static lsq_status tc_sketch_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64
   const int64_t kb_per_split = (kb_chunk + splits - 1) / splits;
   const bool sj = sjlt_s > 0;
   const size_t hash_bytes = sj ? lsq_align256((size_t)A->n * sjlt_s * 4) + lsq_align256((size_t)A->n * 4) : 0;
-  const size_t need =
-      lsq_align256((size_t)kb_chunk * nct * blob) + lsq_align256((size_t)splits * m * d * 4) + 256 + hash_bytes;
+  // more than one chunk: two packed-chunk buffers, so that chunk k + 1 is packed (on the
+  // auxiliary stream) while the tensor cores work on chunk k
+  const int64_t nchunks = (kb_total + kb_chunk - 1) / kb_chunk;
+  const bool two = nchunks > 1;
+  const size_t pk_bytes = (size_t)kb_chunk * nct * blob;
+  const size_t need = lsq_align256(pk_bytes) * (two ? 2 : 1) + lsq_align256((size_t)splits * m * d * 4) + 256 +
+                      hash_bytes;
   lsq_status st = lsq_ensure_scratch(ctx, need);
   if (st != LSQ_OK) return st;
   Carver cv{reinterpret_cast<char*>(ctx->scratch), 0};
-  uint8_t* pk = cv.take<uint8_t>((size_t)kb_chunk * nct * blob);
+  uint8_t* pkb[2];
+  pkb[0] = cv.take<uint8_t>(pk_bytes);
+  pkb[1] = two ? cv.take<uint8_t>(pk_bytes) : pkb[0];
   float* part = cv.take<float>((size_t)splits * m * d);
   int* err = cv.take<int>(1);
   SjltHashes hs{nullptr, nullptr, 0, A->n};
@@ -678,23 +685,49 @@ static lsq_status tc_sketch_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64
     hs = SjltHashes{h, sg, sjlt_s, A->n};
   }
   LSQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  // the packing stream: the context stream, or the auxiliary one, which first waits for the work
+  // already queued on the context stream (it may write A)
+  cudaStream_t ps = ctx->stream;
+  if (two) {
+    if (!ctx->aux) LSQ_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : ctx->ev_aux)
+      if (!e) LSQ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    LSQ_CUDA_TRY(cudaEventRecord(ctx->ev_aux[4], ctx->stream));
+    LSQ_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_aux[4], 0));
+    ps = ctx->aux;
+  }
+  // on an early return the context stream still waits for everything queued on the packing stream
+  auto join = [&](lsq_status r) {
+    if (two && cudaEventRecord(ctx->ev_aux[4], ctx->aux) == cudaSuccess)
+      cudaStreamWaitEvent(ctx->stream, ctx->ev_aux[4], 0);
+    return r;
+  };
   const dim3 grid(tiles_m, nct, splits);
-  for (int64_t kb0 = 0; kb0 < kb_total; kb0 += kb_chunk) {
+  int64_t c = 0;
+  for (int64_t kb0 = 0; kb0 < kb_total; kb0 += kb_chunk, ++c) {
     const int64_t nkb = std::min(kb_chunk, kb_total - kb0);
     const int64_t row0 = kb0 * TC_KS;  // of A; grow0 + row0 in the whole matrix (the generator's index)
+    const int buf = (int)(c & 1);
+    uint8_t* pk = pkb[buf];
+    // the buffer was last read by the MMAs of chunk c - 2
+    if (two && c >= 2 && cudaStreamWaitEvent(ps, ctx->ev_aux[2 + buf], 0) != cudaSuccess) return join(LSQ_ERR_CUDA);
     if (rows_ready) {
-      st = rows_ready(hook_user, row0, std::min<int64_t>(A->n, row0 + nkb * TC_KS));
-      if (st != LSQ_OK) return st;
+      st = rows_ready(hook_user, row0, std::min<int64_t>(A->n, row0 + nkb * TC_KS), ps);
+      if (st != LSQ_OK) return join(st);
     }
     const int64_t units = nkb * 8 * (int64_t)nt * nct;
     const int pgrid = (int)std::min<int64_t>((units + 255) / 256, 16 * (int64_t)ctx->sm_count);
     if (A->dtype == LSQ_F64)
-      pack_kernel<double><<<pgrid, 256, 0, ctx->stream>>>(reinterpret_cast<const double*>(A->data), A->n, d, A->ld,
-                                                          row0, nkb, nt, nct, pk);
+      pack_kernel<double><<<pgrid, 256, 0, ps>>>(reinterpret_cast<const double*>(A->data), A->n, d, A->ld, row0, nkb,
+                                                 nt, nct, pk);
     else
-      pack_kernel<float><<<pgrid, 256, 0, ctx->stream>>>(reinterpret_cast<const float*>(A->data), A->n, d, A->ld,
-                                                         row0, nkb, nt, nct, pk);
-    LSQ_LAUNCH_CHECK();
+      pack_kernel<float><<<pgrid, 256, 0, ps>>>(reinterpret_cast<const float*>(A->data), A->n, d, A->ld, row0, nkb, nt,
+                                                nct, pk);
+    if (cudaGetLastError() != cudaSuccess) return join(LSQ_ERR_CUDA);
+    lsq_count_launch();
+    if (two && (cudaEventRecord(ctx->ev_aux[buf], ps) != cudaSuccess ||
+                cudaStreamWaitEvent(ctx->stream, ctx->ev_aux[buf], 0) != cudaSuccess))
+      return join(LSQ_ERR_CUDA);
     const int acc = kb0 > 0 ? 1 : 0;
     // the Gaussian generator indexes rows of the whole matrix; the SJLT's hashes are A's own rows
     const int64_t r0 = sj ? row0 : grow0 + row0;
@@ -708,7 +741,8 @@ static lsq_status tc_sketch_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64
     else
       st = sj ? launch_tc<256, 4, 1, true>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs)
               : launch_tc<256, 4, 1, false>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs);
-    if (st != LSQ_OK) return st;
+    if (st != LSQ_OK) return join(st);
+    if (two && cudaEventRecord(ctx->ev_aux[2 + buf], ctx->stream) != cudaSuccess) return join(LSQ_ERR_CUDA);
   }
   const int64_t md = (int64_t)m * d;
   const int rgrid = (int)std::min<int64_t>((md + 255) / 256, 4 * (int64_t)ctx->sm_count);

@@ -1476,7 +1476,7 @@ struct ChunkUpload {
   bool started;
 };
 
-static lsq_status chunk_upload(void* user, int64_t r0, int64_t r1) {
+static lsq_status chunk_upload(void* user, int64_t r0, int64_t r1, cudaStream_t consumer) {
   ChunkUpload* cu = static_cast<ChunkUpload*>(user);
   lsq_ctx* ctx = cu->ctx;
   if (!cu->started) {
@@ -1489,7 +1489,7 @@ static lsq_status chunk_upload(void* user, int64_t r0, int64_t r1) {
   lsq_status st = upload_rows(cu->up, cu->A, r0, r1, ctx->copy);
   if (st != LSQ_OK) return st;
   LSQ_CUDA_TRY(cudaEventRecord(ctx->ev_copy, ctx->copy));
-  LSQ_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_copy, 0));
+  LSQ_CUDA_TRY(cudaStreamWaitEvent(consumer, ctx->ev_copy, 0));
   return LSQ_OK;
 }
 
