@@ -253,13 +253,14 @@ def _as_f64(A):
     return A if A.dtype == np.float64 else A.astype(np.float64)
 
 
-def oracle_estimate(args, P, A64=None, sketch_rows=16):
+def oracle_estimate(args, P, A64=None, sketch_rows=None):
     """Oracle time (ms) per solve of the workload: sketch + factor + PCG on the host cores.
 
     * up to 2^20 rows, a Gaussian sketch within GAUSS_ORACLE_FULL_LIMIT multiply-adds, or another
       sketch: the whole workload (above 2^20 rows: the first 2^20 rows, the O(n) phases scaled);
-    * a larger Gaussian sketch: `sketch_rows` rows of S timed over all n rows and scaled by
-      m / sketch_rows (the oracle's sketch is a plain triple loop); the factor timed on an m x d
+    * a larger Gaussian sketch: `sketch_rows` rows of S (default: one per oracle thread, so every
+      core works as in the whole sketch) timed over all n rows and scaled by m / sketch_rows (the
+      oracle's sketch is a plain triple loop, parallel over rows of S); the factor timed on an m x d
       matrix; the iterations as (T + 1) passes over all of A, T = ceil(log(4/tol^2)/log(m/d)) the
       iteration count Section 6 predicts, one pass timed as the mean of two."""
     import oracle as O
@@ -268,6 +269,7 @@ def oracle_estimate(args, P, A64=None, sketch_rows=16):
     A64 = _as_f64(P["A"]) if A64 is None else A64
     b = P["b"]
     if args.sketch == "gauss" and float(m) * n * d > GAUSS_ORACLE_FULL_LIMIT:
+        sketch_rows = min(m, sketch_rows or max(16, O.num_threads()))
         rows = np.linspace(0, m - 1, sketch_rows).astype(np.int64)
         t0 = time.perf_counter()
         O.sketch_gauss_rows(A64, m, 0, rows)
@@ -340,10 +342,10 @@ def run_reference(args):
     A64 = _as_f64(P["A"])
     times = []
     for _ in range(args.warmup):
-        oracle_estimate(args, P, A64, sketch_rows=8)
+        oracle_estimate(args, P, A64)
     sample, cores = "", 0
     for _ in range(args.steps):
-        ms, sample, cores = oracle_estimate(args, P, A64, sketch_rows=8)
+        ms, sample, cores = oracle_estimate(args, P, A64)
         times.append(ms)
     value = statistics.median(times)
     line = {
