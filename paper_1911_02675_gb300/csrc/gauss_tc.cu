@@ -269,8 +269,8 @@ __global__ void __launch_bounds__(256) pack_kernel(const TA* __restrict__ A, int
 // w owns tile rows 8w .. 8w + 7: per stage it zeroes them and writes the entries that land
 // there, so no warp waits on another.  Every product is exact and the FP32 accumulation runs
 // in a fixed order, so the sketch repeats bit for bit.
-template <int NT, int STAGES, int CL, bool SJ>
-__global__ void __launch_bounds__(TC_GEN + 32, 1)
+template <int NT, int STAGES, int BS, int CL, bool SJ>
+__global__ void __launch_bounds__(TC_GEN + 64, 1)
     gauss_tc_kernel(const uint8_t* __restrict__ pk, int64_t nkb, int nct, int d, int m, uint64_t seed, uint32_t t,
                     int64_t row0, int64_t kb_per_split, int accumulate, float* __restrict__ part, int* err,
                     const int32_t* __restrict__ hsj, const uint32_t* __restrict__ ssj, int s_sj, int64_t n_rows) {
@@ -285,8 +285,9 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
   constexpr uint32_t HALF_A = A_BYTES / 2;        // one CTA's part of a stage of S (CL = 2)
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * A_BYTES;
-  __shared__ __align__(8) uint64_t full[STAGES];
+  uint8_t* sB = smem + STAGES * A_BYTES;  // BS slots of the B operand (blobs of A)
+  __shared__ __align__(8) uint64_t full[BS];
+  __shared__ __align__(8) uint64_t bempty[BS];  // this CTA's MMAs that read the B slot are done
   __shared__ __align__(8) uint64_t gen[STAGES];
   __shared__ __align__(8) uint64_t sfull[STAGES];
   __shared__ __align__(8) uint64_t empty[STAGES];
@@ -301,8 +302,11 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
 
   if (warp == 0) tmem_alloc(&tmem_base_s, NT);
   if (tid == 0) {
+    for (int b = 0; b < BS; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&bempty[b], 1);
+    }
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
       mbar_init(&gen[s], GW);
       mbar_init(&sfull[s], 1);
       mbar_init(&empty[s], CL);
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
   const uint32_t tmem = tmem_base_s;
   bool ok = true;
   int64_t copies = 0;  // bulk copies of blobs started (MMA warp)
-  int64_t armed = 0;   // CL = 2: stages armed for the other CTA's half of S (MMA warp)
+  int64_t armed = 0;   // CL = 2: stages armed for the other CTA's half of S (exchange warp)
 
   if (SJ && warp < GW) {
     // ---- SJLT generators.  Per stage: warp w zeroes tile rows 8w .. 8w + 7 of this CTA's
@@ -449,38 +453,29 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive_local(&gen[s]);
     }
-  } else {
-    // ---- copies and MMAs: the whole warp waits, lane 0 issues
-    for (int64_t step = 0; step < nsteps; ++step) {
-      const int s = (int)(step % STAGES);
-      if (step >= STAGES &&
-          !__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((step / STAGES) - 1) & 1), err))) {
-        ok = false;
-        break;
-      }
-      uint8_t* stA = sA + s * A_BYTES;
-      uint8_t* stB = sB + s * B_BYTES;
+  } else if (warp == GW) {
+    // ---- copies and MMAs: the whole warp waits, lane 0 issues.  The B operand has a ring of its
+    // own (BS slots): blob k + BS - 1 is copied into the slot of blob k - 1 right after the MMAs of
+    // step k are issued and those of step k - 1 are done, so a copy has BS - 1 steps of MMAs to
+    // land.  The S slots are the generators' and the exchange warp's to wait for.
+    auto blob = [&](int64_t k) { return pk + ((size_t)(kb_begin + k) * nct + ct) * (size_t)B_BYTES; };
+    for (int64_t k = 0; k < nsteps && k < BS; ++k) {
       if (lane == 0) {
-        mbar_expect_tx(&full[s], (uint32_t)B_BYTES);
-        bulk_g2s(stB, pk + ((size_t)(kb_begin + step) * nct + ct) * (size_t)B_BYTES, (uint32_t)B_BYTES, &full[s]);
+        mbar_expect_tx(&full[k], (uint32_t)B_BYTES);
+        bulk_g2s(sB + k * B_BYTES, blob(k), (uint32_t)B_BYTES, &full[k]);
       }
       ++copies;
+    }
+    for (int64_t step = 0; step < nsteps; ++step) {
+      const int s = (int)(step % STAGES);
+      const int b = (int)(step % BS);
+      uint8_t* stA = sA + s * A_BYTES;
+      uint8_t* stB = sB + b * B_BYTES;
       const uint32_t par = (uint32_t)((step / STAGES) & 1);
       bool got = mbar_wait_bounded(&gen[s], par, err);
-      if constexpr (CL > 1) {
-        if (lane == 0) {
-          // this CTA's half of S to the other CTA (its stage s is free: `empty` counted its
-          // commit too), and this CTA expects the other half
-          const uint32_t peer = rank ^ 1u;
-          if (got) bulk_s2peer(peer_addr(smem_u32(stA + rank * HALF_A), peer), stA + rank * HALF_A, HALF_A,
-                               peer_addr(smem_u32(&sfull[s]), peer));
-          mbar_expect_tx(&sfull[s], HALF_A);
-        }
-        ++armed;
-        __syncwarp();
-        got = got && mbar_wait_cluster_bounded(&sfull[s], par, err);
-      }
-      got = got && mbar_wait_bounded(&full[s], par, err);
+      // CL = 2: the other CTA's half of S, sent by its exchange warp
+      if constexpr (CL > 1) got = got && mbar_wait_cluster_bounded(&sfull[s], par, err);
+      got = got && mbar_wait_bounded(&full[b], (uint32_t)((step / BS) & 1), err);
       if (!__all_sync(0xffffffffu, got)) {
         ok = false;
         break;
@@ -498,8 +493,49 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
         }
         if constexpr (CL > 1) mma_commit_mc(&empty[s], (uint16_t)((1u << CL) - 1u));
         else mma_commit(&empty[s]);
+        mma_commit(&bempty[b]);
       }
       __syncwarp();
+      // refill the B slot of step - 1 with blob step - 1 + BS once that step's MMAs are done
+      if (step >= 1 && step - 1 + BS < nsteps) {
+        const int bp = (int)((step - 1) % BS);
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bempty[bp], (uint32_t)(((step - 1) / BS) & 1), err))) {
+          ok = false;
+          break;
+        }
+        if (lane == 0) {
+          mbar_expect_tx(&full[bp], (uint32_t)B_BYTES);
+          bulk_g2s(sB + bp * B_BYTES, blob(step - 1 + BS), (uint32_t)B_BYTES, &full[bp]);
+        }
+        ++copies;
+      }
+    }
+  } else if (CL > 1 && warp == GW + 1) {
+    // ---- exchange (CL = 2): as soon as this CTA's generators have written their half of a
+    // stage, one shared-to-shared bulk copy sends it to the other CTA (whose stage s is free:
+    // `empty` counts both CTAs' MMA commits), and the stage is armed for the other half
+    for (int64_t step = 0; step < nsteps; ++step) {
+      const int s = (int)(step % STAGES);
+      const uint32_t par = (uint32_t)((step / STAGES) & 1);
+      if (step >= STAGES &&
+          !__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((step / STAGES) - 1) & 1), err))) {
+        ok = false;
+        break;
+      }
+      const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&gen[s], par, err));
+      if (lane == 0) {
+        uint8_t* stA = sA + s * A_BYTES;
+        const uint32_t peer = rank ^ 1u;
+        if (got) bulk_s2peer(peer_addr(smem_u32(stA + rank * HALF_A), peer), stA + rank * HALF_A, HALF_A,
+                             peer_addr(smem_u32(&sfull[s]), peer));
+        mbar_expect_tx(&sfull[s], HALF_A);
+      }
+      ++armed;
+      __syncwarp();
+      if (!got) {
+        ok = false;
+        break;
+      }
     }
   }
   // all MMAs done: the final phase of every stage counts the last commits of every CTA
@@ -508,16 +544,18 @@ __global__ void __launch_bounds__(TC_GEN + 32, 1)
     const int64_t first = nsteps > STAGES ? nsteps - STAGES : 0;
     for (int64_t st = first; st < nsteps && ok; ++st)
       ok = mbar_wait_bounded(&empty[st % STAGES], (uint32_t)((st / STAGES) & 1), err);
+    // and this CTA's own last MMAs, through the B slot commit of the last step
+    if (ok) ok = mbar_wait_bounded(&bempty[(nsteps - 1) % BS], (uint32_t)(((nsteps - 1) / BS) & 1), err);
   }
   ok = !__syncthreads_or(!ok);
-  if (!ok && warp == GW) {
-    // a failed run may leave bulk copies in flight (blobs, and the other CTA's halves of S
-    // into this CTA): wait (bounded) for each stage's last one
-    for (int64_t c = (copies > STAGES ? copies - STAGES : 0); c < copies; ++c)
-      (void)mbar_wait_bounded(&full[c % STAGES], (uint32_t)((c / STAGES) & 1), err);
+  // a failed run may leave bulk copies in flight (blobs, and the other CTA's halves of S into
+  // this CTA): wait (bounded) for each slot's last one
+  if (!ok && warp == GW)
+    for (int64_t c = (copies > BS ? copies - BS : 0); c < copies; ++c)
+      (void)mbar_wait_bounded(&full[c % BS], (uint32_t)((c / BS) & 1), err);
+  if (!ok && warp == GW + 1)
     for (int64_t c = (armed > STAGES ? armed - STAGES : 0); c < armed; ++c)
       (void)mbar_wait_bounded(&sfull[c % STAGES], (uint32_t)((c / STAGES) & 1), err);
-  }
   __syncwarp();
   tc_fence_after();
   if (warp < GW) {
@@ -589,21 +627,21 @@ struct SjltHashes {
   int64_t n;
 };
 
-template <int NT, int STAGES, int CL, bool SJ>
+template <int NT, int STAGES, int BS, int CL, bool SJ>
 lsq_status launch_tc(lsq_ctx* ctx, dim3 grid, const uint8_t* pk, int64_t nkb, int nct, int d, int m, uint64_t seed,
                      uint32_t t, int64_t row0, int64_t kb_per_split, int accumulate, float* part, int* err,
                      const SjltHashes& hs) {
-  const size_t smem = (size_t)STAGES * (TC_M * TC_KS * 2 + NT * TC_KS * 2);
-  auto k = gauss_tc_kernel<NT, STAGES, CL, SJ>;
+  const size_t smem = (size_t)STAGES * (TC_M * TC_KS * 2) + (size_t)BS * (NT * TC_KS * 2);
+  auto k = gauss_tc_kernel<NT, STAGES, BS, CL, SJ>;
   LSQ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (CL == 1) {
-    k<<<grid, TC_GEN + 32, smem, ctx->stream>>>(pk, nkb, nct, d, m, seed, t, row0, kb_per_split, accumulate, part,
+    k<<<grid, TC_GEN + (CL > 1 ? 64 : 32), smem, ctx->stream>>>(pk, nkb, nct, d, m, seed, t, row0, kb_per_split, accumulate, part,
                                                 err, hs.h, hs.sgn, hs.s, hs.n);
   } else {
     // clusters of CL CTAs along the column tiles (grid.y is a multiple of CL)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
-    cfg.blockDim = dim3(TC_GEN + 32);
+    cfg.blockDim = dim3(TC_GEN + 64);  // a CTA pair: the generators, the MMA warp and the exchange warp
     cfg.dynamicSmemBytes = smem;
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];
@@ -733,14 +771,14 @@ static lsq_status tc_sketch_run(lsq_ctx* ctx, const lsq_matrix* A, int m, uint64
     const int64_t r0 = sj ? row0 : grow0 + row0;
     // a CTA pair shares S when d needs two 512-column tiles (nt = 256 only for d <= 256)
     if (nt == 512 && nct % 2 == 0)
-      st = sj ? launch_tc<512, 2, 2, true>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs)
-              : launch_tc<512, 2, 2, false>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs);
+      st = sj ? launch_tc<512, 2, 3, 2, true>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs)
+              : launch_tc<512, 2, 3, 2, false>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs);
     else if (nt == 512)
-      st = sj ? launch_tc<512, 2, 1, true>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs)
-              : launch_tc<512, 2, 1, false>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs);
+      st = sj ? launch_tc<512, 2, 3, 1, true>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs)
+              : launch_tc<512, 2, 3, 1, false>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs);
     else
-      st = sj ? launch_tc<256, 4, 1, true>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs)
-              : launch_tc<256, 4, 1, false>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs);
+      st = sj ? launch_tc<256, 4, 4, 1, true>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs)
+              : launch_tc<256, 4, 4, 1, false>(ctx, grid, pk, nkb, nct, d, m, seed, t, r0, kb_per_split, acc, part, err, hs);
     if (st != LSQ_OK) return join(st);
     if (two && cudaEventRecord(ctx->ev_aux[2 + buf], ctx->stream) != cudaSuccess) return join(LSQ_ERR_CUDA);
   }
