@@ -591,6 +591,8 @@ __global__ void __launch_bounds__(PT, 1) bpass_kernel(BatchArgs a, int force_exa
   }
 }
 
+#include "bring.cuh"
+
 // sum of the chunk partials of problem pr at offset `off` within each chunk's block (fixed
 // order); a problem's chunks are consecutive and their partial blocks equally spaced
 __device__ __forceinline__ double chunk_sum(const BatchArgs& a, const BProb& pr, int off) {
@@ -1134,17 +1136,28 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   const ChunkPlan* plan = &plans[0];
 
   // ---- the pass kernel: dynamic shared memory for the largest problem shape
-  void* kpass = dtype == LSQ_F64 ? (mixed ? (void*)bpass_kernel<double, true> : (void*)bpass_kernel<double, false>)
-                                 : (mixed ? (void*)bpass_kernel<float, true> : (void*)bpass_kernel<float, false>);
+  // FP32 A in the mixed precision with contiguous, 16-byte aligned rows: the ring pass (rows
+  // staged by bulk copies); otherwise the tiled pass
+  bool ring = dtype == LSQ_F32 && mixed;
+  for (int p = 0; p < nprob && ring; ++p)
+    ring = probs[p].A.ld == probs[p].A.d && ((uintptr_t)probs[p].A.data % 16) == 0;
+  void* kpass = ring ? (void*)bpass_ring_kernel
+                     : dtype == LSQ_F64 ? (mixed ? (void*)bpass_kernel<double, true> : (void*)bpass_kernel<double, false>)
+                                        : (mixed ? (void*)bpass_kernel<float, true> : (void*)bpass_kernel<float, false>);
+  const int pass_threads = ring ? RT : PT;
   size_t smem = 0;
-  for (int p = 0; p < nprob; ++p) {
-    const int dpp = dp_of((int)probs[p].A.d), kpp = kp_of(probs[p].k);
-    smem = std::max(smem, pass_smem_shape(mixed, dtype == LSQ_F64, dpp, kpp));
+  if (ring) {
+    smem = RSMEM;
+  } else {
+    for (int p = 0; p < nprob; ++p) {
+      const int dpp = dp_of((int)probs[p].A.d), kpp = kp_of(probs[p].k);
+      smem = std::max(smem, pass_smem_shape(mixed, dtype == LSQ_F64, dpp, kpp));
+    }
   }
   if (smem > 227 * 1024) return LSQ_ERR_ARG;
   LSQ_CUDA_TRY(cudaFuncSetAttribute(kpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpass, PT, smem));
+  LSQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpass, pass_threads, smem));
   if (per_sm < 1) return LSQ_ERR_CUDA;
   const int G_full = per_sm * ctx->sm_count;
   int G = G_full;
@@ -1330,7 +1343,7 @@ extern "C" lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem
   const int gblk = (nbk + BW - 1) / BW;
   auto launch_pass = [&](int force_exact, bool count) -> lsq_status {
     void* args[] = {&a, &force_exact};
-    LSQ_CUDA_TRY(cudaLaunchKernel(kpass, dim3(G), dim3(PT), args, smem, s));
+    LSQ_CUDA_TRY(cudaLaunchKernel(kpass, dim3(G), dim3(pass_threads), args, smem, s));
     if (count) lsq_count_launch();
     return LSQ_OK;
   };

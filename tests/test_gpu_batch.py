@@ -144,3 +144,29 @@ def test_batch_autotuner_and_device_loop(L, ctx):
     assert (infos[0]["pass_chunk_elems"], infos[0]["pass_grid"]) == (infos[1]["pass_chunk_elems"], infos[1]["pass_grid"])
     assert infos[0]["pass_chunk_elems"] in (1 << 19, 1 << 20, 1 << 21)
     assert infos[2]["pass_chunk_elems"] == 1 << 20
+
+
+@pytest.mark.parametrize("x0", [False, True])
+def test_batch_mixed_first_iterations_follow_oracle(L, ctx, x0):
+    """Mixed precision over FP32 A (the pass whose rows are staged by bulk copies): the first
+    iterates follow the FP64 oracle's PCG on the same FP64 sketches to FP32 accuracy, from x0 = 0
+    (FP32 passes only) and from a nonzero x0 (the initial residual from the double-FP32 exact
+    pass).  Shapes take every column width class (dp 32 .. 512, 8 .. 32 lanes per row), every
+    padded count of right-hand sides, rows not a multiple of 4 elements, and problems larger than
+    one 32 KB stage and one work unit."""
+    shapes = [(3001, 37, 3), (5000, 64, 16), (1201, 130, 7), (4100, 200, 9), (999, 33, 4), (6000, 250, 12),
+              (2503, 31, 16), (1500, 300, 5), (70001, 19, 11), (9000, 511, 14)]
+    probs = W.make_batch(shapes, seed=21, scale_max=1e3, dtype=np.float32)
+    rng = np.random.default_rng(5)
+    X0 = [rng.standard_normal(q["B"].shape) for q in probs] if x0 else None
+    for T in (1, 3):
+        X, per, info = L.lsq_solve_batched(ctx, _dev(probs, np.float32), tol=0.0, maxit=T, precision="mixed",
+                                           sketch_precision="f64", seed=3, s=8,
+                                           X0=[to_dev(v) for v in X0] if x0 else None)
+        ref = O.solve_batched([(q["A"].astype(np.float64), q["B"]) for q in probs], kind="sjlt", s=8, m_factor=4.0,
+                              seed=3, tol=0.0, maxit=T, X0=X0)
+        for sh, Xp, (Xr, its, sts), (it, st) in zip(shapes, X, ref, per):
+            assert it == T and st == L.LSQ_ERR_MAXIT, (sh, it, st)
+            err = rel_fro(Xp.cpu().numpy() - (X0[shapes.index(sh)] if x0 else 0.0),
+                          Xr - (X0[shapes.index(sh)] if x0 else 0.0))
+            assert err < 1e-5, (sh, T, err)
