@@ -60,11 +60,11 @@ SECONDARY = {"fp32_4194304x1024_gauss4096_pcg": "fp64_1048576x512_srht4096_pcg"}
 #   supplied by the sketch (profiles/solve_kernel_mixed_262144x512_srht4096.md); ("f64", 512, 1)
 #   adds the solve's own narrow_copy_kernel<16> (1.554 GB, from a full capture of that kernel).
 SOLVE_TRAFFIC = {
-    "sources_sha256": "232fc6a2a9527583b916724cc995f5cd03a73e448fb0ff63976da4503b756e84",
+    "sources_sha256": "087cd550b9f9303f7f15ab8132e1f017e5b9befc536eae6e8c89f9d918b62795",
     "ratios": {
-        ("f32", 1024, 0): (38972452000 + 49136640) / 38654705664,
-        ("f64", 512, 2): (14553740000 + 35124992) / 14495514624,
-        ("f64", 512, 1): (1553537240 + 14553740000 + 35124992) / 16106127360,
+        ("f32", 1024, 0): (38971788544 + 48382720) / 38654705664,
+        ("f64", 512, 2): (14553791744 + 34407936) / 14495514624,
+        ("f64", 512, 1): (1553537240 + 14553791744 + 34407936) / 16106127360,
     },
 }
 
@@ -736,6 +736,28 @@ def run_batch(args):
     pass_bytes = sum(b * it for b, (it, _) in zip(a_bytes, per))
     achieved = pass_bytes / (solve_ms * 1e-3) / 1e9
     statuses = sorted(set(st for _, st in per))
+    # end to end: every problem's A and B copied from pinned host memory into HBM, the batched
+    # solve, every X read back to pinned host memory, all inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pins = [(A.cpu().pin_memory(), B.cpu().pin_memory()) for A, B in probs]
+        x_pins = [torch.empty(B.shape, dtype=torch.float64).pin_memory() for _, B in probs]
+
+        def e2e_once():
+            for (A, B), (Ah, Bh) in zip(probs, pins):
+                A.copy_(Ah, non_blocking=True)
+                B.copy_(Bh, non_blocking=True)
+            Xs, _, _ = solve_once()
+            for Xd, Xh in zip(Xs, x_pins):
+                Xh.copy_(Xd, non_blocking=True)
+
+        e2e_once()  # warm-up
+        e_ms = [t for t, _ in _time_calls(torch, dev, stream, e2e_once, max(1, min(args.steps, 3)))]
+        h2d = sum(A.numel() * A.element_size() + B.numel() * 8 for A, B in probs)
+        d2h = sum(B.numel() * 8 for _, B in probs)
+        del pins, x_pins
+        e2e = {"value": statistics.median(e_ms), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "path": "every A_p and B_p from pinned host memory, lsq_solve_batched, every X_p to host"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ms, sample, cores = oracle_batch_estimate(args, shapes)
@@ -757,7 +779,7 @@ def run_batch(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": None, "kernel": "batch_kernel", "peak_kind": f"{peak_kind} (burst copy)",
                          "algorithmic_bytes_per_launch": pass_bytes},
-            "cpu_baseline": cpu, "e2e": None, "clocks": clk.summary(), "gpu_launches": launches}), flush=True)
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": launches}), flush=True)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
