@@ -4,12 +4,11 @@
 // The same sums as pass_chunk / pass_chunk_df (part[j dp + c] = sum_rows a_c (a . p_j) and
 // q_j = sum_rows (a . p_j)^2, Section 1 eq. (PCG) per right-hand side), with a different
 // schedule: a chunk's rows stream into a ring of RNS shared-memory stages of 32 KB, one
-// cp.async.bulk per stage (the stage's element range rounded down to 16 bytes at both ends, the
-// last < 4 elements read by plain loads) counted in bytes on the stage's `full` mbarrier; the
-// eight warps release a stage on its `empty` mbarrier once they have read it, and lane 0 of warp 0
-// refills it with the stage RNS - 1 ahead before it reads the next one.  Warp w owns the right-hand sides jg JG .. jg JG + JG - 1 (jg = w mod J, J = kp / JG)
-// and every J-th group of rows; inside a warp, L = dp / EPL lanes share a row (32 / L rows at a
-// time) and lane l owns the columns l mod L + L e (e < EPL).  Per row: the lanes' partial dots
+// cp.async.bulk per stage (see rp_issue) counted in bytes on the stage's `full` mbarrier; the
+// eight warps release a stage on its `empty` mbarrier once they have read it, and thread 0 refills
+// it with the stage RNS - 1 ahead.  In the exact (SIMT) pass, warp w owns the right-hand sides
+// jg JG .. jg JG + JG - 1 (jg = w mod J, J = kp / JG) and every J-th group of rows; inside a
+// warp, L = dp / EPL lanes share a row (32 / L rows at a time) and lane l owns the columns l mod L + L e (e < EPL).  Per row: the lanes' partial dots
 // with their registers of P, a butterfly sum over the L lanes (every lane ends with all JG dots),
 // then acc += a y^T in registers -- no tile barriers and no shared-memory staging of Y.  The
 // exact pass takes the same schedule with the double-FP32 products and sums of pass_chunk_df.
@@ -68,9 +67,13 @@ __device__ __forceinline__ void rp_df_add_sym(float& ah, float& al, float bh, fl
 }
 
 // Puts stage t of the chunk [r0, r1) (R rows a stage) in flight into its slot, once the warps
-// have released the slot's previous stage: the stage's element range rounded out to 16 bytes
-// (rounded down at the end, with plain loads of the last < 4 elements, where rounding up would
-// read past the matrix).  Returns false if the wait for the slot gave up.
+// have released the slot's previous stage: the stage's element range and the 8 floats after it
+// (the tensor-core pass reads up to 7 of them, beside zeros of P: the matrix's own next row), the
+// range rounded out to 16 bytes.  Where that would read past the matrix, the copy stops at the
+// last 16-byte boundary, plain loads fetch the last < 4 elements and zeros fill the 8 floats after
+// them (so that stale floats of another problem never meet this one's products), and only then
+// does the thread need a proxy fence before its copy.  Returns false if the wait for the slot
+// gave up.
 __device__ __forceinline__ bool rp_issue(const float* A, int64_t n_elems, int d, int64_t r0, int64_t r1, int R, int t,
                                          uint32_t gs, float* ring, uint64_t* full, uint64_t* empty) {
   const uint32_t g = gs + (uint32_t)t;
@@ -80,20 +83,16 @@ __device__ __forceinline__ bool rp_issue(const float* A, int64_t n_elems, int d,
   const int64_t lo = r0 + (int64_t)t * R, hi = min(r1, lo + R);
   const int64_t e_lo = lo * d, e_hi = hi * d;
   const int64_t a_lo = e_lo & ~(int64_t)3;
-  int64_t a_hi = (e_hi + 3) & ~(int64_t)3;
+  int64_t a_hi = (e_hi + 8 + 3) & ~(int64_t)3;
   float* buf = ring + s * RSTAGE;
   if (a_hi > n_elems) {
     a_hi = e_hi & ~(int64_t)3;
     for (int64_t e = a_hi; e < e_hi; ++e) buf[e - a_lo] = __ldg(A + e);
-  }
-  // zeros in the 8 floats past what lands (the tensor-core pass reads up to 7 of them, beside
-  // zeros of P), so that stale floats of another problem never meet this one's products
-  {
-    const int z0 = (int)((a_hi > e_hi ? a_hi : e_hi) - a_lo);
+    const int z0 = (int)(e_hi - a_lo);
     for (int i = 0; i < 8; ++i) buf[z0 + i] = 0.f;
+    rp_fence_async();  // this thread's plain stores to the ring come before its copies
   }
   const uint32_t bytes = (uint32_t)(a_hi - a_lo) * 4u;
-  rp_fence_async();  // this thread's plain stores to the ring come before the copy
   if (bytes) lsq_apass::ring_issue(buf, A + a_lo, bytes, full + s);
   else rp_arrive(full + s);
   return true;
