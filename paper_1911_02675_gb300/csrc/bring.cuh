@@ -72,14 +72,16 @@ __device__ __forceinline__ void rp_df_add_sym(float& ah, float& al, float bh, fl
 // range rounded out to 16 bytes.  Where that would read past the matrix, the copy stops at the
 // last 16-byte boundary, plain loads fetch the last < 4 elements and zeros fill the 8 floats after
 // them (so that stale floats of another problem never meet this one's products), and only then
-// does the thread need a proxy fence before its copy.  Returns false if the wait for the slot
-// gave up.
+// does the thread need a proxy fence before its copy.  `released`: the caller knows that every
+// warp has released the slot (a CTA barrier after their arrivals), so its wait is skipped.
+// Returns false if the wait for the slot gave up.
 __device__ __forceinline__ bool rp_issue(const float* A, int64_t n_elems, int d, int64_t r0, int64_t r1, int R, int t,
-                                         uint32_t gs, float* ring, uint64_t* full, uint64_t* empty) {
+                                         uint32_t gs, float* ring, uint64_t* full, uint64_t* empty,
+                                         bool released = false) {
   const uint32_t g = gs + (uint32_t)t;
   const int s = (int)(g % RNS);
   const uint32_t u = g / RNS;
-  if (u >= 1 && !rp_wait(empty + s, (u - 1) & 1u)) return false;
+  if (!released && u >= 1 && !rp_wait(empty + s, (u - 1) & 1u)) return false;
   const int64_t lo = r0 + (int64_t)t * R, hi = min(r1, lo + R);
   const int64_t e_lo = lo * d, e_hi = hi * d;
   const int64_t a_lo = e_lo & ~(int64_t)3;
@@ -353,12 +355,12 @@ __device__ __forceinline__ int rp_chunk_mma(const BProb& pr, int64_t r0, int64_t
   const float* A = reinterpret_cast<const float*>(pr.A);
   int issued = 0;
   const bool prod = tid == 0;
-  auto issue = [&](int t) {
-    if (rp_issue(A, pr.n * d, d, r0, r1, R, t, gs, ring, full, empty)) ++issued;
+  auto issue = [&](int t, bool released) {
+    if (rp_issue(A, pr.n * d, d, r0, r1, R, t, gs, ring, full, empty, released)) ++issued;
     else *s_err = 1;
   };
   if (prod)
-    for (int t = 0; t < nst && t < RNS - 1 && !*s_err; ++t) issue(t);
+    for (int t = 0; t < nst && t < RNS - 1 && !*s_err; ++t) issue(t, false);
   // P fragments of this warp's k-steps, head and remainder: b0 = P[8 k + tq][8 nt + g],
   // b1 = P[8 k + tq + 4][..]; zero beyond d, so that the entries read there (the next row's, or
   // the zeros placed past the stage) add nothing
@@ -404,11 +406,24 @@ __device__ __forceinline__ int rp_chunk_mma(const BProb& pr, int64_t r0, int64_t
           for (int i = 0; i < 4; ++i) dh[nt][i] = d1[nt][i] = d2[nt][i] = 0.f;
         const float* pa = raw + (rt * 16 + g) * d + tq + k0 * 8;
         const float* pb = pa + 8 * d;
+        // the next k-step's fragment is loaded before this one's MMAs are issued
+        uint32_t an[4] = {0u, 0u, 0u, 0u};
+        if (nk > 0) {
+          an[0] = __float_as_uint(pa[0]);
+          an[1] = __float_as_uint(pb[0]);
+          an[2] = __float_as_uint(pa[4]);
+          an[3] = __float_as_uint(pb[4]);
+        }
 #pragma unroll
         for (int kk = 0; kk < RKMAX; ++kk) {
           if (kk < nk) {
-            const uint32_t a[4] = {__float_as_uint(pa[kk * 8]), __float_as_uint(pb[kk * 8]),
-                                   __float_as_uint(pa[kk * 8 + 4]), __float_as_uint(pb[kk * 8 + 4])};
+            const uint32_t a[4] = {an[0], an[1], an[2], an[3]};
+            if (kk + 1 < nk) {
+              an[0] = __float_as_uint(pa[kk * 8 + 8]);
+              an[1] = __float_as_uint(pb[kk * 8 + 8]);
+              an[2] = __float_as_uint(pa[kk * 8 + 12]);
+              an[3] = __float_as_uint(pb[kk * 8 + 12]);
+            }
             uint32_t ah[4], al[4];
             tf32_split4(a, ah, al);
 #pragma unroll
@@ -450,7 +465,7 @@ __device__ __forceinline__ int rp_chunk_mma(const BProb& pr, int64_t r0, int64_t
       break;
     }
     // every warp is past stage 2 of stage t - 1: its slot takes stage t + RNS - 1 without a wait
-    if (prod && t + RNS - 1 < nst && !*s_err) issue(t + RNS - 1);
+    if (prod && t + RNS - 1 < nst && !*s_err) issue(t + RNS - 1, t >= 1);
     if (KS > 1) {
       // ---- Y: the KS partial tiles in order; q; the split for stage 2
       for (int e = tid; e < R * KPAD; e += RT) {
