@@ -8,10 +8,11 @@
 // eight warps release a stage on its `empty` mbarrier once they have read it, and thread 0 refills
 // it with the stage RNS - 1 ahead.  In the exact (SIMT) pass, warp w owns the right-hand sides
 // jg JG .. jg JG + JG - 1 (jg = w mod J, J = kp / JG) and every J-th group of rows; inside a
-// warp, L = dp / EPL lanes share a row (32 / L rows at a time) and lane l owns the columns l mod L + L e (e < EPL).  Per row: the lanes' partial dots
-// with their registers of P, a butterfly sum over the L lanes (every lane ends with all JG dots),
-// then acc += a y^T in registers -- no tile barriers and no shared-memory staging of Y.  The
-// exact pass takes the same schedule with the double-FP32 products and sums of pass_chunk_df.
+// warp, L = dp / EPL lanes share a row (32 / L rows at a time) and lane l owns the columns
+// l mod L + L e (e < EPL).  Per row: the lanes' partial dots with their registers of X, a
+// butterfly sum over the L lanes (every lane ends with all JG dots), then acc += a y^T in
+// registers, all in the double-FP32 products and sums of pass_chunk_df.  The FP32 pass runs on
+// the tensor cores (rp_chunk_mma below).
 // Every wait is bounded; on a time-out the CTA records it, waits (bounded) for its copies still
 // in flight and stops.
 #pragma once
