@@ -508,7 +508,6 @@ constexpr int PT = 512;  // threads of a pass CTA (the other kernels use BT)
 // shared memory of the passes for one problem shape (the launch takes the maximum); mirrors
 // the layouts of pass_chunk and pass_chunk_df with PT threads
 __host__ __device__ inline size_t pass_smem_shape(bool mixed, bool a_f64, int dp, int KP) {
-  constexpr int W = PT / 32;
   auto tile = [&](size_t es, int TE) {
     const int tr = TE / dp;
     const int S = tr >= PT ? 1 : PT / tr;

@@ -25,7 +25,6 @@ constexpr int RSTAGE = 8256;           // floats per stage (16 rows of 512 and t
 // per-thread q (RQF)
 constexpr int RYP = 8 * 256, RY = 128 * 16, RQF = 256;
 constexpr size_t RSMEM = ((size_t)RNS * RSTAGE + RYP + 2 * RY + RQF) * 4;  // dynamic shared memory
-constexpr int RQSL = 32;               // row slices (RW x 32 / L at most): q partials kept per slice
 constexpr uint32_t RSPIN = 1u << 24;   // polls of a wait before it gives up
 
 __device__ __forceinline__ bool rp_wait(uint64_t* bar, uint32_t parity) {
@@ -101,11 +100,13 @@ __device__ __forceinline__ bool rp_issue(const float* A, int64_t n_elems, int d,
   return true;
 }
 
-// One chunk, rows [r0, r1) of problem pr, stages gs .. gs + nst - 1 of this CTA's ring.  Returns
-// the number of stages it used.  Called by every thread of the CTA.
-template <int EPL, int JG, bool EXACT>
-__device__ __forceinline__ int rp_chunk(const BProb& pr, int64_t r0, int64_t r1, double* __restrict__ out, float* ring,
-                                     uint64_t* full, uint64_t* empty, double* qred, uint32_t gs, volatile int* s_err) {
+// One exact (double-FP32) chunk, rows [r0, r1) of problem pr, stages gs .. gs + nst - 1 of this
+// CTA's ring: part[j dp + c] = sum_rows a_c (a . x_j), part[kp dp + j] = 0.  Returns the number of
+// stages it used.  Called by every thread of the CTA.
+template <int EPL, int JG>
+__device__ __forceinline__ int rp_chunk_exact(const BProb& pr, int64_t r0, int64_t r1, double* __restrict__ out,
+                                              float* ring, uint64_t* full, uint64_t* empty, uint32_t gs,
+                                              volatile int* s_err) {
   const int d = pr.d, dp = pr.dp, kp = pr.kp;
   const int L = dp / EPL;                 // lanes per row: 8, 16 or 32
   const int lgL = 31 - __clz(L);
@@ -128,9 +129,8 @@ __device__ __forceinline__ int rp_chunk(const BProb& pr, int64_t r0, int64_t r1,
   };
   if (prod)
     for (int t = 0; t < nst && t < RNS - 1 && !*s_err; ++t) issue(t);
-  float pv[EPL][JG], pl[EXACT ? EPL : 1][EXACT ? JG : 1];
-  float acc[EPL][JG], accl[EXACT ? EPL : 1][EXACT ? JG : 1];
-  float q[JG];
+  // head and tail of this warp's right-hand sides of X at the lane's columns; the accumulators
+  float pv[EPL][JG], pl[EPL][JG], acc[EPL][JG], accl[EPL][JG];
 #pragma unroll
   for (int e = 0; e < EPL; ++e) {
     const int c = sl + L * e;
@@ -138,18 +138,11 @@ __device__ __forceinline__ int rp_chunk(const BProb& pr, int64_t r0, int64_t r1,
     for (int j = 0; j < JG; ++j) {
       const int jj = jg * JG + j;
       const bool in = act && c < d;
-      if constexpr (EXACT) {
-        pv[e][j] = in ? pr.Xh[c * kp + jj] : 0.f;
-        pl[e][j] = in ? pr.Xl[c * kp + jj] : 0.f;
-        accl[e][j] = 0.f;
-      } else {
-        pv[e][j] = in ? pr.Pf[c * kp + jj] : 0.f;
-      }
-      acc[e][j] = 0.f;
+      pv[e][j] = in ? pr.Xh[c * kp + jj] : 0.f;
+      pl[e][j] = in ? pr.Xl[c * kp + jj] : 0.f;
+      acc[e][j] = accl[e][j] = 0.f;
     }
   }
-#pragma unroll
-  for (int j = 0; j < JG; ++j) q[j] = 0.f;
   for (int t = 0; t < nst; ++t) {
     const uint32_t g = gs + (uint32_t)t;
     const int s = (int)(g % RNS);
@@ -175,25 +168,7 @@ __device__ __forceinline__ int rp_chunk(const BProb& pr, int64_t r0, int64_t r1,
           const int c = sl + L * e;
           a[e] = (valid && c < d) ? row[c] : 0.f;
         }
-        if constexpr (!EXACT) {
-          float y[JG];
-#pragma unroll
-          for (int j = 0; j < JG; ++j) y[j] = 0.f;
-#pragma unroll
-          for (int e = 0; e < EPL; ++e)
-#pragma unroll
-            for (int j = 0; j < JG; ++j) y[j] = fmaf(a[e], pv[e][j], y[j]);
-          for (int o = L >> 1; o > 0; o >>= 1)
-#pragma unroll
-            for (int j = 0; j < JG; ++j) y[j] += __shfl_xor_sync(0xffffffffu, y[j], o);
-          if (sl == 0)
-#pragma unroll
-            for (int j = 0; j < JG; ++j) q[j] = fmaf(y[j], y[j], q[j]);
-#pragma unroll
-          for (int e = 0; e < EPL; ++e)
-#pragma unroll
-            for (int j = 0; j < JG; ++j) acc[e][j] = fmaf(a[e], y[j], acc[e][j]);
-        } else {
+        {
           float yh[JG], yl[JG];
 #pragma unroll
           for (int j = 0; j < JG; ++j) yh[j] = yl[j] = 0.f;
@@ -229,7 +204,7 @@ __device__ __forceinline__ int rp_chunk(const BProb& pr, int64_t r0, int64_t r1,
     __syncthreads();
     return nst;
   }
-  // per row slice partials of V (FP64) and of q, in the ring
+  // per row slice partials of V (FP64), in the ring
   if (act) {
     double* red = reinterpret_cast<double*>(ring);
     const int slc = rs * RPW + sub;
@@ -238,14 +213,9 @@ __device__ __forceinline__ int rp_chunk(const BProb& pr, int64_t r0, int64_t r1,
       const int c = sl + L * e;
 #pragma unroll
       for (int j = 0; j < JG; ++j) {
-        double v = (double)acc[e][j];
-        if constexpr (EXACT) v += (double)accl[e][j];
-        red[((size_t)slc * kp + jg * JG + j) * dp + c] = v;
+        red[((size_t)slc * kp + jg * JG + j) * dp + c] = (double)acc[e][j] + (double)accl[e][j];
       }
     }
-    if (!EXACT && sl == 0)
-#pragma unroll
-      for (int j = 0; j < JG; ++j) qred[slc * 16 + jg * JG + j] = (double)q[j];
   }
   __syncthreads();
   // fixed-order sums over the row slices
@@ -257,12 +227,7 @@ __device__ __forceinline__ int rp_chunk(const BProb& pr, int64_t r0, int64_t r1,
     for (int q2 = 0; q2 < nsl; ++q2) sum += red[((size_t)q2 * kp + j) * dp + c];
     out[e] = sum;
   }
-  if (tid < kp) {
-    double sum = 0.0;
-    if (!EXACT)
-      for (int q2 = 0; q2 < nsl; ++q2) sum += qred[q2 * 16 + tid];
-    out[kp * dp + tid] = sum;
-  }
+  if (tid < kp) out[kp * dp + tid] = 0.0;  // the exact pass needs no q
   __syncthreads();
   // the ring again holds only finite floats (the tensor-core pass reads past a stage's rows)
   {
@@ -615,24 +580,24 @@ __device__ __forceinline__ int rp_chunk_mma(const BProb& pr, int64_t r0, int64_t
 // right-hand sides per warp, sized so that a lane's operand and accumulator registers (4 EPL JG
 // floats in double-FP32) stay within the budget of one CTA per SM
 __device__ __forceinline__ int rp_run(const BProb& pr, int64_t r0, int64_t r1, double* out, bool exact, float* ring,
-                                      uint64_t* full, uint64_t* empty, double* qred, uint32_t gs,
+                                      uint64_t* full, uint64_t* empty, uint32_t gs,
                                       volatile int* s_err) {
   const int dp = pr.dp, kp = pr.kp;
-#define RP_CALL(E, G, X) return rp_chunk<E, G, X>(pr, r0, r1, out, ring, full, empty, qred, gs, s_err)
+#define RP_CALL(E, G) return rp_chunk_exact<E, G>(pr, r0, r1, out, ring, full, empty, gs, s_err)
   if (!exact) return kp <= 8 ? rp_chunk_mma<1>(pr, r0, r1, out, ring, full, empty, gs, s_err)
                             : rp_chunk_mma<2>(pr, r0, r1, out, ring, full, empty, gs, s_err);
   if (dp <= 128) {
     switch (kp) {
-      case 4: RP_CALL(4, 4, true);
-      case 12: RP_CALL(4, 6, true);
-      default: RP_CALL(4, 8, true);
+      case 4: RP_CALL(4, 4);
+      case 12: RP_CALL(4, 6);
+      default: RP_CALL(4, 8);
     }
   }
   if (dp == 256) {
-    if (kp == 12) RP_CALL(8, 3, true);
-    RP_CALL(8, 4, true);
+    if (kp == 12) RP_CALL(8, 3);
+    RP_CALL(8, 4);
   }
-  RP_CALL(16, 2, true);
+  RP_CALL(16, 2);
 #undef RP_CALL
 }
 
@@ -640,7 +605,6 @@ __device__ __forceinline__ int rp_run(const BProb& pr, int64_t r0, int64_t r1, d
 __global__ void __launch_bounds__(RT, 1) bpass_ring_kernel(BatchArgs a, int force_exact) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[RNS], empty[RNS];
-  __shared__ double qred[RQSL * 16];
   __shared__ int next;
   __shared__ volatile int s_err;
   if (threadIdx.x == 0) {
@@ -673,7 +637,7 @@ __global__ void __launch_bounds__(RT, 1) bpass_ring_kernel(BatchArgs a, int forc
     const BProb& pr = a.probs[cd.x];
     if (!prob_active(pr, it)) continue;
     const bool exact = force_exact != 0 || exact_step(pr, it);
-    gs += (uint32_t)rp_run(pr, cd.y, cd.z, a.part + a.part_off[ch], exact, ring, full, empty, qred, gs, &s_err);
+    gs += (uint32_t)rp_run(pr, cd.y, cd.z, a.part + a.part_off[ch], exact, ring, full, empty, gs, &s_err);
     if (s_err) {
       if (threadIdx.x == 0) atomicCAS(a.err, 0, (int)LSQ_ERR_TIMEOUT);
       break;
