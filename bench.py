@@ -778,7 +778,9 @@ def run_batch(args):
                        "pass_chunk_elems": info["pass_chunk_elems"], "pass_grid": info["pass_grid"],
                        "A_GiB": sum(a_bytes) / 2 ** 30},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": None, "kernel": "batch_kernel", "peak_kind": f"{peak_kind} (burst copy)",
+                         "traffic": None, "peak_kind": f"{peak_kind} (burst copy)",
+                         "kernel": "the batched iterations (bpass_ring_kernel for FP32 A: the passes, about 90 % of "
+                                   "the solve phase; A bytes over the whole solve phase's time)",
                          "algorithmic_bytes_per_launch": pass_bytes},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": launches}), flush=True)
     ctx.close()
