@@ -136,11 +136,12 @@ __device__ __forceinline__ void pass_chunk(const BProb& pr, int64_t r0, int64_t 
   TT* Yp = Ps + dp * KP;
   TT* Ys = Yp + (S > 1 ? S * KP * tr : 0);
   const TA* A = reinterpret_cast<const TA*>(pr.A);
-  // directions (padding columns j >= kp are zero)
+  // directions: zero past the problem's columns and right-hand sides, whose stored entries are
+  // never written (the tile's A is zero there, but a stale non-finite value times zero is not)
   for (int e = tid; e < dp * KP; e += BT) {
     const int c = e / KP, j = e - c * KP;
     TT v = 0;
-    if (j < kp) {
+    if (j < pr.k && c < d) {
       if constexpr (sizeof(TT) == 4) v = pr.Pf[c * kp + j];
       else v = pr.P[j * dp + c];
     }
@@ -386,8 +387,9 @@ __device__ __forceinline__ void pass_chunk_df(const BProb& pr, int64_t r0, int64
   const TA* A = reinterpret_cast<const TA*>(pr.A);
   for (int e = tid; e < dp * KP; e += BT) {
     const int c = e / KP, j = e - c * KP;
-    Xh[e] = j < kp ? pr.Xh[c * kp + j] : 0.f;
-    Xl[e] = j < kp ? pr.Xl[c * kp + j] : 0.f;
+    // (zero past the problem's columns and right-hand sides, as for the directions)
+    Xh[e] = (j < pr.k && c < d) ? pr.Xh[c * kp + j] : 0.f;
+    Xl[e] = (j < pr.k && c < d) ? pr.Xl[c * kp + j] : 0.f;
   }
   const int NC = dp >> 5;
   const int cpw = NC > BW ? NC / BW : 1;

@@ -137,7 +137,7 @@ __device__ __forceinline__ int rp_chunk_exact(const BProb& pr, int64_t r0, int64
 #pragma unroll
     for (int j = 0; j < JG; ++j) {
       const int jj = jg * JG + j;
-      const bool in = act && c < d;
+      const bool in = act && c < d && jj < pr.k;
       pv[e][j] = in ? pr.Xh[c * kp + jj] : 0.f;
       pl[e][j] = in ? pr.Xl[c * kp + jj] : 0.f;
       acc[e][j] = accl[e][j] = 0.f;
@@ -338,7 +338,7 @@ __device__ __forceinline__ int rp_chunk_mma(const BProb& pr, int64_t r0, int64_t
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = (k0 + kk) * 8 + tq + 4 * h, j = nt * 8 + g;
-        const float v = (kk < nk && c < d && j < kp) ? pr.Pf[c * kp + j] : 0.f;
+        const float v = (kk < nk && c < d && j < pr.k) ? pr.Pf[c * kp + j] : 0.f;
         pbh[kk][nt][h] = tf32_head(v);
         pbl[kk][nt][h] = __float_as_uint(v - __uint_as_float(pbh[kk][nt][h]));
       }

@@ -170,3 +170,28 @@ def test_batch_mixed_first_iterations_follow_oracle(L, ctx, x0):
             err = rel_fro(Xp.cpu().numpy() - (X0[shapes.index(sh)] if x0 else 0.0),
                           Xr - (X0[shapes.index(sh)] if x0 else 0.0))
             assert err < 1e-5, (sh, T, err)
+
+
+def test_batch_strided_or_unaligned_rows_take_the_tiled_pass(L, ctx):
+    """The ring pass needs every problem's rows contiguous and 16-byte aligned; a batch with a
+    strided problem (ld = d + 3) and one whose first element sits at an odd float offset runs the
+    tiled pass instead.  Either way every right-hand side reaches 1e-10 against x*."""
+    shapes = [(3001, 37, 3), (5000, 130, 9), (2500, 31, 16)]
+    probs = W.make_batch(shapes, seed=31, scale_max=1e3, dtype=np.float32)
+    aligned = _dev(probs, np.float32)
+    A1 = torch.from_numpy(probs[1]["A"]).cuda()
+    wide = torch.zeros((A1.shape[0], A1.shape[1] + 3), dtype=torch.float32, device=A1.device)
+    wide[:, :A1.shape[1]] = A1
+    A2 = torch.from_numpy(probs[2]["A"]).cuda()
+    flat = torch.zeros(A2.numel() + 1, dtype=torch.float32, device=A2.device)
+    flat[1:] = A2.reshape(-1)
+    shifted = flat[1:].view(A2.shape)
+    assert shifted.data_ptr() % 16 != 0 and wide[:, :A1.shape[1]].stride(0) == A1.shape[1] + 3
+    odd = [aligned[0], (wide[:, :A1.shape[1]], aligned[1][1]), (shifted, aligned[2][1])]
+    for name, batch in (("aligned", aligned), ("strided and shifted", odd)):
+        X, per, info = L.lsq_solve_batched(ctx, batch, tol=1e-10, maxit=300, seed=2)
+        assert info["status"] == 0, (name, per)
+        for q, Xp in zip(probs, X):
+            A64 = q["A"].astype(np.float64)
+            for j in range(q["B"].shape[0]):
+                assert O.rel_h_err(A64, Xp[j].cpu().numpy(), O.solve_direct(A64, q["B"][j])) <= 1e-10
