@@ -195,3 +195,32 @@ def test_batch_strided_or_unaligned_rows_take_the_tiled_pass(L, ctx):
             A64 = q["A"].astype(np.float64)
             for j in range(q["B"].shape[0]):
                 assert O.rel_h_err(A64, Xp[j].cpu().numpy(), O.solve_direct(A64, q["B"][j])) <= 1e-10
+
+
+def test_batch_a_non_finite_problem_stays_isolated(L, ctx):
+    """One problem of the batch has a NaN in A: it ends with a non-zero status while every other
+    problem converges as without it (no non-finite value crosses problems, in shared memory or
+    in the state the passes share), and a later batch on the same context, whose state and
+    shared memory the failed solve has dirtied, converges too."""
+    shapes = [(3000, 40, 3), (2000, 24, 2), (4096, 100, 12)]
+    probs = W.make_batch(shapes, seed=41, scale_max=1e3, dtype=np.float32)
+    bad = probs[1]["A"].copy()
+    bad[777, 5] = np.nan
+    batch = _dev(probs, np.float32)
+    batch[1] = (to_dev(bad), batch[1][1])
+    X, per, info = L.lsq_solve_batched(ctx, batch, tol=1e-10, maxit=300, seed=5)
+    assert per[1][1] != 0 and info["status"] != 0, per
+    for i in (0, 2):
+        q = probs[i]
+        assert per[i][1] == 0, per
+        A64 = q["A"].astype(np.float64)
+        for j in range(q["B"].shape[0]):
+            assert O.rel_h_err(A64, X[i][j].cpu().numpy(), O.solve_direct(A64, q["B"][j])) <= 1e-10
+    shapes2 = [(3001, 37, 3), (5000, 130, 9), (2500, 31, 16)]
+    probs2 = W.make_batch(shapes2, seed=42, scale_max=1e3, dtype=np.float32)
+    X2, per2, info2 = L.lsq_solve_batched(ctx, _dev(probs2, np.float32), tol=1e-10, maxit=300, seed=5)
+    assert info2["status"] == 0, per2
+    for q, Xp in zip(probs2, X2):
+        A64 = q["A"].astype(np.float64)
+        for j in range(q["B"].shape[0]):
+            assert O.rel_h_err(A64, Xp[j].cpu().numpy(), O.solve_direct(A64, q["B"][j])) <= 1e-10
