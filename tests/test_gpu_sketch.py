@@ -264,3 +264,15 @@ def test_sjlt_bf16_tensor_core_bit_exact_on_integers(L, ctx, n, d, m, s):
     A = int_matrix(n, d, seed=n + d)
     SA = L.lsq_sketch(ctx, to_dev(A), "sjlt", m, 6, s=s, precision="bf16").cpu().numpy()
     assert np.array_equal(SA, O.sketch_sjlt(A, m, s, 6, 0))
+
+
+@pytest.mark.parametrize("n,d,m,dtype", [(20000, 130, 512, np.float32), (20001, 600, 1000, np.float32),
+                                         (9000, 300, 256, np.float64)])
+def test_sjlt_bf16_tensor_core_repeats_bit_for_bit(L, ctx, n, d, m, dtype):
+    """The tensor-core SJLT sums its exact +-1 products in a fixed order, so on real-valued A two
+    runs agree bit for bit (single CTAs and CTA pairs), unlike the FP32 scatter's atomic sums."""
+    A = to_dev(W.make_problem(n, d, 1e4, seed=d)["A"].astype(dtype))
+    SA1 = L.lsq_sketch(ctx, A, "sjlt", m, 9, s=8, precision="bf16")
+    SA2 = L.lsq_sketch(ctx, A, "sjlt", m, 9, s=8, precision="bf16")
+    assert torch.equal(SA1, SA2)
+    assert torch.isfinite(SA1).all()
