@@ -450,7 +450,11 @@ LSQ_API void lsq_batch_opts_default(lsq_batch_opts* opts);
  * vector updates and W W^T per right-hand side.
  * A right-hand side stops by rule (1+sqrt(rho))^2 r^T H_S^{-1} r <= tol^2 <b, x> (as in
  * lsq_solve); a problem stops when all of its right-hand sides have. Under LSQ_PREC_MIXED the
- * passes run in FP32 with exact (double-FP32) residual replacement as in lsq_solve.
+ * passes run in FP32-level arithmetic with exact (double-FP32) residual replacement as in
+ * lsq_solve; when every A_p is FP32 with contiguous rows (ld = d) and a 16-byte aligned first
+ * element, those passes run on the tensor cores as three TF32 products per element (a TF32 head
+ * and the FP32 remainder of both operands, the remainders' product dropped: below 2^-22 of the
+ * product), with FP32 sums; otherwise in FP32 on the SIMT pipes.
  * Returns LSQ_OK, LSQ_ERR_MAXIT, LSQ_ERR_BREAKDOWN, LSQ_ERR_RANK (see probs[p].status),
  * LSQ_ERR_TIMEOUT, LSQ_ERR_ARG or LSQ_ERR_CUDA. Synchronises before returning. */
 LSQ_API lsq_status lsq_solve_batched(lsq_ctx* ctx, int32_t nprob, lsq_problem* probs, double tol, int32_t maxit,
