@@ -69,6 +69,27 @@ SOLVE_TRAFFIC = {
 }
 
 
+# The same for the batched ring pass (bpass_ring_kernel): one FP32 pass of iteration 0 over every
+# problem of the 64-problem batch (ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,
+# dram__bytes_write.sum -k regex:bpass_ring -s 1 -c 1, python bench.py --batch 64 --steps 1
+# --warmup 1 --no-cpu --no-e2e): reads of A plus the chunk partials written, over A's bytes.  The
+# exact passes stream A through the same ring.
+BATCH_TRAFFIC = {
+    "sources_sha256": "24f75dc8026795c2dccf6d3c67aa4f6b483408194d47cf2c6680f9ac32380ad6",
+    "ratio": (2664949504 + 27429888) / 2663123140,
+}
+
+
+def batch_sources_sha256() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("bring.cuh", "batch.cu", "common.cuh", "apass.cuh"):
+        with open(os.path.join(ROOT, "paper_1911_02675_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def solve_sources_sha256() -> str:
     import hashlib
 
@@ -737,6 +758,10 @@ def run_batch(args):
     pass_bytes = sum(b * it for b, (it, _) in zip(a_bytes, per))
     achieved = pass_bytes / (solve_ms * 1e-3) / 1e9
     statuses = sorted(set(st for _, st in per))
+    # DRAM bytes of the passes from the calibrated ratio (the ring pass: FP32 A, mixed precision)
+    batch_traffic = None
+    if args.precision == "mixed" and batch_sources_sha256() == BATCH_TRAFFIC["sources_sha256"]:
+        batch_traffic = BATCH_TRAFFIC["ratio"] * pass_bytes
     # end to end: every problem's A and B copied from pinned host memory into HBM, the batched
     # solve, every X read back to pinned host memory, all inside the timed region
     e2e = None
@@ -778,7 +803,7 @@ def run_batch(args):
                        "pass_chunk_elems": info["pass_chunk_elems"], "pass_grid": info["pass_grid"],
                        "A_GiB": sum(a_bytes) / 2 ** 30},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": None, "peak_kind": f"{peak_kind} (burst copy)",
+                         "traffic": batch_traffic, "peak_kind": f"{peak_kind} (burst copy)",
                          "kernel": "the batched iterations (bpass_ring_kernel for FP32 A: the passes, about 90 % of "
                                    "the solve phase; A bytes over the whole solve phase's time)",
                          "algorithmic_bytes_per_launch": pass_bytes},

@@ -62,6 +62,8 @@ def test_traffic_calibration_is_sane():
     h = mod.SOLVE_TRAFFIC["sources_sha256"]
     assert len(h) == 64 and int(h, 16) >= 0
     assert len(mod.solve_sources_sha256()) == 64
+    assert 1.0 <= mod.BATCH_TRAFFIC["ratio"] < 1.02
+    assert len(mod.BATCH_TRAFFIC["sources_sha256"]) == 64 and len(mod.batch_sources_sha256()) == 64
 
 
 def test_oracle_accuracy_matches_the_error_against_xstar():
